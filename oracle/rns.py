@@ -1,0 +1,271 @@
+"""Slow step-by-step model of RNS Montgomery multiplication (test infrastructure only).
+
+Sec. 3.1 of the paper: a bignum X is held as its residues x_i = X mod m_i over
+pairwise coprime moduli (unique for X < M = prod m_i by the CRT); products are
+taken channel by channel; the Montgomery multiplication with R = M computes
+X*Y*M^-1 mod N channel-wise (Bajard et al. 2001) using a second base B' and a
+base extension whose constants depend only on the bases; exponentiation chains
+these multiplications inside the Montgomery domain.  This module writes those
+steps out on Python integers, in the order the method takes them, with no
+blocking or fusion.  It fixes the base choice and every precomputed constant so
+that the CUDA library's own tables can be checked against it value by value.
+
+Readings where the paper is silent (each also recorded in the design notes):
+
+* Bases.  B = the k largest primes below 2^31, B' = the next k primes, plus a
+  redundant modulus m_r = 2^32.  k is the smallest integer with
+  M >= 4 (k+1)^2 2^L and M' >= (k+1) 2^L for the size class of L bits.
+* Extension B -> B' is the fast one without correction (the extended value is
+  q + a*M with 0 <= a < k); extension B' -> B is exact (Shenoy-Kumaresan), its
+  correction factor recovered from the redundant channel.
+* Every multiplication output lies in [0, (k+1) N); only the final result is
+  reduced to [0, N).
+* Inputs longer than the class are split into L-bit chunks x = x_lo + 2^L x_hi
+  and entered as MM(x_lo, M^2 mod N) + MM(x_hi, 2^L M^2 mod N) (at most 2 chunks).
+* Exponentiation: fixed 2^w-ary windows from the top, w squarings then one
+  multiplication by the table entry (entry 0 is the Montgomery form of 1).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from functools import lru_cache
+from typing import Dict, List, Optional, Sequence
+
+from .plain import inverse
+from .primality import first_primes
+
+PRIME_BOUND = 1 << 31
+M_R = 1 << 32
+
+
+def _is_prime_small(n: int) -> bool:
+    if n < 2:
+        return False
+    for p in first_primes(5000):  # primes up to 48611 > sqrt(2^31)
+        if p * p > n:
+            return True
+        if n % p == 0:
+            return n == p
+    return True
+
+
+@lru_cache(maxsize=None)
+def primes_below(bound: int, count: int) -> tuple:
+    """The ``count`` largest primes strictly below ``bound``, in descending order."""
+    out = []
+    n = bound - 1
+    while len(out) < count:
+        if n < 3:
+            raise ValueError("not enough primes below bound")
+        if n % 2 == 1 and _is_prime_small(n):
+            out.append(n)
+        n -= 1
+    return tuple(out)
+
+
+def _prod(xs: Sequence[int]) -> int:
+    r = 1
+    for x in xs:
+        r *= x
+    return r
+
+
+@dataclass
+class RNSClass:
+    """Bases and class-wide constants for moduli of at most L bits."""
+    L: int
+    k: int
+    B: List[int]
+    Bp: List[int]
+    M: int
+    Mp: int
+    mr: int = M_R
+    t: Dict[str, object] = field(default_factory=dict)
+
+
+def class_k(L: int, prime_bound: int = PRIME_BOUND) -> int:
+    k = 1
+    while True:
+        pr = primes_below(prime_bound, 2 * k)
+        M = _prod(pr[:k])
+        Mp = _prod(pr[k:2 * k])
+        if M >= 4 * (k + 1) ** 2 * (1 << L) and Mp >= (k + 1) * (1 << L):
+            return k
+        k += 1
+
+
+@lru_cache(maxsize=None)
+def make_class(L: int, prime_bound: int = PRIME_BOUND) -> RNSClass:
+    """Base choice and the constants that stay fixed for every modulus of the class (Sec. 3.1)."""
+    k = class_k(L, prime_bound)
+    pr = primes_below(prime_bound, 2 * k)
+    B, Bp = list(pr[:k]), list(pr[k:2 * k])
+    M, Mp = _prod(B), _prod(Bp)
+    c = RNSClass(L=L, k=k, B=B, Bp=Bp, M=M, Mp=Mp)
+    t = c.t
+    # B -> B' extension: |M/m_i|_{m'_j}, |M/m_i|_{m_r}, |(M/m_i)^-1|_{m_i}
+    t["M_mi_inv"] = [inverse(M // m, m) for m in B]
+    t["M_mi_Bp"] = [[(M // m) % mp for mp in Bp] for m in B]
+    t["M_mi_r"] = [(M // m) % M_R for m in B]
+    # Montgomery division by M in B' and m_r
+    t["Minv_Bp"] = [inverse(M % mp, mp) for mp in Bp]
+    t["Minv_r"] = inverse(M % M_R, M_R)
+    # B' -> B extension: |(M'/m'_j)^-1|_{m'_j}, |M'/m'_j|_{m_i}, |M'/m'_j|_{m_r}, |M'|_{m_i}, |M'^-1|_{m_r}
+    t["Mp_mj_inv"] = [inverse(Mp // mp, mp) for mp in Bp]
+    t["Mp_mj_B"] = [[(Mp // mp) % m for m in B] for mp in Bp]
+    t["Mp_mj_r"] = [(Mp // mp) % M_R for mp in Bp]
+    t["Mp_B"] = [Mp % m for m in B]
+    t["Mpinv_r"] = inverse(Mp % M_R, M_R)
+    return c
+
+
+@dataclass
+class RNSValue:
+    b: List[int]
+    bp: List[int]
+    r: int
+
+
+def to_rns(c: RNSClass, X: int) -> RNSValue:
+    """Residues of a non-negative integer in B, B' and m_r (the definition, Sec. 3.1)."""
+    return RNSValue([X % m for m in c.B], [X % m for m in c.Bp], X % M_R)
+
+
+def crt_value(c: RNSClass, v: RNSValue) -> int:
+    """RNS -> binary with the CRT and the redundant modulus (Sec. 3.1).
+
+    X = sum_i xi_i (M/m_i) - a M, xi_i = |x_i (M/m_i)^-1|_{m_i}; the integer a =
+    floor(sum xi_i/m_i) < k is recovered exactly from the residue mod m_r.
+    Valid for X < M.
+    """
+    t = c.t
+    xi = [(v.b[i] * t["M_mi_inv"][i]) % c.B[i] for i in range(c.k)]
+    s_r = sum(xi[i] * t["M_mi_r"][i] for i in range(c.k)) % M_R
+    a = ((s_r - v.r) * t["Minv_r"]) % M_R
+    if a >= c.k:
+        raise ArithmeticError("CRT correction out of range: value not below M")
+    return sum(xi[i] * (c.M // c.B[i]) for i in range(c.k)) - a * c.M
+
+
+@dataclass
+class RNSKey:
+    cls: RNSClass
+    N: int
+    t: Dict[str, object] = field(default_factory=dict)
+
+
+def make_key(c: RNSClass, N: int) -> RNSKey:
+    """Per-modulus constants (Sec. 3.1): everything that depends on N."""
+    if N < 3 or N % 2 == 0:
+        raise ValueError("modulus must be odd and >= 3")
+    if N.bit_length() > c.L:
+        raise ValueError("modulus larger than the class")
+    for m in c.B + c.Bp:
+        if N % m == 0:
+            raise ValueError("modulus shares a factor with a channel")
+    key = RNSKey(cls=c, N=N)
+    t = key.t
+    M = c.M
+    # xi_i = s_i * |-N^-1 (M/m_i)^-1|_{m_i}
+    t["kxi"] = [(-inverse(N % m, m) * c.t["M_mi_inv"][i]) % m for i, m in enumerate(c.B)]
+    # r_j = s_j |M^-1| + qhat_j |N M^-1|
+    t["NMinv_Bp"] = [(N * c.t["Minv_Bp"][j]) % mp for j, mp in enumerate(c.Bp)]
+    t["NMinv_r"] = (N * c.t["Minv_r"]) % M_R
+    # Montgomery-domain constants
+    t["one"] = to_rns(c, M % N)                      # 1 in the Montgomery domain
+    t["r2"] = to_rns(c, (M * M) % N)                 # entry: MM(x, M^2 mod N) = xM mod N
+    t["r2h"] = to_rns(c, ((M * M) << c.L) % N)       # entry of the high chunk of a 2L-bit input
+    return key
+
+
+def mm(key: RNSKey, x: RNSValue, y: RNSValue) -> RNSValue:
+    """RNS Montgomery multiplication: r = (xy + qhat N)/M, r == x y M^-1 (mod N).
+
+    Steps in order:
+      1. s = x*y in every channel of B, B' and m_r;
+      2. xi_i = s_i |-N^-1 (M/m_i)^-1|_{m_i} in B;
+      3. extension B -> B' and m_r: qhat_j = sum_i xi_i |M/m_i|_{m'_j};
+      4. r_j = s_j |M^-1|_{m'_j} + qhat_j |N M^-1|_{m'_j} in B' and m_r;
+      5. xi'_j = r_j |(M'/m'_j)^-1|_{m'_j};
+      6. extension B' -> B (exact): t_i = sum_j xi'_j |M'/m'_j|_{m_i},
+         a = (sum_j xi'_j |M'/m'_j|_{m_r} - r_r) |M'^-1|_{m_r} mod m_r,
+         r_i = t_i - a |M'|_{m_i}.
+    """
+    c, t, kt = key.cls, key.cls.t, key.t
+    k = c.k
+    s_b = [(x.b[i] * y.b[i]) % c.B[i] for i in range(k)]
+    s_bp = [(x.bp[j] * y.bp[j]) % c.Bp[j] for j in range(k)]
+    s_r = (x.r * y.r) % M_R
+    xi = [(s_b[i] * kt["kxi"][i]) % c.B[i] for i in range(k)]
+    qhat_bp = [sum(xi[i] * t["M_mi_Bp"][i][j] for i in range(k)) % c.Bp[j] for j in range(k)]
+    qhat_r = sum(xi[i] * t["M_mi_r"][i] for i in range(k)) % M_R
+    r_bp = [(s_bp[j] * t["Minv_Bp"][j] + qhat_bp[j] * kt["NMinv_Bp"][j]) % c.Bp[j] for j in range(k)]
+    r_r = (s_r * t["Minv_r"] + qhat_r * kt["NMinv_r"]) % M_R
+    xip = [(r_bp[j] * t["Mp_mj_inv"][j]) % c.Bp[j] for j in range(k)]
+    t_b = [sum(xip[j] * t["Mp_mj_B"][j][i] for j in range(k)) % c.B[i] for i in range(k)]
+    t_r = sum(xip[j] * t["Mp_mj_r"][j] for j in range(k)) % M_R
+    a = ((t_r - r_r) * t["Mpinv_r"]) % M_R
+    if a >= k:
+        raise ArithmeticError("B'->B correction out of range (operand bound violated)")
+    r_b = [(t_b[i] - a * t["Mp_B"][i]) % c.B[i] for i in range(k)]
+    return RNSValue(r_b, r_bp, r_r)
+
+
+def add(key: RNSKey, x: RNSValue, y: RNSValue) -> RNSValue:
+    c = key.cls
+    return RNSValue([(x.b[i] + y.b[i]) % c.B[i] for i in range(c.k)],
+                    [(x.bp[j] + y.bp[j]) % c.Bp[j] for j in range(c.k)],
+                    (x.r + y.r) % M_R)
+
+
+def enter(key: RNSKey, x: int) -> RNSValue:
+    """Montgomery form of x (up to a multiple of N): x < 2^(2L) is split into two L-bit chunks."""
+    c = key.cls
+    if x < 0 or x.bit_length() > 2 * c.L:
+        raise ValueError("input longer than two class chunks")
+    lo, hi = x & ((1 << c.L) - 1), x >> c.L
+    v = mm(key, to_rns(c, lo), key.t["r2"])
+    if hi:
+        v = add(key, v, mm(key, to_rns(c, hi), key.t["r2h"]))
+    return v
+
+
+def leave(key: RNSKey, v: RNSValue) -> int:
+    """Back from the Montgomery domain and to binary: MM(v, 1), CRT, reduce into [0, N)."""
+    c = key.cls
+    r = mm(key, v, to_rns(c, 1))
+    X = crt_value(c, r)
+    if X >= (c.k + 1) * key.N:
+        raise ArithmeticError("output bound violated")
+    return X % key.N
+
+
+def window_digits(e: int, w: int, nbits: Optional[int] = None) -> List[int]:
+    """w-bit digits of e from the most significant window down (fixed windows)."""
+    nb = e.bit_length() if nbits is None else nbits
+    nwin = (nb + w - 1) // w
+    return [(e >> (w * i)) & ((1 << w) - 1) for i in range(nwin - 1, -1, -1)]
+
+
+def modexp(key: RNSKey, x: int, e: int, w: int = 5) -> int:
+    """x^e mod N by fixed-window exponentiation on RNS Montgomery multiplications."""
+    xt = enter(key, x)
+    table = [key.t["one"], xt]
+    for j in range(2, 1 << w):
+        table.append(mm(key, table[j - 1], xt))
+    digits = window_digits(e, w)
+    acc = table[digits[0]] if digits else key.t["one"]
+    for dgt in digits[1:]:
+        for _ in range(w):
+            acc = mm(key, acc, acc)
+        acc = mm(key, acc, table[dgt])
+    return leave(key, acc)
+
+
+def rsa_decrypt_crt(c_p: RNSKey, c_q: RNSKey, c: int, dp: int, dq: int, qinv: int, w: int = 5) -> int:
+    """CRT decryption on the RNS path: two half-size modexps, Garner's recombination."""
+    p, q = c_p.N, c_q.N
+    mp = modexp(c_p, c, dp, w)
+    mq = modexp(c_q, c, dq, w)
+    h = (qinv * (mp - mq)) % p
+    return mq + h * q

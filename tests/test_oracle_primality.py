@@ -1,0 +1,91 @@
+"""Pins for oracle.primality against published facts and brute force."""
+import os
+import random
+
+import pytest
+
+from oracle import keygen, primality
+from oracle.plain import gcd
+from synth import SplitMix64, load_keys
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_first_primes_published():
+    for line in open(os.path.join(GOLD, "primes.txt")):
+        f = line.split()
+        if f and f[0] == "nth":
+            assert primality.first_primes(int(f[1]))[-1] == int(f[2])
+    ps = primality.first_primes(10000)
+    assert len(ps) == 10000 and ps[:5] == (2, 3, 5, 7, 11)
+
+
+def test_trial_division_matches_brute_force():
+    for n in range(0, 5000):
+        assert primality.trial_division_passes(n) == primality.is_prime_by_trial(n) or n < 2
+
+
+def test_miller_rabin_exhaustive_below_2_16():
+    # Bases {2,3,5,7} decide primality exactly below 3,215,031,751 (published bound).
+    # (n > 7 so that no base is a multiple of n)
+    for n in range(9, 1 << 16, 2):
+        mr = all(primality.miller_rabin(n, [2, 3, 5, 7]))
+        assert mr == primality.is_prime_by_trial(n), n
+
+
+def test_miller_rabin_all_witnesses_small():
+    # A prime passes every witness; an odd composite n > 9 has at most phi(n)/4
+    # strong liars (Monier-Rabin bound).
+    for n in range(5, 400, 2):
+        passed = sum(primality.miller_rabin_round(n, a) for a in range(2, n - 1))
+        if primality.is_prime_by_trial(n):
+            assert passed == n - 3
+        elif n > 9:
+            phi = sum(1 for a in range(1, n) if gcd(a, n) == 1)
+            assert passed + 2 <= phi / 4  # liars in [1, n-1]: the range plus 1 and n-1
+
+
+def test_strong_pseudoprimes_published():
+    for line in open(os.path.join(GOLD, "strong_pseudoprimes.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        n, passed, failed = line.split()
+        n = int(n)
+        if passed != "-":
+            for a in map(int, passed.split(",")):
+                assert primality.miller_rabin_round(n, a), (n, a)
+        assert not primality.miller_rabin_round(n, int(failed)), (n, failed)
+
+
+def test_mersenne_primes_pass_every_witness():
+    r = random.Random(5)
+    for line in open(os.path.join(GOLD, "primes.txt")):
+        f = line.split()
+        if f and f[0] == "mersenne" and int(f[1]) <= 607:
+            p = (1 << int(f[1])) - 1
+            assert all(primality.miller_rabin(p, [r.randrange(2, p - 1) for _ in range(4)]))
+
+
+def test_products_of_generated_primes_fail():
+    for k in load_keys("test_small") + load_keys("rsa1024_x64")[:4]:
+        N = k["N"]
+        r = random.Random(N & 0xFFFF)
+        assert not all(primality.miller_rabin(N, [r.randrange(2, N - 1) for _ in range(3)]))
+        assert all(primality.miller_rabin(k["p"], [2, 3, 5]))
+
+
+def test_witness_edge_values():
+    p = 1000003
+    assert primality.miller_rabin_round(p, 1) and primality.miller_rabin_round(p, p - 1)
+    assert not primality.miller_rabin_round(p, 0) and not primality.miller_rabin_round(p, p)
+    assert primality.miller_rabin_round(2, 5) and not primality.miller_rabin_round(9, 2)
+
+
+def test_keygen_deterministic_and_well_formed():
+    a = keygen.gen_rsa_key(SplitMix64(1).fork(0), 256)
+    b = keygen.gen_rsa_key(SplitMix64(1).fork(0), 256)
+    assert a == b
+    assert a["N"].bit_length() == 256
+    assert a["p"].bit_length() == 128 and a["q"].bit_length() == 128
+    for prime in (a["p"], a["q"]):
+        assert primality.is_prime_by_trial(prime) if prime < 1 << 40 else pow(3, prime - 1, prime) == 1
