@@ -12,12 +12,19 @@ that the CUDA library's own tables can be checked against it value by value.
 
 Readings where the paper is silent (each also recorded in the design notes):
 
-* Bases.  B = the k largest primes below 2^31, B' = the next k primes, plus a
-  redundant modulus m_r = 2^32.  k is the smallest integer with
-  M >= 4 (k+1)^2 2^L and M' >= (k+1) 2^L for the size class of L bits.
+* Bases.  For a size class of L bits and k channels per base, every channel
+  prime lies below b_k = min(2^31, isqrt((2^64-1) // k)), so that a sum of k
+  products of two residues never reaches 2^64.  B = the k largest primes below
+  b_k, B' = the next k primes.  k is the smallest integer with
+  M >= 4 (k+1)^2 2^L and M' >= 2 (k+1) 2^L.
 * Extension B -> B' is the fast one without correction (the extended value is
-  q + a*M with 0 <= a < k); extension B' -> B is exact (Shenoy-Kumaresan), its
-  correction factor recovered from the redundant channel.
+  q + a*M with 0 <= a < k).  Extension B' -> B is exact: its correction factor
+  a' = floor(sum_j xi'_j / m'_j) is computed in fixed point (Kawamura et al.,
+  CHES 2000): a' = (sum_j floor(xi'_j floor(2^(32+Q)/m'_j) / 2^32) + 2^(Q-2)) >> Q
+  with Q = 22, which equals the exact value whenever the extended number is
+  below 3/4 M' (guaranteed by the M' bound above); the model also computes the
+  exact factor from its definition and checks that the two agree.
+* RNS -> binary uses the same fixed-point factor over B (the value is below M/4).
 * Every multiplication output lies in [0, (k+1) N); only the final result is
   reduced to [0, N).
 * Inputs longer than the class are split into L-bit chunks x = x_lo + 2^L x_hi
@@ -29,13 +36,19 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 from functools import lru_cache
+from math import isqrt
 from typing import Dict, List, Optional, Sequence
 
 from .plain import inverse
 from .primality import first_primes
 
-PRIME_BOUND = 1 << 31
-M_R = 1 << 32
+PRIME_CAP = 1 << 31
+KAW_Q = 22          # fixed-point bits of the correction-factor estimate
+
+
+def prime_bound(k: int) -> int:
+    """Channel primes stay below this, so that k products of residues sum below 2^64."""
+    return min(PRIME_CAP, isqrt(((1 << 64) - 1) // k))
 
 
 def _is_prime_small(n: int) -> bool:
@@ -79,43 +92,54 @@ class RNSClass:
     Bp: List[int]
     M: int
     Mp: int
-    mr: int = M_R
+    bound: int
     t: Dict[str, object] = field(default_factory=dict)
 
 
-def class_k(L: int, prime_bound: int = PRIME_BOUND) -> int:
+def class_k(L: int, fixed_bound: Optional[int] = None) -> int:
+    """Smallest k meeting M >= 4 (k+1)^2 2^L and M' >= 2 (k+1) 2^L."""
     k = 1
     while True:
-        pr = primes_below(prime_bound, 2 * k)
+        b = fixed_bound if fixed_bound is not None else prime_bound(k)
+        pr = primes_below(b, 2 * k)
         M = _prod(pr[:k])
         Mp = _prod(pr[k:2 * k])
-        if M >= 4 * (k + 1) ** 2 * (1 << L) and Mp >= (k + 1) * (1 << L):
+        if M >= 4 * (k + 1) ** 2 * (1 << L) and Mp >= 2 * (k + 1) * (1 << L):
             return k
         k += 1
 
 
+def fixed_point_factor(xi: Sequence[int], mods: Sequence[int]) -> int:
+    """floor(sum xi_j / m_j) estimated in Q-bit fixed point with a 1/4 offset (Kawamura)."""
+    acc = 0
+    for x, m in zip(xi, mods):
+        u = (1 << (32 + KAW_Q)) // m
+        acc += (x * u) >> 32
+    return (acc + (1 << (KAW_Q - 2))) >> KAW_Q
+
+
 @lru_cache(maxsize=None)
-def make_class(L: int, prime_bound: int = PRIME_BOUND) -> RNSClass:
-    """Base choice and the constants that stay fixed for every modulus of the class (Sec. 3.1)."""
-    k = class_k(L, prime_bound)
-    pr = primes_below(prime_bound, 2 * k)
+def make_class(L: int, fixed_bound: Optional[int] = None) -> RNSClass:
+    """Base choice and the constants that stay fixed for every modulus of the class (Sec. 3.1).
+
+    ``fixed_bound`` replaces the per-k prime bound (tests use tiny 8-bit bases).
+    """
+    k = class_k(L, fixed_bound)
+    b = fixed_bound if fixed_bound is not None else prime_bound(k)
+    pr = primes_below(b, 2 * k)
     B, Bp = list(pr[:k]), list(pr[k:2 * k])
     M, Mp = _prod(B), _prod(Bp)
-    c = RNSClass(L=L, k=k, B=B, Bp=Bp, M=M, Mp=Mp)
+    c = RNSClass(L=L, k=k, B=B, Bp=Bp, M=M, Mp=Mp, bound=b)
     t = c.t
-    # B -> B' extension: |M/m_i|_{m'_j}, |M/m_i|_{m_r}, |(M/m_i)^-1|_{m_i}
+    # B -> B' extension: |M/m_i|_{m'_j}, |(M/m_i)^-1|_{m_i}
     t["M_mi_inv"] = [inverse(M // m, m) for m in B]
     t["M_mi_Bp"] = [[(M // m) % mp for mp in Bp] for m in B]
-    t["M_mi_r"] = [(M // m) % M_R for m in B]
-    # Montgomery division by M in B' and m_r
+    # Montgomery division by M in B'
     t["Minv_Bp"] = [inverse(M % mp, mp) for mp in Bp]
-    t["Minv_r"] = inverse(M % M_R, M_R)
-    # B' -> B extension: |(M'/m'_j)^-1|_{m'_j}, |M'/m'_j|_{m_i}, |M'/m'_j|_{m_r}, |M'|_{m_i}, |M'^-1|_{m_r}
+    # B' -> B extension: |(M'/m'_j)^-1|_{m'_j}, |M'/m'_j|_{m_i}, |M'|_{m_i}
     t["Mp_mj_inv"] = [inverse(Mp // mp, mp) for mp in Bp]
     t["Mp_mj_B"] = [[(Mp // mp) % m for m in B] for mp in Bp]
-    t["Mp_mj_r"] = [(Mp // mp) % M_R for mp in Bp]
     t["Mp_B"] = [Mp % m for m in B]
-    t["Mpinv_r"] = inverse(Mp % M_R, M_R)
     return c
 
 
@@ -123,28 +147,28 @@ def make_class(L: int, prime_bound: int = PRIME_BOUND) -> RNSClass:
 class RNSValue:
     b: List[int]
     bp: List[int]
-    r: int
 
 
 def to_rns(c: RNSClass, X: int) -> RNSValue:
-    """Residues of a non-negative integer in B, B' and m_r (the definition, Sec. 3.1)."""
-    return RNSValue([X % m for m in c.B], [X % m for m in c.Bp], X % M_R)
+    """Residues of a non-negative integer in B and B' (the definition, Sec. 3.1)."""
+    return RNSValue([X % m for m in c.B], [X % m for m in c.Bp])
 
 
 def crt_value(c: RNSClass, v: RNSValue) -> int:
-    """RNS -> binary with the CRT and the redundant modulus (Sec. 3.1).
+    """RNS -> binary with the CRT (Sec. 3.1).
 
-    X = sum_i xi_i (M/m_i) - a M, xi_i = |x_i (M/m_i)^-1|_{m_i}; the integer a =
-    floor(sum xi_i/m_i) < k is recovered exactly from the residue mod m_r.
-    Valid for X < M.
+    X = sum_i xi_i (M/m_i) - a M with xi_i = |x_i (M/m_i)^-1|_{m_i} and
+    a = floor(sum xi_i/m_i).  a is taken from the fixed-point estimate, which is
+    exact for X < 3M/4; the exact value is checked against it.
     """
     t = c.t
     xi = [(v.b[i] * t["M_mi_inv"][i]) % c.B[i] for i in range(c.k)]
-    s_r = sum(xi[i] * t["M_mi_r"][i] for i in range(c.k)) % M_R
-    a = ((s_r - v.r) * t["Minv_r"]) % M_R
-    if a >= c.k:
-        raise ArithmeticError("CRT correction out of range: value not below M")
-    return sum(xi[i] * (c.M // c.B[i]) for i in range(c.k)) - a * c.M
+    total = sum(xi[i] * (c.M // c.B[i]) for i in range(c.k))
+    a_exact = total // c.M
+    a = fixed_point_factor(xi, c.B)
+    if a != a_exact:
+        raise ArithmeticError("fixed-point CRT factor differs from the exact one (value not below 3M/4)")
+    return total - a * c.M
 
 
 @dataclass
@@ -170,7 +194,6 @@ def make_key(c: RNSClass, N: int) -> RNSKey:
     t["kxi"] = [(-inverse(N % m, m) * c.t["M_mi_inv"][i]) % m for i, m in enumerate(c.B)]
     # r_j = s_j |M^-1| + qhat_j |N M^-1|
     t["NMinv_Bp"] = [(N * c.t["Minv_Bp"][j]) % mp for j, mp in enumerate(c.Bp)]
-    t["NMinv_r"] = (N * c.t["Minv_r"]) % M_R
     # Montgomery-domain constants
     t["one"] = to_rns(c, M % N)                      # 1 in the Montgomery domain
     t["r2"] = to_rns(c, (M * M) % N)                 # entry: MM(x, M^2 mod N) = xM mod N
@@ -182,40 +205,35 @@ def mm(key: RNSKey, x: RNSValue, y: RNSValue) -> RNSValue:
     """RNS Montgomery multiplication: r = (xy + qhat N)/M, r == x y M^-1 (mod N).
 
     Steps in order:
-      1. s = x*y in every channel of B, B' and m_r;
-      2. xi_i = s_i |-N^-1 (M/m_i)^-1|_{m_i} in B;
-      3. extension B -> B' and m_r: qhat_j = sum_i xi_i |M/m_i|_{m'_j};
-      4. r_j = s_j |M^-1|_{m'_j} + qhat_j |N M^-1|_{m'_j} in B' and m_r;
+      1. s = x*y in every channel of B and B';
+      2. xi_i = s_i |-N^-1 (M/m_i)^-1|_{m_i} in B  (so q = sum xi_i M/m_i == -s N^-1 mod M);
+      3. extension B -> B': qhat_j = sum_i xi_i |M/m_i|_{m'_j}  (qhat = q + a M, 0 <= a < k);
+      4. r_j = s_j |M^-1|_{m'_j} + qhat_j |N M^-1|_{m'_j} in B'  (r = (s + qhat N)/M);
       5. xi'_j = r_j |(M'/m'_j)^-1|_{m'_j};
       6. extension B' -> B (exact): t_i = sum_j xi'_j |M'/m'_j|_{m_i},
-         a = (sum_j xi'_j |M'/m'_j|_{m_r} - r_r) |M'^-1|_{m_r} mod m_r,
-         r_i = t_i - a |M'|_{m_i}.
+         a' = floor(sum_j xi'_j / m'_j) in fixed point, r_i = t_i - a' |M'|_{m_i}.
     """
     c, t, kt = key.cls, key.cls.t, key.t
     k = c.k
     s_b = [(x.b[i] * y.b[i]) % c.B[i] for i in range(k)]
     s_bp = [(x.bp[j] * y.bp[j]) % c.Bp[j] for j in range(k)]
-    s_r = (x.r * y.r) % M_R
     xi = [(s_b[i] * kt["kxi"][i]) % c.B[i] for i in range(k)]
     qhat_bp = [sum(xi[i] * t["M_mi_Bp"][i][j] for i in range(k)) % c.Bp[j] for j in range(k)]
-    qhat_r = sum(xi[i] * t["M_mi_r"][i] for i in range(k)) % M_R
     r_bp = [(s_bp[j] * t["Minv_Bp"][j] + qhat_bp[j] * kt["NMinv_Bp"][j]) % c.Bp[j] for j in range(k)]
-    r_r = (s_r * t["Minv_r"] + qhat_r * kt["NMinv_r"]) % M_R
     xip = [(r_bp[j] * t["Mp_mj_inv"][j]) % c.Bp[j] for j in range(k)]
     t_b = [sum(xip[j] * t["Mp_mj_B"][j][i] for j in range(k)) % c.B[i] for i in range(k)]
-    t_r = sum(xip[j] * t["Mp_mj_r"][j] for j in range(k)) % M_R
-    a = ((t_r - r_r) * t["Mpinv_r"]) % M_R
-    if a >= k:
-        raise ArithmeticError("B'->B correction out of range (operand bound violated)")
+    a = fixed_point_factor(xip, c.Bp)
+    a_exact = sum(xip[j] * (c.Mp // c.Bp[j]) for j in range(k)) // c.Mp
+    if a != a_exact:
+        raise ArithmeticError("B'->B correction estimate differs from the exact factor (operand bound violated)")
     r_b = [(t_b[i] - a * t["Mp_B"][i]) % c.B[i] for i in range(k)]
-    return RNSValue(r_b, r_bp, r_r)
+    return RNSValue(r_b, r_bp)
 
 
 def add(key: RNSKey, x: RNSValue, y: RNSValue) -> RNSValue:
     c = key.cls
     return RNSValue([(x.b[i] + y.b[i]) % c.B[i] for i in range(c.k)],
-                    [(x.bp[j] + y.bp[j]) % c.Bp[j] for j in range(c.k)],
-                    (x.r + y.r) % M_R)
+                    [(x.bp[j] + y.bp[j]) % c.Bp[j] for j in range(c.k)])
 
 
 def enter(key: RNSKey, x: int) -> RNSValue:

@@ -7,7 +7,7 @@ import pytest
 from oracle import plain, primality, rns
 from synth import SplitMix64, load_keys
 
-CLASSES = [(512, 17), (1024, 34), (1536, 50), (2048, 67), (3072, 100), (4096, 133)]
+CLASSES = [(512, 18), (1024, 36), (1536, 54), (2048, 72), (3072, 108), (4096, 145)]
 
 
 @pytest.mark.parametrize("L,k", CLASSES)
@@ -15,20 +15,34 @@ def test_class_base_choice(L, k):
     c = rns.make_class(L)
     assert c.k == k
     pr = c.B + c.Bp
-    assert len(set(pr)) == 2 * k and all(p < (1 << 31) for p in pr)
-    assert pr == sorted(pr, reverse=True)
+    assert len(set(pr)) == 2 * k and pr == sorted(pr, reverse=True)
+    # channel bound: k products of residues always sum below 2^64
+    assert c.bound <= 1 << 31 and k * (c.bound - 1) ** 2 < 1 << 64
+    assert all(p < c.bound for p in pr)
     for p in pr[:8] + pr[-8:]:
         assert primality.is_prime_by_trial(p)
-    # minimality: the bound holds for k but fails for k-1
-    assert c.M >= 4 * (k + 1) ** 2 << L and c.Mp >= (k + 1) << L
-    pk = rns.primes_below(1 << 31, 2 * (k - 1))
+    # the base bounds hold for k ...
+    assert c.M >= 4 * (k + 1) ** 2 << L and c.Mp >= 2 * (k + 1) << L
+    # ... and fail for k-1 with the bound of k-1 channels
+    pk = rns.primes_below(rns.prime_bound(k - 1), 2 * (k - 1))
     M1 = 1
     for p in pk[: k - 1]:
         M1 *= p
     Mp1 = 1
     for p in pk[k - 1:]:
         Mp1 *= p
-    assert not (M1 >= 4 * k ** 2 << L and Mp1 >= k << L)
+    assert not (M1 >= 4 * k ** 2 << L and Mp1 >= 2 * k << L)
+
+
+def test_fixed_point_factor_exact_near_limits():
+    # floor(sum xi/m) recovered exactly when the value is below 3/4 of the product
+    c = rns.make_class(1024)
+    r = random.Random(9)
+    for X in [0, 1, c.M // 2, (3 * c.M) // 4 - 1] + [r.randrange((3 * c.M) // 4) for _ in range(200)]:
+        xi = [(X % m) * c.t["M_mi_inv"][i] % m for i, m in enumerate(c.B)]
+        total = sum(xi[i] * (c.M // m) for i, m in enumerate(c.B))
+        assert (total - X) % c.M == 0
+        assert rns.fixed_point_factor(xi, c.B) == total // c.M
 
 
 def test_primes_below_matches_brute_force():
@@ -44,7 +58,9 @@ def test_primes_below_matches_brute_force():
 def test_crt_roundtrip(L):
     c = rns.make_class(L)
     r = random.Random(L)
-    for X in [0, 1, c.M - 1, c.M // 3] + [r.randrange(c.M) for _ in range(30)]:
+    # the fixed-point CRT factor is exact below 3M/4; MM outputs stay far below that
+    lim = (3 * c.M) // 4
+    for X in [0, 1, lim - 1, c.M // 3] + [r.randrange(lim) for _ in range(30)]:
         assert rns.crt_value(c, rns.to_rns(c, X)) == X
 
 
@@ -72,7 +88,7 @@ def test_mm_congruence_and_bound(L):
 
 def test_mm_exhaustive_tiny_bases():
     # 8-bit channel primes, 12-bit class: every x, y below N for several moduli
-    c = rns.make_class(12, prime_bound=256)
+    c = rns.make_class(12, fixed_bound=256)
     assert c.k == 3
     for N in (3, 5, 7, 9, 15, 17, 33, 35, 63, 101):
         key = rns.make_key(c, N)
@@ -82,7 +98,7 @@ def test_mm_exhaustive_tiny_bases():
 
 
 def test_mm_random_tiny_bases_extended_range():
-    c = rns.make_class(12, prime_bound=256)
+    c = rns.make_class(12, fixed_bound=256)
     r = random.Random(4)
     for N in (4093, 4091, 2049, 3001, 255):
         key = rns.make_key(c, N)
@@ -92,7 +108,7 @@ def test_mm_random_tiny_bases_extended_range():
 
 
 def test_modexp_exhaustive_tiny():
-    c = rns.make_class(12, prime_bound=256)
+    c = rns.make_class(12, fixed_bound=256)
     for N in (3, 25, 77, 255, 4091):
         key = rns.make_key(c, N)
         xs = range(N) if N < 100 else [0, 1, 2, N - 1, N // 2, 1234 % N]
