@@ -1,0 +1,358 @@
+"""Benchmark: RSA-2048 CRT decryption throughput on the RNS exponentiation path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one mr_rsa_decrypt_crt call over 4096 ciphertexts (uniform in [0, N))
+spread over 16 seeded RSA-2048 keys: 8192 RNS modular exponentiations of
+1024-bit numbers with full-length CRT exponents, plus 4096 Garner recombinations.
+The metric is modular exponentiations per second over all ranks; with N > 1
+(launched under torchrun) every rank runs its own batch (weak scaling, no
+collective on the data path).  `--impl reference` times the CPU oracle (plain
+Python integers, its own square-and-multiply) on the same workload instead.
+
+Everything is printed on stderr except the single JSON result line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "modexp/s: RSA-2048 CRT decrypt and ragged mixed-size batch vs per-size launches"
+UNIT = "modexp/s"
+N_CT = 4096
+KEYSET = "rsa2048_x16"
+SEED = 0x4D520002
+# Peak of the 32x32->64-bit multiply-add pipe: SMs x 64 per clock x max SM clock
+IMAD_PER_CLK_PER_SM = 64
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------- workload
+def workload(rank: int = 0):
+    from synth import SplitMix64, load_keys
+    keys = load_keys(KEYSET)
+    r = SplitMix64(SEED + 0x1000 * rank)
+    per = N_CT // len(keys)
+    idx = [i // per for i in range(N_CT)]
+    cts = [r.below(keys[i]["N"]) for i in idx]
+    return keys, idx, cts
+
+
+def algorithmic_products_per_modexp(k: int, W: int, WX: int, ebits: int, w: int, chunks: int) -> int:
+    """32x32->64 products the method performs for one exponentiation (reductions not counted).
+
+    Per RNS Montgomery multiplication: 2k^2 (the two base extensions) + 7k
+    (x*y in both bases, xi, the two products of r_j, xi'_j, a'*|M'|).  One
+    exponentiation with fixed w-bit windows: `chunks` entry products, 2^w - 2
+    table products, w squarings + 1 multiplication per window after the first,
+    one exit product; plus binary->RNS (chunks * W * 2k) and RNS->binary (k * WX).
+    """
+    per_mm = 2 * k * k + 7 * k
+    nwin = max(1, math.ceil(ebits / w))
+    mms = chunks + (2 ** w - 2) + (w + 1) * (nwin - 1) + 1
+    return mms * per_mm + chunks * W * 2 * k + k * WX
+
+
+# ------------------------------------------------------------- clock sampler
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.rows = []
+        self.proc = None
+        self.mark = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", gpu_index], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line.strip()))
+
+    def window(self, t0, t1):
+        out = []
+        for t, line in self.rows:
+            if t0 <= t <= t1:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    out.append(f)
+        return out
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = self.window(t0, t1)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in the timed region"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0) for r in rows)}
+
+
+# --------------------------------------------------------- CPU oracle timing
+def _oracle_decrypt_chunk(args):
+    from oracle import plain
+    t0 = time.perf_counter()
+    out = [plain.rsa_decrypt_crt(c, p, q, dp, dq, qi) for (c, p, q, dp, dq, qi) in args]
+    return time.perf_counter() - t0, len(out)
+
+
+def oracle_throughput(keys, idx, cts, seconds: float, steps: int = 1, warmup: int = 0):
+    """Time the oracle's CRT decryption on every host core over a bounded sample.
+
+    Returns (modexp/s of the timed steps, cores, sample description, per-step seconds)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    tasks = [(cts[j], keys[idx[j]]["p"], keys[idx[j]]["q"], keys[idx[j]]["dp"], keys[idx[j]]["dq"],
+              keys[idx[j]]["qinv"]) for j in range(len(cts))]
+    ctxm = mp.get_context("spawn")
+    with ctxm.Pool(cores) as pool:
+        # calibrate: one decryption per core
+        t0 = time.perf_counter()
+        pool.map(_oracle_decrypt_chunk, [[tasks[j]] for j in range(cores)])
+        per = max(1e-4, (time.perf_counter() - t0))
+        n = max(cores, min(len(tasks), int(seconds / per) * cores))
+        n = (n // cores) * cores
+        sample = tasks[:n]
+        chunks = [sample[i::cores] for i in range(cores)]
+        times = []
+        for s in range(warmup + steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_decrypt_chunk, chunks)
+            dt = time.perf_counter() - t0
+            if s >= warmup:
+                times.append(dt)
+    value = 2 * n / statistics.mean(times)
+    desc = (f"first {n} of the {len(cts)} ciphertexts of the workload ({2 * n} modexps), "
+            f"oracle.plain.rsa_decrypt_crt on {cores} processes")
+    return value, cores, desc, times
+
+
+# --------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    keys, idx, cts = workload(0)
+    budget = max(4.0, 90.0 / max(1, args.steps + args.warmup))
+    value, cores, desc, times = oracle_throughput(keys, idx, cts, budget, steps=args.steps, warmup=args.warmup)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int (Python arbitrary precision)",
+        "data": "synthetic (seeded keys and ciphertexts)", "impl": "reference",
+        "config": {"workload": "rsa2048_crt_decrypt", "ciphertexts": N_CT, "keys": 16,
+                   "modexps_per_step": 2 * N_CT, "sample_per_step": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1305_3699_gb300 import mr
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    keys, idx, cts = workload(rank)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        log("timing the CPU oracle on a bounded sample ...")
+        v, cores, desc, _ = oracle_throughput(keys, idx, cts, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    ctx = mr.Context(local_rank)
+    hk = [ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]) for k in keys]
+    kl = mr.KeyList([hk[i] for i in idx])
+    c_dev = mr.to_tensor(cts, 64, device=dev)
+    m_dev = torch.zeros_like(c_dev)
+    status = torch.zeros(N_CT, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def step():
+        ctx.mr_rsa_decrypt_crt(kl, c_dev, m_dev, status, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    # spot check on every run: one decryption against the plain definition
+    got = mr.from_tensor(m_dev[:1])[0]
+    k0 = keys[idx[0]]
+    assert got == pow(cts[0], k0["d"], k0["N"]), "benchmark output mismatch"
+    assert int(status.sum()) == 0
+
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    gpu_index = vis[local_rank] if local_rank < len(vis) else (vis[0] if vis else str(local_rank))
+    sampler = ClockSampler(gpu_index) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    ctx.mr_profile_enable(True)
+    ctx.mr_profile_read()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.zero_()  # evict L2 between timed steps (outside the step's events)
+            evs[s][0].record(stream)
+            step()
+            evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall1 = time.time()
+    prof = ctx.mr_profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = 2 * N_CT * world * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D of the ciphertexts, the call, D2H of the plaintexts
+    c_host = c_dev.cpu().pin_memory()
+    m_host = torch.empty_like(c_host).pin_memory()
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for s in range(max(3, args.steps // 4)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c_dev.copy_(c_host, non_blocking=True)
+            step()
+            m_host.copy_(m_dev, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+    assert mr.from_tensor(m_host[:1])[0] == got
+    e2e_val = 2 * N_CT * world / (statistics.mean(e2e_ms) / 1e3)
+    clocks = sampler.summary(t_wall0, t_wall1) if sampler else None
+    if sampler:
+        sampler.stop()
+
+    # roofline of the dominant kernel (exponentiation): algorithmic products / kernel time
+    (mx_launch, mx_ms), (crt_launch, crt_ms) = prof
+    props = torch.cuda.get_device_properties(dev)
+    L_half, k = mr.mr_class_for_bits(1024)
+    W, WX = 32, None
+    WX = len(mr.mr_debug_class_table(L_half, "M"))
+    prods = 0
+    for i in idx:
+        for dpq in (keys[i]["dp"], keys[i]["dq"]):
+            prods += algorithmic_products_per_modexp(k, W, WX, dpq.bit_length(), 5, 2)
+    per_launch = prods  # one exponentiation launch per step covers all 8192 halves
+    max_mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            max_mhz = float(json.load(f).get("sm_max_mhz", max_mhz))
+    except (OSError, ValueError):
+        pass
+    peak = props.multi_processor_count * IMAD_PER_CLK_PER_SM * max_mhz * 1e6
+    mx_avg_ms = mx_ms / max(1, mx_launch)
+    achieved = per_launch / (mx_avg_ms / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tmul/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "modexp_kernel<k=36,TPI=4>", "kernel_ms": mx_avg_ms,
+                "products_per_launch": per_launch,
+                "peak_def": f"{props.multi_processor_count} SMs x {IMAD_PER_CLK_PER_SM} mad.wide.u32/clk x {max_mhz:.0f} MHz",
+                "crt_kernel_ms": crt_ms / max(1, crt_launch)}
+    if clocks and clocks.get("sm_mhz"):
+        roofline["frac_at_observed_clock"] = achieved / (props.multi_processor_count * IMAD_PER_CLK_PER_SM *
+                                                          clocks["sm_mhz"] * 1e6)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded keys and ciphertexts)",
+            "config": {"workload": "rsa2048_crt_decrypt", "ciphertexts_per_gpu": N_CT, "keys": 16,
+                       "modexps_per_step_per_gpu": 2 * N_CT, "decrypt_per_s": value / 2,
+                       "k": k, "window": 5, "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"items partitioned over {world} GPU(s)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(c_host.numel() * 4),
+                    "d2h_bytes_per_step": int(m_host.numel() * 4)},
+            "clocks": clocks,
+            "gpu_launches": int(mx_launch + crt_launch),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", init_method="env://")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * mr.h -- C ABI of the GB300 RNS modular-exponentiation library (libmrmod.so).
+ *
+ * What it computes.  Batched x^e mod N for odd moduli of up to 4096 bits, RSA
+ * encryption, RSA decryption through the CRT, and Miller-Rabin rounds.  Numbers
+ * are held in a Residue Number System (RNS): residues modulo pairwise coprime
+ * primes below 2^31, one base B of k primes plus a second base B' of k primes.
+ * Multiplication modulo N is the RNS Montgomery
+ * multiplication with R = M = prod(B), which needs two base extensions per
+ * product; exponentiation chains these products inside the Montgomery domain
+ * ("Secrets from the GPU", Sec. 3.1; the constants that depend only on the
+ * bases are computed once and kept resident on the GPU, same section).
+ *
+ * Conventions for every call.
+ *  - Big integers are little-endian arrays of uint32_t limbs (limb 0 = least
+ *    significant 32 bits).  A batch is a dense row-major array: row i starts at
+ *    base + i*stride limbs; unused high limbs of a row must be zero.
+ *  - Pointers documented as "device" point to memory of the context's GPU
+ *    (cudaMalloc / torch tensors); "host" pointers point to ordinary memory.
+ *    The caller owns every buffer it passes; the library owns only the context,
+ *    the key handles and the tables behind them.
+ *  - Batched calls are asynchronous on `stream` (a cudaStream_t; NULL = the
+ *    legacy default stream).  They return after the work is enqueued; results
+ *    and per-item status bytes are valid once the stream reaches that point.
+ *    Scratch memory is taken from a stream-ordered pool owned by the context.
+ *  - The call-level return value reports argument, setup and launch errors;
+ *    mr_last_error() gives a message.  Per-item problems (an input not below
+ *    its modulus, for instance) are written to dev_status[i] (device, one byte
+ *    per item; 0 = ok, otherwise an mr_status code) when dev_status is not NULL.
+ *  - A context is not thread-safe: serialise calls on one context.
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef MR_H
+#define MR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mr_ctx mr_ctx; /* opaque, library-owned */
+typedef struct mr_key mr_key; /* opaque, library-owned */
+
+typedef enum {
+  MR_OK = 0,
+  MR_ERR_ARG = 1,           /* bad argument (NULL pointer, zero stride, ...) */
+  MR_ERR_EVEN_MODULUS = 2,  /* modulus even or below 3 */
+  MR_ERR_NOT_COPRIME = 3,   /* modulus shares a factor with an RNS channel prime */
+  MR_ERR_SIZE = 4,          /* modulus or operand longer than the largest size class */
+  MR_ERR_RANGE = 5,         /* per item: input not below its modulus */
+  MR_ERR_OOM = 6,           /* device or host allocation failed */
+  MR_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+  MR_ERR_TIMEOUT = 8,       /* a bounded device wait ran out */
+  MR_ERR_BUSY = 9,          /* admission refused (footprint limit) */
+  MR_ERR_KEY = 10           /* key lacks the parts the call needs (e.g. no private CRT parts) */
+} mr_status;
+
+/* ---------------------------------------------------------------- context -- */
+
+/* Create a context on CUDA device `device` (the device becomes current on the
+ * calling thread).  *out receives the handle.  Errors: MR_ERR_ARG, MR_ERR_CUDA. */
+mr_status mr_init(int device, mr_ctx **out);
+
+/* Release the context, its keys and its device tables.  NULL is ignored. */
+void mr_shutdown(mr_ctx *ctx);
+
+/* Message of the last failing call on this context ("" when none).  The string
+ * is owned by the context and valid until the next call on it. */
+const char *mr_last_error(const mr_ctx *ctx);
+
+/* Size class that holds a modulus of `bits` bits: *class_bits = L (one of 512,
+ * 1024, 1536, 2048, 3072, 4096), *k = number of primes in each of B and B'.
+ * The primes lie below isqrt((2^64-1)/k) so that k-term dot products of
+ * residues fit 64-bit accumulators, and the bases satisfy M >= 4 (k+1)^2 2^L
+ * and M' >= 2 (k+1) 2^L, under which every Montgomery product stays below
+ * (k+1) N and the B'->B extension is exact.  (Sec. 3.1 sizes a base as "k
+ * channels hold keys of about 31k bits" and leaves the choice of primes open;
+ * these bounds are our reading.)  Errors: MR_ERR_SIZE. */
+mr_status mr_class_for_bits(uint32_t bits, uint32_t *class_bits, uint32_t *k);
+
+/* -------------------------------------------------------------- key setup -- */
+
+/* Per-modulus setup (Sec. 3.1: constants precomputed once and installed in GPU
+ * memory).  N: host, n_limbs limbs.  Builds (or reuses) the class tables for
+ * N's size class and the per-modulus constants (-N^-1 (M/m_i)^-1 mod m_i,
+ * N M^-1 mod m'_j, the RNS forms of M mod N, M^2 mod N and 2^L M^2 mod N), copies
+ * them to the device and returns a handle in *out.
+ * Errors: MR_ERR_ARG, MR_ERR_EVEN_MODULUS, MR_ERR_NOT_COPRIME, MR_ERR_SIZE,
+ * MR_ERR_OOM, MR_ERR_CUDA. */
+mr_status mr_rns_setup(mr_ctx *ctx, const uint32_t *N, uint32_t n_limbs, mr_key **out);
+
+/* RSA key (Sec. 3.3): the public modulus N = pq with public exponent e, and,
+ * when p, q, dp, dq, qinv are all non-NULL, the private CRT parts (dp = d mod
+ * (p-1), dq = d mod (q-1), qinv = q^-1 mod p).  All host arrays: N and e have
+ * n_limbs / e_limbs limbs; p, q, dp, dq, qinv have half_limbs limbs each.
+ * Private parts stay in device memory.  p and q must lie in one size class.
+ * Errors: as mr_rns_setup, plus MR_ERR_ARG when N != p*q. */
+mr_status mr_rsa_key_setup(mr_ctx *ctx, const uint32_t *N, uint32_t n_limbs, const uint32_t *e,
+                           uint32_t e_limbs, const uint32_t *p, const uint32_t *q, const uint32_t *dp,
+                           const uint32_t *dq, const uint32_t *qinv, uint32_t half_limbs, mr_key **out);
+
+/* Size class (k) of the public modulus, k of the private halves (0 without
+ * them), and device bytes held by the key.  Any output pointer may be NULL. */
+mr_status mr_key_info(const mr_key *key, uint32_t *k, uint32_t *k_half, uint64_t *device_bytes);
+
+/* Release a key (waits for the device to finish using it). NULL is ignored. */
+mr_status mr_key_free(mr_ctx *ctx, mr_key *key);
+
+/* ---------------------------------------------------------- batched calls -- */
+
+/* out[i] = x[i]^e[i] mod N_i for i < n (Sec. 3.1: square-and-multiply chaining
+ * RNS Montgomery multiplications, precomputation outside the loop).
+ *   keys    host array of n handles (N_i = modulus of keys[i]; any mix of sizes)
+ *   x       device, n rows of x_stride limbs, each x[i] < N_i (else status RANGE)
+ *   e       device, n rows of e_stride limbs, any value (e = 0 gives 1 mod N_i)
+ *   out     device, n rows of out_stride limbs; out_stride must hold N_i's limbs;
+ *           the result is written in [0, N_i) and zero-padded
+ *   dev_status  device, n bytes, or NULL
+ * Errors: MR_ERR_ARG, MR_ERR_SIZE, MR_ERR_OOM, MR_ERR_CUDA. */
+mr_status mr_modexp_batch(mr_ctx *ctx, const mr_key *const *keys, size_t n, const uint32_t *x,
+                          uint32_t x_stride, const uint32_t *e, uint32_t e_stride, uint32_t *out,
+                          uint32_t out_stride, uint8_t *dev_status, void *stream);
+
+/* RSA encryption c[i] = m[i]^e_i mod N_i with each key's public exponent
+ * (Sec. 3.3: one exponentiation per message block).  Layout as mr_modexp_batch. */
+mr_status mr_rsa_encrypt(mr_ctx *ctx, const mr_key *const *keys, size_t n, const uint32_t *m,
+                         uint32_t m_stride, uint32_t *c, uint32_t c_stride, uint8_t *dev_status,
+                         void *stream);
+
+/* RSA decryption through the CRT: m_p = c^dp mod p, m_q = c^dq mod q (two
+ * independent half-size exponentiations), h = qinv (m_p - m_q) mod p,
+ * m = m_q + h q.  Equals c^d mod N (Sec. 3.3 defines d).  Keys need their
+ * private parts (else MR_ERR_KEY).  c[i] < N_i (else status RANGE).
+ * Layout as mr_modexp_batch. */
+mr_status mr_rsa_decrypt_crt(mr_ctx *ctx, const mr_key *const *keys, size_t n, const uint32_t *c,
+                             uint32_t c_stride, uint32_t *m, uint32_t m_stride, uint8_t *dev_status,
+                             void *stream);
+
+/* Miller-Rabin rounds (Sec. 3.2: Montgomery-domain primality test with a
+ * caller-chosen number of iterations) on n odd candidates of one length.
+ *   cand       device, n rows of n_limbs limbs (odd, >= 5, top limb non-zero
+ *              not required)
+ *   witness    device, n*rounds rows of n_limbs limbs; row i*rounds+r is the
+ *              witness of round r for candidate i (meant to lie in [2, n-2])
+ *   dev_is_probable_prime  device, n bytes: 1 when every round passed, else 0
+ *   dev_round_mask  device, n uint32 words or NULL: bit r set when round r
+ *              passed (rounds <= 32 when given)
+ * Per-candidate constants (RNS form of the candidate, Montgomery constants)
+ * are derived on the device; no candidate leaves the GPU.
+ * Errors: MR_ERR_ARG, MR_ERR_SIZE, MR_ERR_OOM, MR_ERR_CUDA. */
+mr_status mr_miller_rabin_batch(mr_ctx *ctx, const uint32_t *cand, uint32_t n_limbs, size_t n,
+                                const uint32_t *witness, uint32_t rounds, uint8_t *dev_is_probable_prime,
+                                uint32_t *dev_round_mask, void *stream);
+
+/* --------------------------------------------------------- instrumentation -- */
+
+/* Per-kernel timing.  While enabled, every batched call records a pair of CUDA
+ * events around each kernel it launches, on the call's own stream.  Kernel
+ * kinds: 0 = exponentiation (the RNS Montgomery loop), 1 = CRT recombination. */
+typedef struct {
+  uint32_t launches; /* kernels of this kind launched since the last read */
+  double ms;         /* their summed device time (ms); 0 when timing was off */
+} mr_kernel_time;
+
+/* Turn event timing on (on != 0) or off.  Launch counting is always on. */
+mr_status mr_profile_enable(mr_ctx *ctx, int on);
+
+/* Wait for the recorded events, then return per-kind totals since the last
+ * read in times[0..n_kinds) (n_kinds <= 2) and reset the counters. */
+mr_status mr_profile_read(mr_ctx *ctx, mr_kernel_time *times, uint32_t n_kinds);
+
+/* ------------------------------------------------------------ inspection -- */
+
+/* Copy one precomputed table of a size class (or of a key when key != NULL) to
+ * host memory, as plain residues (not the device's internal scaled form), in
+ * the order of the same-named tables of the CPU model of the method.  Used by
+ * tests to check the setup value by value; needs no device (ctx may be NULL
+ * for class tables).  *count receives the number of uint32 words; out may be
+ * NULL to query it.  Class tables: "B", "Bp" (the channel primes), "M_mi_inv"
+ * (|(M/m_i)^-1|_{m_i}), "M_mi_Bp" (row i, column j: |M/m_i|_{m'_j}), "Minv_Bp",
+ * "Mp_mj_inv", "Mp_mj_B" (row j, column i), "Mp_B", "M" (limbs of M), "bound"
+ * (the channel-prime bound as two words, low first).  Key tables: "kxi",
+ * "NMinv_Bp", "one", "r2", "r2h" (RNS vectors: B residues, then B').
+ * Errors: MR_ERR_ARG (unknown name, or out too small), MR_ERR_SIZE. */
+mr_status mr_debug_table(mr_ctx *ctx, uint32_t class_bits, const mr_key *key, const char *name,
+                         uint32_t *out, size_t capacity, size_t *count);
+
+/* As mr_debug_table for the key tables of modulus N (host, n_limbs limbs),
+ * computed on the host only (no context, no device).  Errors as mr_rns_setup. */
+mr_status mr_debug_key_table_host(const uint32_t *N, uint32_t n_limbs, const char *name, uint32_t *out,
+                                  size_t capacity, size_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MR_H */

@@ -1,0 +1,226 @@
+// Kernels of the RNS exponentiation path, templated on the size class.
+//   modexp_kernel  x^e mod N per work item (Sec. 3.1: square-and-multiply chaining
+//                  RNS Montgomery products inside the Montgomery domain, the
+//                  window table precomputed outside the main loop)
+//   crt_kernel     Garner recombination of RSA CRT halves (Sec. 3.3 defines d;
+//                  the CRT split is the decryption form of the workload)
+#pragma once
+#include <cstdint>
+
+#include "kernels_api.h"
+#include "rns_device.cuh"
+
+namespace mr {
+
+__device__ __forceinline__ uint32_t exp_bits(const uint32_t* e, uint32_t el) {
+  for (int w = (int)el - 1; w >= 0; w--) {
+    uint32_t v = e[w];
+    if (v) return 32u * w + 32u - __clz(v);
+  }
+  return 0;
+}
+
+__device__ __forceinline__ uint32_t exp_digit(const uint32_t* e, uint32_t el, uint32_t pos, uint32_t wb) {
+  uint32_t l = pos >> 5, b = pos & 31;
+  uint64_t v = (l < el ? e[l] : 0u) | ((uint64_t)(l + 1 < el ? e[l + 1] : 0u) << 32);
+  return (uint32_t)(v >> b) & ((1u << wb) - 1u);
+}
+
+template <class C>
+__device__ __forceinline__ void tab_store(uint32_t* wt, int ent, const uint32_t (&b)[C::NPT], const uint32_t (&p)[C::NPT],
+                                          int lane) {
+  uint32_t* base = wt + (size_t)ent * (2 * C::NPT) * 32 + lane;
+#pragma unroll
+  for (int s = 0; s < C::NPT; s++) {
+    base[s * 32] = b[s];
+    base[(C::NPT + s) * 32] = p[s];
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void tab_load(const uint32_t* wt, int ent, uint32_t (&b)[C::NPT], uint32_t (&p)[C::NPT],
+                                         int lane) {
+  const uint32_t* base = wt + (size_t)ent * (2 * C::NPT) * 32 + lane;
+#pragma unroll
+  for (int s = 0; s < C::NPT; s++) {
+    b[s] = base[s * 32];
+    p[s] = base[(C::NPT + s) * 32];
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem_raw[];
+  Smem<C> sm{smem_raw};
+  load_class_smem<C>(sm, a.cls);
+  __syncthreads();
+
+  constexpr int NPT = C::NPT, TPI = C::TPI;
+  const int lane = threadIdx.x & 31;
+  const int t = threadIdx.x % TPI;
+  const int item_in_block = threadIdx.x / TPI;
+  const uint32_t g_raw = blockIdx.x * C::IPB + item_in_block;
+  const bool live = g_raw < a.n_items;
+  const uint32_t g = live ? g_raw : a.n_items - 1;  // idle groups shadow the last item, write nothing
+  const MxItem it = reinterpret_cast<const MxItem*>(a.items)[g];
+  const KeyOff ko = key_offsets(C::K, C::W);
+  const uint32_t* key = it.key;
+  uint32_t* xib = sm.xi(item_in_block);
+  uint32_t* xpb = xib + C::KP;
+  const int warp_global = (blockIdx.x * C::THREADS + threadIdx.x) >> 5;
+  uint32_t* wt = a.scratch + (size_t)warp_global * ((size_t)1 << a.wbits) * (2 * NPT) * 32;
+
+  // input range check: x < xlim
+  uint32_t bad = 0;
+  if (t == 0) bad = less_than(it.x, it.x_limbs, it.xlim, it.xlim_limbs) ? 0u : 1u;
+  bad = __shfl_sync(0xffffffffu, bad, lane - t);
+
+  uint32_t kxi[NPT], cmul[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int o = t * NPT + s;
+    kxi[s] = o < C::K ? __ldg(key + ko.kxi + o) : 0u;
+    cmul[s] = o < C::K ? __ldg(key + ko.cmul + o) : 0u;
+  }
+
+  // entry into the Montgomery domain: x~ = MM(x_lo, M^2 mod N) [+ MM(x_hi, 2^L M^2 mod N)]
+  uint32_t xb[NPT], xp[NPT], yb[NPT], yp[NPT];
+  const int nl0 = bad ? 0 : (int)(it.x_limbs < (uint32_t)C::W ? it.x_limbs : C::W);
+  to_rns<C>(xb, xp, it.x, nl0, a.cls, sm, t);
+  load_vec<C>(yb, yp, key + ko.r2, t);
+  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  const bool two = !bad && it.x_limbs > (uint32_t)C::W;
+  if (__any_sync(0xffffffffu, two)) {
+    uint32_t hb[NPT], hp[NPT];
+    const int nl1 = two ? min((int)it.x_limbs - C::W, C::W) : 0;
+    to_rns<C>(hb, hp, it.x + C::W, nl1, a.cls, sm, t);
+    load_vec<C>(yb, yp, key + ko.r2h, t);
+    mont_mul<C>(hb, hp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+    add_vec<C>(xb, xp, hb, hp, sm, t);
+  }
+
+  // window table: entry 0 = 1 (Montgomery form M mod N), entry j = x~^j
+  const int wb = (int)a.wbits, E = 1 << wb;
+  load_vec<C>(yb, yp, key + ko.one, t);
+  tab_store<C>(wt, 0, yb, yp, lane);
+  tab_store<C>(wt, 1, xb, xp, lane);
+  {
+    uint32_t cb[NPT], cp[NPT];
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      cb[s] = xb[s];
+      cp[s] = xp[s];
+    }
+    for (int j = 2; j < E; j++) {
+      mont_mul<C>(cb, cp, xb, xp, kxi, cmul, sm, xib, xpb, t);
+      tab_store<C>(wt, j, cb, cp, lane);
+    }
+  }
+
+  // exponent: fixed windows from the top; groups of a warp run in lockstep
+  const uint32_t el = it.e_limbs;
+  uint32_t ebits = 0;
+  if (t == 0) ebits = bad ? 0u : exp_bits(it.e, el);
+  ebits = __shfl_sync(0xffffffffu, ebits, lane - t);
+  const uint32_t nwin = __reduce_max_sync(0xffffffffu, (ebits + wb - 1) / wb);
+  uint32_t d = (nwin && !bad) ? exp_digit(it.e, el, (nwin - 1) * wb, wb) : 0u;
+  __syncwarp();
+  tab_load<C>(wt, d, xb, xp, lane);
+  for (int widx = (int)nwin - 2; widx >= 0; widx--) {
+    for (int q = 0; q < wb; q++) mont_mul<C>(xb, xp, xb, xp, kxi, cmul, sm, xib, xpb, t);
+    d = bad ? 0u : exp_digit(it.e, el, (uint32_t)widx * wb, wb);
+    if (__any_sync(0xffffffffu, d != 0)) {
+      tab_load<C>(wt, d, yb, yp, lane);
+      mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+    }
+  }
+
+  // leave the domain: MM(x, 1), then RNS -> binary, reduced into [0, N)
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int o = t * NPT + s;
+    yb[s] = sm.cb4(o).z;  // hat form of 1 = 2^32 mod m
+    yp[s] = sm.cp4(o).z;
+  }
+  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  from_rns_reduce<C>(xb, a.cls, key, sm, xib, t, it.out, (int)it.out_limbs, live && !bad);
+  if (live && t == 0) {
+    if (bad)
+      for (uint32_t w = 0; w < it.out_limbs; w++) it.out[w] = 0u;
+    if (a.status && it.status != 0xffffffffu) a.status[it.status] = bad ? 5u : 0u;
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS) crt_kernel(LaunchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem_raw[];
+  Smem<C> sm{smem_raw};
+  load_class_smem<C>(sm, a.cls);
+  __syncthreads();
+
+  constexpr int NPT = C::NPT, TPI = C::TPI, W = C::W;
+  const int t = threadIdx.x % TPI;
+  const int item_in_block = threadIdx.x / TPI;
+  const uint32_t g_raw = blockIdx.x * C::IPB + item_in_block;
+  const bool live = g_raw < a.n_items;
+  const uint32_t g = live ? g_raw : a.n_items - 1;
+  const CrtItem it = reinterpret_cast<const CrtItem*>(a.items)[g];
+  const KeyOff ko = key_offsets(C::K, C::W);
+  const CrtOff cro = crt_offsets(C::K, C::W);
+  const uint32_t* key = it.keyp;
+  uint32_t* xib = sm.xi(item_in_block);
+  uint32_t* xpb = xib + C::KP;
+
+  uint32_t kxi[NPT], cmul[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int o = t * NPT + s;
+    kxi[s] = o < C::K ? __ldg(key + ko.kxi + o) : 0u;
+    cmul[s] = o < C::K ? __ldg(key + ko.cmul + o) : 0u;
+  }
+  // d = m_p + P2 - m_q  (a positive integer below 3 * 2^L, congruent to m_p - m_q mod p)
+  uint32_t db[NPT], dp[NPT], qb[NPT], qp[NPT], yb[NPT], yp[NPT];
+  to_rns<C>(db, dp, it.mp, W, a.cls, sm, t);
+  to_rns<C>(qb, qp, it.mq, W, a.cls, sm, t);
+  load_vec<C>(yb, yp, it.crt + cro.p2, t);
+  add_vec<C>(db, dp, yb, yp, sm, t);
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {  // subtract m_q: d + m - q lies in [0, 2m]
+    const int o = t * NPT + s;
+    const uint32_t mb = sm.cb4(o).x, mp = sm.cp4(o).x;
+    uint32_t u = db[s] + mb - qb[s];
+    db[s] = min(u, u - mb);
+    uint32_t v = dp[s] + mp - qp[s];
+    dp[s] = min(v, v - mp);
+  }
+  // h = MM(d, qinv M mod p) = d qinv mod p, then to binary in [0, p)
+  load_vec<C>(yb, yp, it.crt + cro.qm, t);
+  mont_mul<C>(db, dp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  uint32_t h[W];
+  from_rns_reduce<C>(db, a.cls, key, sm, xib, t, h, W, true);
+  // m = m_q + h q  (2W limbs)
+  if (live && t == 0) {
+    const uint32_t* q = it.crt + cro.q;
+    const int ol = (int)it.out_limbs;
+    // column-wise schoolbook with a 96-bit column accumulator
+    uint32_t c0 = 0, c1 = 0;
+    for (int w = 0; w < 2 * W; w++) {
+      uint32_t s0 = c0, s1 = c1, s2 = 0;
+      int ilo = w - (W - 1) > 0 ? w - (W - 1) : 0;
+      int ihi = w < W - 1 ? w : W - 1;
+      for (int i = ilo; i <= ihi; i++) mac96(s0, s1, s2, h[i], __ldg(q + (w - i)));
+      if (w < W) {  // + m_q
+        uint32_t mqw = it.mq[w];
+        asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.u32 %2, %2, 0;"
+            : "+r"(s0), "+r"(s1), "+r"(s2)
+            : "r"(mqw));
+      }
+      if (w < ol) it.out[w] = s0;
+      c0 = s1;
+      c1 = s2;
+    }
+    for (int w = 2 * W; w < ol; w++) it.out[w] = 0u;
+  }
+}
+
+}  // namespace mr

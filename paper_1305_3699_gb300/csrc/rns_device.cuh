@@ -1,0 +1,412 @@
+// Device side of the RNS modular exponentiation ("Secrets from the GPU",
+// Sec. 3.1): channel arithmetic, RNS Montgomery multiplication with its two
+// base extensions, fixed-window exponentiation, binary <-> RNS conversion.
+//
+// Mapping.  One number is owned by a group of TPI consecutive lanes of a warp
+// (32/TPI numbers per warp).  Lane t of the group owns the NPT = ceil(k/TPI)
+// consecutive channels [t*NPT, t*NPT+NPT) of base B and the same positions of
+// base B'; its residues stay in registers for the whole exponentiation.  The
+// two base extensions are the only all-to-all steps: each lane publishes its
+// CRT coefficients xi to shared memory, the group reads all k of them
+// (broadcast loads) and every lane forms the k-term dot products of its own
+// output channels against the extension matrix, which is shared by every
+// number of the size class and kept in shared memory.  A group only ever
+// synchronises with __syncwarp; no block-wide barrier after the prologue.
+//
+// Word arithmetic.  Channel primes m < 2^31 with k*m^2 < 2^64 (chosen at
+// setup), so a k-term dot product of residues accumulates exactly in one
+// 64-bit register with one mad.wide.u32 per term (full IMAD rate on sm_103)
+// and is reduced once.  Residues are kept in per-channel Montgomery form
+// x*2^32 mod m ("hat"); reductions use mad.wide (no mul.hi).
+#pragma once
+#include <cstdint>
+
+#include "layout.h"
+
+namespace mr {
+
+__device__ __forceinline__ uint64_t madw(uint32_t a, uint32_t b, uint64_t c) {
+  uint64_t r;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ uint64_t mulw(uint32_t a, uint32_t b) {
+  uint64_t r;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t lo32(uint64_t v) { return (uint32_t)v; }
+__device__ __forceinline__ uint32_t hi32(uint64_t v) { return (uint32_t)(v >> 32); }
+
+// Word Montgomery reduction: v * 2^-32 mod m for v < 2^32 (m + 1), mi = -m^-1 mod 2^32.
+// Result in [0, m] (in [0, m) when v < 2^32 m).  Requires m < 2^31.
+__device__ __forceinline__ uint32_t redc(uint64_t v, uint32_t m, uint32_t mi) {
+  uint32_t q = lo32(v) * mi;
+  uint32_t r = hi32(madw(q, m, v));
+  return min(r, r - m);
+}
+// Any v < 2^64: fold the high word with r32 = 2^32 mod m, then reduce.  Result v 2^-32 mod m in [0, m].
+__device__ __forceinline__ uint32_t redc64(uint64_t v, uint32_t m, uint32_t mi, uint32_t r32) {
+  return redc(madw(hi32(v), r32, lo32(v)), m, mi);
+}
+
+// 96-bit accumulate (s2:s1:s0) += a*b (one-time conversions only)
+__device__ __forceinline__ void mac96(uint32_t& s0, uint32_t& s1, uint32_t& s2, uint32_t a, uint32_t b) {
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\tmadc.hi.cc.u32 %1, %3, %4, %1;\n\taddc.u32 %2, %2, 0;"
+      : "+r"(s0), "+r"(s1), "+r"(s2)
+      : "r"(a), "r"(b));
+}
+
+template <int K_, int W_, int WX_, int TPI_, int THREADS_, int VEC_>
+struct Cfg {
+  static constexpr int K = K_;                    // channels per base
+  static constexpr int W = W_;                    // limbs of the class bound
+  static constexpr int WX = WX_;                  // limbs of k*M (RNS -> binary)
+  static constexpr int TPI = TPI_;                // lanes per number
+  static constexpr int NPT = (K + TPI - 1) / TPI; // channels per lane and base
+  static constexpr int VEC = VEC_;                // words per shared-memory load of a matrix row (2 or 4)
+  static constexpr int NPTP = (NPT + VEC - 1) / VEC * VEC;  // padded to whole vector loads
+  static constexpr int ROW = TPI * NPTP;          // words per extension-matrix row in smem
+  static constexpr int SL = TPI * NPT;            // slot-indexed constant arrays
+  static constexpr int KP = (K + 3) & ~3;         // xi buffer stride
+  static constexpr int THREADS = THREADS_;
+  static constexpr int IPB = THREADS / TPI;       // numbers per block
+  static constexpr int IPW = 32 / TPI;            // numbers per warp
+  // shared memory, in 16-byte units where vectors live
+  static constexpr int SM_T1 = 0;
+  static constexpr int SM_T2 = SM_T1 + K * ROW;
+  static constexpr int SM_CB4 = SM_T2 + K * ROW;  // uint4 {m, mi, r32, mphh}   B
+  static constexpr int SM_CP4 = SM_CB4 + 4 * SL;  // uint4 {m, mi, r32, ahat}   B'
+  static constexpr int SM_CB2 = SM_CP4 + 4 * SL;  // uint2 {mmiinv, ub}         B
+  static constexpr int SM_CP2 = SM_CB2 + 2 * SL;  // uint2 {d, ubp}             B'
+  static constexpr int SM_XI = SM_CP2 + 2 * SL;   // IPB x 2 x KP
+  static constexpr int SM_WORDS = SM_XI + IPB * 2 * KP;
+  static constexpr int SMEM_BYTES = SM_WORDS * 4;
+  static_assert(TPI == 1 || TPI == 2 || TPI == 4 || TPI == 8 || TPI == 16 || TPI == 32, "TPI must divide 32");
+  static_assert(VEC == 2 || VEC == 4, "vector width");
+  static_assert((SM_T2 % 4) == 0 && (SM_CB4 % 4) == 0 && (SM_CB2 % 2) == 0 && (SM_XI % 4) == 0, "alignment");
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+};
+
+template <class C>
+struct Smem {
+  uint32_t* base;
+  __device__ const uint32_t* T1() const { return base + C::SM_T1; }
+  __device__ const uint32_t* T2() const { return base + C::SM_T2; }
+  __device__ uint4 cb4(int o) const { return reinterpret_cast<const uint4*>(base + C::SM_CB4)[o]; }
+  __device__ uint4 cp4(int o) const { return reinterpret_cast<const uint4*>(base + C::SM_CP4)[o]; }
+  __device__ uint2 cb2(int o) const { return reinterpret_cast<const uint2*>(base + C::SM_CB2)[o]; }
+  __device__ uint2 cp2(int o) const { return reinterpret_cast<const uint2*>(base + C::SM_CP2)[o]; }
+  __device__ uint32_t* xi(int item_in_block) const { return base + C::SM_XI + item_in_block * 2 * C::KP; }
+};
+
+// Block prologue: copy the class tables into shared memory in the lane-slot layout.
+template <class C>
+__device__ void load_class_smem(const Smem<C>& sm, const uint32_t* cls) {
+  const ClassOff o = class_offsets(C::K, C::W, C::WX);
+  uint32_t* s = sm.base;
+  for (int idx = threadIdx.x; idx < C::K * C::ROW; idx += blockDim.x) {
+    int row = idx / C::ROW, col = idx % C::ROW;
+    int t = col / C::NPTP, sl = col % C::NPTP;
+    int ch = t * C::NPT + sl;
+    bool ok = sl < C::NPT && ch < C::K;
+    s[C::SM_T1 + idx] = ok ? cls[o.T1 + row * C::K + ch] : 0u;
+    s[C::SM_T2 + idx] = ok ? cls[o.T2 + row * C::K + ch] : 0u;
+  }
+  for (int ch = threadIdx.x; ch < C::SL; ch += blockDim.x) {
+    bool ok = ch < C::K;
+    uint32_t* cb4 = s + C::SM_CB4 + 4 * ch;
+    uint32_t* cp4 = s + C::SM_CP4 + 4 * ch;
+    uint32_t* cb2 = s + C::SM_CB2 + 2 * ch;
+    uint32_t* cp2 = s + C::SM_CP2 + 2 * ch;
+    cb4[0] = ok ? cls[o.m + ch] : 0u;
+    cb4[1] = ok ? cls[o.mi + ch] : 0u;
+    cb4[2] = ok ? cls[o.r32 + ch] : 0u;
+    cb4[3] = ok ? cls[o.mphh + ch] : 0u;
+    cp4[0] = ok ? cls[o.m + C::K + ch] : 0u;
+    cp4[1] = ok ? cls[o.mi + C::K + ch] : 0u;
+    cp4[2] = ok ? cls[o.r32 + C::K + ch] : 0u;
+    cp4[3] = ok ? cls[o.ahat + ch] : 0u;
+    cb2[0] = ok ? cls[o.mmiinv + ch] : 0u;
+    cb2[1] = ok ? cls[o.ub + ch] : 0u;
+    cp2[0] = ok ? cls[o.d + ch] : 0u;
+    cp2[1] = ok ? cls[o.ubp + ch] : 0u;
+  }
+  for (int idx = threadIdx.x; idx < C::IPB * 2 * C::KP; idx += blockDim.x) s[C::SM_XI + idx] = 0u;
+}
+
+// Sum a value over the TPI lanes of this lane's group.
+template <int TPI>
+__device__ __forceinline__ uint32_t group_sum(uint32_t v) {
+#pragma unroll
+  for (int off = 1; off < TPI; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// acc[s] = sum_{i<k} xs[i] * T[i][slot s of lane t]  (64-bit, exact: k m^2 < 2^64)
+template <class C>
+__device__ __forceinline__ void ext_dot(uint64_t (&acc)[C::NPT], const uint32_t* xs, const uint32_t* T, int t) {
+  constexpr int NPT = C::NPT, K = C::K;
+#pragma unroll
+  for (int s = 0; s < NPT; s++) acc[s] = 0;
+#pragma unroll
+  for (int i0 = 0; i0 < K; i0 += 4) {
+    const uint4 x4 = *reinterpret_cast<const uint4*>(xs + i0);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (i0 + q < K) {
+        const uint32_t xv = q == 0 ? x4.x : q == 1 ? x4.y : q == 2 ? x4.z : x4.w;
+        const uint32_t* row = T + (i0 + q) * C::ROW + t * C::NPTP;
+        if constexpr (C::VEC == 4) {
+#pragma unroll
+          for (int s4 = 0; s4 < C::NPTP; s4 += 4) {
+            const uint4 tv = *reinterpret_cast<const uint4*>(row + s4);
+            if (s4 + 0 < NPT) acc[s4 + 0] = madw(xv, tv.x, acc[s4 + 0]);
+            if (s4 + 1 < NPT) acc[s4 + 1] = madw(xv, tv.y, acc[s4 + 1]);
+            if (s4 + 2 < NPT) acc[s4 + 2] = madw(xv, tv.z, acc[s4 + 2]);
+            if (s4 + 3 < NPT) acc[s4 + 3] = madw(xv, tv.w, acc[s4 + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int s2 = 0; s2 < C::NPTP; s2 += 2) {
+            const uint2 tv = *reinterpret_cast<const uint2*>(row + s2);
+            if (s2 + 0 < NPT) acc[s2 + 0] = madw(xv, tv.x, acc[s2 + 0]);
+            if (s2 + 1 < NPT) acc[s2 + 1] = madw(xv, tv.y, acc[s2 + 1]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// RNS Montgomery multiplication (Sec. 3.1, R = M): x <- x*y*M^-1 mod N, with
+// outputs below (k+1)N for operands whose product is below 4(k+1)^2 2^L N.
+//   xb, xp: hat residues of x in this lane's B and B' channels (in/out)
+//   yb, yp: hat residues of y (may alias xb, xp for a squaring)
+//   kxi:    |-N^-1 (M/m_i)^-1|_{m_i} plain, cmul: |N M^-1|_{m'_j} hat  (per modulus)
+//   xib, xpb: this number's xi / xi' exchange buffers in shared memory
+// ------------------------------------------------------------------------
+template <class C>
+__device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], const uint32_t (&yb)[C::NPT],
+                                         const uint32_t (&yp)[C::NPT], const uint32_t (&kxi)[C::NPT],
+                                         const uint32_t (&cmul)[C::NPT], const Smem<C>& sm, uint32_t* xib,
+                                         uint32_t* xpb, int t) {
+  constexpr int NPT = C::NPT, K = C::K;
+  uint32_t sp[NPT];
+  // 1-2. s = x*y in both bases; xi_i = s_i |-N^-1 (M/m_i)^-1| (plain CRT coefficients of q)
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int o = t * NPT + s;
+    const uint4 cb = sm.cb4(o);
+    uint32_t sb = redc(mulw(xb[s], yb[s]), cb.x, cb.y);
+    uint32_t xi = redc(mulw(sb, kxi[s]), cb.x, cb.y);
+    if (o < K) xib[o] = xi;
+    const uint4 cp = sm.cp4(o);
+    sp[s] = redc(mulw(xp[s], yp[s]), cp.x, cp.y);
+  }
+  __syncwarp();
+  // 3. extension B -> B': qhat_j = sum_i xi_i |M/m_i|_{m'_j}   (k-term 64-bit dot products)
+  uint64_t acc[NPT];
+  ext_dot<C>(acc, xib, sm.T1(), t);
+  // 4-5. r_j = s_j |M^-1| + qhat_j |N M^-1| (hat, the new B' residues); xi'_j = r_j |(M'/m'_j)^-1| (plain)
+  uint32_t kaw = 0;
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int o = t * NPT + s;
+    const uint4 cp = sm.cp4(o);
+    const uint2 c2 = sm.cp2(o);
+    uint32_t qh = redc64(acc[s], cp.x, cp.y, cp.z);
+    uint32_t r = redc(madw(sp[s], cp.w, mulw(qh, cmul[s])), cp.x, cp.y);
+    xp[s] = r;
+    uint32_t xpj = redc(mulw(r, c2.x), cp.x, cp.y);
+    if (o < K) xpb[o] = xpj;
+    kaw += hi32(mulw(xpj, c2.y));  // floor(xi'_j 2^Q / m'_j), up to 2 units low
+  }
+  __syncwarp();
+  // 6. extension B' -> B, exact: a' = floor(sum xi'_j / m'_j) from the fixed-point sum with a 1/4 offset
+  const uint32_t alpha = (group_sum<C::TPI>(kaw) + (1u << (KAW_Q - 2))) >> KAW_Q;
+  ext_dot<C>(acc, xpb, sm.T2(), t);
+  // r_i = t_i - a' |M'|_{m_i}  (hat, the new B residues)
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int o = t * NPT + s;
+    const uint4 cb = sm.cb4(o);
+    uint32_t th = redc64(acc[s], cb.x, cb.y, cb.z);
+    uint32_t corr = redc(mulw(alpha, cb.w), cb.x, cb.y);
+    uint32_t r = th + cb.x - corr;
+    xb[s] = min(r, r - cb.x);
+  }
+}
+
+// Binary -> hat residues of this lane's channels: x = sum_w X_w 2^(32w), read
+// from `x` (nl limbs, limbs past nl are zero), with the class table P.
+template <class C>
+__device__ __forceinline__ void to_rns(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], const uint32_t* x, int nl,
+                                       const uint32_t* cls, const Smem<C>& sm, int t) {
+  constexpr int NPT = C::NPT, K = C::K;
+  const ClassOff co = class_offsets(C::K, C::W, C::WX);
+  const uint32_t* P = cls + co.P;
+  uint64_t ab[NPT], ap[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; s++) ab[s] = ap[s] = 0;
+  for (int w = 0; w < C::W; w++) {
+    const uint32_t xw = w < nl ? x[w] : 0u;
+    const uint32_t* prow = P + w * 2 * K;
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      const int o = t * NPT + s;
+      if (o < K) {
+        ab[s] = madw(xw, __ldg(prow + o), ab[s]);
+        ap[s] = madw(xw, __ldg(prow + K + o), ap[s]);
+      }
+    }
+    if (w & 1) {  // keep the sums below 2^64: fold every two limbs
+#pragma unroll
+      for (int s = 0; s < NPT; s++) {
+        const int o = t * NPT + s;
+        const uint32_t rb = sm.cb4(o).z, rp = sm.cp4(o).z;
+        ab[s] = madw(hi32(ab[s]), rb, lo32(ab[s]));
+        ap[s] = madw(hi32(ap[s]), rp, lo32(ap[s]));
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int o = t * NPT + s;
+    const uint4 cb = sm.cb4(o), cp = sm.cp4(o);
+    xb[s] = redc64(ab[s], cb.x, cb.y, cb.z);
+    xp[s] = redc64(ap[s], cp.x, cp.y, cp.z);
+  }
+}
+
+// Load this lane's hat residues of an RNS vector laid out [B: k][B': k].
+template <class C>
+__device__ __forceinline__ void load_vec(uint32_t (&vb)[C::NPT], uint32_t (&vp)[C::NPT], const uint32_t* v, int t) {
+#pragma unroll
+  for (int s = 0; s < C::NPT; s++) {
+    const int o = t * C::NPT + s;
+    vb[s] = o < C::K ? __ldg(v + o) : 0u;
+    vp[s] = o < C::K ? __ldg(v + C::K + o) : 0u;
+  }
+}
+
+// (a + b) mod m channel-wise on hat residues in [0, m]
+template <class C>
+__device__ __forceinline__ void add_vec(uint32_t (&ab)[C::NPT], uint32_t (&ap)[C::NPT], const uint32_t (&bb)[C::NPT],
+                                        const uint32_t (&bp)[C::NPT], const Smem<C>& sm, int t) {
+#pragma unroll
+  for (int s = 0; s < C::NPT; s++) {
+    const int o = t * C::NPT + s;
+    const uint32_t mb = sm.cb4(o).x, mp = sm.cp4(o).x;
+    uint32_t u = ab[s] + bb[s];
+    ab[s] = min(u, u - mb);
+    uint32_t v = ap[s] + bp[s];
+    ap[s] = min(v, v - mp);
+  }
+}
+
+// a < b for little-endian numbers of na and nb limbs
+__device__ __forceinline__ bool less_than(const uint32_t* a, int na, const uint32_t* b, int nb) {
+  int n = na > nb ? na : nb;
+  for (int i = n - 1; i >= 0; i--) {
+    uint32_t av = i < na ? a[i] : 0u, bv = i < nb ? b[i] : 0u;
+    if (av != bv) return av < bv;
+  }
+  return false;
+}
+
+// RNS (hat residues of a value X < (k+1) N, X < M/4) -> binary X mod N, written
+// to dst[0..dst_limbs) (zero-padded).  CRT: X = sum_i xi_i (M/m_i) - a M with
+// xi_i = |x_i (M/m_i)^-1|_{m_i}; a = floor(sum xi_i/m_i) from the fixed-point
+// sum; then X mod N by a quotient estimate from the top bits and at most a few
+// corrective subtractions.  All lanes of the group must call it; lane 0 of the
+// group does the serial carry work.
+template <class C>
+__device__ void from_rns_reduce(const uint32_t (&xb)[C::NPT], const uint32_t* cls, const uint32_t* key,
+                                const Smem<C>& sm, uint32_t* xib, int t, uint32_t* dst, int dst_limbs, bool write) {
+  constexpr int NPT = C::NPT, K = C::K, WX = C::WX, W = C::W;
+  const ClassOff co = class_offsets(C::K, C::W, C::WX);
+  const KeyOff ko = key_offsets(C::K, C::W);
+  uint32_t kaw = 0;
+#pragma unroll
+  for (int s = 0; s < NPT; s++) {
+    const int o = t * NPT + s;
+    const uint4 cb = sm.cb4(o);
+    const uint2 c2 = sm.cb2(o);
+    uint32_t xi = redc(mulw(xb[s], c2.x), cb.x, cb.y);  // plain, [0, m)
+    if (o < K) xib[o] = xi;
+    kaw += hi32(mulw(xi, c2.y));
+  }
+  __syncwarp();
+  const uint32_t alpha = (group_sum<C::TPI>(kaw) + (1u << (KAW_Q - 2))) >> KAW_Q;
+  if (t == 0) {
+    uint32_t X[WX];
+    const uint32_t* MD = cls + co.MD;
+    const uint32_t* ML = cls + co.ML;
+    uint32_t c0 = 0, c1 = 0;
+    for (int w = 0; w < WX; w++) {
+      uint32_t s0 = c0, s1 = c1, s2 = 0;
+      for (int i = 0; i < K; i++) mac96(s0, s1, s2, xib[i], __ldg(MD + i * WX + w));
+      X[w] = s0;
+      c0 = s1;
+      c1 = s2;
+    }
+    // X -= alpha * M
+    uint32_t carry = 0, br = 0;
+    for (int w = 0; w < WX; w++) {
+      uint64_t pw = mulw(alpha, __ldg(ML + w)) + carry;
+      carry = hi32(pw);
+      uint64_t d = (uint64_t)X[w] - lo32(pw) - br;
+      X[w] = lo32(d);
+      br = hi32(d) ? 1u : 0u;
+    }
+    // X mod N: X < (k+1) N
+    const uint32_t nbits = __ldg(key + ko.hdr);
+    const uint32_t* N = key + ko.N;
+    const int sh = nbits > 32 ? (int)nbits - 32 : 0;
+    auto bits64 = [&](const uint32_t* a, int na, int pos) -> uint64_t {
+      int l = pos >> 5, b = pos & 31;
+      uint64_t v0 = l < na ? a[l] : 0u, v1 = l + 1 < na ? a[l + 1] : 0u, v2 = l + 2 < na ? a[l + 2] : 0u;
+      uint64_t lo = (v0 >> b) | (v1 << (32 - b));
+      if (b == 0) lo = v0 | (v1 << 32);
+      else lo |= (v2 << (64 - b));
+      return lo;
+    };
+    const uint64_t xt = bits64(X, WX, sh);
+    const uint64_t nt = (uint32_t)bits64(N, W, sh);
+    uint64_t qe = xt / (nt + 1);
+    if (qe) {
+      uint32_t cq = 0, b2 = 0;
+      for (int w = 0; w < WX; w++) {
+        uint64_t pw = mulw((uint32_t)qe, w < W ? __ldg(N + w) : 0u) + cq;
+        cq = hi32(pw);
+        uint64_t d = (uint64_t)X[w] - lo32(pw) - b2;
+        X[w] = lo32(d);
+        b2 = hi32(d) ? 1u : 0u;
+      }
+    }
+    for (int it = 0; it < 4; it++) {  // at most 2 are ever needed
+      bool ge = true;
+      for (int w = WX - 1; w >= 0; w--) {
+        uint32_t nv = w < W ? __ldg(N + w) : 0u;
+        if (X[w] != nv) {
+          ge = X[w] > nv;
+          break;
+        }
+      }
+      if (!ge) break;
+      uint32_t b3 = 0;
+      for (int w = 0; w < WX; w++) {
+        uint64_t d = (uint64_t)X[w] - (w < W ? __ldg(N + w) : 0u) - b3;
+        X[w] = lo32(d);
+        b3 = hi32(d) ? 1u : 0u;
+      }
+    }
+    if (write)
+      for (int w = 0; w < dst_limbs; w++) dst[w] = w < WX ? X[w] : 0u;
+  }
+  __syncwarp();
+}
+
+}  // namespace mr

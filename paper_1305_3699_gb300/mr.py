@@ -1,0 +1,296 @@
+"""Thin ctypes binding of libmrmod.so (include/mr.h), same names as the C ABI.
+
+Every function marshals arguments only: big integers become little-endian
+uint32 limb arrays, torch device tensors become raw device pointers, streams
+become cudaStream_t handles.  All arithmetic runs in the library's CUDA
+kernels; there is no CPU fallback -- importing this module fails loudly when
+the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libmrmod.so")
+
+MR_OK = 0
+STATUS_NAMES = {
+    0: "MR_OK", 1: "MR_ERR_ARG", 2: "MR_ERR_EVEN_MODULUS", 3: "MR_ERR_NOT_COPRIME", 4: "MR_ERR_SIZE",
+    5: "MR_ERR_RANGE", 6: "MR_ERR_OOM", 7: "MR_ERR_CUDA", 8: "MR_ERR_TIMEOUT", 9: "MR_ERR_BUSY", 10: "MR_ERR_KEY",
+}
+
+EXPORTED = [
+    "mr_init", "mr_shutdown", "mr_last_error", "mr_class_for_bits", "mr_rns_setup", "mr_rsa_key_setup",
+    "mr_key_info", "mr_key_free", "mr_modexp_batch", "mr_rsa_encrypt", "mr_rsa_decrypt_crt",
+    "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
+]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint32), ("ms", ctypes.c_double)]
+
+
+class MRError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1305_3699_gb300.build` "
+                          "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    U32 = ctypes.c_uint32
+    PU32 = ctypes.POINTER(ctypes.c_uint32)
+    SZ = ctypes.c_size_t
+    sig = {
+        "mr_init": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(P)]),
+        "mr_shutdown": (None, [P]),
+        "mr_last_error": (ctypes.c_char_p, [P]),
+        "mr_class_for_bits": (ctypes.c_int, [U32, PU32, PU32]),
+        "mr_rns_setup": (ctypes.c_int, [P, PU32, U32, ctypes.POINTER(P)]),
+        "mr_rsa_key_setup": (ctypes.c_int, [P, PU32, U32, PU32, U32, PU32, PU32, PU32, PU32, PU32, U32,
+                                            ctypes.POINTER(P)]),
+        "mr_key_info": (ctypes.c_int, [P, PU32, PU32, ctypes.POINTER(ctypes.c_uint64)]),
+        "mr_key_free": (ctypes.c_int, [P, P]),
+        "mr_modexp_batch": (ctypes.c_int, [P, P, SZ, P, U32, P, U32, P, U32, P, P]),
+        "mr_rsa_encrypt": (ctypes.c_int, [P, P, SZ, P, U32, P, U32, P, P]),
+        "mr_rsa_decrypt_crt": (ctypes.c_int, [P, P, SZ, P, U32, P, U32, P, P]),
+        "mr_miller_rabin_batch": (ctypes.c_int, [P, P, U32, SZ, P, U32, P, P, P]),
+        "mr_debug_table": (ctypes.c_int, [P, U32, P, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
+        "mr_debug_key_table_host": (ctypes.c_int, [PU32, U32, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
+        "mr_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
+        "mr_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelTime), U32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _limbs(x: int, n: Optional[int] = None) -> np.ndarray:
+    if x < 0:
+        raise ValueError("negative integer")
+    nl = max(1, (x.bit_length() + 31) // 32) if n is None else n
+    return np.frombuffer(x.to_bytes(4 * nl, "little"), dtype="<u4").astype(np.uint32)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+def _dev(t) -> int:
+    """Device pointer of a torch tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _rows(t) -> tuple:
+    if t.dim() != 2 or t.element_size() != 4:
+        raise ValueError("expected a 2-D tensor of 32-bit limbs (rows x limbs)")
+    return t.shape[0], t.shape[1]
+
+
+def mr_class_for_bits(bits: int):
+    L, k = ctypes.c_uint32(), ctypes.c_uint32()
+    rc = lib.mr_class_for_bits(bits, ctypes.byref(L), ctypes.byref(k))
+    if rc:
+        raise MRError(rc, f"no size class for {bits} bits")
+    return L.value, k.value
+
+
+def mr_debug_key_table_host(N: int, name: str) -> List[int]:
+    nl = _limbs(N)
+    cnt = ctypes.c_size_t()
+    rc = lib.mr_debug_key_table_host(_ptr(nl), len(nl), name.encode(), None, 0, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, f"table {name}")
+    out = np.zeros(cnt.value, dtype=np.uint32)
+    rc = lib.mr_debug_key_table_host(_ptr(nl), len(nl), name.encode(), _ptr(out), cnt.value, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, f"table {name}")
+    return [int(v) for v in out]
+
+
+def mr_debug_class_table(class_bits: int, name: str) -> List[int]:
+    cnt = ctypes.c_size_t()
+    rc = lib.mr_debug_table(None, class_bits, None, name.encode(), None, 0, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, f"table {name}")
+    out = np.zeros(cnt.value, dtype=np.uint32)
+    rc = lib.mr_debug_table(None, class_bits, None, name.encode(), _ptr(out), cnt.value, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, f"table {name}")
+    return [int(v) for v in out]
+
+
+class Key:
+    """A modulus (or RSA key) set up on the device; owned by its Context."""
+
+    def __init__(self, ctx: "Context", handle: int, N: int, e: Optional[int] = None, private: bool = False):
+        self.ctx, self.handle, self.N, self.e, self.private = ctx, handle, N, e, private
+
+    @property
+    def limbs(self) -> int:
+        return max(1, (self.N.bit_length() + 31) // 32)
+
+    def info(self):
+        k, kh, nb = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+        self.ctx._check(lib.mr_key_info(self.handle, ctypes.byref(k), ctypes.byref(kh), ctypes.byref(nb)))
+        return {"k": k.value, "k_half": kh.value, "device_bytes": nb.value}
+
+    def free(self):
+        if self.handle:
+            self.ctx._check(lib.mr_key_free(self.ctx.handle, self.handle))
+            self.handle = None
+
+
+class KeyList:
+    """A reusable host array of key handles for batched calls."""
+
+    def __init__(self, keys: Sequence[Key]):
+        self.keys = list(keys)
+        self.arr = (ctypes.c_void_p * len(self.keys))(*[k.handle for k in self.keys])
+
+    def __len__(self):
+        return len(self.keys)
+
+
+def _keylist(keys) -> KeyList:
+    return keys if isinstance(keys, KeyList) else KeyList(keys)
+
+
+class Context:
+    """mr_init / mr_shutdown around one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        rc = lib.mr_init(device, ctypes.byref(h))
+        if rc:
+            raise MRError(rc, f"mr_init(device={device}) failed")
+        self.handle = h.value
+        self.device = device
+
+    def _check(self, rc: int):
+        if rc:
+            raise MRError(rc, lib.mr_last_error(self.handle).decode(errors="replace"))
+
+    def last_error(self) -> str:
+        return lib.mr_last_error(self.handle).decode(errors="replace")
+
+    def close(self):
+        if self.handle:
+            lib.mr_shutdown(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- setup
+    def mr_rns_setup(self, N: int) -> Key:
+        nl = _limbs(N)
+        h = ctypes.c_void_p()
+        self._check(lib.mr_rns_setup(self.handle, _ptr(nl), len(nl), ctypes.byref(h)))
+        return Key(self, h.value, N)
+
+    def mr_rsa_key_setup(self, N: int, e: int, p: Optional[int] = None, q: Optional[int] = None,
+                         dp: Optional[int] = None, dq: Optional[int] = None, qinv: Optional[int] = None) -> Key:
+        nl, el = _limbs(N), _limbs(e)
+        h = ctypes.c_void_p()
+        if p is None:
+            self._check(lib.mr_rsa_key_setup(self.handle, _ptr(nl), len(nl), _ptr(el), len(el), None, None, None,
+                                             None, None, 0, ctypes.byref(h)))
+            return Key(self, h.value, N, e, False)
+        hl = max(_limbs(v).size for v in (p, q, dp, dq, qinv))
+        parts = [_limbs(v, hl) for v in (p, q, dp, dq, qinv)]
+        self._check(lib.mr_rsa_key_setup(self.handle, _ptr(nl), len(nl), _ptr(el), len(el),
+                                         *[_ptr(a) for a in parts], hl, ctypes.byref(h)))
+        return Key(self, h.value, N, e, True)
+
+    # ---- batched calls (torch tensors: rows x limbs, 32-bit, contiguous, on this device)
+    def mr_modexp_batch(self, keys, x, e, out, status=None, stream=None):
+        kl = _keylist(keys)
+        n, xs = _rows(x)
+        _, es = _rows(e)
+        _, os_ = _rows(out)
+        self._check(lib.mr_modexp_batch(self.handle, kl.arr, len(kl), _dev(x), xs, _dev(e), es, _dev(out), os_,
+                                        _dev(status), _stream(stream)))
+
+    def mr_rsa_encrypt(self, keys, m, c, status=None, stream=None):
+        kl = _keylist(keys)
+        _, ms = _rows(m)
+        _, cs = _rows(c)
+        self._check(lib.mr_rsa_encrypt(self.handle, kl.arr, len(kl), _dev(m), ms, _dev(c), cs, _dev(status),
+                                       _stream(stream)))
+
+    def mr_rsa_decrypt_crt(self, keys, c, m, status=None, stream=None):
+        kl = _keylist(keys)
+        _, cs = _rows(c)
+        _, ms = _rows(m)
+        self._check(lib.mr_rsa_decrypt_crt(self.handle, kl.arr, len(kl), _dev(c), cs, _dev(m), ms, _dev(status),
+                                           _stream(stream)))
+
+    def mr_miller_rabin_batch(self, cand, witness, rounds: int, is_prime, round_mask=None, stream=None):
+        n, nl = _rows(cand)
+        self._check(lib.mr_miller_rabin_batch(self.handle, _dev(cand), nl, n, _dev(witness), rounds, _dev(is_prime),
+                                              _dev(round_mask), _stream(stream)))
+
+    def mr_profile_enable(self, on: bool = True):
+        self._check(lib.mr_profile_enable(self.handle, 1 if on else 0))
+
+    def mr_profile_read(self):
+        """[(launches, ms) for the exponentiation kernels, (launches, ms) for the CRT kernels]"""
+        arr = (KernelTime * 2)()
+        self._check(lib.mr_profile_read(self.handle, arr, 2))
+        return [(arr[i].launches, arr[i].ms) for i in range(2)]
+
+    def mr_debug_table(self, name: str, key: Optional[Key] = None, class_bits: int = 0) -> List[int]:
+        cnt = ctypes.c_size_t()
+        kh = key.handle if key else None
+        self._check(lib.mr_debug_table(self.handle, class_bits, kh, name.encode(), None, 0, ctypes.byref(cnt)))
+        out = np.zeros(cnt.value, dtype=np.uint32)
+        self._check(lib.mr_debug_table(self.handle, class_bits, kh, name.encode(), _ptr(out), cnt.value,
+                                       ctypes.byref(cnt)))
+        return [int(v) for v in out]
+
+
+def to_tensor(values: Iterable[int], n_limbs: int, device="cuda"):
+    """Pack Python ints into a (rows x n_limbs) int32 tensor of little-endian limbs."""
+    import torch
+    vals = list(values)
+    arr = np.zeros((len(vals), n_limbs), dtype=np.uint32)
+    for i, v in enumerate(vals):
+        arr[i] = _limbs(v, n_limbs)
+    return torch.from_numpy(arr.view(np.int32)).to(device)
+
+
+def from_tensor(t) -> List[int]:
+    """Unpack a (rows x limbs) 32-bit tensor into Python ints."""
+    a = t.detach().cpu().contiguous().numpy().view(np.uint32)
+    return [int.from_bytes(row.astype("<u4").tobytes(), "little") for row in a]

@@ -1,0 +1,97 @@
+"""The C-ABI library loads, exports every declared symbol, and its host-side
+setup (base choice and every precomputed table) equals the oracle's RNS model
+value by value.  No GPU needed: nothing here launches device work."""
+import os
+import re
+
+import pytest
+
+from oracle import rns
+from synth import SplitMix64, load_keys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mr.h")
+
+mr = pytest.importorskip("paper_1305_3699_gb300.mr", reason="libmrmod.so not built")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mr_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol():
+    syms = declared_symbols()
+    assert len(syms) >= 14
+    for s in syms:
+        assert hasattr(mr.lib, s), s
+    assert sorted(mr.EXPORTED) == syms
+
+
+CLASSES = [512, 1024, 1536, 2048, 3072, 4096]
+
+
+@pytest.mark.parametrize("L", CLASSES)
+def test_class_tables_match_model(L):
+    c = rns.make_class(L)
+    Lc, k = mr.mr_class_for_bits(L)
+    assert (Lc, k) == (L, c.k)
+    assert mr.mr_debug_class_table(L, "B") == c.B
+    assert mr.mr_debug_class_table(L, "Bp") == c.Bp
+    b = mr.mr_debug_class_table(L, "bound")
+    assert b[0] | (b[1] << 32) == c.bound
+    m_limbs = mr.mr_debug_class_table(L, "M")
+    assert int.from_bytes(b"".join(v.to_bytes(4, "little") for v in m_limbs), "little") == c.M
+    for name in ("M_mi_inv", "Minv_Bp", "Mp_mj_inv", "Mp_B"):
+        assert mr.mr_debug_class_table(L, name) == c.t[name], name
+    for name in ("M_mi_Bp", "Mp_mj_B"):
+        flat = [v for row in c.t[name] for v in row]
+        assert mr.mr_debug_class_table(L, name) == flat, name
+
+
+def test_class_for_bits_boundaries():
+    assert mr.mr_class_for_bits(1)[0] == 512
+    assert mr.mr_class_for_bits(512)[0] == 512
+    assert mr.mr_class_for_bits(513)[0] == 1024
+    assert mr.mr_class_for_bits(4096)[0] == 4096
+    with pytest.raises(mr.MRError):
+        mr.mr_class_for_bits(4097)
+
+
+def _key_cases():
+    r = SplitMix64(1234)
+    out = []
+    for bits in (3, 64, 511, 512, 700, 1024, 1536, 2048, 3000, 4096):
+        N = r.randbits(bits) | 1 | (1 << (bits - 1))
+        out.append(N)
+    out += [k["p"] for k in load_keys("rsa2048_x16")[:2]] + [k["N"] for k in load_keys("rsa1024_x64")[:2]]
+    return out
+
+
+@pytest.mark.parametrize("N", _key_cases())
+def test_key_tables_match_model(N):
+    L, _ = mr.mr_class_for_bits(N.bit_length())
+    c = rns.make_class(L)
+    key = rns.make_key(c, N)
+    assert mr.mr_debug_key_table_host(N, "kxi") == key.t["kxi"]
+    assert mr.mr_debug_key_table_host(N, "NMinv_Bp") == key.t["NMinv_Bp"]
+    for name in ("one", "r2", "r2h"):
+        v = key.t[name]
+        assert mr.mr_debug_key_table_host(N, name) == v.b + v.bp, name
+
+
+def test_key_setup_errors():
+    with pytest.raises(mr.MRError) as e:
+        mr.mr_debug_key_table_host(1 << 100, "kxi")
+    assert e.value.code == 2  # MR_ERR_EVEN_MODULUS
+    with pytest.raises(mr.MRError) as e:
+        mr.mr_debug_key_table_host((1 << 5000) + 1, "kxi")
+    assert e.value.code == 4  # MR_ERR_SIZE
+    c = rns.make_class(512)
+    with pytest.raises(mr.MRError) as e:
+        mr.mr_debug_key_table_host(c.B[3] * 1000003, "kxi")
+    assert e.value.code == 3  # MR_ERR_NOT_COPRIME
+    with pytest.raises(mr.MRError) as e:
+        mr.mr_debug_key_table_host(12345679, "no_such_table")
+    assert e.value.code == 1
