@@ -154,6 +154,29 @@ mr_status mr_miller_rabin_batch(mr_ctx *ctx, const uint32_t *cand, uint32_t n_li
                                 const uint32_t *witness, uint32_t rounds, uint8_t *dev_is_probable_prime,
                                 uint32_t *dev_round_mask, void *stream);
 
+/* Allocation-free exponentiation: out[i] = x[i]^e[i] mod N for i < n, one
+ * modulus per call.  The paper has no counterpart; this entry point exists for
+ * callers that cannot allocate device memory when they call it -- an engine that
+ * has reserved all GPU memory for its own pool, or a latency-bound loop that must
+ * not enter the CUDA allocator (which may synchronise the device or grow a pool).
+ * It calls no cudaMalloc, cudaFree or other allocating routine and uploads no
+ * work list: the caller passes inputs and outputs, and the kernel's only scratch
+ * (its window tables) lives in a static device array of 16 MiB that every GPU
+ * using the library keeps until the process exits.
+ *   key     modulus of at most 2048 bits (else MR_ERR_SIZE)
+ *   x, e, out, dev_status   as mr_modexp_batch (device rows), n items
+ * A batch whose window tables exceed the 16 MiB array is refused with
+ * MR_ERR_SIZE (about 1,700 items of a 1024-bit modulus with a long exponent);
+ * split it.  The first call on a device looks up the array's device address;
+ * make that first call before any stream capture.  All calls share the array
+ * (it keeps the previous call's contents, which no call reads before writing),
+ * so calls that overlap on the GPU -- on different streams, or from different
+ * host threads -- race and must be serialised by the caller.
+ * Errors: MR_ERR_ARG, MR_ERR_SIZE, MR_ERR_CUDA. */
+mr_status mr_modexp_batch_noalloc(mr_ctx *ctx, const mr_key *key, size_t n, const uint32_t *x, uint32_t x_stride,
+                                  const uint32_t *e, uint32_t e_stride, uint32_t *out, uint32_t out_stride,
+                                  uint8_t *dev_status, void *stream);
+
 /* --------------------------------------------------------- instrumentation -- */
 
 /* Per-kernel timing.  While enabled, every batched call records a pair of CUDA

@@ -13,6 +13,7 @@
 
 #include "../../include/mr.h"
 #include "kernels_api.h"
+#include "noalloc.h"
 #include "setup.h"
 
 using namespace mr;
@@ -668,6 +669,36 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
   (void)dev_round_mask;
   (void)stream;
   return fail(ctx, MR_ERR_ARG, "mr_miller_rabin_batch: not built yet");
+}
+
+mr_status mr_modexp_batch_noalloc(mr_ctx* ctx, const mr_key* key, size_t n, const uint32_t* x, uint32_t x_stride,
+                                  const uint32_t* e, uint32_t e_stride, uint32_t* out, uint32_t out_stride,
+                                  uint8_t* dev_status, void* stream) {
+  if (!ctx) return MR_ERR_ARG;
+  if (n == 0) return MR_OK;
+  if (!key || key->ctx != ctx || !x || !e || !out || !x_stride || !e_stride || !out_stride)
+    return fail(ctx, MR_ERR_ARG, "null argument, zero stride or foreign key");
+  if (n > 0xffffffffull) return fail(ctx, MR_ERR_ARG, "batch too large");
+  if (out_stride < key->pub.nlimbs()) return fail(ctx, MR_ERR_ARG, "out_stride smaller than the modulus");
+  cudaSetDevice(ctx->device);
+  NoallocCall c{};
+  c.device = ctx->device;
+  c.class_bits = key->pub.cls->host.L;
+  c.cls = key->pub.cls->dev;
+  c.key = key->pub.dev;
+  c.x = x;
+  c.e = e;
+  c.out = out;
+  c.status = dev_status;
+  c.n = (uint32_t)n;
+  c.x_stride = x_stride;
+  c.e_stride = e_stride;
+  c.out_stride = out_stride;
+  c.wbits = choose_window(32 * e_stride, 0);
+  c.stream = (cudaStream_t)stream;
+  std::string err;
+  int rc = noalloc_modexp(c, err);
+  return rc ? fail(ctx, (mr_status)rc, err) : MR_OK;
 }
 
 mr_status mr_profile_enable(mr_ctx* ctx, int on) {

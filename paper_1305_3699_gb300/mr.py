@@ -27,6 +27,7 @@ EXPORTED = [
     "mr_init", "mr_shutdown", "mr_last_error", "mr_class_for_bits", "mr_rns_setup", "mr_rsa_key_setup",
     "mr_key_info", "mr_key_free", "mr_modexp_batch", "mr_rsa_encrypt", "mr_rsa_decrypt_crt",
     "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
+    "mr_modexp_batch_noalloc",
 ]
 
 
@@ -66,6 +67,7 @@ def _load() -> ctypes.CDLL:
         "mr_debug_table": (ctypes.c_int, [P, U32, P, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_debug_key_table_host": (ctypes.c_int, [PU32, U32, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
+        "mr_modexp_batch_noalloc": (ctypes.c_int, [P, P, SZ, P, U32, P, U32, P, U32, P, P]),
         "mr_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelTime), U32]),
     }
     for name, (res, args) in sig.items():
@@ -241,6 +243,14 @@ class Context:
         _, os_ = _rows(out)
         self._check(lib.mr_modexp_batch(self.handle, kl.arr, len(kl), _dev(x), xs, _dev(e), es, _dev(out), os_,
                                         _dev(status), _stream(stream)))
+
+    def mr_modexp_batch_noalloc(self, key: Key, x, e, out, status=None, stream=None):
+        """Allocation-free exponentiation for one modulus (see mr_modexp_batch_noalloc in mr.h)."""
+        n, xs = _rows(x)
+        _, es = _rows(e)
+        _, os_ = _rows(out)
+        self._check(lib.mr_modexp_batch_noalloc(self.handle, key.handle, n, _dev(x), xs, _dev(e), es, _dev(out), os_,
+                                                _dev(status), _stream(stream)))
 
     def mr_rsa_encrypt(self, keys, m, c, status=None, stream=None):
         kl = _keylist(keys)
