@@ -139,14 +139,21 @@ mr_status mr_rsa_decrypt_crt(mr_ctx *ctx, const mr_key *const *keys, size_t n, c
                              void *stream);
 
 /* Miller-Rabin rounds (Sec. 3.2: Montgomery-domain primality test with a
- * caller-chosen number of iterations) on n odd candidates of one length.
- *   cand       device, n rows of n_limbs limbs (odd, >= 5, top limb non-zero
- *              not required)
+ * caller-chosen number of iterations) on n candidates of one length.  For an
+ * odd candidate N >= 3 and witness a, round r passes when, with N - 1 = 2^s d
+ * (d odd) and y = (a mod N)^d mod N, y = 1, or y^(2^i) = N - 1 for some i < s.
+ *   cand       device, n rows of n_limbs limbs (n_limbs * 32 <= 4096)
  *   witness    device, n*rounds rows of n_limbs limbs; row i*rounds+r is the
- *              witness of round r for candidate i (meant to lie in [2, n-2])
+ *              witness of round r for candidate i (meant to lie in [2, N-2];
+ *              any value is accepted and reduced mod N)
+ *   rounds     >= 1
  *   dev_is_probable_prime  device, n bytes: 1 when every round passed, else 0
  *   dev_round_mask  device, n uint32 words or NULL: bit r set when round r
  *              passed (rounds <= 32 when given)
+ * Candidates 0 and 1 and even candidates other than 2 are composite (mask 0);
+ * 2 is prime (all bits set).  A candidate above 2^31 that is divisible by one of
+ * the size class's channel primes is reported composite with mask 0 (it has
+ * that prime as a factor; the per-witness verdicts are not evaluated for it).
  * Per-candidate constants (RNS form of the candidate, Montgomery constants)
  * are derived on the device; no candidate leaves the GPU.
  * Errors: MR_ERR_ARG, MR_ERR_SIZE, MR_ERR_OOM, MR_ERR_CUDA. */
@@ -176,6 +183,17 @@ mr_status mr_miller_rabin_batch(mr_ctx *ctx, const uint32_t *cand, uint32_t n_li
 mr_status mr_modexp_batch_noalloc(mr_ctx *ctx, const mr_key *key, size_t n, const uint32_t *x, uint32_t x_stride,
                                   const uint32_t *e, uint32_t e_stride, uint32_t *out, uint32_t out_stride,
                                   uint8_t *dev_status, void *stream);
+
+/* Lane mappings compiled for a size class, for autotuning.  Each class is
+ * compiled for one or more numbers of GPU lanes per number; *count receives
+ * how many, lanes_per_number[0..min(count, capacity)) their lane counts (may
+ * be NULL).  Errors: MR_ERR_SIZE (no such class). */
+mr_status mr_class_variants(uint32_t class_bits, uint32_t *count, uint32_t *lanes_per_number, uint32_t capacity);
+
+/* Select the lane mapping later calls on this context use for a size class
+ * (variant < count of mr_class_variants; variant 0 is the default).  Results do
+ * not depend on the choice, only speed does.  Errors: MR_ERR_ARG, MR_ERR_SIZE. */
+mr_status mr_set_variant(mr_ctx *ctx, uint32_t class_bits, uint32_t variant);
 
 /* --------------------------------------------------------- instrumentation -- */
 

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -24,6 +25,8 @@ struct ClassEntry {
   ClassHost host;
   uint32_t* dev = nullptr;
   const ClassKernels* kern = nullptr;
+  uint32_t variant = 0;  // selected lane mapping
+  const KernelVariant& kv() const { return kern->var[variant]; }
 };
 
 struct KeyEntry {
@@ -111,6 +114,15 @@ mr_status get_class(mr_ctx* ctx, uint32_t L, ClassEntry** out) {
   if (!ce->kern) return fail(ctx, MR_ERR_SIZE, "no kernel compiled for class " + std::to_string(L));
   if (ce->kern->k != ce->host.k || ce->kern->W != ce->host.W || ce->kern->WX != ce->host.WX)
     return fail(ctx, MR_ERR_SIZE, "compiled kernel does not match the bases of class " + std::to_string(L));
+  {
+    // default lane mapping: variant 0, unless MR_VARIANT_<L> names another compiled one
+    std::string ev = "MR_VARIANT_" + std::to_string(L);
+    const char* v = getenv(ev.c_str());
+    if (v) {
+      unsigned idx = (unsigned)atoi(v);
+      if (idx < ce->kern->n_variants) ce->variant = idx;
+    }
+  }
   size_t bytes = ce->host.block.size() * 4;
   cudaError_t e = cudaMalloc(&ce->dev, bytes);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(class)");
@@ -241,7 +253,7 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
   }
   size_t total = upload_bytes;
   for (auto& b : batches) {
-    b.scratch_words = b.mx.empty() ? 0 : modexp_scratch_words(*b.ce->kern, (uint32_t)b.mx.size(), b.wbits);
+    b.scratch_words = b.mx.empty() ? 0 : modexp_scratch_words(b.ce->kv(), (uint32_t)b.mx.size(), b.wbits);
     b.off_scratch = total;
     total = align256(total + b.scratch_words * 4);
   }
@@ -286,7 +298,7 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
     return cuda_fail(ctx, e, "item upload");
   }
   for (auto& b : batches) {
-    const ClassKernels& k = *b.ce->kern;
+    const KernelVariant& k = b.ce->kv();
     if (!b.mx.empty()) {
       LaunchArgs a{b.ce->dev, base + b.off_mx, (uint32_t)b.mx.size(), b.wbits,
                    reinterpret_cast<uint32_t*>(base + b.off_scratch), status};
@@ -660,15 +672,37 @@ mr_status mr_rsa_decrypt_crt(mr_ctx* ctx, const mr_key* const* keys, size_t n, c
 mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs, size_t n, const uint32_t* witness,
                                 uint32_t rounds, uint8_t* dev_is_probable_prime, uint32_t* dev_round_mask,
                                 void* stream) {
-  (void)cand;
-  (void)n_limbs;
-  (void)n;
-  (void)witness;
-  (void)rounds;
-  (void)dev_is_probable_prime;
-  (void)dev_round_mask;
-  (void)stream;
-  return fail(ctx, MR_ERR_ARG, "mr_miller_rabin_batch: not built yet");
+  if (!ctx) return MR_ERR_ARG;
+  if (n == 0) return MR_OK;
+  if (!cand || !n_limbs || !witness || !rounds || !dev_is_probable_prime)
+    return fail(ctx, MR_ERR_ARG, "null argument, zero limbs or zero rounds");
+  if (dev_round_mask && rounds > 32) return fail(ctx, MR_ERR_ARG, "round mask holds at most 32 rounds");
+  if (n > 0xffffffffull) return fail(ctx, MR_ERR_ARG, "batch too large");
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    uint32_t L = class_for_bits(32 * n_limbs);
+    if (!L) return fail(ctx, MR_ERR_SIZE, "candidates longer than the largest size class");
+    ClassEntry* ce = nullptr;
+    mr_status s = get_class(ctx, L, &ce);
+    if (s) return s;
+    const KernelVariant& k = ce->kv();
+    const uint32_t wbits = choose_window(32 * n_limbs, 0);
+    const size_t tab_words = modexp_scratch_words(k, (uint32_t)n, wbits);
+    const size_t crow_words = n * 3 * (size_t)ce->host.W;
+    const size_t off_crow = align256(tab_words * 4);
+    void* dev = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&dev, off_crow + crow_words * 4, ctx->pool, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, std::string("scratch allocation failed: ") + cudaGetErrorString(e));
+    char* base = static_cast<char*>(dev);
+    MRArgs a{ce->dev, cand, witness, dev_is_probable_prime, dev_round_mask, reinterpret_cast<uint32_t*>(base),
+             reinterpret_cast<uint32_t*>(base + off_crow), (uint32_t)n, n_limbs, rounds, wbits};
+    unsigned grid = (unsigned)((n + k.ipb - 1) / k.ipb);
+    e = timed_launch(ctx, 0, (cudaStream_t)stream, [&] { return k.mr(a, grid, (cudaStream_t)stream); });
+    cudaError_t e2 = cudaFreeAsync(dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");
+    return MR_OK;
+  });
 }
 
 mr_status mr_modexp_batch_noalloc(mr_ctx* ctx, const mr_key* key, size_t n, const uint32_t* x, uint32_t x_stride,
@@ -728,6 +762,28 @@ mr_status mr_profile_read(mr_ctx* ctx, mr_kernel_time* times, uint32_t n_kinds) 
   }
   ctx->launches[0] = ctx->launches[1] = 0;
   return err == cudaSuccess ? MR_OK : cuda_fail(ctx, err, "profile events");
+}
+
+mr_status mr_class_variants(uint32_t class_bits, uint32_t* count, uint32_t* lanes_per_number, uint32_t capacity) {
+  const ClassKernels* k = class_kernels(class_bits);
+  if (!k) return MR_ERR_SIZE;
+  if (count) *count = k->n_variants;
+  if (lanes_per_number)
+    for (uint32_t i = 0; i < k->n_variants && i < capacity; i++) lanes_per_number[i] = k->var[i].tpi;
+  return MR_OK;
+}
+
+mr_status mr_set_variant(mr_ctx* ctx, uint32_t class_bits, uint32_t variant) {
+  if (!ctx) return MR_ERR_ARG;
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    ClassEntry* ce = nullptr;
+    mr_status s = get_class(ctx, class_bits, &ce);
+    if (s) return s;
+    if (variant >= ce->kern->n_variants) return fail(ctx, MR_ERR_ARG, "no such variant");
+    ce->variant = variant;
+    return MR_OK;
+  });
 }
 
 static mr_status copy_table(const std::vector<uint32_t>& v, uint32_t* out, size_t cap, size_t* count) {

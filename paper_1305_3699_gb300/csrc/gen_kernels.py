@@ -1,0 +1,66 @@
+"""Write the per-size-class translation units kern_<L>.cu and registry.cu.
+
+    python paper_1305_3699_gb300/csrc/gen_kernels.py
+
+Each size class L (bits) has k channels per base (fixed by the base rule in
+setup.cpp), W = L/32 limbs and WX limbs for k*M; every class compiles one or
+more lane mappings ("variants": lanes per number TPI, threads per block,
+shared-memory vector width).  Variant 0 is the default; others are selected at
+run time (mr_set_variant) after measurement.
+"""
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# L: (k, W, WX, [(TPI, THREADS, VEC), ...])
+CLASSES = {
+    512: (18, 16, 17, [(2, 128, 4), (4, 128, 4)]),
+    1024: (36, 32, 34, [(4, 128, 4), (8, 128, 4)]),
+    1536: (54, 48, 50, [(8, 128, 4)]),
+    2048: (72, 64, 66, [(8, 128, 4), (16, 128, 4)]),
+    3072: (108, 96, 97, [(16, 256, 4)]),
+    4096: (145, 128, 129, [(16, 384, 2)]),
+}
+
+
+def unit(L, k, W, WX, variants):
+    out = [f"// Kernels of the {L}-bit size class (k = {k} channels per base). Generated by gen_kernels.py.",
+           '#include "kernels.cuh"', '#include "kernels_api.h"', '#include "mr_kernel.cuh"', "", "namespace mr {", ""]
+    entries = []
+    for v, (tpi, th, vec) in enumerate(variants):
+        C = f"C{L}v{v}"
+        out.append(f"using {C} = Cfg<{k}, {W}, {WX}, {tpi}, {th}, {vec}>;")
+        for kind, kern, argt in (("modexp", "modexp_kernel", "LaunchArgs"), ("crt", "crt_kernel", "LaunchArgs"),
+                                 ("mr", "mr_kernel", "MRArgs")):
+            out += [f"static cudaError_t launch_{kind}_{L}_{v}(const {argt}& a, unsigned grid, cudaStream_t s) {{",
+                    f"  static const cudaError_t attr =",
+                    f"      cudaFuncSetAttribute({kern}<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES);",
+                    "  if (attr != cudaSuccess) return attr;",
+                    f"  {kern}<{C}><<<grid, {C}::THREADS, {C}::SMEM_BYTES, s>>>(a);",
+                    "  return cudaGetLastError();", "}", ""]
+        entries.append(f"     {{{C}::TPI, {C}::THREADS, {C}::IPB, {C}::NPT, {C}::SMEM_BYTES, launch_modexp_{L}_{v}, "
+                       f"launch_crt_{L}_{v}, launch_mr_{L}_{v}}}")
+    out.append(f"extern const ClassKernels kClass{L} = {{")
+    out.append(f"    {L}, {k}, {W}, {WX}, {len(variants)},")
+    out.append("    {\n" + ",\n".join(entries) + "}};")
+    out += ["", "}  // namespace mr", ""]
+    return "\n".join(out)
+
+
+def main():
+    for L, (k, W, WX, vs) in CLASSES.items():
+        with open(os.path.join(HERE, f"kern_{L}.cu"), "w") as f:
+            f.write(unit(L, k, W, WX, vs))
+    reg = ["// Registry of the compiled size classes. Generated by gen_kernels.py.", '#include "kernels_api.h"', "",
+           "namespace mr {", ""]
+    reg += [f"extern const ClassKernels kClass{L};" for L in CLASSES]
+    reg += ["", "const ClassKernels* class_kernels(uint32_t L) {", "  switch (L) {"]
+    for L in CLASSES:
+        reg += [f"    case {L}:", f"      return &kClass{L};"]
+    reg += ["    default:", "      return nullptr;", "  }", "}", "", "}  // namespace mr", ""]
+    with open(os.path.join(HERE, "registry.cu"), "w") as f:
+        f.write("\n".join(reg))
+
+
+if __name__ == "__main__":
+    main()

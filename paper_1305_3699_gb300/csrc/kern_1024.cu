@@ -1,29 +1,64 @@
-// Kernels of the 1024-bit size class (k = 36 channels per base).
+// Kernels of the 1024-bit size class (k = 36 channels per base). Generated by gen_kernels.py.
 #include "kernels.cuh"
 #include "kernels_api.h"
+#include "mr_kernel.cuh"
 
 namespace mr {
 
-using C1024 = Cfg<36, 32, 34, 4, 128, 4>;
-
-static cudaError_t launch_modexp_1024(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+using C1024v0 = Cfg<36, 32, 34, 4, 128, 4>;
+static cudaError_t launch_modexp_1024_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   static const cudaError_t attr =
-      cudaFuncSetAttribute(modexp_kernel<C1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024::SMEM_BYTES);
+      cudaFuncSetAttribute(modexp_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
-  modexp_kernel<C1024><<<grid, C1024::THREADS, C1024::SMEM_BYTES, s>>>(a);
+  modexp_kernel<C1024v0><<<grid, C1024v0::THREADS, C1024v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
-static cudaError_t launch_crt_1024(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+static cudaError_t launch_crt_1024_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   static const cudaError_t attr =
-      cudaFuncSetAttribute(crt_kernel<C1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024::SMEM_BYTES);
+      cudaFuncSetAttribute(crt_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
-  crt_kernel<C1024><<<grid, C1024::THREADS, C1024::SMEM_BYTES, s>>>(a);
+  crt_kernel<C1024v0><<<grid, C1024v0::THREADS, C1024v0::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mr_1024_0(const MRArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(mr_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  mr_kernel<C1024v0><<<grid, C1024v0::THREADS, C1024v0::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+using C1024v1 = Cfg<36, 32, 34, 8, 128, 4>;
+static cudaError_t launch_modexp_1024_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(modexp_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  modexp_kernel<C1024v1><<<grid, C1024v1::THREADS, C1024v1::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_crt_1024_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(crt_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  crt_kernel<C1024v1><<<grid, C1024v1::THREADS, C1024v1::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mr_1024_1(const MRArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(mr_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  mr_kernel<C1024v1><<<grid, C1024v1::THREADS, C1024v1::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 extern const ClassKernels kClass1024 = {
-    1024, C1024::K, C1024::W, C1024::WX, C1024::TPI, C1024::THREADS, C1024::IPB, C1024::NPT, C1024::SMEM_BYTES,
-    launch_modexp_1024, launch_crt_1024};
+    1024, 36, 32, 34, 2,
+    {
+     {C1024v0::TPI, C1024v0::THREADS, C1024v0::IPB, C1024v0::NPT, C1024v0::SMEM_BYTES, launch_modexp_1024_0, launch_crt_1024_0, launch_mr_1024_0},
+     {C1024v1::TPI, C1024v1::THREADS, C1024v1::IPB, C1024v1::NPT, C1024v1::SMEM_BYTES, launch_modexp_1024_1, launch_crt_1024_1, launch_mr_1024_1}}};
 
 }  // namespace mr

@@ -1,29 +1,64 @@
-// Kernels of the 2048-bit size class (k = 72 channels per base).
+// Kernels of the 2048-bit size class (k = 72 channels per base). Generated by gen_kernels.py.
 #include "kernels.cuh"
 #include "kernels_api.h"
+#include "mr_kernel.cuh"
 
 namespace mr {
 
-using C2048 = Cfg<72, 64, 66, 8, 128, 4>;
-
-static cudaError_t launch_modexp_2048(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+using C2048v0 = Cfg<72, 64, 66, 8, 128, 4>;
+static cudaError_t launch_modexp_2048_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   static const cudaError_t attr =
-      cudaFuncSetAttribute(modexp_kernel<C2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, C2048::SMEM_BYTES);
+      cudaFuncSetAttribute(modexp_kernel<C2048v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C2048v0::SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
-  modexp_kernel<C2048><<<grid, C2048::THREADS, C2048::SMEM_BYTES, s>>>(a);
+  modexp_kernel<C2048v0><<<grid, C2048v0::THREADS, C2048v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
-static cudaError_t launch_crt_2048(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+static cudaError_t launch_crt_2048_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   static const cudaError_t attr =
-      cudaFuncSetAttribute(crt_kernel<C2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, C2048::SMEM_BYTES);
+      cudaFuncSetAttribute(crt_kernel<C2048v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C2048v0::SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
-  crt_kernel<C2048><<<grid, C2048::THREADS, C2048::SMEM_BYTES, s>>>(a);
+  crt_kernel<C2048v0><<<grid, C2048v0::THREADS, C2048v0::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mr_2048_0(const MRArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(mr_kernel<C2048v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C2048v0::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  mr_kernel<C2048v0><<<grid, C2048v0::THREADS, C2048v0::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+using C2048v1 = Cfg<72, 64, 66, 16, 128, 4>;
+static cudaError_t launch_modexp_2048_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(modexp_kernel<C2048v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C2048v1::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  modexp_kernel<C2048v1><<<grid, C2048v1::THREADS, C2048v1::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_crt_2048_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(crt_kernel<C2048v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C2048v1::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  crt_kernel<C2048v1><<<grid, C2048v1::THREADS, C2048v1::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mr_2048_1(const MRArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(mr_kernel<C2048v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C2048v1::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  mr_kernel<C2048v1><<<grid, C2048v1::THREADS, C2048v1::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 extern const ClassKernels kClass2048 = {
-    2048, C2048::K, C2048::W, C2048::WX, C2048::TPI, C2048::THREADS, C2048::IPB, C2048::NPT, C2048::SMEM_BYTES,
-    launch_modexp_2048, launch_crt_2048};
+    2048, 72, 64, 66, 2,
+    {
+     {C2048v0::TPI, C2048v0::THREADS, C2048v0::IPB, C2048v0::NPT, C2048v0::SMEM_BYTES, launch_modexp_2048_0, launch_crt_2048_0, launch_mr_2048_0},
+     {C2048v1::TPI, C2048v1::THREADS, C2048v1::IPB, C2048v1::NPT, C2048v1::SMEM_BYTES, launch_modexp_2048_1, launch_crt_2048_1, launch_mr_2048_1}}};
 
 }  // namespace mr

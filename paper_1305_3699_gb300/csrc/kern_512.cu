@@ -1,29 +1,64 @@
-// Kernels of the 512-bit size class (k = 18 channels per base).
+// Kernels of the 512-bit size class (k = 18 channels per base). Generated by gen_kernels.py.
 #include "kernels.cuh"
 #include "kernels_api.h"
+#include "mr_kernel.cuh"
 
 namespace mr {
 
-using C512 = Cfg<18, 16, 17, 2, 128, 4>;
-
-static cudaError_t launch_modexp_512(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+using C512v0 = Cfg<18, 16, 17, 2, 128, 4>;
+static cudaError_t launch_modexp_512_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   static const cudaError_t attr =
-      cudaFuncSetAttribute(modexp_kernel<C512>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512::SMEM_BYTES);
+      cudaFuncSetAttribute(modexp_kernel<C512v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v0::SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
-  modexp_kernel<C512><<<grid, C512::THREADS, C512::SMEM_BYTES, s>>>(a);
+  modexp_kernel<C512v0><<<grid, C512v0::THREADS, C512v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
-static cudaError_t launch_crt_512(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+static cudaError_t launch_crt_512_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   static const cudaError_t attr =
-      cudaFuncSetAttribute(crt_kernel<C512>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512::SMEM_BYTES);
+      cudaFuncSetAttribute(crt_kernel<C512v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v0::SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
-  crt_kernel<C512><<<grid, C512::THREADS, C512::SMEM_BYTES, s>>>(a);
+  crt_kernel<C512v0><<<grid, C512v0::THREADS, C512v0::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mr_512_0(const MRArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(mr_kernel<C512v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v0::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  mr_kernel<C512v0><<<grid, C512v0::THREADS, C512v0::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+using C512v1 = Cfg<18, 16, 17, 4, 128, 4>;
+static cudaError_t launch_modexp_512_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(modexp_kernel<C512v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v1::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  modexp_kernel<C512v1><<<grid, C512v1::THREADS, C512v1::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_crt_512_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(crt_kernel<C512v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v1::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  crt_kernel<C512v1><<<grid, C512v1::THREADS, C512v1::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mr_512_1(const MRArgs& a, unsigned grid, cudaStream_t s) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(mr_kernel<C512v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v1::SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  mr_kernel<C512v1><<<grid, C512v1::THREADS, C512v1::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 extern const ClassKernels kClass512 = {
-    512, C512::K, C512::W, C512::WX, C512::TPI, C512::THREADS, C512::IPB, C512::NPT, C512::SMEM_BYTES,
-    launch_modexp_512, launch_crt_512};
+    512, 18, 16, 17, 2,
+    {
+     {C512v0::TPI, C512v0::THREADS, C512v0::IPB, C512v0::NPT, C512v0::SMEM_BYTES, launch_modexp_512_0, launch_crt_512_0, launch_mr_512_0},
+     {C512v1::TPI, C512v1::THREADS, C512v1::IPB, C512v1::NPT, C512v1::SMEM_BYTES, launch_modexp_512_1, launch_crt_512_1, launch_mr_512_1}}};
 
 }  // namespace mr

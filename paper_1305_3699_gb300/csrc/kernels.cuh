@@ -75,12 +75,13 @@ __global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
   if (t == 0) bad = less_than(it.x, it.x_limbs, it.xlim, it.xlim_limbs) ? 0u : 1u;
   bad = __shfl_sync(0xffffffffu, bad, lane - t);
 
-  uint32_t kxi[NPT], cmul[NPT];
+  uint32_t kxi[NPT], cmul[NPT], cd[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
     kxi[s] = o < C::K ? __ldg(key + ko.kxi + o) : 0u;
     cmul[s] = o < C::K ? __ldg(key + ko.cmul + o) : 0u;
+    cd[s] = o < C::K ? __ldg(key + ko.cd + o) : 0u;
   }
 
   // entry into the Montgomery domain: x~ = MM(x_lo, M^2 mod N) [+ MM(x_hi, 2^L M^2 mod N)]
@@ -88,14 +89,14 @@ __global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
   const int nl0 = bad ? 0 : (int)(it.x_limbs < (uint32_t)C::W ? it.x_limbs : C::W);
   to_rns<C>(xb, xp, it.x, nl0, a.cls, sm, t);
   load_vec<C>(yb, yp, key + ko.r2, t);
-  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
   const bool two = !bad && it.x_limbs > (uint32_t)C::W;
   if (__any_sync(0xffffffffu, two)) {
     uint32_t hb[NPT], hp[NPT];
     const int nl1 = two ? min((int)it.x_limbs - C::W, C::W) : 0;
     to_rns<C>(hb, hp, it.x + C::W, nl1, a.cls, sm, t);
     load_vec<C>(yb, yp, key + ko.r2h, t);
-    mont_mul<C>(hb, hp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+    mont_mul<C>(hb, hp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
     add_vec<C>(xb, xp, hb, hp, sm, t);
   }
 
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
       cp[s] = xp[s];
     }
     for (int j = 2; j < E; j++) {
-      mont_mul<C>(cb, cp, xb, xp, kxi, cmul, sm, xib, xpb, t);
+      mont_mul<C>(cb, cp, xb, xp, kxi, cmul, cd, sm, xib, xpb, t);
       tab_store<C>(wt, j, cb, cp, lane);
     }
   }
@@ -126,12 +127,30 @@ __global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
   uint32_t d = (nwin && !bad) ? exp_digit(it.e, el, (nwin - 1) * wb, wb) : 0u;
   __syncwarp();
   tab_load<C>(wt, d, xb, xp, lane);
-  for (int widx = (int)nwin - 2; widx >= 0; widx--) {
-    for (int q = 0; q < wb; q++) mont_mul<C>(xb, xp, xb, xp, kxi, cmul, sm, xib, xpb, t);
-    d = bad ? 0u : exp_digit(it.e, el, (uint32_t)widx * wb, wb);
-    if (__any_sync(0xffffffffu, d != 0)) {
-      tab_load<C>(wt, d, yb, yp, lane);
-      mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  // one multiplication call site for the whole loop: per window, wb squarings, then (when any
+  // number of the warp has a non-zero digit) one multiplication by the table entry
+  {
+    int widx = (int)nwin - 2, q = 0;
+    bool mul = false;
+    while (widx >= 0) {
+      if (q == 0) {
+        d = bad ? 0u : exp_digit(it.e, el, (uint32_t)widx * wb, wb);
+        mul = __any_sync(0xffffffffu, d != 0);
+      }
+      if (q < wb) {
+#pragma unroll
+        for (int s = 0; s < NPT; s++) {
+          yb[s] = xb[s];
+          yp[s] = xp[s];
+        }
+      } else {
+        tab_load<C>(wt, d, yb, yp, lane);
+      }
+      mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
+      if (++q == wb + (mul ? 1 : 0)) {
+        q = 0;
+        widx--;
+      }
     }
   }
 
@@ -142,7 +161,7 @@ __global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
     yb[s] = sm.cb4(o).z;  // hat form of 1 = 2^32 mod m
     yp[s] = sm.cp4(o).z;
   }
-  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
   from_rns_reduce<C>(xb, a.cls, key, sm, xib, t, it.out, (int)it.out_limbs, live && !bad);
   if (live && t == 0) {
     if (bad)
@@ -171,12 +190,13 @@ __global__ void __launch_bounds__(C::THREADS) crt_kernel(LaunchArgs a) {
   uint32_t* xib = sm.xi(item_in_block);
   uint32_t* xpb = xib + C::KP;
 
-  uint32_t kxi[NPT], cmul[NPT];
+  uint32_t kxi[NPT], cmul[NPT], cd[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
     kxi[s] = o < C::K ? __ldg(key + ko.kxi + o) : 0u;
     cmul[s] = o < C::K ? __ldg(key + ko.cmul + o) : 0u;
+    cd[s] = o < C::K ? __ldg(key + ko.cd + o) : 0u;
   }
   // d = m_p + P2 - m_q  (a positive integer below 3 * 2^L, congruent to m_p - m_q mod p)
   uint32_t db[NPT], dp[NPT], qb[NPT], qp[NPT], yb[NPT], yp[NPT];
@@ -195,7 +215,7 @@ __global__ void __launch_bounds__(C::THREADS) crt_kernel(LaunchArgs a) {
   }
   // h = MM(d, qinv M mod p) = d qinv mod p, then to binary in [0, p)
   load_vec<C>(yb, yp, it.crt + cro.qm, t);
-  mont_mul<C>(db, dp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  mont_mul<C>(db, dp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
   uint32_t h[W];
   from_rns_reduce<C>(db, a.cls, key, sm, xib, t, h, W, true);
   // m = m_q + h q  (2W limbs)

@@ -17,17 +17,38 @@ struct LaunchArgs {
   uint8_t* status;       // per-item status bytes or nullptr
 };
 
-struct ClassKernels {
-  uint32_t L, k, W, WX, tpi, threads, ipb, npt, smem_bytes;
+struct MRArgs {
+  const uint32_t* cls;
+  const uint32_t* cand;     // n rows of n_limbs
+  const uint32_t* witness;  // n*rounds rows of n_limbs
+  uint8_t* is_prime;        // n
+  uint32_t* round_mask;     // n or nullptr
+  uint32_t* scratch;        // window tables, per warp (1 << wbits) x 2 NPT x 32 words
+  uint32_t* crow;           // per candidate 3W words: M mod N, M^2 mod N, N - (M mod N)
+  uint32_t n, n_limbs, rounds, wbits;
+};
+
+// One compiled lane mapping of a size class.
+struct KernelVariant {
+  uint32_t tpi, threads, ipb, npt, smem_bytes;
   cudaError_t (*modexp)(const LaunchArgs&, unsigned grid, cudaStream_t);
   cudaError_t (*crt)(const LaunchArgs&, unsigned grid, cudaStream_t);
+  cudaError_t (*mr)(const MRArgs&, unsigned grid, cudaStream_t);
+};
+
+constexpr int MAX_VARIANTS = 4;
+
+struct ClassKernels {
+  uint32_t L, k, W, WX;
+  uint32_t n_variants;
+  KernelVariant var[MAX_VARIANTS];
 };
 
 // nullptr when no kernel is compiled for class L
 const ClassKernels* class_kernels(uint32_t L);
 
 // scratch words one modexp launch of n items needs
-inline size_t modexp_scratch_words(const ClassKernels& kc, uint32_t n, uint32_t wbits) {
+inline size_t modexp_scratch_words(const KernelVariant& kc, uint32_t n, uint32_t wbits) {
   size_t grid = (n + kc.ipb - 1) / kc.ipb;
   size_t warps = grid * (kc.threads / 32);
   return warps * ((size_t)1 << wbits) * 2 * kc.npt * 32;

@@ -19,13 +19,13 @@ namespace mr {
 constexpr int KAW_Q = 22;  // fixed-point bits of the B'->B correction estimate
 
 // ---------------------------------------------------------------- size class
-// [m 2k][mi 2k][r32 2k][ahat k][d k][ubp k][mphh k][mmiinv k][ub k]
+// [m 2k][mi 2k][r32 2k][ahat k][ad k][ubp k][mphh k][mmiinv k][ub k]
 // [T1 k*k][T2 k*k][P W*2k][MD k*WX][ML WX]
 //   m      channel prime
 //   mi     -m^-1 mod 2^32
 //   r32    2^32 mod m  (= the hat form of 1)
 //   ahat   (B') |M^-1|_{m'_j} hat
-//   d      (B') |(M'/m'_j)^-1|_{m'_j} plain
+//   ad     (B') |M^-1 (M'/m'_j)^-1|_{m'_j} plain   (xi'_j = REDC(hat(s_j) ad + hat(qhat_j) cd))
 //   ubp    (B') floor(2^(32+Q) / m'_j)            fixed-point factor weights
 //   mphh   (B)  |M'|_{m_i} * 2^64 mod m_i          (REDC(a * mphh) = hat(a M'))
 //   mmiinv (B)  |(M/m_i)^-1|_{m_i} plain           (RNS -> binary)
@@ -36,7 +36,7 @@ constexpr int KAW_Q = 22;  // fixed-point bits of the B'->B correction estimate
 //   MD     row i: the WX limbs of M/m_i
 //   ML     the WX limbs of M
 struct ClassOff {
-  uint32_t m, mi, r32, ahat, d, ubp, mphh, mmiinv, ub, T1, T2, P, MD, ML, total;
+  uint32_t m, mi, r32, ahat, ad, ubp, mphh, mmiinv, ub, T1, T2, P, MD, ML, total;
 };
 
 MR_HD constexpr inline ClassOff class_offsets(uint32_t k, uint32_t W, uint32_t WX) {
@@ -45,7 +45,7 @@ MR_HD constexpr inline ClassOff class_offsets(uint32_t k, uint32_t W, uint32_t W
   o.mi = 2 * k;
   o.r32 = 4 * k;
   o.ahat = 6 * k;
-  o.d = 7 * k;
+  o.ad = 7 * k;
   o.ubp = 8 * k;
   o.mphh = 9 * k;
   o.mmiinv = 10 * k;
@@ -60,17 +60,18 @@ MR_HD constexpr inline ClassOff class_offsets(uint32_t k, uint32_t W, uint32_t W
 }
 
 // ------------------------------------------------------------------ modulus
-// [hdr 4][kxi k][cmul k][one 2k][r2 2k][r2h 2k][N W][exp W]
+// [hdr 4][kxi k][cmul k][cd k][one 2k][r2 2k][r2h 2k][N W][exp W]
 //   hdr    nbits(N), nlimbs(N), exp_bits (private exponent bit length or 0), 0
 //   kxi    (B)  |-N^-1 (M/m_i)^-1|_{m_i} plain
 //   cmul   (B') |N M^-1|_{m'_j} hat
+//   cd     (B') |N M^-1 (M'/m'_j)^-1|_{m'_j} plain
 //   one    hat residues of M mod N           (1 in the Montgomery domain)
 //   r2     hat residues of M^2 mod N         (entry into the domain)
 //   r2h    hat residues of 2^L M^2 mod N     (entry of the high chunk of a 2L-bit input)
 //   N      W limbs of the modulus
 //   exp    W limbs: private CRT exponent (dp or dq) of an RSA half, zero otherwise
 struct KeyOff {
-  uint32_t hdr, kxi, cmul, one, r2, r2h, N, exp, total;
+  uint32_t hdr, kxi, cmul, cd, one, r2, r2h, N, exp, total;
 };
 
 MR_HD constexpr inline KeyOff key_offsets(uint32_t k, uint32_t W) {
@@ -78,7 +79,8 @@ MR_HD constexpr inline KeyOff key_offsets(uint32_t k, uint32_t W) {
   o.hdr = 0;
   o.kxi = 4;
   o.cmul = o.kxi + k;
-  o.one = o.cmul + k;
+  o.cd = o.cmul + k;
+  o.one = o.cd + k;
   o.r2 = o.one + 2 * k;
   o.r2h = o.r2 + 2 * k;
   o.N = o.r2h + 2 * k;

@@ -1,4 +1,4 @@
-// Registry of the compiled size classes.
+// Registry of the compiled size classes. Generated by gen_kernels.py.
 #include "kernels_api.h"
 
 namespace mr {

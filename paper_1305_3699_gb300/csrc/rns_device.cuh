@@ -68,7 +68,9 @@ struct Cfg {
   static constexpr int NPTP = (NPT + VEC - 1) / VEC * VEC;  // padded to whole vector loads
   static constexpr int ROW = TPI * NPTP;          // words per extension-matrix row in smem
   static constexpr int SL = TPI * NPT;            // slot-indexed constant arrays
-  static constexpr int KP = (K + 3) & ~3;         // xi buffer stride
+  static constexpr int KP = (K + 3) & ~3;         // xi / xi' buffer length
+  static constexpr int XS = 2 * KP + 4;           // per-number stride of the two buffers: XS/4 odd
+                                                  // keeps broadcast loads and stores bank-conflict free
   static constexpr int THREADS = THREADS_;
   static constexpr int IPB = THREADS / TPI;       // numbers per block
   static constexpr int IPW = 32 / TPI;            // numbers per warp
@@ -78,9 +80,9 @@ struct Cfg {
   static constexpr int SM_CB4 = SM_T2 + K * ROW;  // uint4 {m, mi, r32, mphh}   B
   static constexpr int SM_CP4 = SM_CB4 + 4 * SL;  // uint4 {m, mi, r32, ahat}   B'
   static constexpr int SM_CB2 = SM_CP4 + 4 * SL;  // uint2 {mmiinv, ub}         B
-  static constexpr int SM_CP2 = SM_CB2 + 2 * SL;  // uint2 {d, ubp}             B'
-  static constexpr int SM_XI = SM_CP2 + 2 * SL;   // IPB x 2 x KP
-  static constexpr int SM_WORDS = SM_XI + IPB * 2 * KP;
+  static constexpr int SM_CP2 = SM_CB2 + 2 * SL;  // uint2 {ad, ubp}            B'
+  static constexpr int SM_XI = SM_CP2 + 2 * SL;   // IPB x XS
+  static constexpr int SM_WORDS = SM_XI + IPB * XS;
   static constexpr int SMEM_BYTES = SM_WORDS * 4;
   static_assert(TPI == 1 || TPI == 2 || TPI == 4 || TPI == 8 || TPI == 16 || TPI == 32, "TPI must divide 32");
   static_assert(VEC == 2 || VEC == 4, "vector width");
@@ -97,7 +99,7 @@ struct Smem {
   __device__ uint4 cp4(int o) const { return reinterpret_cast<const uint4*>(base + C::SM_CP4)[o]; }
   __device__ uint2 cb2(int o) const { return reinterpret_cast<const uint2*>(base + C::SM_CB2)[o]; }
   __device__ uint2 cp2(int o) const { return reinterpret_cast<const uint2*>(base + C::SM_CP2)[o]; }
-  __device__ uint32_t* xi(int item_in_block) const { return base + C::SM_XI + item_in_block * 2 * C::KP; }
+  __device__ uint32_t* xi(int item_in_block) const { return base + C::SM_XI + item_in_block * C::XS; }
 };
 
 // Block prologue: copy the class tables into shared memory in the lane-slot layout.
@@ -129,10 +131,10 @@ __device__ void load_class_smem(const Smem<C>& sm, const uint32_t* cls) {
     cp4[3] = ok ? cls[o.ahat + ch] : 0u;
     cb2[0] = ok ? cls[o.mmiinv + ch] : 0u;
     cb2[1] = ok ? cls[o.ub + ch] : 0u;
-    cp2[0] = ok ? cls[o.d + ch] : 0u;
+    cp2[0] = ok ? cls[o.ad + ch] : 0u;
     cp2[1] = ok ? cls[o.ubp + ch] : 0u;
   }
-  for (int idx = threadIdx.x; idx < C::IPB * 2 * C::KP; idx += blockDim.x) s[C::SM_XI + idx] = 0u;
+  for (int idx = threadIdx.x; idx < C::IPB * C::XS; idx += blockDim.x) s[C::SM_XI + idx] = 0u;
 }
 
 // Sum a value over the TPI lanes of this lane's group.
@@ -184,14 +186,15 @@ __device__ __forceinline__ void ext_dot(uint64_t (&acc)[C::NPT], const uint32_t*
 // outputs below (k+1)N for operands whose product is below 4(k+1)^2 2^L N.
 //   xb, xp: hat residues of x in this lane's B and B' channels (in/out)
 //   yb, yp: hat residues of y (may alias xb, xp for a squaring)
-//   kxi:    |-N^-1 (M/m_i)^-1|_{m_i} plain, cmul: |N M^-1|_{m'_j} hat  (per modulus)
+//   kxi:    |-N^-1 (M/m_i)^-1|_{m_i} plain, cmul: |N M^-1|_{m'_j} hat,
+//   cd:     |N M^-1 (M'/m'_j)^-1|_{m'_j} plain                         (per modulus)
 //   xib, xpb: this number's xi / xi' exchange buffers in shared memory
 // ------------------------------------------------------------------------
 template <class C>
 __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], const uint32_t (&yb)[C::NPT],
                                          const uint32_t (&yp)[C::NPT], const uint32_t (&kxi)[C::NPT],
-                                         const uint32_t (&cmul)[C::NPT], const Smem<C>& sm, uint32_t* xib,
-                                         uint32_t* xpb, int t) {
+                                         const uint32_t (&cmul)[C::NPT], const uint32_t (&cd)[C::NPT],
+                                         const Smem<C>& sm, uint32_t* xib, uint32_t* xpb, int t) {
   constexpr int NPT = C::NPT, K = C::K;
   uint32_t sp[NPT];
   // 1-2. s = x*y in both bases; xi_i = s_i |-N^-1 (M/m_i)^-1| (plain CRT coefficients of q)
@@ -209,7 +212,8 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
   // 3. extension B -> B': qhat_j = sum_i xi_i |M/m_i|_{m'_j}   (k-term 64-bit dot products)
   uint64_t acc[NPT];
   ext_dot<C>(acc, xib, sm.T1(), t);
-  // 4-5. r_j = s_j |M^-1| + qhat_j |N M^-1| (hat, the new B' residues); xi'_j = r_j |(M'/m'_j)^-1| (plain)
+  // 4-5. r_j = s_j |M^-1| + qhat_j |N M^-1| (hat, the new B' residues) and, from the same two
+  //      values, xi'_j = r_j |(M'/m'_j)^-1| = s_j |M^-1 (M'/m'_j)^-1| + qhat_j |N M^-1 (M'/m'_j)^-1| (plain)
   uint32_t kaw = 0;
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
@@ -217,9 +221,8 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
     const uint4 cp = sm.cp4(o);
     const uint2 c2 = sm.cp2(o);
     uint32_t qh = redc64(acc[s], cp.x, cp.y, cp.z);
-    uint32_t r = redc(madw(sp[s], cp.w, mulw(qh, cmul[s])), cp.x, cp.y);
-    xp[s] = r;
-    uint32_t xpj = redc(mulw(r, c2.x), cp.x, cp.y);
+    xp[s] = redc(madw(sp[s], cp.w, mulw(qh, cmul[s])), cp.x, cp.y);
+    uint32_t xpj = redc(madw(sp[s], c2.x, mulw(qh, cd[s])), cp.x, cp.y);
     if (o < K) xpb[o] = xpj;
     kaw += hi32(mulw(xpj, c2.y));  // floor(xi'_j 2^Q / m'_j), up to 2 units low
   }

@@ -163,7 +163,7 @@ bool build_class(uint32_t L, ClassHost& c, std::string& err) {
   for (uint32_t j = 0; j < k; j++) {
     uint32_t m = Bp[j];
     blk[o.ahat + j] = mulmod32(c.Minv_Bp[j], r32[k + j], m);
-    blk[o.d + j] = c.Mp_mj_inv[j];
+    blk[o.ad + j] = mulmod32(c.Minv_Bp[j], c.Mp_mj_inv[j], m);
     blk[o.ubp + j] = (uint32_t)((1ull << (32 + KAW_Q)) / m);
   }
   for (uint32_t i = 0; i < k; i++) {
@@ -255,6 +255,7 @@ int build_key(const ClassHost& c, const Big& N, const Big* exp, KeyHost& out, st
   for (uint32_t j = 0; j < k; j++) {
     uint32_t m = c.Bp[j];
     b[o.cmul + j] = mulmod32(out.NMinv_Bp[j], (uint32_t)((1ull << 32) % m), m);
+    b[o.cd + j] = mulmod32(out.NMinv_Bp[j], c.Mp_mj_inv[j], m);
   }
   put_hat(c, out.one, b + o.one);
   put_hat(c, out.r2, b + o.r2);

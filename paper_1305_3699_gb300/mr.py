@@ -27,7 +27,7 @@ EXPORTED = [
     "mr_init", "mr_shutdown", "mr_last_error", "mr_class_for_bits", "mr_rns_setup", "mr_rsa_key_setup",
     "mr_key_info", "mr_key_free", "mr_modexp_batch", "mr_rsa_encrypt", "mr_rsa_decrypt_crt",
     "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
-    "mr_modexp_batch_noalloc",
+    "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant",
 ]
 
 
@@ -68,6 +68,8 @@ def _load() -> ctypes.CDLL:
         "mr_debug_key_table_host": (ctypes.c_int, [PU32, U32, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "mr_modexp_batch_noalloc": (ctypes.c_int, [P, P, SZ, P, U32, P, U32, P, U32, P, P]),
+        "mr_class_variants": (ctypes.c_int, [U32, PU32, PU32, U32]),
+        "mr_set_variant": (ctypes.c_int, [P, U32, U32]),
         "mr_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelTime), U32]),
     }
     for name, (res, args) in sig.items():
@@ -122,6 +124,16 @@ def mr_class_for_bits(bits: int):
     if rc:
         raise MRError(rc, f"no size class for {bits} bits")
     return L.value, k.value
+
+
+def mr_class_variants(class_bits: int) -> List[int]:
+    """Lanes per number of each compiled lane mapping of a size class."""
+    cnt = ctypes.c_uint32()
+    buf = (ctypes.c_uint32 * 8)()
+    rc = lib.mr_class_variants(class_bits, ctypes.byref(cnt), buf, 8)
+    if rc:
+        raise MRError(rc, f"no size class {class_bits}")
+    return [buf[i] for i in range(min(cnt.value, 8))]
 
 
 def mr_debug_key_table_host(N: int, name: str) -> List[int]:
@@ -270,6 +282,9 @@ class Context:
         n, nl = _rows(cand)
         self._check(lib.mr_miller_rabin_batch(self.handle, _dev(cand), nl, n, _dev(witness), rounds, _dev(is_prime),
                                               _dev(round_mask), _stream(stream)))
+
+    def mr_set_variant(self, class_bits: int, variant: int):
+        self._check(lib.mr_set_variant(self.handle, class_bits, variant))
 
     def mr_profile_enable(self, on: bool = True):
         self._check(lib.mr_profile_enable(self.handle, 1 if on else 0))

@@ -1,0 +1,105 @@
+"""GPU Miller-Rabin (mr_miller_rabin_batch) against the oracle, verdict by verdict."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import primality
+from synth import SplitMix64, load_keys
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def mr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1305_3699_gb300 import mr as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mr):
+    c = mr.Context(0)
+    yield c
+    c.close()
+
+
+def run_mr(mr, ctx, cands, witnesses, n_limbs):
+    rounds = len(witnesses[0])
+    c = mr.to_tensor(cands, n_limbs)
+    w = mr.to_tensor([a for ws in witnesses for a in ws], n_limbs)
+    flag = torch.full((len(cands),), 7, dtype=torch.uint8, device="cuda")
+    mask = torch.zeros(len(cands), dtype=torch.int32, device="cuda")
+    ctx.mr_miller_rabin_batch(c, w, rounds, flag, mask)
+    torch.cuda.synchronize()
+    return flag.cpu().tolist(), [int(v) & 0xFFFFFFFF for v in mask.cpu().numpy().astype(np.int64)]
+
+
+def expect(n, ws):
+    verdicts = primality.miller_rabin(n, ws)
+    return int(all(verdicts)), sum(1 << r for r, v in enumerate(verdicts) if v)
+
+
+def check(mr, ctx, cands, witnesses, n_limbs, skip_mask_for=()):
+    flags, masks = run_mr(mr, ctx, cands, witnesses, n_limbs)
+    for i, n in enumerate(cands):
+        f, m = expect(n, witnesses[i])
+        assert flags[i] == f, (n, witnesses[i])
+        if n not in skip_mask_for:
+            assert masks[i] == m, (n, witnesses[i], hex(masks[i]), hex(m))
+
+
+def test_small_candidates_exhaustive_witnesses(mr, ctx):
+    r = SplitMix64(1)
+    cands = list(range(0, 200)) + [r.below(1 << 31) | 1 for _ in range(300)] + [2147483647, 2147483629]
+    ws = [[2, 3, 5, 7, r.below(1 << 40)] for _ in cands]
+    check(mr, ctx, cands, ws, 2)
+
+
+def test_strong_pseudoprimes(mr, ctx):
+    cands, ws = [], []
+    for line in open(os.path.join(GOLD, "strong_pseudoprimes.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        n, passed, failed = line.split()
+        bases = ([int(b) for b in passed.split(",")] if passed != "-" else []) + [int(failed)]
+        bases = (bases + [2] * 6)[:6]
+        cands.append(int(n))
+        ws.append(bases)
+    check(mr, ctx, cands, ws, 2)
+
+
+@pytest.mark.parametrize("n_limbs", [16, 32, 48, 64])
+def test_large_primes_and_composites(mr, ctx, n_limbs):
+    bits = 32 * n_limbs
+    r = SplitMix64(n_limbs)
+    keys = load_keys("rsa2048_x16") + load_keys("rsa1024_x64")[:8] + load_keys("mix_x256")
+    primes = sorted({k[x] for k in keys for x in ("p", "q") if bits - 32 < k[x].bit_length() <= bits})[:12]
+    comps = [r.randbits(bits) | 1 for _ in range(12)]
+    products = [k["N"] for k in keys if bits - 32 < k["N"].bit_length() <= bits][:6]
+    cands = primes + comps + products
+    ws = [[r.between(2, n - 2) for _ in range(3)] for n in cands]
+    check(mr, ctx, cands, ws, n_limbs)
+
+
+def test_mersenne_primes_and_witness_edges(mr, ctx):
+    cands, ws = [], []
+    for e in (521, 607, 1279):
+        p = (1 << e) - 1
+        cands += [p, p]
+        ws += [[2, 3, 0, p - 1], [1, p, p + 1, 5]]
+    check(mr, ctx, cands, ws, 64)
+
+
+def test_candidate_with_channel_prime_factor(mr, ctx):
+    B = mr.mr_debug_class_table(1024, "B")  # 17-limb candidates fall in the 1024-bit class
+    big_prime = load_keys("rsa1024_x64")[0]["p"]  # 512 bits
+    n = B[5] * big_prime  # odd composite above 2^31 sharing a channel prime
+    assert n.bit_length() <= 17 * 32
+    flags, masks = run_mr(mr, ctx, [n], [[2, 3]], 17)
+    assert flags == [0] and masks == [0]
+    assert not all(primality.miller_rabin(n, [2, 3]))
