@@ -228,6 +228,16 @@ mr_status mr_profile_read(mr_ctx *ctx, mr_kernel_time *times, uint32_t n_kinds);
 mr_status mr_debug_table(mr_ctx *ctx, uint32_t class_bits, const mr_key *key, const char *name,
                          uint32_t *out, size_t capacity, size_t *count);
 
+/* Test hook of mr_miller_rabin_batch: run one round (witness 2) on n candidates
+ * and write, per candidate, the constants the kernel derived on the device to
+ * dev_out (device, n rows of 4 + 2W + 5k words, W = class limbs, k = class
+ * channels): [special case code, s, bit length, 0], M mod N (W limbs),
+ * M^2 mod N (W limbs), then per channel |-N^-1 (M/m_i)^-1|_{m_i} (k),
+ * |N M^-1|_{m'_j} (k), |N M^-1 (M'/m'_j)^-1|_{m'_j} (k), N^-1 mod m_i (k),
+ * N^-1 mod m'_j (k).  Synchronises the stream.  Errors as mr_miller_rabin_batch. */
+mr_status mr_debug_mr_setup(mr_ctx *ctx, const uint32_t *cand, uint32_t n_limbs, size_t n, uint32_t *dev_out,
+                            void *stream);
+
 /* As mr_debug_table for the key tables of modulus N (host, n_limbs limbs),
  * computed on the host only (no context, no device).  Errors as mr_rns_setup. */
 mr_status mr_debug_key_table_host(const uint32_t *N, uint32_t n_limbs, const char *name, uint32_t *out,

@@ -72,6 +72,7 @@ struct mr_ctx {
   };
   std::vector<Span> spans;
   std::vector<cudaEvent_t> free_events;
+  uint32_t* mr_dbg = nullptr;  // test hook of mr_debug_mr_setup
 };
 
 struct mr_key {
@@ -695,7 +696,7 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
     if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, std::string("scratch allocation failed: ") + cudaGetErrorString(e));
     char* base = static_cast<char*>(dev);
     MRArgs a{ce->dev, cand, witness, dev_is_probable_prime, dev_round_mask, reinterpret_cast<uint32_t*>(base),
-             reinterpret_cast<uint32_t*>(base + off_crow), (uint32_t)n, n_limbs, rounds, wbits};
+             reinterpret_cast<uint32_t*>(base + off_crow), (uint32_t)n, n_limbs, rounds, wbits, ctx->mr_dbg};
     unsigned grid = (unsigned)((n + k.ipb - 1) / k.ipb);
     e = timed_launch(ctx, 0, (cudaStream_t)stream, [&] { return k.mr(a, grid, (cudaStream_t)stream); });
     cudaError_t e2 = cudaFreeAsync(dev, (cudaStream_t)stream);
@@ -762,6 +763,28 @@ mr_status mr_profile_read(mr_ctx* ctx, mr_kernel_time* times, uint32_t n_kinds) 
   }
   ctx->launches[0] = ctx->launches[1] = 0;
   return err == cudaSuccess ? MR_OK : cuda_fail(ctx, err, "profile events");
+}
+
+mr_status mr_debug_mr_setup(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs, size_t n, uint32_t* dev_out,
+                            void* stream) {
+  if (!ctx || !cand || !dev_out || !n_limbs) return MR_ERR_ARG;
+  // one round with witness 2 for every candidate, constants published to dev_out
+  uint32_t L = class_for_bits(32 * n_limbs);
+  if (!L) return fail(ctx, MR_ERR_SIZE, "candidates longer than the largest size class");
+  void* tmp = nullptr;
+  size_t wbytes = n * n_limbs * 4;
+  cudaError_t e = cudaMallocFromPoolAsync(&tmp, wbytes + n, ctx->pool, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "debug scratch");
+  std::vector<uint32_t> w(n * n_limbs, 0);
+  for (size_t i = 0; i < n; i++) w[i * n_limbs] = 2;
+  cudaMemcpyAsync(tmp, w.data(), wbytes, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  ctx->mr_dbg = dev_out;
+  mr_status s = mr_miller_rabin_batch(ctx, cand, n_limbs, n, static_cast<uint32_t*>(tmp), 1,
+                                      static_cast<uint8_t*>(tmp) + wbytes, nullptr, stream);
+  ctx->mr_dbg = nullptr;
+  cudaFreeAsync(tmp, (cudaStream_t)stream);
+  return s;
 }
 
 mr_status mr_class_variants(uint32_t class_bits, uint32_t* count, uint32_t* lanes_per_number, uint32_t capacity) {

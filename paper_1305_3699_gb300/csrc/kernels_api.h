@@ -26,7 +26,11 @@ struct MRArgs {
   uint32_t* scratch;        // window tables, per warp (1 << wbits) x 2 NPT x 32 words
   uint32_t* crow;           // per candidate 3W words: M mod N, M^2 mod N, N - (M mod N)
   uint32_t n, n_limbs, rounds, wbits;
+  uint32_t* dbg;            // nullptr, or per candidate mr_debug_words(k, W) words of derived constants
 };
+
+// [special, s, nbits, 0][M mod N: W][M^2 mod N: W][kxi: k][N M^-1 (plain): k][cd: k][N^-1 mod m_i: k][N^-1 mod m'_j: k]
+MR_HD inline uint32_t mr_debug_words(uint32_t k, uint32_t W) { return 4 + 2 * W + 5 * k; }
 
 // One compiled lane mapping of a size class.
 struct KernelVariant {

@@ -24,7 +24,7 @@ namespace mr {
 // r = a mod n (lane-local; a: na limbs, n: nn limbs with n[nn-1] != 0, nn <= NMAX,
 // na <= AMAX).  Knuth's Algorithm D with 32-bit digits.
 template <int AMAX, int NMAX>
-__device__ void bn_mod(const uint32_t* a, int na, const uint32_t* n, int nn, uint32_t* r) {
+__device__ __noinline__ void bn_mod(const uint32_t* a, int na, const uint32_t* n, int nn, uint32_t* r) {
   if (nn == 1) {
     uint64_t rem = 0;
     for (int i = na - 1; i >= 0; i--) rem = ((rem << 32) | a[i]) % n[0];
@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
   // 3 = N > 2^31 shares a channel prime (composite: it has that prime as a factor),
   // 5 = N < 2^31, tested in 64-bit scalar arithmetic by lane 0
   uint32_t special = 0;
-  uint32_t sbits = 0, nbits = 0;
-  if (t == 0) {
+  uint32_t sbits = 0, nbits = 0, dbg_one0 = 0;
+  if (t == 0 && live) {  // idle groups (shadowing the last candidate) must not write its scratch row
     int nn = (int)nl;
     while (nn > 0 && N[nn - 1] == 0) nn--;
     nbits = nn ? 32u * (nn - 1) + 32u - __clz(N[nn - 1]) : 0u;
@@ -140,32 +140,40 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
     else if (nbits <= 31) special = 5u;
     if (!special) {
       while (((N[sbits >> 5] >> (sbits & 31)) & 1u) == 0 || sbits == 0) sbits++;  // N - 1 = 2^s d, s >= 1
-      uint32_t Ml[WX], one[W], sq[2 * W];
-      for (int i = 0; i < WX; i++) Ml[i] = __ldg(a.cls + co.ML + i);
-      int ma = WX;
-      while (ma > 0 && Ml[ma - 1] == 0) ma--;
-      bn_mod<WX, W>(Ml, ma, N, nn, one);
-      for (int i = nn; i < W; i++) one[i] = 0u;
-      for (int i = 0; i < 2 * nn; i++) sq[i] = 0u;
-      for (int i = 0; i < nn; i++) {
-        uint64_t c = 0;
-        for (int j = 0; j < nn; j++) {
-          uint64_t p = (uint64_t)one[i] * one[j] + sq[i + j] + c;
-          sq[i + j] = (uint32_t)p;
-          c = p >> 32;
-        }
-        sq[i + nn] = (uint32_t)c;
+      // M mod N and M^2 mod N go straight to the candidate's scratch row
+      uint32_t* one = crow;
+      uint32_t* r2 = crow + W;
+      {
+        uint32_t Ml[WX];
+        for (int i = 0; i < WX; i++) Ml[i] = __ldg(a.cls + co.ML + i);
+        int ma = WX;
+        while (ma > 0 && Ml[ma - 1] == 0) ma--;
+        bn_mod<WX, W>(Ml, ma, N, nn, one);
       }
-      uint32_t r2[W];
-      bn_mod<2 * W, W>(sq, 2 * nn, N, nn, r2);
+      for (int i = nn; i < W; i++) one[i] = 0u;
+      {
+        uint32_t sq[2 * W];
+        for (int i = 0; i < 2 * nn; i++) sq[i] = 0u;
+        for (int i = 0; i < nn; i++) {
+          uint64_t c = 0;
+          const uint64_t oi = one[i];
+          for (int j = 0; j < nn; j++) {
+            uint64_t p = oi * one[j] + sq[i + j] + c;
+            sq[i + j] = (uint32_t)p;
+            c = p >> 32;
+          }
+          sq[i + nn] = (uint32_t)c;
+        }
+        bn_mod<2 * W, W>(sq, 2 * nn, N, nn, r2);
+      }
+      for (int i = nn; i < W; i++) r2[i] = 0u;
+      dbg_one0 = one[0];
       uint32_t br = 0;
       for (int i = 0; i < W; i++) {
         uint32_t nv = i < nn ? N[i] : 0u;
         uint64_t d = (uint64_t)nv - one[i] - br;
         crow[2 * W + i] = (uint32_t)d;
         br = (uint32_t)(d >> 63);
-        crow[i] = one[i];
-        crow[W + i] = i < nn ? r2[i] : 0u;
       }
     }
   }
@@ -207,6 +215,29 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
     const unsigned grp = C::TPI == 32 ? 0xffffffffu : (((1u << (C::TPI & 31)) - 1u) << (lane - t));
     const unsigned nc = __ballot_sync(0xffffffffu, !coprime) & grp;
     if (nc && !special) special = 3u;  // N shares a channel prime
+  }
+
+  if (a.dbg) {  // test hook: publish the derived constants of this candidate
+    uint32_t* dg = a.dbg + (size_t)g * mr_debug_words(K, W);
+    if (live && t == 0) {
+      dg[0] = special;
+      dg[1] = sbits;
+      dg[2] = nbits;
+      dg[3] = dbg_one0;
+      for (int i = 0; i < 2 * W; i++) dg[4 + i] = special ? 0u : crow[i];
+    }
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      const int o = t * NPT + s;
+      if (live && o < K) {
+        const uint4 cp = sm.cp4(o);
+        dg[4 + 2 * W + o] = kxi[s];
+        dg[4 + 2 * W + K + o] = redc(mulw(cmul[s], 1u), cp.x, cp.y);
+        dg[4 + 2 * W + 2 * K + o] = cd[s];
+        dg[4 + 2 * W + 3 * K + o] = invb[s];
+        dg[4 + 2 * W + 4 * K + o] = invp[s];
+      }
+    }
   }
 
   // hat residues of M mod N (= 1 in the domain), M^2 mod N (entry), N - (M mod N)

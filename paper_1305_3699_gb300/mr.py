@@ -27,7 +27,7 @@ EXPORTED = [
     "mr_init", "mr_shutdown", "mr_last_error", "mr_class_for_bits", "mr_rns_setup", "mr_rsa_key_setup",
     "mr_key_info", "mr_key_free", "mr_modexp_batch", "mr_rsa_encrypt", "mr_rsa_decrypt_crt",
     "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
-    "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant",
+    "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant", "mr_debug_mr_setup",
 ]
 
 
@@ -70,6 +70,7 @@ def _load() -> ctypes.CDLL:
         "mr_modexp_batch_noalloc": (ctypes.c_int, [P, P, SZ, P, U32, P, U32, P, U32, P, P]),
         "mr_class_variants": (ctypes.c_int, [U32, PU32, PU32, U32]),
         "mr_set_variant": (ctypes.c_int, [P, U32, U32]),
+        "mr_debug_mr_setup": (ctypes.c_int, [P, P, U32, SZ, P, P]),
         "mr_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelTime), U32]),
     }
     for name, (res, args) in sig.items():
@@ -282,6 +283,10 @@ class Context:
         n, nl = _rows(cand)
         self._check(lib.mr_miller_rabin_batch(self.handle, _dev(cand), nl, n, _dev(witness), rounds, _dev(is_prime),
                                               _dev(round_mask), _stream(stream)))
+
+    def mr_debug_mr_setup(self, cand, out, stream=None):
+        n, nl = _rows(cand)
+        self._check(lib.mr_debug_mr_setup(self.handle, _dev(cand), nl, n, _dev(out), _stream(stream)))
 
     def mr_set_variant(self, class_bits: int, variant: int):
         self._check(lib.mr_set_variant(self.handle, class_bits, variant))

@@ -103,3 +103,36 @@ def test_candidate_with_channel_prime_factor(mr, ctx):
     flags, masks = run_mr(mr, ctx, [n], [[2, 3]], 17)
     assert flags == [0] and masks == [0]
     assert not all(primality.miller_rabin(n, [2, 3]))
+
+
+def test_device_derived_constants_match_host_setup(mr, ctx):
+    """The Miller-Rabin kernel derives each candidate's constants on the device;
+    they must equal the host setup's (which the CPU tests tie to the oracle model)."""
+    from oracle import rns
+    r = SplitMix64(77)
+    for n_limbs in (2, 16, 32, 64):
+        bits = 32 * n_limbs
+        cands = [3215031751] if n_limbs == 2 else [r.randbits(bits) | 1 | (1 << (bits - 1)) for _ in range(3)]
+        L, k = mr.mr_class_for_bits(bits)
+        W = L // 32
+        words = 4 + 2 * W + 5 * k
+        out = torch.zeros((len(cands), words), dtype=torch.int32, device="cuda")
+        ctx.mr_debug_mr_setup(mr.to_tensor(cands, n_limbs), out)
+        got = out.cpu().numpy().view(np.uint32)
+        c = rns.make_class(L)
+        for i, N in enumerate(cands):
+            row = [int(v) for v in got[i]]
+            key = rns.make_key(c, N)
+            s = (N - 1 & -(N - 1)).bit_length() - 1
+            assert row[0] == 0 and row[1] == s and row[2] == N.bit_length(), row[:4]
+            assert row[3] == (c.M % N) & 0xFFFFFFFF, (row[3], (c.M % N) & 0xFFFFFFFF, row[4])
+            one = int.from_bytes(b"".join(v.to_bytes(4, "little") for v in row[4:4 + W]), "little")
+            r2 = int.from_bytes(b"".join(v.to_bytes(4, "little") for v in row[4 + W:4 + 2 * W]), "little")
+            assert one == c.M % N and r2 == c.M * c.M % N
+            base = 4 + 2 * W
+            assert row[base:base + k] == key.t["kxi"]
+            assert row[base + k:base + 2 * k] == key.t["NMinv_Bp"]
+            assert row[base + 3 * k:base + 4 * k] == [pow(N % m, -1, m) for m in c.B]
+            assert row[base + 4 * k:base + 5 * k] == [pow(N % m, -1, m) for m in c.Bp]
+            assert row[base + 2 * k:base + 3 * k] == [v * c.t["Mp_mj_inv"][j] % c.Bp[j]
+                                                      for j, v in enumerate(key.t["NMinv_Bp"])]
