@@ -138,6 +138,58 @@ mr_status mr_rsa_decrypt_crt(mr_ctx *ctx, const mr_key *const *keys, size_t n, c
                              uint32_t c_stride, uint32_t *m, uint32_t m_stride, uint8_t *dev_status,
                              void *stream);
 
+/* ------------------------------------------------------- mixed batches -- */
+
+/* Operations of a mixed batch. */
+enum { MR_OP_ENCRYPT = 0, MR_OP_DECRYPT = 1 };
+
+/* Launch modes of a mixed batch (bit flags).
+ *   0                    one kernel per (size class, window) group, one after another
+ *                        on the call's stream ("per-size plain launches")
+ *   MR_PLAN_CONCURRENT   the groups run at the same time, one stream each
+ *   MR_PLAN_PERSISTENT   each group runs as a persistent kernel whose warps take
+ *                        work from a device queue (items ordered by exponent length,
+ *                        longest first), with a grid sized to the group's share of
+ *                        the total work
+ *   MR_PLAN_GRAPH        (plans only) the launch sequence is captured once in a CUDA
+ *                        graph and replayed by mr_plan_launch */
+#define MR_PLAN_CONCURRENT 1u
+#define MR_PLAN_PERSISTENT 2u
+#define MR_PLAN_GRAPH 4u
+
+/* One call over RSA requests of any sizes and keys (Sec. 3.3: encryption and
+ * decryption by modular exponentiation; decryption here through the CRT):
+ * out[i] = in[i]^e mod N_i when ops[i] == MR_OP_ENCRYPT, in[i]^d mod N_i when
+ * ops[i] == MR_OP_DECRYPT (keys need private parts).  keys, ops: host arrays of
+ * n; in, out: device rows (strides in limbs; out_stride must hold every
+ * modulus); dev_status as mr_modexp_batch; flags: MR_PLAN_CONCURRENT and/or
+ * MR_PLAN_PERSISTENT (MR_PLAN_GRAPH is ignored).  Results do not depend on the
+ * flags.  Errors as mr_rsa_decrypt_crt. */
+mr_status mr_rsa_mixed(mr_ctx *ctx, const mr_key *const *keys, const uint8_t *ops, size_t n, const uint32_t *in,
+                       uint32_t in_stride, uint32_t *out, uint32_t out_stride, uint8_t *dev_status, uint32_t flags,
+                       void *stream);
+
+/* A prepared mixed batch: the same requests (same buffers, same keys) launched
+ * many times, e.g. by a serving loop that refills `in` between launches.  The
+ * plan owns its device work lists and scratch (allocated here, released by
+ * mr_plan_free); with MR_PLAN_GRAPH its launches are one CUDA-graph launch. */
+typedef struct mr_plan mr_plan;
+
+mr_status mr_plan_create(mr_ctx *ctx, const mr_key *const *keys, const uint8_t *ops, size_t n, const uint32_t *in,
+                         uint32_t in_stride, uint32_t *out, uint32_t out_stride, uint8_t *dev_status, uint32_t flags,
+                         mr_plan **out_plan);
+
+/* Enqueue one execution of the plan on `stream`. */
+mr_status mr_plan_launch(mr_plan *plan, void *stream);
+
+/* Kernels per launch, number of (class, window) groups, device bytes held, and
+ * the estimated 32x32->64-bit products per launch (any pointer may be NULL). */
+mr_status mr_plan_info(const mr_plan *plan, uint32_t *kernels, uint32_t *groups, uint64_t *device_bytes,
+                       double *products);
+
+/* Release a plan (waits for the device). NULL is ignored. */
+void mr_plan_free(mr_plan *plan);
+
 /* Miller-Rabin rounds (Sec. 3.2: Montgomery-domain primality test with a
  * caller-chosen number of iterations) on n candidates of one length.  For an
  * odd candidate N >= 3 and witness a, round r passes when, with N - 1 = 2^s d

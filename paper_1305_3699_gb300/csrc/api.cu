@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -73,7 +74,12 @@ struct mr_ctx {
   std::vector<Span> spans;
   std::vector<cudaEvent_t> free_events;
   uint32_t* mr_dbg = nullptr;  // test hook of mr_debug_mr_setup
+  std::vector<cudaStream_t> side;     // streams for concurrent groups of one-shot mixed calls
+  std::vector<cudaEvent_t> side_join;
+  cudaEvent_t side_fork = nullptr;
 };
+
+struct mr_plan;
 
 struct mr_key {
   mr_ctx* ctx = nullptr;
@@ -115,6 +121,10 @@ mr_status get_class(mr_ctx* ctx, uint32_t L, ClassEntry** out) {
   if (!ce->kern) return fail(ctx, MR_ERR_SIZE, "no kernel compiled for class " + std::to_string(L));
   if (ce->kern->k != ce->host.k || ce->kern->W != ce->host.W || ce->kern->WX != ce->host.WX)
     return fail(ctx, MR_ERR_SIZE, "compiled kernel does not match the bases of class " + std::to_string(L));
+  for (uint32_t v = 0; v < ce->kern->n_variants; v++) {
+    cudaError_t pe = ce->kern->var[v].prepare();  // kernel attributes, once, outside any capture
+    if (pe != cudaSuccess) return cuda_fail(ctx, pe, "kernel attributes");
+  }
   {
     // default lane mapping: variant 0, unless MR_VARIANT_<L> names another compiled one
     std::string ev = "MR_VARIANT_" + std::to_string(L);
@@ -320,6 +330,213 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
   return MR_OK;
 }
 
+
+// ------------------------------------------------------------ mixed batches
+// A mixed batch holds RSA encryptions and CRT decryptions of any sizes.  Its
+// exponentiations are grouped by (size class, window width); each group is one
+// kernel launch (plus one CRT-recombination launch for decryption halves).
+struct GroupLaunch {
+  ClassEntry* ce = nullptr;
+  uint32_t wbits = 1;
+  std::vector<MxItem> mx;
+  std::vector<CrtItem> crt;
+  std::vector<uint32_t> ebits;  // per mx item, for ordering
+  double work = 0;              // estimated 32x32->64 products
+  size_t off_mx = 0, off_crt = 0, off_scratch = 0, off_half = 0;
+  uint32_t grid = 0, crt_grid = 0;
+  bool persistent = false;
+};
+
+double mm_products(uint32_t k) { return 2.0 * k * k + 7.0 * k; }
+
+double modexp_work(uint32_t k, uint32_t ebits, uint32_t w) {
+  double nwin = ebits ? std::ceil(ebits / (double)w) : 1.0;
+  return (ebits + nwin + (double)(1u << w)) * mm_products(k);
+}
+
+mr_status build_groups(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, size_t n, const uint32_t* in,
+                       uint32_t in_stride, uint32_t* out, uint32_t out_stride, std::vector<GroupLaunch>& groups) {
+  std::map<std::pair<ClassEntry*, uint32_t>, size_t> idx;
+  auto group = [&](ClassEntry* ce, uint32_t w) -> GroupLaunch& {
+    auto key = std::make_pair(ce, w);
+    auto it = idx.find(key);
+    if (it != idx.end()) return groups[it->second];
+    idx[key] = groups.size();
+    groups.emplace_back();
+    groups.back().ce = ce;
+    groups.back().wbits = w;
+    return groups.back();
+  };
+  for (size_t i = 0; i < n; i++) {
+    const mr_key* k = keys[i];
+    if (!k || k->ctx != ctx) return fail(ctx, MR_ERR_ARG, "invalid key handle at index " + std::to_string(i));
+    if (out_stride < k->pub.nlimbs()) return fail(ctx, MR_ERR_ARG, "out_stride smaller than a modulus");
+    const KeyEntry& pub = k->pub;
+    const uint32_t* nlim = pub.dev + key_offsets(pub.cls->host.k, pub.cls->host.W).N;
+    if (ops[i] == MR_OP_ENCRYPT) {
+      if (!k->dev_e) return fail(ctx, MR_ERR_KEY, "key has no public exponent");
+      uint32_t eb = (uint32_t)k->e.bits();
+      GroupLaunch& g = group(pub.cls, choose_window(eb, popcount_big(k->e)));
+      MxItem it{};
+      it.key = pub.dev;
+      it.x = in + i * in_stride;
+      it.e = k->dev_e;
+      it.out = out + i * out_stride;
+      it.xlim = nlim;
+      it.x_limbs = in_stride;
+      it.e_limbs = k->e_limbs;
+      it.out_limbs = out_stride;
+      it.xlim_limbs = pub.cls->host.W;
+      it.status = (uint32_t)i;
+      g.mx.push_back(it);
+      g.ebits.push_back(eb);
+      g.work += modexp_work(pub.cls->host.k, eb, g.wbits);
+    } else if (ops[i] == MR_OP_DECRYPT) {
+      if (!k->priv) return fail(ctx, MR_ERR_KEY, "key has no private CRT parts");
+      ClassEntry* ce = k->p.cls;
+      uint32_t eb = std::max(k->p.host.block[2], k->q.host.block[2]);
+      GroupLaunch& g = group(ce, choose_window(eb, 0));
+      const KeyOff ko = key_offsets(ce->host.k, ce->host.W);
+      for (int h = 0; h < 2; h++) {
+        const KeyEntry& ke = h == 0 ? k->p : k->q;
+        MxItem it{};
+        it.key = ke.dev;
+        it.x = in + i * in_stride;
+        it.e = ke.dev + ko.exp;
+        it.out = nullptr;                                 // result row of this half, set at staging
+        it.pad_ = (uint32_t)(2 * g.crt.size() + h) + 1u;  // 1 + half index
+        it.xlim = nlim;
+        it.x_limbs = in_stride;
+        it.e_limbs = ce->host.W;
+        it.out_limbs = ce->host.W;
+        it.xlim_limbs = pub.cls->host.W;
+        it.status = (uint32_t)i;
+        g.mx.push_back(it);
+        g.ebits.push_back(h == 0 ? k->p.host.block[2] : k->q.host.block[2]);
+        g.work += modexp_work(ce->host.k, g.ebits.back(), g.wbits);
+      }
+      CrtItem ci{};
+      ci.keyp = k->p.dev;
+      ci.crt = k->dev_crt;
+      ci.out = out + i * out_stride;
+      ci.out_limbs = out_stride;
+      ci.status = (uint32_t)i;
+      g.crt.push_back(ci);
+    } else {
+      return fail(ctx, MR_ERR_ARG, "unknown operation at index " + std::to_string(i));
+    }
+  }
+  return MR_OK;
+}
+
+// Grids, orders and device offsets of the groups; returns the total device bytes.
+size_t layout_groups(mr_ctx* ctx, std::vector<GroupLaunch>& groups, uint32_t flags, size_t* upload_bytes,
+                     size_t* queue_off) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  double total = 0;
+  for (auto& g : groups) total += g.work;
+  size_t off = 0;
+  for (auto& g : groups) {
+    const KernelVariant& kv = g.ce->kv();
+    g.persistent = (flags & MR_PLAN_PERSISTENT) != 0;
+    // items in decreasing exponent length: long items first, groups of a warp homogeneous
+    std::vector<size_t> ord(g.mx.size());
+    for (size_t i = 0; i < ord.size(); i++) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return g.ebits[a] > g.ebits[b]; });
+    std::vector<MxItem> mx(g.mx.size());
+    std::vector<uint32_t> eb(g.mx.size());
+    for (size_t i = 0; i < ord.size(); i++) {
+      mx[i] = g.mx[ord[i]];
+      eb[i] = g.ebits[ord[i]];
+    }
+    g.mx.swap(mx);
+    g.ebits.swap(eb);
+    const uint32_t full_grid = (uint32_t)((g.mx.size() + kv.ipb - 1) / kv.ipb);
+    if (g.persistent) {
+      double share = total > 0 ? g.work / total : 1.0;
+      uint32_t blocks = (uint32_t)std::floor(share * kv.occupancy() * sms);
+      if (!(flags & MR_PLAN_CONCURRENT)) blocks = (uint32_t)(kv.occupancy() * sms);
+      g.grid = std::max<uint32_t>(1, std::min<uint32_t>(blocks, full_grid));
+    } else {
+      g.grid = full_grid;
+    }
+    g.crt_grid = (uint32_t)((g.crt.size() + kv.ipb - 1) / kv.ipb);
+    g.off_mx = off;
+    off = align256(off + g.mx.size() * sizeof(MxItem));
+    g.off_crt = off;
+    off = align256(off + g.crt.size() * sizeof(CrtItem));
+  }
+  *upload_bytes = off;
+  *queue_off = off;
+  off = align256(off + groups.size() * 4);
+  for (auto& g : groups) {
+    const KernelVariant& kv = g.ce->kv();
+    size_t words = g.persistent ? persistent_scratch_words(kv, g.grid, g.wbits)
+                                : modexp_scratch_words(kv, (uint32_t)g.mx.size(), g.wbits);
+    g.off_scratch = off;
+    off = align256(off + words * 4);
+    g.off_half = off;
+    off = align256(off + g.crt.size() * 2 * (size_t)g.ce->host.W * 4);
+  }
+  return off;
+}
+
+// Enqueue the kernels of a laid-out batch on `stream` (optionally one stream per group).
+mr_status enqueue_groups(mr_ctx* ctx, std::vector<GroupLaunch>& groups, char* base, size_t queue_off, uint8_t* status,
+                         uint32_t flags, cudaStream_t stream, const std::vector<cudaStream_t>& side,
+                         cudaEvent_t fork, const std::vector<cudaEvent_t>& joins, uint32_t* launches) {
+  cudaError_t e = cudaSuccess;
+  uint32_t* queues = reinterpret_cast<uint32_t*>(base + queue_off);
+  const bool conc = (flags & MR_PLAN_CONCURRENT) && side.size() >= groups.size();
+  if (flags & MR_PLAN_PERSISTENT) e = cudaMemsetAsync(queues, 0, groups.size() * 4, stream);
+  if (e == cudaSuccess && conc) e = cudaEventRecord(fork, stream);
+  // largest groups first, so that a sequential launch order also starts the long work early
+  std::vector<size_t> order(groups.size());
+  for (size_t i = 0; i < order.size(); i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return groups[a].work > groups[b].work; });
+  for (size_t oi = 0; oi < order.size() && e == cudaSuccess; oi++) {
+    size_t gi = order[oi];
+    GroupLaunch& g = groups[gi];
+    cudaStream_t s = conc ? side[gi] : stream;
+    if (conc) e = cudaStreamWaitEvent(s, fork, 0);
+    const KernelVariant& kv = g.ce->kv();
+    if (e == cudaSuccess && !g.mx.empty()) {
+      LaunchArgs a{g.ce->dev, base + g.off_mx, (uint32_t)g.mx.size(), g.wbits,
+                   reinterpret_cast<uint32_t*>(base + g.off_scratch), status, g.persistent ? queues + gi : nullptr};
+      e = kv.modexp(a, g.grid, s);
+      (*launches)++;
+    }
+    if (e == cudaSuccess && !g.crt.empty()) {
+      LaunchArgs a{g.ce->dev, base + g.off_crt, (uint32_t)g.crt.size(), 0, nullptr, status, nullptr};
+      e = kv.crt(a, g.crt_grid, s);
+      (*launches)++;
+    }
+    if (e == cudaSuccess && conc) e = cudaEventRecord(joins[gi], s);
+  }
+  if (conc)
+    for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; gi++) e = cudaStreamWaitEvent(stream, joins[gi], 0);
+  return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "mixed-batch launch");
+}
+
+// Device copies of the item arrays, with half-result pointers resolved against `base`.
+void stage_items(std::vector<GroupLaunch>& groups, char* base, char* host) {
+  for (auto& g : groups) {
+    uint32_t W = g.ce->host.W;
+    uint32_t* halves = reinterpret_cast<uint32_t*>(base + g.off_half);
+    std::vector<MxItem> mx = g.mx;
+    for (auto& it : mx)
+      if (it.pad_) it.out = halves + (size_t)(it.pad_ - 1u) * W;
+    std::vector<CrtItem> crt = g.crt;
+    for (size_t i = 0; i < crt.size(); i++) {
+      crt[i].mp = halves + (2 * i) * W;
+      crt[i].mq = halves + (2 * i + 1) * W;
+    }
+    if (!mx.empty()) memcpy(host + g.off_mx, mx.data(), mx.size() * sizeof(MxItem));
+    if (!crt.empty()) memcpy(host + g.off_crt, crt.data(), crt.size() * sizeof(CrtItem));
+  }
+}
+
 template <class F>
 mr_status guarded(mr_ctx* ctx, F&& f) {
   try {
@@ -343,6 +560,22 @@ ClassBatch& batch_for(std::vector<ClassBatch>& v, std::map<ClassEntry*, size_t>&
 }
 
 }  // namespace
+
+struct mr_plan {
+  mr_ctx* ctx = nullptr;
+  uint32_t flags = 0;
+  std::vector<GroupLaunch> groups;
+  void* dev = nullptr;
+  size_t dev_bytes = 0, queue_off = 0;
+  uint8_t* status = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint32_t kernels = 0;
+  double products = 0;
+};
 
 extern "C" {
 
@@ -396,6 +629,9 @@ void mr_shutdown(mr_ctx* ctx) {
     cudaEventDestroy(sp.b);
   }
   for (cudaEvent_t ev : ctx->free_events) cudaEventDestroy(ev);
+  for (auto ss : ctx->side) cudaStreamDestroy(ss);
+  for (auto ev : ctx->side_join) cudaEventDestroy(ev);
+  if (ctx->side_fork) cudaEventDestroy(ctx->side_fork);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
 }
@@ -704,6 +940,196 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");
     return MR_OK;
   });
+}
+
+
+mr_status mr_rsa_mixed(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, size_t n, const uint32_t* in,
+                       uint32_t in_stride, uint32_t* out, uint32_t out_stride, uint8_t* dev_status, uint32_t flags,
+                       void* stream) {
+  if (!ctx) return MR_ERR_ARG;
+  if (n == 0) return MR_OK;
+  if (!keys || !ops || !in || !out || !in_stride || !out_stride) return fail(ctx, MR_ERR_ARG, "null argument or zero stride");
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<GroupLaunch> groups;
+    mr_status s = build_groups(ctx, keys, ops, n, in, in_stride, out, out_stride, groups);
+    if (s) return s;
+    flags &= (MR_PLAN_CONCURRENT | MR_PLAN_PERSISTENT);
+    size_t upload = 0, qoff = 0;
+    size_t total = layout_groups(ctx, groups, flags, &upload, &qoff);
+    void* dev = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&dev, total, ctx->pool, st);
+    if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, std::string("scratch allocation failed: ") + cudaGetErrorString(e));
+    char* base = static_cast<char*>(dev);
+    s = staging_reserve(ctx, upload);
+    if (s) {
+      cudaFreeAsync(dev, st);
+      return s;
+    }
+    stage_items(groups, base, static_cast<char*>(ctx->staging));
+    e = cudaMemcpyAsync(base, ctx->staging, upload, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->staging_evt, st);
+    ctx->staging_used = true;
+    if (e != cudaSuccess) {
+      cudaFreeAsync(dev, st);
+      return cuda_fail(ctx, e, "item upload");
+    }
+    // side streams of the context for concurrent groups
+    while ((flags & MR_PLAN_CONCURRENT) && ctx->side.size() < groups.size()) {
+      cudaStream_t ss;
+      cudaEvent_t ev;
+      if (cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(ctx, cudaGetLastError(), "side streams");
+      ctx->side.push_back(ss);
+      ctx->side_join.push_back(ev);
+    }
+    if ((flags & MR_PLAN_CONCURRENT) && !ctx->side_fork &&
+        cudaEventCreateWithFlags(&ctx->side_fork, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(ctx, cudaGetLastError(), "fork event");
+    uint32_t launches = 0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ctx->prof_on) {
+      a = take_event(ctx);
+      b = take_event(ctx);
+      if (a) cudaEventRecord(a, st);
+    }
+    s = enqueue_groups(ctx, groups, base, qoff, dev_status, flags, st, ctx->side, ctx->side_fork, ctx->side_join,
+                       &launches);
+    if (a && b) {
+      cudaEventRecord(b, st);
+      ctx->spans.push_back({0, a, b});
+    }
+    ctx->launches[0] += launches;
+    cudaError_t e2 = cudaFreeAsync(dev, st);
+    if (s) return s;
+    return e2 == cudaSuccess ? MR_OK : cuda_fail(ctx, e2, "cudaFreeAsync");
+  });
+}
+
+mr_status mr_plan_create(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, size_t n, const uint32_t* in,
+                         uint32_t in_stride, uint32_t* out, uint32_t out_stride, uint8_t* dev_status, uint32_t flags,
+                         mr_plan** out_plan) {
+  if (!ctx || !out_plan) return MR_ERR_ARG;
+  *out_plan = nullptr;
+  if (!n || !keys || !ops || !in || !out || !in_stride || !out_stride)
+    return fail(ctx, MR_ERR_ARG, "empty plan, null argument or zero stride");
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    auto plan = std::make_unique<mr_plan>();
+    plan->ctx = ctx;
+    plan->flags = flags;
+    plan->status = dev_status;
+    mr_status s = build_groups(ctx, keys, ops, n, in, in_stride, out, out_stride, plan->groups);
+    if (s) return s;
+    size_t upload = 0;
+    size_t total = layout_groups(ctx, plan->groups, flags, &upload, &plan->queue_off);
+    cudaError_t e = cudaMalloc(&plan->dev, total);
+    if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, std::string("plan allocation failed: ") + cudaGetErrorString(e));
+    plan->dev_bytes = total;
+    std::vector<char> host(upload);
+    stage_items(plan->groups, static_cast<char*>(plan->dev), host.data());
+    e = cudaMemcpy(plan->dev, host.data(), upload, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plan upload");
+    for (auto& g : plan->groups) plan->products += g.work;
+    if (flags & MR_PLAN_CONCURRENT) {
+      for (size_t i = 0; i < plan->groups.size(); i++) {
+        cudaStream_t ss;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+          return cuda_fail(ctx, cudaGetLastError(), "plan streams");
+        plan->side.push_back(ss);
+        plan->joins.push_back(ev);
+      }
+      if (cudaEventCreateWithFlags(&plan->fork, cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(ctx, cudaGetLastError(), "plan fork event");
+    }
+    if (flags & MR_PLAN_GRAPH) {
+      cudaStream_t cap;
+      e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "capture stream");
+      e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return cuda_fail(ctx, e, "begin capture");
+      }
+      uint32_t launches = 0;
+      s = enqueue_groups(ctx, plan->groups, static_cast<char*>(plan->dev), plan->queue_off, plan->status, flags, cap,
+                         plan->side, plan->fork, plan->joins, &launches);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(cap, &graph);
+      cudaStreamDestroy(cap);
+      if (s) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+      plan->graph = graph;
+      e = cudaGraphInstantiate(&plan->exec, graph, 0);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+      plan->kernels = launches;
+    } else {
+      plan->kernels = 0;
+      for (auto& g : plan->groups) plan->kernels += (g.mx.empty() ? 0 : 1) + (g.crt.empty() ? 0 : 1);
+    }
+    *out_plan = plan.release();
+    return MR_OK;
+  });
+}
+
+mr_status mr_plan_launch(mr_plan* plan, void* stream) {
+  if (!plan) return MR_ERR_ARG;
+  mr_ctx* ctx = plan->ctx;
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ctx->prof_on) {
+      a = take_event(ctx);
+      b = take_event(ctx);
+      if (a) cudaEventRecord(a, st);
+    }
+    mr_status s = MR_OK;
+    if (plan->exec) {
+      cudaError_t e = cudaGraphLaunch(plan->exec, st);
+      if (e != cudaSuccess) s = cuda_fail(ctx, e, "graph launch");
+    } else {
+      uint32_t launches = 0;
+      s = enqueue_groups(ctx, plan->groups, static_cast<char*>(plan->dev), plan->queue_off, plan->status, plan->flags, st,
+                         plan->side, plan->fork, plan->joins, &launches);
+    }
+    if (a && b) {
+      cudaEventRecord(b, st);
+      ctx->spans.push_back({0, a, b});
+    }
+    ctx->launches[0] += plan->kernels;
+    return s;
+  });
+}
+
+mr_status mr_plan_info(const mr_plan* plan, uint32_t* kernels, uint32_t* groups, uint64_t* device_bytes,
+                       double* products) {
+  if (!plan) return MR_ERR_ARG;
+  if (kernels) *kernels = plan->kernels;
+  if (groups) *groups = (uint32_t)plan->groups.size();
+  if (device_bytes) *device_bytes = plan->dev_bytes;
+  if (products) *products = plan->products;
+  return MR_OK;
+}
+
+void mr_plan_free(mr_plan* plan) {
+  if (!plan) return;
+  cudaSetDevice(plan->ctx->device);
+  cudaDeviceSynchronize();
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  for (auto s : plan->side) cudaStreamDestroy(s);
+  for (auto ev : plan->joins) cudaEventDestroy(ev);
+  if (plan->fork) cudaEventDestroy(plan->fork);
+  if (plan->dev) cudaFree(plan->dev);
+  delete plan;
 }
 
 mr_status mr_modexp_batch_noalloc(mr_ctx* ctx, const mr_key* key, size_t n, const uint32_t* x, uint32_t x_stride,

@@ -33,13 +33,20 @@ def unit(L, k, W, WX, variants):
         for kind, kern, argt in (("modexp", "modexp_kernel", "LaunchArgs"), ("crt", "crt_kernel", "LaunchArgs"),
                                  ("mr", "mr_kernel", "MRArgs")):
             out += [f"static cudaError_t launch_{kind}_{L}_{v}(const {argt}& a, unsigned grid, cudaStream_t s) {{",
-                    f"  static const cudaError_t attr =",
-                    f"      cudaFuncSetAttribute({kern}<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES);",
-                    "  if (attr != cudaSuccess) return attr;",
                     f"  {kern}<{C}><<<grid, {C}::THREADS, {C}::SMEM_BYTES, s>>>(a);",
                     "  return cudaGetLastError();", "}", ""]
+        out += [f"static cudaError_t prepare_{L}_{v}() {{",
+                "  cudaError_t e = cudaSuccess, r;",
+                f"  if ((r = cudaFuncSetAttribute(modexp_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES)) != cudaSuccess) e = r;",
+                f"  if ((r = cudaFuncSetAttribute(crt_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES)) != cudaSuccess) e = r;",
+                f"  if ((r = cudaFuncSetAttribute(mr_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES)) != cudaSuccess) e = r;",
+                "  return e;", "}", "",
+                f"static int occupancy_{L}_{v}() {{",
+                "  int n = 0;",
+                f"  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<{C}>, {C}::THREADS, {C}::SMEM_BYTES) != cudaSuccess) n = 1;",
+                "  return n > 0 ? n : 1;", "}", ""]
         entries.append(f"     {{{C}::TPI, {C}::THREADS, {C}::IPB, {C}::NPT, {C}::SMEM_BYTES, launch_modexp_{L}_{v}, "
-                       f"launch_crt_{L}_{v}, launch_mr_{L}_{v}}}")
+                       f"launch_crt_{L}_{v}, launch_mr_{L}_{v}, prepare_{L}_{v}, occupancy_{L}_{v}}}")
     out.append(f"extern const ClassKernels kClass{L} = {{")
     out.append(f"    {L}, {k}, {W}, {WX}, {len(variants)},")
     out.append("    {\n" + ",\n".join(entries) + "}};")

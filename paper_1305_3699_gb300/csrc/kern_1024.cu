@@ -7,58 +7,68 @@ namespace mr {
 
 using C1024v0 = Cfg<36, 32, 34, 4, 128, 4>;
 static cudaError_t launch_modexp_1024_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(modexp_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES);
-  if (attr != cudaSuccess) return attr;
   modexp_kernel<C1024v0><<<grid, C1024v0::THREADS, C1024v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 static cudaError_t launch_crt_1024_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(crt_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES);
-  if (attr != cudaSuccess) return attr;
   crt_kernel<C1024v0><<<grid, C1024v0::THREADS, C1024v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 static cudaError_t launch_mr_1024_0(const MRArgs& a, unsigned grid, cudaStream_t s) {
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(mr_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES);
-  if (attr != cudaSuccess) return attr;
   mr_kernel<C1024v0><<<grid, C1024v0::THREADS, C1024v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
+static cudaError_t prepare_1024_0() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(crt_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(mr_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES)) != cudaSuccess) e = r;
+  return e;
+}
+
+static int occupancy_1024_0() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1024v0>, C1024v0::THREADS, C1024v0::SMEM_BYTES) != cudaSuccess) n = 1;
+  return n > 0 ? n : 1;
+}
+
 using C1024v1 = Cfg<36, 32, 34, 8, 128, 4>;
 static cudaError_t launch_modexp_1024_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(modexp_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES);
-  if (attr != cudaSuccess) return attr;
   modexp_kernel<C1024v1><<<grid, C1024v1::THREADS, C1024v1::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 static cudaError_t launch_crt_1024_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(crt_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES);
-  if (attr != cudaSuccess) return attr;
   crt_kernel<C1024v1><<<grid, C1024v1::THREADS, C1024v1::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 static cudaError_t launch_mr_1024_1(const MRArgs& a, unsigned grid, cudaStream_t s) {
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(mr_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES);
-  if (attr != cudaSuccess) return attr;
   mr_kernel<C1024v1><<<grid, C1024v1::THREADS, C1024v1::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
+}
+
+static cudaError_t prepare_1024_1() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(crt_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(mr_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES)) != cudaSuccess) e = r;
+  return e;
+}
+
+static int occupancy_1024_1() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1024v1>, C1024v1::THREADS, C1024v1::SMEM_BYTES) != cudaSuccess) n = 1;
+  return n > 0 ? n : 1;
 }
 
 extern const ClassKernels kClass1024 = {
     1024, 36, 32, 34, 2,
     {
-     {C1024v0::TPI, C1024v0::THREADS, C1024v0::IPB, C1024v0::NPT, C1024v0::SMEM_BYTES, launch_modexp_1024_0, launch_crt_1024_0, launch_mr_1024_0},
-     {C1024v1::TPI, C1024v1::THREADS, C1024v1::IPB, C1024v1::NPT, C1024v1::SMEM_BYTES, launch_modexp_1024_1, launch_crt_1024_1, launch_mr_1024_1}}};
+     {C1024v0::TPI, C1024v0::THREADS, C1024v0::IPB, C1024v0::NPT, C1024v0::SMEM_BYTES, launch_modexp_1024_0, launch_crt_1024_0, launch_mr_1024_0, prepare_1024_0, occupancy_1024_0},
+     {C1024v1::TPI, C1024v1::THREADS, C1024v1::IPB, C1024v1::NPT, C1024v1::SMEM_BYTES, launch_modexp_1024_1, launch_crt_1024_1, launch_mr_1024_1, prepare_1024_1, occupancy_1024_1}}};
 
 }  // namespace mr

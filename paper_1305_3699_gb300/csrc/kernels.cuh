@@ -48,18 +48,14 @@ __device__ __forceinline__ void tab_load(const uint32_t* wt, int ent, uint32_t (
   }
 }
 
+// One exponentiation per lane group (x^e mod N of work item g_raw); all lanes of the warp call it
+// together.  wt: this warp's window-table scratch.
 template <class C>
-__global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
-  extern __shared__ __align__(16) uint32_t smem_raw[];
-  Smem<C> sm{smem_raw};
-  load_class_smem<C>(sm, a.cls);
-  __syncthreads();
-
+__device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& sm, uint32_t g_raw, uint32_t* wt) {
   constexpr int NPT = C::NPT, TPI = C::TPI;
   const int lane = threadIdx.x & 31;
   const int t = threadIdx.x % TPI;
   const int item_in_block = threadIdx.x / TPI;
-  const uint32_t g_raw = blockIdx.x * C::IPB + item_in_block;
   const bool live = g_raw < a.n_items;
   const uint32_t g = live ? g_raw : a.n_items - 1;  // idle groups shadow the last item, write nothing
   const MxItem it = reinterpret_cast<const MxItem*>(a.items)[g];
@@ -67,9 +63,6 @@ __global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
   const uint32_t* key = it.key;
   uint32_t* xib = sm.xi(item_in_block);
   uint32_t* xpb = xib + C::KP;
-  const int warp_global = (blockIdx.x * C::THREADS + threadIdx.x) >> 5;
-  uint32_t* wt = a.scratch + (size_t)warp_global * ((size_t)1 << a.wbits) * (2 * NPT) * 32;
-
   // input range check: x < xlim
   uint32_t bad = 0;
   if (t == 0) bad = less_than(it.x, it.x_limbs, it.xlim, it.xlim_limbs) ? 0u : 1u;
@@ -167,6 +160,30 @@ __global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
     if (bad)
       for (uint32_t w = 0; w < it.out_limbs; w++) it.out[w] = 0u;
     if (a.status && it.status != 0xffffffffu) a.status[it.status] = bad ? 5u : 0u;
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem_raw[];
+  Smem<C> sm{smem_raw};
+  load_class_smem<C>(sm, a.cls);
+  __syncthreads();
+  const int warp_global = (blockIdx.x * C::THREADS + threadIdx.x) >> 5;
+  uint32_t* wt = a.scratch + (size_t)warp_global * ((size_t)1 << a.wbits) * (2 * C::NPT) * 32;
+  if (!a.queue) {
+    modexp_item<C>(a, sm, blockIdx.x * C::IPB + threadIdx.x / C::TPI, wt);
+    return;
+  }
+  // persistent: each warp takes the next group of 32/TPI items (items are ordered by cost, largest first)
+  const uint32_t n_groups = (a.n_items + C::IPW - 1) / C::IPW;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    uint32_t wg = 0;
+    if (lane == 0) wg = atomicAdd(a.queue, 1u);
+    wg = __shfl_sync(0xffffffffu, wg, 0);
+    if (wg >= n_groups) break;
+    modexp_item<C>(a, sm, wg * C::IPW + (lane / C::TPI), wt);
   }
 }
 

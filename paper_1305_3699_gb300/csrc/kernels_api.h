@@ -15,6 +15,7 @@ struct LaunchArgs {
   uint32_t wbits;        // window width (modexp), 1..6
   uint32_t* scratch;     // window tables (modexp): per warp (1 << wbits) x 2 NPT x 32 words
   uint8_t* status;       // per-item status bytes or nullptr
+  uint32_t* queue;       // persistent mode: work-group counter (zeroed before the launch), else nullptr
 };
 
 struct MRArgs {
@@ -38,6 +39,8 @@ struct KernelVariant {
   cudaError_t (*modexp)(const LaunchArgs&, unsigned grid, cudaStream_t);
   cudaError_t (*crt)(const LaunchArgs&, unsigned grid, cudaStream_t);
   cudaError_t (*mr)(const MRArgs&, unsigned grid, cudaStream_t);
+  cudaError_t (*prepare)();  // set kernel attributes (call before any stream capture)
+  int (*occupancy)();        // resident blocks per SM of the exponentiation kernel
 };
 
 constexpr int MAX_VARIANTS = 4;
@@ -56,6 +59,11 @@ inline size_t modexp_scratch_words(const KernelVariant& kc, uint32_t n, uint32_t
   size_t grid = (n + kc.ipb - 1) / kc.ipb;
   size_t warps = grid * (kc.threads / 32);
   return warps * ((size_t)1 << wbits) * 2 * kc.npt * 32;
+}
+
+// scratch words of a persistent launch of `blocks` blocks
+inline size_t persistent_scratch_words(const KernelVariant& kc, uint32_t blocks, uint32_t wbits) {
+  return (size_t)blocks * (kc.threads / 32) * ((size_t)1 << wbits) * 2 * kc.npt * 32;
 }
 
 }  // namespace mr

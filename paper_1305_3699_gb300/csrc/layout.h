@@ -116,7 +116,7 @@ struct MxItem {            // one modular exponentiation
   const uint32_t* xlim;    // x must be below this number (xlim_limbs limbs)
   uint32_t x_limbs, e_limbs, out_limbs, xlim_limbs;
   uint32_t status;         // index into the status array, or 0xffffffff
-  uint32_t pad_;
+  uint32_t pad_;           // host-side bookkeeping only (ignored by the kernels)
 };
 
 struct CrtItem {           // Garner recombination of one CRT decryption

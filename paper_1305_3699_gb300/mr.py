@@ -28,7 +28,14 @@ EXPORTED = [
     "mr_key_info", "mr_key_free", "mr_modexp_batch", "mr_rsa_encrypt", "mr_rsa_decrypt_crt",
     "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
     "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant", "mr_debug_mr_setup",
+    "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
 ]
+
+MR_OP_ENCRYPT = 0
+MR_OP_DECRYPT = 1
+MR_PLAN_CONCURRENT = 1
+MR_PLAN_PERSISTENT = 2
+MR_PLAN_GRAPH = 4
 
 
 class KernelTime(ctypes.Structure):
@@ -71,6 +78,11 @@ def _load() -> ctypes.CDLL:
         "mr_class_variants": (ctypes.c_int, [U32, PU32, PU32, U32]),
         "mr_set_variant": (ctypes.c_int, [P, U32, U32]),
         "mr_debug_mr_setup": (ctypes.c_int, [P, P, U32, SZ, P, P]),
+        "mr_rsa_mixed": (ctypes.c_int, [P, P, P, SZ, P, U32, P, U32, P, U32, P]),
+        "mr_plan_create": (ctypes.c_int, [P, P, P, SZ, P, U32, P, U32, P, U32, ctypes.POINTER(P)]),
+        "mr_plan_launch": (ctypes.c_int, [P, P]),
+        "mr_plan_info": (ctypes.c_int, [P, PU32, PU32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
+        "mr_plan_free": (None, [P]),
         "mr_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelTime), U32]),
     }
     for name, (res, args) in sig.items():
@@ -194,6 +206,31 @@ class KeyList:
         return len(self.keys)
 
 
+class Plan:
+    """A prepared mixed batch (mr_plan_create); launch() enqueues one execution."""
+
+    def __init__(self, ctx: "Context", handle: int, refs):
+        self.ctx, self.handle, self._refs = ctx, handle, refs
+
+    def launch(self, stream=None):
+        self.ctx._check(lib.mr_plan_launch(self.handle, _stream(stream)))
+
+    def info(self):
+        k, g, b, p = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_double()
+        self.ctx._check(lib.mr_plan_info(self.handle, ctypes.byref(k), ctypes.byref(g), ctypes.byref(b), ctypes.byref(p)))
+        return {"kernels": k.value, "groups": g.value, "device_bytes": b.value, "products": p.value}
+
+    def free(self):
+        if self.handle:
+            lib.mr_plan_free(self.handle)
+            self.handle = None
+
+
+def _ops(ops):
+    a = np.ascontiguousarray(np.asarray(ops, dtype=np.uint8))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
 def _keylist(keys) -> KeyList:
     return keys if isinstance(keys, KeyList) else KeyList(keys)
 
@@ -278,6 +315,25 @@ class Context:
         _, ms = _rows(m)
         self._check(lib.mr_rsa_decrypt_crt(self.handle, kl.arr, len(kl), _dev(c), cs, _dev(m), ms, _dev(status),
                                            _stream(stream)))
+
+    def mr_rsa_mixed(self, keys, ops, inp, out, status=None, flags: int = 0, stream=None):
+        """Mixed RSA encryptions / CRT decryptions of any sizes in one call (ops: MR_OP_* per row)."""
+        kl = _keylist(keys)
+        oa, op = _ops(ops)
+        _, is_ = _rows(inp)
+        _, os_ = _rows(out)
+        self._check(lib.mr_rsa_mixed(self.handle, kl.arr, len(kl), op, _dev(inp), is_, _dev(out), os_, _dev(status),
+                                     flags, _stream(stream)))
+
+    def mr_plan_create(self, keys, ops, inp, out, status=None, flags: int = 0) -> Plan:
+        kl = _keylist(keys)
+        oa, op = _ops(ops)
+        _, is_ = _rows(inp)
+        _, os_ = _rows(out)
+        h = ctypes.c_void_p()
+        self._check(lib.mr_plan_create(self.handle, kl.arr, len(kl), op, _dev(inp), is_, _dev(out), os_, _dev(status),
+                                       flags, ctypes.byref(h)))
+        return Plan(self, h.value, (kl, inp, out, status))
 
     def mr_miller_rabin_batch(self, cand, witness, rounds: int, is_prime, round_mask=None, stream=None):
         n, nl = _rows(cand)
