@@ -327,6 +327,99 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# -------------------------------------------------------------- ragged mix
+MIX = ((1024, 4), (2048, 3), (3072, 2), (4096, 1))  # sizes and weights (40/30/20/10%)
+N_RAGGED = 65536
+
+
+def ragged_workload(rank: int = 0, n: int = N_RAGGED):
+    """Requests over the 256 mixed-size keys: size by the 40/30/20/10 mix, key uniform within the
+    size, half encryptions (e = 65537) and half CRT decryptions, inputs uniform in [0, N)."""
+    from synth import SplitMix64, load_keys
+    keys = load_keys("mix_x256")
+    by_bits = {}
+    for i, k in enumerate(keys):
+        by_bits.setdefault(k["bits"], []).append(i)
+    r = SplitMix64(0x4D520004 + 0x1000 * rank)
+    cum = []
+    acc = 0
+    for bits, w in MIX:
+        acc += w
+        cum.append((acc, bits))
+    idx, ops, xs = [], [], []
+    for _ in range(n):
+        u = r.below(acc)
+        bits = next(b for c, b in cum if u < c)
+        pool = by_bits[bits]
+        ki = pool[r.below(len(pool))]
+        idx.append(ki)
+        ops.append(r.below(2))
+        xs.append(r.below(keys[ki]["N"]))
+    return keys, idx, ops, xs
+
+
+def run_ragged(args, rank, world, local_rank):
+    """Ragged batch: one prepared plan per launch mode over the same 65,536 requests."""
+    import torch
+    from paper_1305_3699_gb300 import mr
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    keys, idx, ops, xs = ragged_workload(rank)
+    ctx = mr.Context(local_rank)
+    hk = [ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]) for k in keys]
+    kl = mr.KeyList([hk[i] for i in idx])
+    inp = mr.to_tensor(xs, 128, device=dev)
+    out = torch.zeros_like(inp)
+    status = torch.zeros(len(xs), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    modexps = sum(1 if o == 0 else 2 for o in ops)
+    modes = {"per_size_plain": 0,
+             "ragged_persistent_graph": mr.MR_PLAN_CONCURRENT | mr.MR_PLAN_PERSISTENT | mr.MR_PLAN_GRAPH}
+    res = {}
+    ref = None
+    for name, flags in modes.items():
+        plan = ctx.mr_plan_create(kl, ops, inp, out, status, flags=flags)
+        info = plan.info()
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                plan.launch(stream)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = out.clone()
+        assert torch.equal(out, ref), "launch modes disagree"
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for s in range(args.steps):
+                flush.zero_()
+                evs[s][0].record(stream)
+                plan.launch(stream)
+                evs[s][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        res[name] = {"ms_per_step": ms, "modexp_per_s": modexps / (ms / 1e3), "kernels": info["kernels"],
+                     "groups": info["groups"], "products": info["products"]}
+        plan.free()
+    # spot check against the plain definition
+    got = mr.from_tensor(out[:4])
+    for j in range(4):
+        k = keys[idx[j]]
+        want = pow(xs[j], k["e"] if ops[j] == 0 else k["d"], k["N"])
+        assert got[j] == want
+    rp = res["ragged_persistent_graph"]
+    line = {"metric": METRIC, "value": rp["modexp_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rp["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded keys and inputs)",
+            "config": {"workload": "ragged_mix_65536", "requests": len(xs), "modexps_per_step": modexps,
+                       "keys": 256, "mix_bits": [b for b, _ in MIX], "mix_weights": [w for _, w in MIX],
+                       "l2": "flushed between timed steps (512 MB write)", "modes": res,
+                       "speedup_vs_per_size_plain": res["per_size_plain"]["ms_per_step"] / rp["ms_per_step"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,6 +428,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -347,6 +441,11 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", init_method="env://")
     try:
+        if args.workload == "ragged":
+            return run_ragged(args, rank, world, local_rank)
+        if args.workload == "serving":
+            from paper_1305_3699_gb300.serve import run_serving_bench
+            return run_serving_bench(args, rank, world, local_rank, METRIC, UNIT)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

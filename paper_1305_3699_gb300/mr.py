@@ -322,7 +322,7 @@ class Context:
         oa, op = _ops(ops)
         _, is_ = _rows(inp)
         _, os_ = _rows(out)
-        self._check(lib.mr_rsa_mixed(self.handle, kl.arr, len(kl), op, _dev(inp), is_, _dev(out), os_, _dev(status),
+        self._check(lib.mr_rsa_mixed(self.handle, kl.arr, op, len(kl), _dev(inp), is_, _dev(out), os_, _dev(status),
                                      flags, _stream(stream)))
 
     def mr_plan_create(self, keys, ops, inp, out, status=None, flags: int = 0) -> Plan:
@@ -331,7 +331,7 @@ class Context:
         _, is_ = _rows(inp)
         _, os_ = _rows(out)
         h = ctypes.c_void_p()
-        self._check(lib.mr_plan_create(self.handle, kl.arr, len(kl), op, _dev(inp), is_, _dev(out), os_, _dev(status),
+        self._check(lib.mr_plan_create(self.handle, kl.arr, op, len(kl), _dev(inp), is_, _dev(out), os_, _dev(status),
                                        flags, ctypes.byref(h)))
         return Plan(self, h.value, (kl, inp, out, status))
 
