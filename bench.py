@@ -34,7 +34,10 @@ N_CT = 4096
 KEYSET = "rsa2048_x16"
 SEED = 0x4D520002
 # Peak of the 32x32->64-bit multiply-add pipe: SMs x 64 per clock x max SM clock
-IMAD_PER_CLK_PER_SM = 64
+IMAD_PER_CLK_PER_SM = 64   # int32 multiplies per clock per SM (integer multiply pipe)
+# DRAM bytes (read + write) of one exponentiation launch of this workload from an ncu capture;
+# None until a capture of the current kernel exists
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def log(*a):
@@ -276,17 +279,20 @@ def run_ours(args, rank, world, local_rank):
     if sampler:
         sampler.stop()
 
-    # roofline of the dominant kernel (exponentiation): algorithmic products / kernel time
+    # roofline of the dominant kernel (exponentiation).  Work is counted in int32-multiply ops: one
+    # 32x32->64 product of the method is two of them (low and high word), the unit of the integer
+    # multiply pipe's table rate (64 per clock per SM); the peak is that rate at the maximum SM clock.
+    # The same figure against a measured dependent-free mad.wide.u32 stream is reported beside it.
     (mx_launch, mx_ms), (crt_launch, crt_ms) = prof
     props = torch.cuda.get_device_properties(dev)
     L_half, k = mr.mr_class_for_bits(1024)
-    W, WX = 32, None
+    W = 32
     WX = len(mr.mr_debug_class_table(L_half, "M"))
     prods = 0
     for i in idx:
         for dpq in (keys[i]["dp"], keys[i]["dq"]):
             prods += algorithmic_products_per_modexp(k, W, WX, dpq.bit_length(), 5, 2)
-    per_launch = prods  # one exponentiation launch per step covers all 8192 halves
+    ops_per_launch = 2 * prods  # one exponentiation launch per step covers all 8192 halves
     max_mhz = 2070.0
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -295,12 +301,17 @@ def run_ours(args, rank, world, local_rank):
         pass
     peak = props.multi_processor_count * IMAD_PER_CLK_PER_SM * max_mhz * 1e6
     mx_avg_ms = mx_ms / max(1, mx_launch)
-    achieved = per_launch / (mx_avg_ms / 1e3)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tmul/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "modexp_kernel<k=36,TPI=4>", "kernel_ms": mx_avg_ms,
-                "products_per_launch": per_launch,
-                "peak_def": f"{props.multi_processor_count} SMs x {IMAD_PER_CLK_PER_SM} mad.wide.u32/clk x {max_mhz:.0f} MHz",
+    achieved = ops_per_launch / (mx_avg_ms / 1e3)
+    wide_rate = ctx.mr_imad_peak(0, stream)
+    lo_rate = ctx.mr_imad_peak(1, stream)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T int32-mul/s",
+                "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+                "kernel": f"modexp_kernel<k={k},TPI=4>", "kernel_ms": mx_avg_ms,
+                "int32_mul_ops_per_launch": ops_per_launch, "wide_products_per_launch": prods,
+                "peak_def": f"{props.multi_processor_count} SMs x {IMAD_PER_CLK_PER_SM} int32-mul/clk x "
+                            f"{max_mhz:.0f} MHz (a 32x32->64 product counts 2)",
+                "microbench": {"mad_wide_per_s": wide_rate, "mad_lo_per_s": lo_rate,
+                               "peak_int32_mul_per_s": 2 * wide_rate, "frac": achieved / (2 * wide_rate)},
                 "crt_kernel_ms": crt_ms / max(1, crt_launch)}
     if clocks and clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / (props.multi_processor_count * IMAD_PER_CLK_PER_SM *
@@ -375,6 +386,7 @@ def run_ragged(args, rank, world, local_rank):
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     modexps = sum(1 if o == 0 else 2 for o in ops)
     modes = {"per_size_plain": 0,
+             "ragged_concurrent_graph": mr.MR_PLAN_CONCURRENT | mr.MR_PLAN_GRAPH,
              "ragged_persistent_graph": mr.MR_PLAN_CONCURRENT | mr.MR_PLAN_PERSISTENT | mr.MR_PLAN_GRAPH}
     res = {}
     ref = None

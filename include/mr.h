@@ -264,6 +264,17 @@ mr_status mr_profile_enable(mr_ctx *ctx, int on);
  * read in times[0..n_kinds) (n_kinds <= 2) and reset the counters. */
 mr_status mr_profile_read(mr_ctx *ctx, mr_kernel_time *times, uint32_t n_kinds);
 
+/* Measured integer-multiply throughput of this GPU, the denominator the
+ * exponentiation kernels are compared against: a dependent-free stream of
+ * 32x32 multiply-adds in every lane of every SM, timed with CUDA events on
+ * `stream` (NULL = the default stream).  kind 0: mad.wide.u32 (64-bit product
+ * added to a 64-bit accumulator, the instruction of the channel products and
+ * base-extension dot products); kind 1: mad.lo.u32.  *per_second receives
+ * instructions per second summed over all lanes.  Takes a few milliseconds of
+ * device time; allocates 8 bytes of device memory for the duration.
+ * Errors: MR_ERR_ARG (kind > 1, NULL pointer), MR_ERR_CUDA. */
+mr_status mr_imad_peak(mr_ctx *ctx, uint32_t kind, void *stream, double *per_second);
+
 /* ------------------------------------------------------------ inspection -- */
 
 /* Copy one precomputed table of a size class (or of a key when key != NULL) to

@@ -17,6 +17,7 @@
 #include "kernels_api.h"
 #include "noalloc.h"
 #include "setup.h"
+#include "peak.h"
 
 using namespace mr;
 
@@ -434,8 +435,6 @@ size_t layout_groups(mr_ctx* ctx, std::vector<GroupLaunch>& groups, uint32_t fla
                      size_t* queue_off) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  double total = 0;
-  for (auto& g : groups) total += g.work;
   size_t off = 0;
   for (auto& g : groups) {
     const KernelVariant& kv = g.ce->kv();
@@ -454,9 +453,9 @@ size_t layout_groups(mr_ctx* ctx, std::vector<GroupLaunch>& groups, uint32_t fla
     g.ebits.swap(eb);
     const uint32_t full_grid = (uint32_t)((g.mx.size() + kv.ipb - 1) / kv.ipb);
     if (g.persistent) {
-      double share = total > 0 ? g.work / total : 1.0;
-      uint32_t blocks = (uint32_t)std::floor(share * kv.occupancy() * sms);
-      if (!(flags & MR_PLAN_CONCURRENT)) blocks = (uint32_t)(kv.occupancy() * sms);
+      // a full GPU of resident blocks per group: concurrent groups then fill the SMs that the
+      // tail of an earlier group frees, instead of idling on a fixed share
+      uint32_t blocks = (uint32_t)(kv.occupancy() * sms);
       g.grid = std::max<uint32_t>(1, std::min<uint32_t>(blocks, full_grid));
     } else {
       g.grid = full_grid;
@@ -1189,6 +1188,13 @@ mr_status mr_profile_read(mr_ctx* ctx, mr_kernel_time* times, uint32_t n_kinds) 
   }
   ctx->launches[0] = ctx->launches[1] = 0;
   return err == cudaSuccess ? MR_OK : cuda_fail(ctx, err, "profile events");
+}
+
+mr_status mr_imad_peak(mr_ctx* ctx, uint32_t kind, void* stream, double* per_second) {
+  if (!ctx || !per_second || kind > 1) return fail(ctx, MR_ERR_ARG, "bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = mr::imad_stream_rate(ctx->device, (cudaStream_t)stream, kind == 0, per_second);
+  return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "integer-multiply probe");
 }
 
 mr_status mr_debug_mr_setup(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs, size_t n, uint32_t* dev_out,

@@ -120,30 +120,14 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   uint32_t d = (nwin && !bad) ? exp_digit(it.e, el, (nwin - 1) * wb, wb) : 0u;
   __syncwarp();
   tab_load<C>(wt, d, xb, xp, lane);
-  // one multiplication call site for the whole loop: per window, wb squarings, then (when any
-  // number of the warp has a non-zero digit) one multiplication by the table entry
-  {
-    int widx = (int)nwin - 2, q = 0;
-    bool mul = false;
-    while (widx >= 0) {
-      if (q == 0) {
-        d = bad ? 0u : exp_digit(it.e, el, (uint32_t)widx * wb, wb);
-        mul = __any_sync(0xffffffffu, d != 0);
-      }
-      if (q < wb) {
-#pragma unroll
-        for (int s = 0; s < NPT; s++) {
-          yb[s] = xb[s];
-          yp[s] = xp[s];
-        }
-      } else {
-        tab_load<C>(wt, d, yb, yp, lane);
-      }
+  // per window: wb squarings, then (when any number of the warp has a non-zero digit) one
+  // multiplication by the table entry; a squaring passes x as both operands
+  for (int widx = (int)nwin - 2; widx >= 0; widx--) {
+    for (int q = 0; q < wb; q++) mont_mul<C>(xb, xp, xb, xp, kxi, cmul, cd, sm, xib, xpb, t);
+    d = bad ? 0u : exp_digit(it.e, el, (uint32_t)widx * wb, wb);
+    if (__any_sync(0xffffffffu, d != 0)) {
+      tab_load<C>(wt, d, yb, yp, lane);
       mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
-      if (++q == wb + (mul ? 1 : 0)) {
-        q = 0;
-        widx--;
-      }
     }
   }
 
@@ -171,19 +155,20 @@ __global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
   __syncthreads();
   const int warp_global = (blockIdx.x * C::THREADS + threadIdx.x) >> 5;
   uint32_t* wt = a.scratch + (size_t)warp_global * ((size_t)1 << a.wbits) * (2 * C::NPT) * 32;
-  if (!a.queue) {
-    modexp_item<C>(a, sm, blockIdx.x * C::IPB + threadIdx.x / C::TPI, wt);
-    return;
-  }
-  // persistent: each warp takes the next group of 32/TPI items (items are ordered by cost, largest first)
+  // plain launch: warp w of the grid runs group w once.  Persistent launch: each warp takes the
+  // next group of 32/TPI items from the queue (items are ordered by cost, largest first) until it
+  // is empty.  One call site for both keeps a single copy of the exponentiation code.
   const uint32_t n_groups = (a.n_items + C::IPW - 1) / C::IPW;
   const int lane = threadIdx.x & 31;
   for (;;) {
-    uint32_t wg = 0;
-    if (lane == 0) wg = atomicAdd(a.queue, 1u);
-    wg = __shfl_sync(0xffffffffu, wg, 0);
-    if (wg >= n_groups) break;
+    uint32_t wg = (uint32_t)warp_global;
+    if (a.queue) {
+      if (lane == 0) wg = atomicAdd(a.queue, 1u);
+      wg = __shfl_sync(0xffffffffu, wg, 0);
+      if (wg >= n_groups) break;
+    }
     modexp_item<C>(a, sm, wg * C::IPW + (lane / C::TPI), wt);
+    if (!a.queue) break;
   }
 }
 

@@ -29,6 +29,7 @@ EXPORTED = [
     "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
     "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant", "mr_debug_mr_setup",
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
+    "mr_imad_peak",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -84,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "mr_plan_info": (ctypes.c_int, [P, PU32, PU32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
         "mr_plan_free": (None, [P]),
         "mr_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelTime), U32]),
+        "mr_imad_peak": (ctypes.c_int, [P, U32, P, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -355,6 +357,12 @@ class Context:
         arr = (KernelTime * 2)()
         self._check(lib.mr_profile_read(self.handle, arr, 2))
         return [(arr[i].launches, arr[i].ms) for i in range(2)]
+
+    def mr_imad_peak(self, kind: int = 0, stream=None) -> float:
+        """Measured multiply-adds per second: kind 0 mad.wide.u32, kind 1 mad.lo.u32."""
+        v = ctypes.c_double()
+        self._check(lib.mr_imad_peak(self.handle, kind, _stream(stream), ctypes.byref(v)))
+        return v.value
 
     def mr_debug_table(self, name: str, key: Optional[Key] = None, class_bits: int = 0) -> List[int]:
         cnt = ctypes.c_size_t()
