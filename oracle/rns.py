@@ -51,28 +51,32 @@ def prime_bound(k: int) -> int:
     return min(PRIME_CAP, isqrt(((1 << 64) - 1) // k))
 
 
-def _is_prime_small(n: int) -> bool:
-    if n < 2:
-        return False
-    for p in first_primes(5000):  # primes up to 48611 > sqrt(2^31)
-        if p * p > n:
-            return True
-        if n % p == 0:
-            return n == p
-    return True
-
-
 @lru_cache(maxsize=None)
 def primes_below(bound: int, count: int) -> tuple:
-    """The ``count`` largest primes strictly below ``bound``, in descending order."""
+    """The ``count`` largest primes strictly below ``bound``, in descending order.
+
+    Sieve of Eratosthenes over windows [lo, hi) just below the bound, striking the
+    multiples of every prime up to isqrt(bound); windows move down until enough
+    primes are found."""
+    small = [p for p in first_primes(5000) if p * p < bound]  # up to 48611, enough below 2^31
     out = []
-    n = bound - 1
+    hi = bound
+    span = max(1024, 64 * count)
     while len(out) < count:
-        if n < 3:
+        lo = max(2, hi - span)
+        if hi <= 2:
             raise ValueError("not enough primes below bound")
-        if n % 2 == 1 and _is_prime_small(n):
-            out.append(n)
-        n -= 1
+        alive = [True] * (hi - lo)
+        for p in small:
+            start = max(p * p, ((lo + p - 1) // p) * p)
+            for mult in range(start, hi, p):
+                alive[mult - lo] = False
+        for n in range(hi - 1, lo - 1, -1):
+            if alive[n - lo]:
+                out.append(n)
+                if len(out) == count:
+                    break
+        hi = lo
     return tuple(out)
 
 
@@ -97,8 +101,11 @@ class RNSClass:
 
 
 def class_k(L: int, fixed_bound: Optional[int] = None) -> int:
-    """Smallest k meeting M >= 4 (k+1)^2 2^L and M' >= 2 (k+1) 2^L."""
-    k = 1
+    """Smallest k meeting M >= 4 (k+1)^2 2^L and M' >= 2 (k+1) 2^L.
+
+    Every channel prime is below 2^31, so M < 2^(31k) and M >= 2^L needs k > L/31:
+    the search starts there."""
+    k = max(1, L // 31)
     while True:
         b = fixed_bound if fixed_bound is not None else prime_bound(k)
         pr = primes_below(b, 2 * k)
