@@ -1,7 +1,7 @@
 /*
  * mr.h -- C ABI of the GB300 RNS modular-exponentiation library (libmrmod.so).
  *
- * What it computes.  Batched x^e mod N for odd moduli of up to 4096 bits, RSA
+ * What it computes.  Batched x^e mod N for odd moduli of up to 16384 bits, RSA
  * encryption, RSA decryption through the CRT, and Miller-Rabin rounds.  Numbers
  * are held in a Residue Number System (RNS): residues modulo pairwise coprime
  * primes below 2^31, one base B of k primes plus a second base B' of k primes.
@@ -29,6 +29,14 @@
  *    per item; 0 = ok, otherwise an mr_status code) when dev_status is not NULL.
  *  - A context is not thread-safe: serialise calls on one context.
  *  - No C++ exception crosses this interface.
+ *
+ * Size classes.  Classes up to 4096 bits run one number per group of GPU
+ * lanes and support every call.  The large classes (8192 and 16384 bits) run
+ * one group of 32 numbers across several thread blocks that exchange the base
+ * extension's coefficients through device memory, in one cooperative launch;
+ * they serve mr_modexp_batch and mr_rsa_encrypt.  CRT decryption takes keys of
+ * at most 8192 bits (halves of at most 4096), Miller-Rabin and mixed batches
+ * take at most 4096-bit numbers; larger inputs return MR_ERR_SIZE.
  */
 #ifndef MR_H
 #define MR_H
@@ -71,7 +79,8 @@ void mr_shutdown(mr_ctx *ctx);
 const char *mr_last_error(const mr_ctx *ctx);
 
 /* Size class that holds a modulus of `bits` bits: *class_bits = L (one of 512,
- * 1024, 1536, 2048, 3072, 4096), *k = number of primes in each of B and B'.
+ * 1024, 1536, 2048, 3072, 4096, 8192, 16384), *k = number of primes in each of
+ * B and B'.
  * The primes lie below isqrt((2^64-1)/k) so that k-term dot products of
  * residues fit 64-bit accumulators, and the bases satisfy M >= 4 (k+1)^2 2^L
  * and M' >= 2 (k+1) 2^L, under which every Montgomery product stays below
@@ -117,7 +126,8 @@ mr_status mr_key_free(mr_ctx *ctx, mr_key *key);
  *   e       device, n rows of e_stride limbs, any value (e = 0 gives 1 mod N_i)
  *   out     device, n rows of out_stride limbs; out_stride must hold N_i's limbs;
  *           the result is written in [0, N_i) and zero-padded
- *   dev_status  device, n bytes, or NULL
+ *   dev_status  device, n bytes, or NULL (large classes write MR_ERR_TIMEOUT
+ *               for items left unfinished when a bounded inter-block wait ran out)
  * Errors: MR_ERR_ARG, MR_ERR_SIZE, MR_ERR_OOM, MR_ERR_CUDA. */
 mr_status mr_modexp_batch(mr_ctx *ctx, const mr_key *const *keys, size_t n, const uint32_t *x,
                           uint32_t x_stride, const uint32_t *e, uint32_t e_stride, uint32_t *out,

@@ -26,9 +26,11 @@ namespace {
 struct ClassEntry {
   ClassHost host;
   uint32_t* dev = nullptr;
+  uint32_t* tslice = nullptr;  // large classes: extension matrices by channel slice
   const ClassKernels* kern = nullptr;
   uint32_t variant = 0;  // selected lane mapping
   const KernelVariant& kv() const { return kern->var[variant]; }
+  bool big() const { return kern && kern->big; }
 };
 
 struct KeyEntry {
@@ -126,6 +128,23 @@ mr_status get_class(mr_ctx* ctx, uint32_t L, ClassEntry** out) {
     cudaError_t pe = ce->kern->var[v].prepare();  // kernel attributes, once, outside any capture
     if (pe != cudaSuccess) return cuda_fail(ctx, pe, "kernel attributes");
   }
+  if (ce->big()) {
+    const BigKernel& bk = *ce->kern->big;
+    cudaError_t pe = bk.prepare();
+    if (pe != cudaSuccess) return cuda_fail(ctx, pe, "kernel attributes");
+    // [T1 | T2][slice][row][SC]: the columns of each channel slice contiguous, zero past channel k
+    const uint32_t k = ce->host.k, sc = bk.sc, sl = bk.slices;
+    const ClassOff o = class_offsets(k, ce->host.W, ce->host.WX);
+    std::vector<uint32_t> ts((size_t)2 * sl * k * sc, 0);
+    for (uint32_t m = 0; m < 2; m++)
+      for (uint32_t c = 0; c < sl; c++)
+        for (uint32_t i = 0; i < k; i++)
+          for (uint32_t q = 0; q < sc && c * sc + q < k; q++)
+            ts[(((size_t)m * sl + c) * k + i) * sc + q] = ce->host.block[(m ? o.T2 : o.T1) + (size_t)i * k + c * sc + q];
+    cudaError_t e = cudaMalloc(&ce->tslice, ts.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(ce->tslice, ts.data(), ts.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "class slice tables");
+  }
   {
     // default lane mapping: variant 0, unless MR_VARIANT_<L> names another compiled one
     std::string ev = "MR_VARIANT_" + std::to_string(L);
@@ -170,11 +189,11 @@ void free_key_entry(KeyEntry& ke) {
 }
 
 // window width minimising squarings + multiplications + table size for an exponent of `bits`
-uint32_t choose_window(uint32_t bits, uint32_t popcount_hint) {
+uint32_t choose_window(uint32_t bits, uint32_t popcount_hint, uint32_t max_w = 6) {
   if (bits <= 1) return 1;
   uint64_t best = ~0ull;
   uint32_t bw = 1;
-  for (uint32_t w = 1; w <= 6; w++) {
+  for (uint32_t w = 1; w <= max_w; w++) {
     uint64_t nwin = (bits + w - 1) / w;
     uint64_t mults = (w == 1 && popcount_hint) ? popcount_hint : nwin;
     uint64_t cost = (uint64_t)(nwin - 1) * w + mults + ((1ull << w) - 2);
@@ -201,6 +220,7 @@ struct ClassBatch {
   // offsets (bytes) into the call's device scratch allocation
   size_t off_mx = 0, off_crt = 0, off_scratch = 0, off_half = 0;
   size_t scratch_words = 0;
+  uint32_t slots = 0;  // large class: item groups in flight
 };
 
 // Reserve pinned staging space; waits for the previous upload to finish first.
@@ -265,7 +285,20 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
   }
   size_t total = upload_bytes;
   for (auto& b : batches) {
-    b.scratch_words = b.mx.empty() ? 0 : modexp_scratch_words(b.ce->kv(), (uint32_t)b.mx.size(), b.wbits);
+    if (b.mx.empty()) {
+      b.scratch_words = 0;
+    } else if (b.ce->big()) {
+      // as many groups of 32 in flight as one cooperative launch can hold
+      const BigKernel& bk = *b.ce->kern->big;
+      int sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+      const uint32_t fit = (uint32_t)(bk.occupancy() * sms) / bk.slices;
+      if (fit == 0) return fail(ctx, MR_ERR_CUDA, "large-class kernel does not fit the device");
+      b.slots = std::min<uint32_t>(fit, (uint32_t)((b.mx.size() + 31) / 32));
+      b.scratch_words = (size_t)b.slots * bk.slot_words(b.wbits) + align256((b.slots + 1) * 4) / 4;
+    } else {
+      b.scratch_words = modexp_scratch_words(b.ce->kv(), (uint32_t)b.mx.size(), b.wbits);
+    }
     b.off_scratch = total;
     total = align256(total + b.scratch_words * 4);
   }
@@ -310,6 +343,18 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
     return cuda_fail(ctx, e, "item upload");
   }
   for (auto& b : batches) {
+    if (b.ce->big()) {
+      if (b.mx.empty()) continue;
+      const BigKernel& bk = *b.ce->kern->big;
+      uint32_t* scr = reinterpret_cast<uint32_t*>(base + b.off_scratch);
+      uint32_t* sync = scr + (size_t)b.slots * bk.slot_words(b.wbits);
+      BigArgs a{b.ce->dev, b.ce->tslice, reinterpret_cast<const MxItem*>(base + b.off_mx), (uint32_t)b.mx.size(),
+                b.wbits, scr, status, sync, b.slots};
+      e = cudaMemsetAsync(sync, 0, (b.slots + 1) * 4, stream);
+      if (e == cudaSuccess) e = timed_launch(ctx, 0, stream, [&] { return bk.modexp(a, stream); });
+      if (e != cudaSuccess) break;
+      continue;
+    }
     const KernelVariant& k = b.ce->kv();
     if (!b.mx.empty()) {
       LaunchArgs a{b.ce->dev, base + b.off_mx, (uint32_t)b.mx.size(), b.wbits,
@@ -374,6 +419,7 @@ mr_status build_groups(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* op
     if (out_stride < k->pub.nlimbs()) return fail(ctx, MR_ERR_ARG, "out_stride smaller than a modulus");
     const KeyEntry& pub = k->pub;
     const uint32_t* nlim = pub.dev + key_offsets(pub.cls->host.k, pub.cls->host.W).N;
+    if (pub.cls->big()) return fail(ctx, MR_ERR_SIZE, "mixed batches take keys of at most 4096 bits");
     if (ops[i] == MR_OP_ENCRYPT) {
       if (!k->dev_e) return fail(ctx, MR_ERR_KEY, "key has no public exponent");
       uint32_t eb = (uint32_t)k->e.bits();
@@ -619,8 +665,10 @@ void mr_shutdown(mr_ctx* ctx) {
     if (k->dev_crt) cudaFree(k->dev_crt);
     delete k;
   }
-  for (auto& kv : ctx->classes)
+  for (auto& kv : ctx->classes) {
     if (kv.second->dev) cudaFree(kv.second->dev);
+    if (kv.second->tslice) cudaFree(kv.second->tslice);
+  }
   if (ctx->staging) cudaFreeHost(ctx->staging);
   if (ctx->staging_evt) cudaEventDestroy(ctx->staging_evt);
   for (auto& sp : ctx->spans) {
@@ -799,7 +847,7 @@ mr_status mr_modexp_batch(mr_ctx* ctx, const mr_key* const* keys, size_t n, cons
     }
     for (auto& b : batches) {
       std::stable_sort(b.mx.begin(), b.mx.end(), [](const MxItem& a, const MxItem& c) { return a.key < c.key; });
-      b.wbits = choose_window(32 * e_stride, 0);
+      b.wbits = choose_window(32 * e_stride, 0, b.ce->big() ? 8 : 6);
     }
     return run_batches(ctx, batches, dev_status, (cudaStream_t)stream, 0);
   });
@@ -840,7 +888,7 @@ mr_status mr_rsa_encrypt(mr_ctx* ctx, const mr_key* const* keys, size_t n, const
     }
     for (auto& b : batches) {
       std::stable_sort(b.mx.begin(), b.mx.end(), [](const MxItem& a, const MxItem& c2) { return a.key < c2.key; });
-      b.wbits = choose_window(cost_bits[b.ce], cost_pop[b.ce]);
+      b.wbits = choose_window(cost_bits[b.ce], cost_pop[b.ce], b.ce->big() ? 8 : 6);
     }
     return run_batches(ctx, batches, dev_status, (cudaStream_t)stream, 0);
   });
@@ -871,6 +919,7 @@ mr_status mr_rsa_decrypt_crt(mr_ctx* ctx, const mr_key* const* keys, size_t n, c
       if (!k->priv) return fail(ctx, MR_ERR_KEY, "key has no private CRT parts");
       if (m_stride < k->pub.nlimbs()) return fail(ctx, MR_ERR_ARG, "m_stride smaller than a modulus");
       ClassEntry* ce = k->p.cls;
+      if (ce->big()) return fail(ctx, MR_ERR_SIZE, "CRT decryption takes keys of at most 8192 bits");
       ClassBatch& b = batch_for(batches, idx, ce);
       const KeyOff ko = key_offsets(ce->host.k, ce->host.W);
       const KeyEntry& pub = k->pub;
@@ -921,6 +970,7 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
     ClassEntry* ce = nullptr;
     mr_status s = get_class(ctx, L, &ce);
     if (s) return s;
+    if (ce->big()) return fail(ctx, MR_ERR_SIZE, "Miller-Rabin takes candidates of at most 4096 bits");
     const KernelVariant& k = ce->kv();
     const uint32_t wbits = choose_window(32 * n_limbs, 0);
     const size_t tab_words = modexp_scratch_words(k, (uint32_t)n, wbits);

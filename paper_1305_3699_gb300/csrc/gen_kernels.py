@@ -23,6 +23,37 @@ CLASSES = {
 }
 
 
+# Large classes: several CTAs per group of 32 numbers (big_kernel.cuh).  L: (k, W, WX, NPT, NW)
+BIG = {
+    8192: (295, 256, 258, 4, 8),
+    16384: (599, 512, 513, 4, 8),
+}
+
+
+def big_unit(L, k, W, WX, npt, nw):
+    C = f"CB{L}"
+    return "\n".join([
+        f"// Kernel of the {L}-bit size class (k = {k} channels per base). Generated by gen_kernels.py.",
+        '#include "big_kernel.cuh"', '#include "kernels_api.h"', "", "namespace mr {", "",
+        f"using {C} = BigCfg<{k}, {W}, {WX}, {npt}, {nw}>;",
+        f"static size_t slot_words_{L}(uint32_t wbits) {{ return {C}::slot_words(wbits); }}", "",
+        f"static cudaError_t launch_big_{L}(const BigArgs& a, cudaStream_t s) {{",
+        "  void* args[] = {const_cast<BigArgs*>(&a)};",
+        f"  return cudaLaunchCooperativeKernel((const void*)big_modexp_kernel<{C}>, dim3(a.slots * {C}::SLICES),",
+        f"                                     dim3({C}::THREADS), args, {C}::SMEM_BYTES, s);", "}", "",
+        f"static cudaError_t prepare_big_{L}() {{",
+        f"  return cudaFuncSetAttribute(big_modexp_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES);",
+        "}", "",
+        f"static int occupancy_big_{L}() {{",
+        "  int n = 0;",
+        f"  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big_modexp_kernel<{C}>, {C}::THREADS, {C}::SMEM_BYTES) != cudaSuccess) n = 0;",
+        "  return n;", "}", "",
+        f"static const BigKernel kBig{L} = {{{C}::SC, {C}::SLICES, {C}::THREADS, {C}::SMEM_BYTES, slot_words_{L},",
+        f"                                 launch_big_{L}, prepare_big_{L}, occupancy_big_{L}}};",
+        f"extern const ClassKernels kClass{L} = {{{L}, {k}, {W}, {WX}, 0, {{}}, &kBig{L}}};", "",
+        "}  // namespace mr", ""])
+
+
 def unit(L, k, W, WX, variants):
     out = [f"// Kernels of the {L}-bit size class (k = {k} channels per base). Generated by gen_kernels.py.",
            '#include "kernels.cuh"', '#include "kernels_api.h"', '#include "mr_kernel.cuh"', "", "namespace mr {", ""]
@@ -49,7 +80,8 @@ def unit(L, k, W, WX, variants):
                        f"launch_crt_{L}_{v}, launch_mr_{L}_{v}, prepare_{L}_{v}, occupancy_{L}_{v}}}")
     out.append(f"extern const ClassKernels kClass{L} = {{")
     out.append(f"    {L}, {k}, {W}, {WX}, {len(variants)},")
-    out.append("    {\n" + ",\n".join(entries) + "}};")
+    out.append("    {\n" + ",\n".join(entries) + "},")
+    out.append("    nullptr};")
     out += ["", "}  // namespace mr", ""]
     return "\n".join(out)
 
@@ -58,11 +90,15 @@ def main():
     for L, (k, W, WX, vs) in CLASSES.items():
         with open(os.path.join(HERE, f"kern_{L}.cu"), "w") as f:
             f.write(unit(L, k, W, WX, vs))
+    for L, (k, W, WX, npt, nw) in BIG.items():
+        with open(os.path.join(HERE, f"kern_{L}.cu"), "w") as f:
+            f.write(big_unit(L, k, W, WX, npt, nw))
+    allc = list(CLASSES) + list(BIG)
     reg = ["// Registry of the compiled size classes. Generated by gen_kernels.py.", '#include "kernels_api.h"', "",
            "namespace mr {", ""]
-    reg += [f"extern const ClassKernels kClass{L};" for L in CLASSES]
+    reg += [f"extern const ClassKernels kClass{L};" for L in allc]
     reg += ["", "const ClassKernels* class_kernels(uint32_t L) {", "  switch (L) {"]
-    for L in CLASSES:
+    for L in allc:
         reg += [f"    case {L}:", f"      return &kClass{L};"]
     reg += ["    default:", "      return nullptr;", "  }", "}", "", "}  // namespace mr", ""]
     with open(os.path.join(HERE, "registry.cu"), "w") as f:

@@ -30,6 +30,19 @@ struct MRArgs {
   uint32_t* dbg;            // nullptr, or per candidate mr_debug_words(k, W) words of derived constants
 };
 
+// Exponentiation of a large size class (several CTAs per item group, cooperative launch).
+struct BigArgs {
+  const uint32_t* cls;     // class table block (device)
+  const uint32_t* tslice;  // extension matrices by channel slice: [T1 | T2][slice][k][SC]
+  const MxItem* items;
+  uint32_t n_items;
+  uint32_t wbits;          // window width, 1..8
+  uint32_t* scratch;       // per group slot: slot_words(wbits) words
+  uint8_t* status;         // per-item status bytes or nullptr
+  uint32_t* sync;          // [slots] barrier counters, then the abort flag; zeroed before the launch
+  uint32_t slots;          // item groups in flight (grid = slots * slices)
+};
+
 // [special, s, nbits, 0][M mod N: W][M^2 mod N: W][kxi: k][N M^-1 (plain): k][cd: k][N^-1 mod m_i: k][N^-1 mod m'_j: k]
 MR_HD inline uint32_t mr_debug_words(uint32_t k, uint32_t W) { return 4 + 2 * W + 5 * k; }
 
@@ -45,10 +58,20 @@ struct KernelVariant {
 
 constexpr int MAX_VARIANTS = 4;
 
+// Kernel of a large size class: one cooperative launch of slots * slices CTAs.
+struct BigKernel {
+  uint32_t sc, slices, threads, smem_bytes;
+  size_t (*slot_words)(uint32_t wbits);
+  cudaError_t (*modexp)(const BigArgs&, cudaStream_t);
+  cudaError_t (*prepare)();
+  int (*occupancy)();  // resident CTAs per SM
+};
+
 struct ClassKernels {
   uint32_t L, k, W, WX;
-  uint32_t n_variants;
+  uint32_t n_variants;  // lane-group variants (0 for a large class)
   KernelVariant var[MAX_VARIANTS];
+  const BigKernel* big;  // non-null for a large class
 };
 
 // nullptr when no kernel is compiled for class L

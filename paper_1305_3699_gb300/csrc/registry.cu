@@ -9,6 +9,8 @@ extern const ClassKernels kClass1536;
 extern const ClassKernels kClass2048;
 extern const ClassKernels kClass3072;
 extern const ClassKernels kClass4096;
+extern const ClassKernels kClass8192;
+extern const ClassKernels kClass16384;
 
 const ClassKernels* class_kernels(uint32_t L) {
   switch (L) {
@@ -24,6 +26,10 @@ const ClassKernels* class_kernels(uint32_t L) {
       return &kClass3072;
     case 4096:
       return &kClass4096;
+    case 8192:
+      return &kClass8192;
+    case 16384:
+      return &kClass16384;
     default:
       return nullptr;
   }

@@ -9,6 +9,7 @@
 // (k+1)N) and M' >= 2 (k+1) 2^L (the fixed-point B'->B correction is exact).
 #include "setup.h"
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 
@@ -17,7 +18,7 @@
 namespace mr {
 
 const std::vector<uint32_t>& class_bits_list() {
-  static const std::vector<uint32_t> v = {512, 1024, 1536, 2048, 3072, 4096};
+  static const std::vector<uint32_t> v = {512, 1024, 1536, 2048, 3072, 4096, 8192, 16384};
   return v;
 }
 
@@ -80,7 +81,8 @@ bool build_class(uint32_t L, ClassHost& c, std::string& err) {
     return false;
   }
   Big four_k1sq_2L, two_k1_2L;
-  uint32_t k = 1;
+  // every channel prime is below 2^31, so M < 2^(31k) and M >= 2^L needs k > L/31
+  uint32_t k = std::max<uint32_t>(1, L / 31);
   for (;; k++) {
     if (k > 4096) {
       err = "no base found";

@@ -29,7 +29,7 @@ def test_exports_every_declared_symbol():
     assert sorted(mr.EXPORTED) == syms
 
 
-CLASSES = [512, 1024, 1536, 2048, 3072, 4096]
+CLASSES = [512, 1024, 1536, 2048, 3072, 4096, 8192, 16384]
 
 
 @pytest.mark.parametrize("L", CLASSES)
@@ -55,21 +55,23 @@ def test_class_for_bits_boundaries():
     assert mr.mr_class_for_bits(512)[0] == 512
     assert mr.mr_class_for_bits(513)[0] == 1024
     assert mr.mr_class_for_bits(4096)[0] == 4096
+    assert mr.mr_class_for_bits(4097) == (8192, 295)
+    assert mr.mr_class_for_bits(16384) == (16384, 599)
     with pytest.raises(mr.MRError):
-        mr.mr_class_for_bits(4097)
+        mr.mr_class_for_bits(16385)
 
 
 def _key_cases():
     r = SplitMix64(1234)
     out = []
-    for bits in (3, 64, 511, 512, 700, 1024, 1536, 2048, 3000, 4096):
+    for bits in (3, 64, 511, 512, 700, 1024, 1536, 2048, 3000, 4096, 8000, 16384):
         N = r.randbits(bits) | 1 | (1 << (bits - 1))
         out.append(N)
     out += [k["p"] for k in load_keys("rsa2048_x16")[:2]] + [k["N"] for k in load_keys("rsa1024_x64")[:2]]
     return out
 
 
-@pytest.mark.parametrize("N", _key_cases())
+@pytest.mark.parametrize("N", _key_cases(), ids=lambda N: f"{N.bit_length()}b")
 def test_key_tables_match_model(N):
     L, _ = mr.mr_class_for_bits(N.bit_length())
     c = rns.make_class(L)
@@ -86,7 +88,7 @@ def test_key_setup_errors():
         mr.mr_debug_key_table_host(1 << 100, "kxi")
     assert e.value.code == 2  # MR_ERR_EVEN_MODULUS
     with pytest.raises(mr.MRError) as e:
-        mr.mr_debug_key_table_host((1 << 5000) + 1, "kxi")
+        mr.mr_debug_key_table_host((1 << 16384) + 1, "kxi")
     assert e.value.code == 4  # MR_ERR_SIZE
     c = rns.make_class(512)
     with pytest.raises(mr.MRError) as e:

@@ -1,0 +1,115 @@
+"""GPU parity of the large size classes (8192 and 16384 bits: groups of 32 numbers
+spread over several thread blocks, one cooperative launch).  Every output equals
+the oracle's plain exponentiation bit for bit.  Most exponents are short so the
+oracle and the device finish quickly; a few are full length."""
+import pytest
+
+from oracle import plain
+from synth import SplitMix64, load_keys
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1305_3699_gb300 import mr as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(mr):
+    c = mr.Context(0)
+    yield c
+    c.close()
+
+
+def _run(mr, ctx, handles, Ns, xs, es, W, e_limbs):
+    n = len(xs)
+    x = mr.to_tensor(xs, W)
+    e = mr.to_tensor(es, e_limbs)
+    out = torch.full((n, W), -1, dtype=torch.int32, device="cuda")
+    st = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+    ctx.mr_modexp_batch(handles, x, e, out, st)
+    torch.cuda.synchronize()
+    return mr.from_tensor(out), st.cpu().tolist()
+
+
+def test_modexp_16384_ragged_groups_and_edges(mr, ctx):
+    keys = load_keys("mod16384_x4")
+    handles_all = [ctx.mr_rns_setup(k["N"]) for k in keys]
+    r = SplitMix64(0x4D520003)
+    n = 40  # two groups of 32, the second one partial
+    idx = [i % len(keys) for i in range(n)]
+    Ns = [keys[i]["N"] for i in idx]
+    xs = [r.below(N) for N in Ns]
+    es = [r.randbits(64 + 61 * (j % 7)) for j in range(n)]
+    xs[0], es[0] = 0, 5
+    xs[1], es[1] = 1, r.randbits(300)
+    xs[2], es[2] = Ns[2] - 1, 3
+    xs[3], es[3] = r.below(Ns[3]), 0
+    xs[4], es[4] = r.below(Ns[4]), 1
+    es[5] = r.randbits(16128) | (1 << 16127)  # one full-length exponent (sets the group's window count)
+    got, st = _run(mr, ctx, [handles_all[i] for i in idx], Ns, xs, es, 512, 504)
+    for j in range(n):
+        assert got[j] == plain.modexp(xs[j], es[j], Ns[j]), j
+    assert st == [0] * n
+
+
+def test_modexp_16384_range_status(mr, ctx):
+    keys = load_keys("mod16384_x4")
+    h = ctx.mr_rns_setup(keys[0]["N"])
+    N = keys[0]["N"]
+    xs = [N, N + 1, 7]
+    got, st = _run(mr, ctx, [h] * 3, [N] * 3, xs, [65537] * 3, 512, 1)
+    assert st == [5, 5, 0]
+    assert got[:2] == [0, 0]
+    assert got[2] == pow(7, 65537, N)
+
+
+def test_encrypt_16384_rsa_keys(mr, ctx):
+    keys = load_keys("mod16384_x4")
+    hk = [ctx.mr_rsa_key_setup(k["N"], k["e"]) for k in keys]
+    r = SplitMix64(0x4D520013)
+    msgs = [r.below(k["N"]) for k in keys]
+    m = mr.to_tensor(msgs, 512)
+    c = torch.zeros_like(m)
+    ctx.mr_rsa_encrypt(hk, m, c)
+    torch.cuda.synchronize()
+    got = mr.from_tensor(c)
+    for i, k in enumerate(keys):
+        assert got[i] == plain.rsa_encrypt(msgs[i], k["e"], k["N"]), i
+
+
+def test_modexp_8192_random_moduli(mr, ctx):
+    r = SplitMix64(0x4D520023)
+    Ns = []
+    while len(Ns) < 3:
+        N = r.randbits(8192) | 1 | (1 << 8191)
+        Ns.append(N)
+    hs = [ctx.mr_rns_setup(N) for N in Ns]
+    n = 33
+    idx = [j % 3 for j in range(n)]
+    xs = [r.below(Ns[i]) for i in idx]
+    es = [r.randbits(40 + 97 * (j % 5)) for j in range(n)]
+    es[7] = r.randbits(8192)
+    got, st = _run(mr, ctx, [hs[i] for i in idx], [Ns[i] for i in idx], xs, es, 256, 256)
+    for j in range(n):
+        assert got[j] == plain.modexp(xs[j], es[j], Ns[idx[j]]), j
+    assert st == [0] * n
+
+
+def test_large_class_unsupported_calls(mr, ctx):
+    k = load_keys("mod16384_x4")[0]
+    h = ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"])
+    c = mr.to_tensor([5], 512)
+    m = torch.zeros_like(c)
+    with pytest.raises(mr.MRError) as e:
+        ctx.mr_rsa_decrypt_crt([h], c, m)
+    assert e.value.code == 4  # MR_ERR_SIZE: CRT halves of 8192 bits
+    with pytest.raises(mr.MRError) as e:
+        ctx.mr_rsa_mixed([h], [0], c, m)
+    assert e.value.code == 4
