@@ -35,9 +35,14 @@ KEYSET = "rsa2048_x16"
 SEED = 0x4D520002
 # Peak of the 32x32->64-bit multiply-add pipe: SMs x 64 per clock x max SM clock
 IMAD_PER_CLK_PER_SM = 64   # int32 multiplies per clock per SM (integer multiply pipe)
-# DRAM bytes (read + write) of one exponentiation launch of this workload from an ncu capture;
-# None until a capture of the current kernel exists
-TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) of one exponentiation launch of the RSA-2048 CRT workload, from an ncu
+# capture of the current kernel on this workload (dram__bytes_read.sum + dram__bytes_write.sum)
+TRAFFIC_BYTES_PER_LAUNCH = 2_626_304 + 23_122_688
+# long-exponent workload: 256 exponentiations modulo 16384-bit RSA moduli with 16128-bit exponents
+BIG_KEYSET = "mod16384_x4"
+BIG_N = 256
+BIG_EBITS = 16128
+BIG_SEED = 0x4D520003
 
 
 def log(*a):
@@ -168,9 +173,95 @@ def oracle_throughput(keys, idx, cts, seconds: float, steps: int = 1, warmup: in
     return value, cores, desc, times
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time: every rank's work counts, the whole job ends with the last one."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sm_max_mhz() -> float:
+    """Maximum SM clock: MEASURED_PEAKS.json's figure when present, else the GB300 maximum."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError):
+        return 2070.0
+
+
+def window_for_bits(bits: int, max_w: int = 5) -> int:
+    """The library's window width for an exponent of `bits` bits: minimises squarings +
+    multiplications + table entries over w = 1..max_w (5 for the lane-group classes, 8 for the
+    large ones, lower when MR_MAX_WINDOW is set)."""
+    cap = os.environ.get("MR_MAX_WINDOW")
+    if cap and cap.isdigit() and 1 <= int(cap) < max_w:
+        max_w = int(cap)
+    if bits <= 1:
+        return 1
+    best, bw = None, 1
+    for w in range(1, max_w + 1):
+        nwin = (bits + w - 1) // w
+        cost = (nwin - 1) * w + nwin + (1 << w) - 2
+        if best is None or cost < best:
+            best, bw = cost, w
+    return bw
+
+
+def big_workload(rank: int = 0, ebits: int = BIG_EBITS):
+    from synth import SplitMix64, load_keys
+    keys = load_keys(BIG_KEYSET)
+    r = SplitMix64(BIG_SEED + 0x1000 * rank)
+    idx = [i % len(keys) for i in range(BIG_N)]
+    xs = [r.below(keys[i]["N"]) for i in idx]
+    es = [r.randbits(ebits - 1) | (1 << (ebits - 1)) for _ in range(BIG_N)]
+    return keys, idx, xs, es
+
+
+def _oracle_modexp_chunk(args):
+    from oracle import plain
+    t0 = time.perf_counter()
+    out = [plain.modexp(x, e, N) for (x, e, N) in args]
+    return time.perf_counter() - t0, len(out)
+
+
+def oracle_big_throughput(keys, idx, xs, es, steps: int = 1, warmup: int = 0):
+    """The oracle's exponentiation on every host core, one item per core per step."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    n = min(len(xs), cores)
+    tasks = [[(xs[j], es[j], keys[idx[j]]["N"])] for j in range(n)]
+    times = []
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for s in range(warmup + steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_modexp_chunk, tasks)
+            if s >= warmup:
+                times.append(time.perf_counter() - t0)
+    value = n / statistics.mean(times)
+    desc = (f"first {n} of the {len(xs)} items of the workload (16384-bit moduli, 16128-bit exponents), "
+            f"oracle.plain.modexp, one item per process on {cores} processes")
+    return value, cores, desc, times
+
+
 # --------------------------------------------------------------- reference
 def run_reference(args, rank, world):
     if rank != 0:
+        return 0
+    if args.workload == "modexp16384":
+        keys, idx, xs, es = big_workload(0)
+        value, cores, desc, times = oracle_big_throughput(keys, idx, xs, es, steps=args.steps, warmup=args.warmup)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int (Python)", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": "modexp16384_long_exponent", "items": BIG_N, "sample_per_step": desc},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return 0
     keys, idx, cts = workload(0)
     budget = max(4.0, 90.0 / max(1, args.steps + args.warmup))
@@ -251,11 +342,7 @@ def run_ours(args, rank, world, local_rank):
     t_wall1 = time.time()
     prof = ctx.mr_profile_read()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     value = 2 * N_CT * world * args.steps / (total_ms / 1e3)
 
     # end to end through the C ABI with host buffers: H2D of the ciphertexts, the call, D2H of the plaintexts
@@ -288,17 +375,13 @@ def run_ours(args, rank, world, local_rank):
     L_half, k = mr.mr_class_for_bits(1024)
     W = 32
     WX = len(mr.mr_debug_class_table(L_half, "M"))
+    w = window_for_bits(max(max(keys[i]["dp"].bit_length(), keys[i]["dq"].bit_length()) for i in idx))
     prods = 0
     for i in idx:
         for dpq in (keys[i]["dp"], keys[i]["dq"]):
-            prods += algorithmic_products_per_modexp(k, W, WX, dpq.bit_length(), 5, 2)
+            prods += algorithmic_products_per_modexp(k, W, WX, dpq.bit_length(), w, 2)
     ops_per_launch = 2 * prods  # one exponentiation launch per step covers all 8192 halves
-    max_mhz = 2070.0
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            max_mhz = float(json.load(f).get("sm_max_mhz", max_mhz))
-    except (OSError, ValueError):
-        pass
+    max_mhz = sm_max_mhz()
     peak = props.multi_processor_count * IMAD_PER_CLK_PER_SM * max_mhz * 1e6
     mx_avg_ms = mx_ms / max(1, mx_launch)
     achieved = ops_per_launch / (mx_avg_ms / 1e3)
@@ -324,7 +407,7 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic (seeded keys and ciphertexts)",
             "config": {"workload": "rsa2048_crt_decrypt", "ciphertexts_per_gpu": N_CT, "keys": 16,
                        "modexps_per_step_per_gpu": 2 * N_CT, "decrypt_per_s": value / 2,
-                       "k": k, "window": 5, "l2": "flushed between timed steps (512 MB write)",
+                       "k": k, "window": w, "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"items partitioned over {world} GPU(s)"},
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -432,6 +515,124 @@ def run_ragged(args, rank, world, local_rank):
     return 0
 
 
+def run_big(args, rank, world, local_rank):
+    """Long-exponent workload: 256 exponentiations x^e mod N over four 16384-bit RSA moduli with
+    uniform 16128-bit exponents, one mr_modexp_batch call per step (the 16384-bit class runs as
+    one cooperative launch of 8 groups x 19 channel slices)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1305_3699_gb300 import mr
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    keys, idx, xs, es = big_workload(rank, args.ebits)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        log("timing the CPU oracle on a bounded sample ...")
+        v, cores, desc, _ = oracle_big_throughput(keys, idx, xs, es)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    ctx = mr.Context(local_rank)
+    hk = [ctx.mr_rns_setup(k["N"]) for k in keys]
+    kl = mr.KeyList([hk[i] for i in idx])
+    W, EL = 512, (args.ebits + 31) // 32
+    x_dev = mr.to_tensor(xs, W, device=dev)
+    e_dev = mr.to_tensor(es, EL, device=dev)
+    out = torch.zeros_like(x_dev)
+    status = torch.zeros(BIG_N, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.mr_modexp_batch(kl, x_dev, e_dev, out, status, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    got = mr.from_tensor(out[:2])
+    for j in range(2):
+        assert got[j] == pow(xs[j], es[j], keys[idx[j]]["N"]), "benchmark output mismatch"
+    assert int(status.sum()) == 0
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    gpu_index = vis[local_rank] if local_rank < len(vis) else (vis[0] if vis else str(local_rank))
+    sampler = ClockSampler(gpu_index) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    ctx.mr_profile_enable(True)
+    ctx.mr_profile_read()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.zero_()
+            evs[s][0].record(stream)
+            step()
+            evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall1 = time.time()
+    prof = ctx.mr_profile_read()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
+    value = BIG_N * world * args.steps / (total_ms / 1e3)
+    # end to end: H2D of bases and exponents, the call, D2H of the results
+    x_host, e_host = x_dev.cpu().pin_memory(), e_dev.cpu().pin_memory()
+    o_host = torch.empty_like(x_host).pin_memory()
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for _ in range(max(2, args.steps // 2)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            x_dev.copy_(x_host, non_blocking=True)
+            e_dev.copy_(e_host, non_blocking=True)
+            step()
+            o_host.copy_(out, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_val = BIG_N * world / (statistics.mean(e2e_ms) / 1e3)
+    clocks = sampler.summary(t_wall0, t_wall1) if sampler else None
+    if sampler:
+        sampler.stop()
+    L, k = mr.mr_class_for_bits(16384)
+    WX = len(mr.mr_debug_class_table(L, "M"))
+    w = window_for_bits(args.ebits, 8)
+    prods = sum(algorithmic_products_per_modexp(k, W, WX, e.bit_length(), w, 1) for e in es)
+    (mx_launch, mx_ms), _ = prof
+    mx_avg_ms = mx_ms / max(1, mx_launch)
+    props = torch.cuda.get_device_properties(dev)
+    max_mhz = sm_max_mhz()
+    peak = props.multi_processor_count * IMAD_PER_CLK_PER_SM * max_mhz * 1e6
+    achieved = 2 * prods / (mx_avg_ms / 1e3)
+    wide_rate = ctx.mr_imad_peak(0, stream)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T int32-mul/s",
+                "frac": achieved / peak, "traffic": None, "kernel": f"big_modexp_kernel<k={k}, 8 warps x 4 channels>",
+                "kernel_ms": mx_avg_ms, "int32_mul_ops_per_launch": 2 * prods, "window": w,
+                "peak_def": f"{props.multi_processor_count} SMs x {IMAD_PER_CLK_PER_SM} int32-mul/clk x "
+                            f"{max_mhz:.0f} MHz (a 32x32->64 product counts 2)",
+                "microbench": {"mad_wide_per_s": wide_rate, "peak_int32_mul_per_s": 2 * wide_rate,
+                               "frac": achieved / (2 * wide_rate)}}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic (seeded 16384-bit RSA moduli, bases and exponents)",
+                "config": {"workload": "modexp16384_long_exponent", "items_per_gpu": BIG_N, "keys": len(keys),
+                           "modulus_bits": 16384, "exponent_bits": args.ebits, "k": k,
+                           "l2": "flushed between timed steps (512 MB write)",
+                           "parallelism": f"items partitioned over {world} GPU(s)"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int((x_host.numel() + e_host.numel()) * 4),
+                        "d2h_bytes_per_step": int(o_host.numel() * 4)},
+                "clocks": clocks, "gpu_launches": prof[0][0] + prof[1][0]}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -440,7 +641,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving"])
+    ap.add_argument("--ebits", type=int, default=BIG_EBITS,
+                    help="exponent bits of the modexp16384 workload (smaller values for profiling runs)")
+    ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving", "modexp16384"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -455,6 +658,8 @@ def main():
     try:
         if args.workload == "ragged":
             return run_ragged(args, rank, world, local_rank)
+        if args.workload == "modexp16384":
+            return run_big(args, rank, world, local_rank)
         if args.workload == "serving":
             from paper_1305_3699_gb300.serve import run_serving_bench
             return run_serving_bench(args, rank, world, local_rank, METRIC, UNIT)

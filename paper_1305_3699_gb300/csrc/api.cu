@@ -189,7 +189,20 @@ void free_key_entry(KeyEntry& ke) {
 }
 
 // window width minimising squarings + multiplications + table size for an exponent of `bits`
-uint32_t choose_window(uint32_t bits, uint32_t popcount_hint, uint32_t max_w = 6) {
+// Largest window width a call may use: 5 for the lane-group classes (one table per number: at
+// w = 6 the tables of a large batch outgrow L2, which costs more than the two multiplications
+// w = 6 saves on a 1024-bit exponent), 8 for the large classes (tables per group slot only);
+// lowered by MR_MAX_WINDOW when set (1..8).
+uint32_t window_cap(bool big) {
+  uint32_t cap = big ? 8u : 5u;
+  if (const char* v = getenv("MR_MAX_WINDOW")) {
+    int w = atoi(v);
+    if (w >= 1 && (uint32_t)w < cap) cap = (uint32_t)w;
+  }
+  return cap;
+}
+
+uint32_t choose_window(uint32_t bits, uint32_t popcount_hint, uint32_t max_w = window_cap(false)) {
   if (bits <= 1) return 1;
   uint64_t best = ~0ull;
   uint32_t bw = 1;
@@ -847,7 +860,7 @@ mr_status mr_modexp_batch(mr_ctx* ctx, const mr_key* const* keys, size_t n, cons
     }
     for (auto& b : batches) {
       std::stable_sort(b.mx.begin(), b.mx.end(), [](const MxItem& a, const MxItem& c) { return a.key < c.key; });
-      b.wbits = choose_window(32 * e_stride, 0, b.ce->big() ? 8 : 6);
+      b.wbits = choose_window(32 * e_stride, 0, window_cap(b.ce->big()));
     }
     return run_batches(ctx, batches, dev_status, (cudaStream_t)stream, 0);
   });
@@ -888,7 +901,7 @@ mr_status mr_rsa_encrypt(mr_ctx* ctx, const mr_key* const* keys, size_t n, const
     }
     for (auto& b : batches) {
       std::stable_sort(b.mx.begin(), b.mx.end(), [](const MxItem& a, const MxItem& c2) { return a.key < c2.key; });
-      b.wbits = choose_window(cost_bits[b.ce], cost_pop[b.ce], b.ce->big() ? 8 : 6);
+      b.wbits = choose_window(cost_bits[b.ce], cost_pop[b.ce], window_cap(b.ce->big()));
     }
     return run_batches(ctx, batches, dev_status, (cudaStream_t)stream, 0);
   });

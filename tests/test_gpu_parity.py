@@ -159,7 +159,7 @@ def test_setup_errors(mr, ctx):
         ctx.mr_rns_setup(1 << 300)
     assert e.value.code == 2
     with pytest.raises(mr.MRError) as e:
-        ctx.mr_rns_setup((1 << 4200) + 1)
+        ctx.mr_rns_setup((1 << 16384) + 1)
     assert e.value.code == 4
     k = load_keys("test_small")[0]
     with pytest.raises(mr.MRError):
