@@ -12,14 +12,16 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-# L: (k, W, WX, [(TPI, THREADS, VEC), ...])
+# L: (k, W, WX, [(TPI, THREADS, VEC, MINB), ...]).  MINB is the exponentiation kernel's minimum
+# resident blocks per SM (its register budget, 0 = compiler's choice), picked per variant by timing
+# each value on 1024-16384 numbers of the class with full-length exponents.
 CLASSES = {
-    512: (18, 16, 17, [(2, 128, 4), (4, 128, 4)]),
-    1024: (36, 32, 34, [(4, 128, 4), (8, 128, 4)]),
-    1536: (54, 48, 50, [(8, 128, 4)]),
-    2048: (72, 64, 66, [(8, 128, 4), (16, 128, 4)]),
-    3072: (108, 96, 97, [(16, 256, 4)]),
-    4096: (145, 128, 129, [(16, 384, 2)]),
+    512: (18, 16, 17, [(2, 128, 4, 2), (4, 128, 4, 4)]),
+    1024: (36, 32, 34, [(4, 128, 4, 3), (8, 128, 4, 4)]),
+    1536: (54, 48, 50, [(8, 128, 4, 4)]),
+    2048: (72, 64, 66, [(8, 128, 4, 0), (16, 128, 4, 4)]),
+    3072: (108, 96, 97, [(16, 256, 4, 2)]),
+    4096: (145, 128, 129, [(16, 384, 2, 1)]),
 }
 
 
@@ -58,9 +60,9 @@ def unit(L, k, W, WX, variants):
     out = [f"// Kernels of the {L}-bit size class (k = {k} channels per base). Generated by gen_kernels.py.",
            '#include "kernels.cuh"', '#include "kernels_api.h"', '#include "mr_kernel.cuh"', "", "namespace mr {", ""]
     entries = []
-    for v, (tpi, th, vec) in enumerate(variants):
+    for v, (tpi, th, vec, minb) in enumerate(variants):
         C = f"C{L}v{v}"
-        out.append(f"using {C} = Cfg<{k}, {W}, {WX}, {tpi}, {th}, {vec}>;")
+        out.append(f"using {C} = Cfg<{k}, {W}, {WX}, {tpi}, {th}, {vec}, {minb}>;")
         for kind, kern, argt in (("modexp", "modexp_kernel", "LaunchArgs"), ("crt", "crt_kernel", "LaunchArgs"),
                                  ("mr", "mr_kernel", "MRArgs")):
             out += [f"static cudaError_t launch_{kind}_{L}_{v}(const {argt}& a, unsigned grid, cudaStream_t s) {{",

@@ -5,7 +5,7 @@
 
 namespace mr {
 
-using C1024v0 = Cfg<36, 32, 34, 4, 128, 4>;
+using C1024v0 = Cfg<36, 32, 34, 4, 128, 4, 3>;
 static cudaError_t launch_modexp_1024_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   modexp_kernel<C1024v0><<<grid, C1024v0::THREADS, C1024v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
@@ -35,7 +35,7 @@ static int occupancy_1024_0() {
   return n > 0 ? n : 1;
 }
 
-using C1024v1 = Cfg<36, 32, 34, 8, 128, 4>;
+using C1024v1 = Cfg<36, 32, 34, 8, 128, 4, 4>;
 static cudaError_t launch_modexp_1024_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   modexp_kernel<C1024v1><<<grid, C1024v1::THREADS, C1024v1::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();

@@ -5,7 +5,7 @@
 
 namespace mr {
 
-using C512v0 = Cfg<18, 16, 17, 2, 128, 4>;
+using C512v0 = Cfg<18, 16, 17, 2, 128, 4, 2>;
 static cudaError_t launch_modexp_512_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   modexp_kernel<C512v0><<<grid, C512v0::THREADS, C512v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
@@ -35,7 +35,7 @@ static int occupancy_512_0() {
   return n > 0 ? n : 1;
 }
 
-using C512v1 = Cfg<18, 16, 17, 4, 128, 4>;
+using C512v1 = Cfg<18, 16, 17, 4, 128, 4, 4>;
 static cudaError_t launch_modexp_512_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   modexp_kernel<C512v1><<<grid, C512v1::THREADS, C512v1::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();

@@ -148,7 +148,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
 }
 
 template <class C>
-__global__ void __launch_bounds__(C::THREADS) modexp_kernel(LaunchArgs a) {
+__global__ void __launch_bounds__(C::THREADS, C::MINB) modexp_kernel(LaunchArgs a) {
   extern __shared__ __align__(16) uint32_t smem_raw[];
   Smem<C> sm{smem_raw};
   load_class_smem<C>(sm, a.cls);

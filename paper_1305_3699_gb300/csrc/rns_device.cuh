@@ -57,8 +57,10 @@ __device__ __forceinline__ void mac96(uint32_t& s0, uint32_t& s1, uint32_t& s2, 
       : "r"(a), "r"(b));
 }
 
-template <int K_, int W_, int WX_, int TPI_, int THREADS_, int VEC_>
+template <int K_, int W_, int WX_, int TPI_, int THREADS_, int VEC_, int MINB_ = 0>
 struct Cfg {
+  static constexpr int MINB = MINB_;             // exponentiation kernel's minimum resident blocks per SM
+                                                  // (register budget; 0 leaves the choice to the compiler)
   static constexpr int K = K_;                    // channels per base
   static constexpr int W = W_;                    // limbs of the class bound
   static constexpr int WX = WX_;                  // limbs of k*M (RNS -> binary)
