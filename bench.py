@@ -468,6 +468,20 @@ def run_ragged(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     modexps = sum(1 if o == 0 else 2 for o in ops)
+    # every mode runs the same tuned kernels: tune each size class of the mix once, with its item
+    # count and longest exponent in this workload
+    per_class = {}
+    for i, o in zip(idx, ops):
+        k = keys[i]
+        L = mr.mr_class_for_bits(k["N"].bit_length() if o == 0 else k["p"].bit_length())[0]
+        ebits = k["e"].bit_length() if o == 0 else max(k["dp"].bit_length(), k["dq"].bit_length())
+        c = per_class.setdefault(L, [0, 0])
+        c[0] += 1 if o == 0 else 2
+        c[1] = max(c[1], ebits)
+    tuning = {}
+    if not args.no_autotune:
+        for L, (cnt, eb) in sorted(per_class.items()):
+            tuning[L] = ctx.mr_autotune(L, max(256, min(cnt, 8192)), eb)
     modes = {"per_size_plain": 0,
              "ragged_concurrent_graph": mr.MR_PLAN_CONCURRENT | mr.MR_PLAN_GRAPH,
              "ragged_persistent_graph": mr.MR_PLAN_CONCURRENT | mr.MR_PLAN_PERSISTENT | mr.MR_PLAN_GRAPH}
@@ -508,6 +522,7 @@ def run_ragged(args, rank, world, local_rank):
             "config": {"workload": "ragged_mix_65536", "requests": len(xs), "modexps_per_step": modexps,
                        "keys": 256, "mix_bits": [b for b, _ in MIX], "mix_weights": [w for _, w in MIX],
                        "l2": "flushed between timed steps (512 MB write)", "modes": res,
+                       "autotune": {str(L): v for L, v in tuning.items()},
                        "speedup_vs_per_size_plain": res["per_size_plain"]["ms_per_step"] / rp["ms_per_step"]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -640,6 +655,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="ragged workload: keep the default configurations")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ebits", type=int, default=BIG_EBITS,
                     help="exponent bits of the modexp16384 workload (smaller values for profiling runs)")

@@ -159,22 +159,27 @@ enum { MR_OP_ENCRYPT = 0, MR_OP_DECRYPT = 1 };
  *   MR_PLAN_CONCURRENT   the groups run at the same time, one stream each
  *   MR_PLAN_PERSISTENT   each group runs as a persistent kernel whose warps take
  *                        work from a device queue (items ordered by exponent length,
- *                        longest first), with a grid sized to the group's share of
- *                        the total work
+ *                        longest first), with a grid of one full GPU of resident
+ *                        blocks, so that concurrent groups fill the SMs an earlier
+ *                        group's tail frees
  *   MR_PLAN_GRAPH        (plans only) the launch sequence is captured once in a CUDA
- *                        graph and replayed by mr_plan_launch */
+ *                        graph and replayed by mr_plan_launch
+ *   MR_PLAN_AUTOTUNE     before grouping, every size class of the batch that has not
+ *                        been tuned on this context is tuned by mr_autotune with the
+ *                        batch's item count and longest exponent of that class */
 #define MR_PLAN_CONCURRENT 1u
 #define MR_PLAN_PERSISTENT 2u
 #define MR_PLAN_GRAPH 4u
+#define MR_PLAN_AUTOTUNE 8u
 
 /* One call over RSA requests of any sizes and keys (Sec. 3.3: encryption and
  * decryption by modular exponentiation; decryption here through the CRT):
  * out[i] = in[i]^e mod N_i when ops[i] == MR_OP_ENCRYPT, in[i]^d mod N_i when
  * ops[i] == MR_OP_DECRYPT (keys need private parts).  keys, ops: host arrays of
  * n; in, out: device rows (strides in limbs; out_stride must hold every
- * modulus); dev_status as mr_modexp_batch; flags: MR_PLAN_CONCURRENT and/or
- * MR_PLAN_PERSISTENT (MR_PLAN_GRAPH is ignored).  Results do not depend on the
- * flags.  Errors as mr_rsa_decrypt_crt. */
+ * modulus); dev_status as mr_modexp_batch; flags: MR_PLAN_CONCURRENT,
+ * MR_PLAN_PERSISTENT, MR_PLAN_AUTOTUNE (MR_PLAN_GRAPH is ignored).  Results do not
+ * depend on the flags.  Errors as mr_rsa_decrypt_crt. */
 mr_status mr_rsa_mixed(mr_ctx *ctx, const mr_key *const *keys, const uint8_t *ops, size_t n, const uint32_t *in,
                        uint32_t in_stride, uint32_t *out, uint32_t out_stride, uint8_t *dev_status, uint32_t flags,
                        void *stream);
@@ -256,6 +261,30 @@ mr_status mr_class_variants(uint32_t class_bits, uint32_t *count, uint32_t *lane
  * (variant < count of mr_class_variants; variant 0 is the default).  Results do
  * not depend on the choice, only speed does.  Errors: MR_ERR_ARG, MR_ERR_SIZE. */
 mr_status mr_set_variant(mr_ctx *ctx, uint32_t class_bits, uint32_t variant);
+
+/* Result of mr_autotune. */
+typedef struct {
+  uint32_t variant;          /* chosen lane mapping (as for mr_set_variant; 0 for the large classes) */
+  uint32_t lanes_per_number; /* its lanes per number (0 for the large classes) */
+  uint32_t window;           /* chosen window-width cap */
+  uint32_t configs;          /* configurations timed */
+  double ms;                 /* device time of one call with the chosen configuration */
+  double ms_default;         /* the same with variant 0 and the default window rule */
+} mr_tune_result;
+
+/* Measure, on this context's GPU, every compiled lane mapping of the size class
+ * holding `class_bits`-bit moduli together with the window widths up to the
+ * exponent-length optimum (at most 6, or 8 for the large classes), on a
+ * synthetic batch of n_items exponentiations with exp_bits-bit exponents
+ * modulo a seeded class_bits-bit modulus (one call per configuration after a
+ * warm-up, best of two), and make the fastest the class's configuration on
+ * this context (lane mapping as mr_set_variant; window width as a cap on the
+ * default rule).  Results of later calls do not depend on the choice, only
+ * their speed.  Synchronous; allocates about n_items * (class limbs * 8 +
+ * exponent limbs * 4) bytes of device memory for the duration.  res may be
+ * NULL.  Errors: MR_ERR_ARG (n_items or exp_bits zero, n_items > 2^20,
+ * exp_bits > 65536), MR_ERR_SIZE, MR_ERR_OOM, MR_ERR_CUDA. */
+mr_status mr_autotune(mr_ctx *ctx, uint32_t class_bits, uint32_t n_items, uint32_t exp_bits, mr_tune_result *res);
 
 /* --------------------------------------------------------- instrumentation -- */
 

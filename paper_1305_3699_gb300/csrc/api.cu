@@ -29,6 +29,8 @@ struct ClassEntry {
   uint32_t* tslice = nullptr;  // large classes: extension matrices by channel slice
   const ClassKernels* kern = nullptr;
   uint32_t variant = 0;  // selected lane mapping
+  uint32_t wcap = 0;     // window-width cap chosen by mr_autotune (0 = the default rule)
+  bool tuned = false;
   const KernelVariant& kv() const { return kern->var[variant]; }
   bool big() const { return kern && kern->big; }
 };
@@ -191,10 +193,11 @@ void free_key_entry(KeyEntry& ke) {
 // window width minimising squarings + multiplications + table size for an exponent of `bits`
 // Largest window width a call may use: 5 for the lane-group classes (one table per number: at
 // w = 6 the tables of a large batch outgrow L2, which costs more than the two multiplications
-// w = 6 saves on a 1024-bit exponent), 8 for the large classes (tables per group slot only);
-// lowered by MR_MAX_WINDOW when set (1..8).
-uint32_t window_cap(bool big) {
-  uint32_t cap = big ? 8u : 5u;
+// w = 6 saves on a 1024-bit exponent), 8 for the large classes (tables per group slot only), or
+// the class's cap chosen by mr_autotune; lowered by MR_MAX_WINDOW when set (1..8).
+uint32_t window_cap(const ClassEntry* ce) {
+  uint32_t cap = ce && ce->big() ? 8u : 5u;
+  if (ce && ce->wcap) cap = ce->wcap;
   if (const char* v = getenv("MR_MAX_WINDOW")) {
     int w = atoi(v);
     if (w >= 1 && (uint32_t)w < cap) cap = (uint32_t)w;
@@ -202,7 +205,7 @@ uint32_t window_cap(bool big) {
   return cap;
 }
 
-uint32_t choose_window(uint32_t bits, uint32_t popcount_hint, uint32_t max_w = window_cap(false)) {
+uint32_t choose_window(uint32_t bits, uint32_t popcount_hint, uint32_t max_w) {
   if (bits <= 1) return 1;
   uint64_t best = ~0ull;
   uint32_t bw = 1;
@@ -436,7 +439,7 @@ mr_status build_groups(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* op
     if (ops[i] == MR_OP_ENCRYPT) {
       if (!k->dev_e) return fail(ctx, MR_ERR_KEY, "key has no public exponent");
       uint32_t eb = (uint32_t)k->e.bits();
-      GroupLaunch& g = group(pub.cls, choose_window(eb, popcount_big(k->e)));
+      GroupLaunch& g = group(pub.cls, choose_window(eb, popcount_big(k->e), window_cap(pub.cls)));
       MxItem it{};
       it.key = pub.dev;
       it.x = in + i * in_stride;
@@ -455,7 +458,7 @@ mr_status build_groups(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* op
       if (!k->priv) return fail(ctx, MR_ERR_KEY, "key has no private CRT parts");
       ClassEntry* ce = k->p.cls;
       uint32_t eb = std::max(k->p.host.block[2], k->q.host.block[2]);
-      GroupLaunch& g = group(ce, choose_window(eb, 0));
+      GroupLaunch& g = group(ce, choose_window(eb, 0, window_cap(ce)));
       const KeyOff ko = key_offsets(ce->host.k, ce->host.W);
       for (int h = 0; h < 2; h++) {
         const KeyEntry& ke = h == 0 ? k->p : k->q;
@@ -606,6 +609,175 @@ mr_status guarded(mr_ctx* ctx, F&& f) {
   } catch (...) {
     return fail(ctx, MR_ERR_ARG, "unexpected error");
   }
+}
+
+// ------------------------------------------------------------- autotuning
+
+// Seeded host generator for the synthetic tuning batch (SplitMix64).
+struct TuneRng {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+  }
+  uint32_t u32() { return (uint32_t)(next() >> 32); }
+};
+
+mr_status autotune_class(mr_ctx* ctx, ClassEntry* ce, uint32_t n, uint32_t exp_bits, mr_tune_result* res) {
+  const uint32_t L = ce->host.L, W = ce->host.W, EL = (exp_bits + 31) / 32;
+  TuneRng r{0x4D52A070ull ^ ((uint64_t)L << 20) ^ exp_bits};
+  KeyEntry ke;
+  for (int attempt = 0;; attempt++) {  // a seeded L-bit odd modulus, coprime to the channel primes
+    std::vector<uint32_t> l(W);
+    for (auto& v : l) v = r.u32();
+    l[0] |= 1u;
+    l[W - 1] |= 0x80000000u;
+    mr_status s = make_key_entry(ctx, Big::from_limbs(l.data(), W), nullptr, L, ke);
+    if (s == MR_OK) break;
+    free_key_entry(ke);
+    if (s != MR_ERR_NOT_COPRIME || attempt > 8) return s;
+  }
+  // bases below 2^(L-32) < N; exponents of exactly exp_bits bits
+  std::vector<uint32_t> hx((size_t)n * W, 0u), he((size_t)n * EL, 0u);
+  const uint32_t top = exp_bits - 32 * (EL - 1);
+  for (uint32_t i = 0; i < n; i++) {
+    for (uint32_t w = 0; w + 1 < W; w++) hx[(size_t)i * W + w] = r.u32();
+    for (uint32_t w = 0; w < EL; w++) he[(size_t)i * EL + w] = r.u32();
+    uint32_t& t = he[(size_t)i * EL + EL - 1];
+    t = (top == 32 ? t : (t & ((1u << top) - 1u))) | (1u << (top - 1));
+  }
+  uint32_t* dx = nullptr;
+  const size_t xw = (size_t)n * W, ew = (size_t)n * EL;
+  cudaError_t e = cudaMalloc(&dx, (2 * xw + ew) * 4);
+  if (e != cudaSuccess) {
+    free_key_entry(ke);
+    return fail(ctx, MR_ERR_OOM, "tuning buffers");
+  }
+  uint32_t* de = dx + xw;
+  uint32_t* dout = de + ew;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  e = cudaMemcpy(dx, hx.data(), xw * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(de, he.data(), ew * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&ea);
+  if (e == cudaSuccess) e = cudaEventCreate(&eb);
+  const bool prof = ctx->prof_on;
+  ctx->prof_on = false;  // tuning launches stay out of the profile counters
+  const uint32_t saved_launches[2] = {ctx->launches[0], ctx->launches[1]};
+  mr_status s = e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "tuning setup");
+  const uint32_t nv = ce->big() ? 1u : ce->kern->n_variants;
+  auto time_config = [&](uint32_t variant, uint32_t w, double* ms) -> mr_status {
+    ce->variant = ce->big() ? 0u : variant;
+    double best = 1e30;
+    for (int rep = 0; rep < 3; rep++) {  // warm-up, then best of two
+      std::vector<ClassBatch> batches(1);
+      ClassBatch& b = batches[0];
+      b.ce = ce;
+      b.wbits = w;
+      b.mx.resize(n);
+      for (uint32_t i = 0; i < n; i++) {
+        MxItem& it = b.mx[i];
+        it = MxItem{};
+        it.key = ke.dev;
+        it.x = dx + (size_t)i * W;
+        it.e = de + (size_t)i * EL;
+        it.out = dout + (size_t)i * W;
+        it.xlim = ke.dev + key_offsets(ce->host.k, W).N;
+        it.x_limbs = W;
+        it.e_limbs = EL;
+        it.out_limbs = W;
+        it.xlim_limbs = W;
+        it.status = 0xffffffffu;
+      }
+      cudaEventRecord(ea, st);
+      mr_status rs = run_batches(ctx, batches, nullptr, st, 0);
+      cudaEventRecord(eb, st);
+      cudaError_t se = cudaEventSynchronize(eb);
+      if (rs) return rs;
+      if (se != cudaSuccess) return cuda_fail(ctx, se, "tuning run");
+      float t = 0;
+      cudaEventElapsedTime(&t, ea, eb);
+      if (rep > 0) best = std::min(best, (double)t);
+    }
+    *ms = best;
+    return MR_OK;
+  };
+  const uint32_t wmax = ce->big() ? 8u : 6u;
+  const uint32_t wopt = choose_window(exp_bits, 0, wmax);
+  const uint32_t wdef = choose_window(exp_bits, 0, ce->big() ? 8u : 5u);
+  double best_ms = 1e30, def_ms = 0;
+  uint32_t best_v = 0, best_w = wdef, configs = 0;
+  if (!s) s = time_config(0, wdef, &def_ms);
+  if (!s) {
+    configs++;
+    best_ms = def_ms;
+  }
+  for (uint32_t v = 0; v < nv && !s; v++)
+    for (uint32_t w = wopt > 2 ? wopt - 2 : 1; w <= wopt && !s; w++) {
+      if (v == 0 && w == wdef) continue;
+      double ms = 0;
+      s = time_config(v, w, &ms);
+      configs++;
+      if (!s && ms < best_ms) {
+        best_ms = ms;
+        best_v = v;
+        best_w = w;
+      }
+    }
+  ctx->prof_on = prof;
+  ctx->launches[0] = saved_launches[0];
+  ctx->launches[1] = saved_launches[1];
+  if (st) cudaStreamSynchronize(st);
+  if (ea) cudaEventDestroy(ea);
+  if (eb) cudaEventDestroy(eb);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(dx);
+  free_key_entry(ke);
+  if (s) {
+    ce->variant = 0;
+    return s;
+  }
+  ce->variant = best_v;
+  ce->wcap = best_w;
+  ce->tuned = true;
+  if (res) {
+    res->variant = best_v;
+    res->lanes_per_number = ce->big() ? 0u : ce->kern->var[best_v].tpi;
+    res->window = best_w;
+    res->configs = configs;
+    res->ms = best_ms;
+    res->ms_default = def_ms;
+  }
+  return MR_OK;
+}
+
+// MR_PLAN_AUTOTUNE: tune every not yet tuned size class of a mixed batch with the batch's item
+// count (at least 256, at most 8192) and longest exponent of that class.
+mr_status autotune_mixed(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, size_t n) {
+  std::map<ClassEntry*, std::pair<uint32_t, uint32_t>> need;  // class -> (items, longest exponent bits)
+  for (size_t i = 0; i < n; i++) {
+    const mr_key* k = keys[i];
+    if (!k || k->ctx != ctx) return fail(ctx, MR_ERR_ARG, "invalid key handle at index " + std::to_string(i));
+    if (ops[i] == MR_OP_ENCRYPT) {
+      auto& v = need[k->pub.cls];
+      v.first += 1;
+      v.second = std::max<uint32_t>(v.second, (uint32_t)k->e.bits());
+    } else if (ops[i] == MR_OP_DECRYPT && k->priv) {
+      auto& v = need[k->p.cls];
+      v.first += 2;
+      v.second = std::max<uint32_t>(v.second, std::max(k->p.host.block[2], k->q.host.block[2]));
+    }
+  }
+  for (auto& kv : need) {
+    if (kv.first->tuned || kv.first->big()) continue;
+    uint32_t items = std::min<uint32_t>(8192, std::max<uint32_t>(256, kv.second.first));
+    mr_status s = autotune_class(ctx, kv.first, items, std::max<uint32_t>(2, kv.second.second), nullptr);
+    if (s) return s;
+  }
+  return MR_OK;
 }
 
 ClassBatch& batch_for(std::vector<ClassBatch>& v, std::map<ClassEntry*, size_t>& idx, ClassEntry* ce) {
@@ -860,7 +1032,7 @@ mr_status mr_modexp_batch(mr_ctx* ctx, const mr_key* const* keys, size_t n, cons
     }
     for (auto& b : batches) {
       std::stable_sort(b.mx.begin(), b.mx.end(), [](const MxItem& a, const MxItem& c) { return a.key < c.key; });
-      b.wbits = choose_window(32 * e_stride, 0, window_cap(b.ce->big()));
+      b.wbits = choose_window(32 * e_stride, 0, window_cap(b.ce));
     }
     return run_batches(ctx, batches, dev_status, (cudaStream_t)stream, 0);
   });
@@ -901,7 +1073,7 @@ mr_status mr_rsa_encrypt(mr_ctx* ctx, const mr_key* const* keys, size_t n, const
     }
     for (auto& b : batches) {
       std::stable_sort(b.mx.begin(), b.mx.end(), [](const MxItem& a, const MxItem& c2) { return a.key < c2.key; });
-      b.wbits = choose_window(cost_bits[b.ce], cost_pop[b.ce], window_cap(b.ce->big()));
+      b.wbits = choose_window(cost_bits[b.ce], cost_pop[b.ce], window_cap(b.ce));
     }
     return run_batches(ctx, batches, dev_status, (cudaStream_t)stream, 0);
   });
@@ -962,7 +1134,7 @@ mr_status mr_rsa_decrypt_crt(mr_ctx* ctx, const mr_key* const* keys, size_t n, c
       uint32_t eb = (uint32_t)std::max(k->p.host.block[2], k->q.host.block[2]);
       ebits[ce] = std::max(ebits[ce], eb);
     }
-    for (auto& b : batches) b.wbits = choose_window(ebits[b.ce], 0);
+    for (auto& b : batches) b.wbits = choose_window(ebits[b.ce], 0, window_cap(b.ce));
     return run_batches(ctx, batches, dev_status, (cudaStream_t)stream, maxW);
   });
 }
@@ -985,7 +1157,7 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
     if (s) return s;
     if (ce->big()) return fail(ctx, MR_ERR_SIZE, "Miller-Rabin takes candidates of at most 4096 bits");
     const KernelVariant& k = ce->kv();
-    const uint32_t wbits = choose_window(32 * n_limbs, 0);
+    const uint32_t wbits = choose_window(32 * n_limbs, 0, window_cap(ce));
     const size_t tab_words = modexp_scratch_words(k, (uint32_t)n, wbits);
     const size_t crow_words = n * 3 * (size_t)ce->host.W;
     const size_t off_crow = align256(tab_words * 4);
@@ -1015,7 +1187,9 @@ mr_status mr_rsa_mixed(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* op
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<GroupLaunch> groups;
-    mr_status s = build_groups(ctx, keys, ops, n, in, in_stride, out, out_stride, groups);
+    mr_status s = (flags & MR_PLAN_AUTOTUNE) ? autotune_mixed(ctx, keys, ops, n) : MR_OK;
+    if (s) return s;
+    s = build_groups(ctx, keys, ops, n, in, in_stride, out, out_stride, groups);
     if (s) return s;
     flags &= (MR_PLAN_CONCURRENT | MR_PLAN_PERSISTENT);
     size_t upload = 0, qoff = 0;
@@ -1083,7 +1257,9 @@ mr_status mr_plan_create(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* 
     plan->ctx = ctx;
     plan->flags = flags;
     plan->status = dev_status;
-    mr_status s = build_groups(ctx, keys, ops, n, in, in_stride, out, out_stride, plan->groups);
+    mr_status s = (flags & MR_PLAN_AUTOTUNE) ? autotune_mixed(ctx, keys, ops, n) : MR_OK;
+    if (s) return s;
+    s = build_groups(ctx, keys, ops, n, in, in_stride, out, out_stride, plan->groups);
     if (s) return s;
     size_t upload = 0;
     size_t total = layout_groups(ctx, plan->groups, flags, &upload, &plan->queue_off);
@@ -1217,7 +1393,7 @@ mr_status mr_modexp_batch_noalloc(mr_ctx* ctx, const mr_key* key, size_t n, cons
   c.x_stride = x_stride;
   c.e_stride = e_stride;
   c.out_stride = out_stride;
-  c.wbits = choose_window(32 * e_stride, 0);
+  c.wbits = choose_window(32 * e_stride, 0, window_cap(key->pub.cls));
   c.stream = (cudaStream_t)stream;
   std::string err;
   int rc = noalloc_modexp(c, err);
@@ -1301,6 +1477,21 @@ mr_status mr_set_variant(mr_ctx* ctx, uint32_t class_bits, uint32_t variant) {
     if (variant >= ce->kern->n_variants) return fail(ctx, MR_ERR_ARG, "no such variant");
     ce->variant = variant;
     return MR_OK;
+  });
+}
+
+mr_status mr_autotune(mr_ctx* ctx, uint32_t class_bits, uint32_t n_items, uint32_t exp_bits, mr_tune_result* res) {
+  if (!ctx) return MR_ERR_ARG;
+  if (!n_items || !exp_bits || n_items > (1u << 20) || exp_bits > 65536)
+    return fail(ctx, MR_ERR_ARG, "n_items and exp_bits must be positive (n_items <= 2^20, exp_bits <= 65536)");
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    uint32_t L = class_for_bits(class_bits);
+    if (!L) return fail(ctx, MR_ERR_SIZE, "no size class holds " + std::to_string(class_bits) + "-bit moduli");
+    ClassEntry* ce = nullptr;
+    mr_status s = get_class(ctx, L, &ce);
+    if (s) return s;
+    return autotune_class(ctx, ce, n_items, exp_bits, res);
   });
 }
 

@@ -29,7 +29,7 @@ EXPORTED = [
     "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
     "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant", "mr_debug_mr_setup",
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
-    "mr_imad_peak",
+    "mr_imad_peak", "mr_autotune",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -37,10 +37,16 @@ MR_OP_DECRYPT = 1
 MR_PLAN_CONCURRENT = 1
 MR_PLAN_PERSISTENT = 2
 MR_PLAN_GRAPH = 4
+MR_PLAN_AUTOTUNE = 8
 
 
 class KernelTime(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint32), ("ms", ctypes.c_double)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_uint32), ("lanes_per_number", ctypes.c_uint32), ("window", ctypes.c_uint32),
+                ("configs", ctypes.c_uint32), ("ms", ctypes.c_double), ("ms_default", ctypes.c_double)]
 
 
 class MRError(RuntimeError):
@@ -86,6 +92,7 @@ def _load() -> ctypes.CDLL:
         "mr_plan_free": (None, [P]),
         "mr_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelTime), U32]),
         "mr_imad_peak": (ctypes.c_int, [P, U32, P, ctypes.POINTER(ctypes.c_double)]),
+        "mr_autotune": (ctypes.c_int, [P, U32, U32, U32, ctypes.POINTER(TuneResult)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -357,6 +364,13 @@ class Context:
         arr = (KernelTime * 2)()
         self._check(lib.mr_profile_read(self.handle, arr, 2))
         return [(arr[i].launches, arr[i].ms) for i in range(2)]
+
+    def mr_autotune(self, class_bits: int, n_items: int, exp_bits: int) -> dict:
+        """Time the lane mappings and window widths of a size class; keep the fastest (see mr.h)."""
+        r = TuneResult()
+        self._check(lib.mr_autotune(self.handle, class_bits, n_items, exp_bits, ctypes.byref(r)))
+        return {"variant": r.variant, "lanes_per_number": r.lanes_per_number, "window": r.window,
+                "configs": r.configs, "ms": r.ms, "ms_default": r.ms_default}
 
     def mr_imad_peak(self, kind: int = 0, stream=None) -> float:
         """Measured multiply-adds per second: kind 0 mad.wide.u32, kind 1 mad.lo.u32."""
