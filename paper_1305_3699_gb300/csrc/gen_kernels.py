@@ -18,10 +18,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CLASSES = {
     512: (18, 16, 17, [(2, 128, 4, 2), (4, 128, 4, 4)]),
     1024: (36, 32, 34, [(4, 128, 4, 3), (8, 128, 4, 4)]),
-    1536: (54, 48, 50, [(8, 128, 4, 4)]),
-    2048: (72, 64, 66, [(8, 128, 4, 0), (16, 128, 4, 4)]),
-    3072: (108, 96, 97, [(16, 256, 4, 2)]),
-    4096: (145, 128, 129, [(16, 384, 2, 1)]),
+    1536: (54, 48, 50, [(8, 128, 4, 0)]),
+    2048: (72, 64, 66, [(8, 128, 4, 0), (16, 128, 4, 1)]),
+    3072: (108, 96, 97, [(16, 256, 4, 0)]),
+    4096: (145, 128, 129, [(16, 384, 2, 0)]),
 }
 
 

@@ -5,7 +5,7 @@
 
 namespace mr {
 
-using C1536v0 = Cfg<54, 48, 50, 8, 128, 4, 4>;
+using C1536v0 = Cfg<54, 48, 50, 8, 128, 4, 0>;
 static cudaError_t launch_modexp_1536_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   modexp_kernel<C1536v0><<<grid, C1536v0::THREADS, C1536v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();

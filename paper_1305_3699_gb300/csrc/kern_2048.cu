@@ -35,7 +35,7 @@ static int occupancy_2048_0() {
   return n > 0 ? n : 1;
 }
 
-using C2048v1 = Cfg<72, 64, 66, 16, 128, 4, 4>;
+using C2048v1 = Cfg<72, 64, 66, 16, 128, 4, 1>;
 static cudaError_t launch_modexp_2048_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   modexp_kernel<C2048v1><<<grid, C2048v1::THREADS, C2048v1::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();

@@ -5,7 +5,7 @@
 
 namespace mr {
 
-using C3072v0 = Cfg<108, 96, 97, 16, 256, 4, 2>;
+using C3072v0 = Cfg<108, 96, 97, 16, 256, 4, 0>;
 static cudaError_t launch_modexp_3072_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   modexp_kernel<C3072v0><<<grid, C3072v0::THREADS, C3072v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();

@@ -5,7 +5,7 @@
 
 namespace mr {
 
-using C4096v0 = Cfg<145, 128, 129, 16, 384, 2, 1>;
+using C4096v0 = Cfg<145, 128, 129, 16, 384, 2, 0>;
 static cudaError_t launch_modexp_4096_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
   modexp_kernel<C4096v0><<<grid, C4096v0::THREADS, C4096v0::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();

@@ -134,9 +134,8 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   // leave the domain: MM(x, 1), then RNS -> binary, reduced into [0, N)
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
-    const int o = t * NPT + s;
-    yb[s] = sm.cb4(o).z;  // hat form of 1 = 2^32 mod m
-    yp[s] = sm.cp4(o).z;
+    yb[s] = sm.cb4(t, s).z;  // hat form of 1 = 2^32 mod m
+    yp[s] = sm.cp4(t, s).z;
   }
   mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
   from_rns_reduce<C>(xb, a.cls, key, sm, xib, t, it.out, (int)it.out_limbs, live && !bad);
@@ -208,8 +207,7 @@ __global__ void __launch_bounds__(C::THREADS) crt_kernel(LaunchArgs a) {
   add_vec<C>(db, dp, yb, yp, sm, t);
 #pragma unroll
   for (int s = 0; s < NPT; s++) {  // subtract m_q: d + m - q lies in [0, 2m]
-    const int o = t * NPT + s;
-    const uint32_t mb = sm.cb4(o).x, mp = sm.cp4(o).x;
+    const uint32_t mb = sm.cb4(t, s).x, mp = sm.cp4(t, s).x;
     uint32_t u = db[s] + mb - qb[s];
     db[s] = min(u, u - mb);
     uint32_t v = dp[s] + mp - qp[s];

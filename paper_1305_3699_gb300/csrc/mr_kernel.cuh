@@ -86,7 +86,7 @@ __device__ __forceinline__ bool rns_is_zero_mod_n(const uint32_t (&vb)[C::NPT], 
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
     if (o < K) {
-      const uint4 cb = sm.cb4(o), cp = sm.cp4(o);
+      const uint4 cb = sm.cb4(t, s), cp = sm.cp4(t, s);
       uint32_t ub = redc(mulw(vb[s], invb[s]), cb.x, cb.y);
       uint32_t up = redc(mulw(vp[s], invp[s]), cp.x, cp.y);
       if (j == 0xffffffffu) j = ub;
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
-    const uint4 cb = sm.cb4(o), cp = sm.cp4(o);
-    const uint2 c2 = sm.cb2(o);
+    const uint4 cb = sm.cb4(t, s), cp = sm.cp4(t, s);
+    const uint2 c2 = sm.cb2(t, s);
     // N^-1 mod m by Fermat (x^(m-2)), in Montgomery form; hat(1) = 2^32 mod m
     uint32_t ib = cb.z, ip = cp.z, bb = nb[s], bp = np[s];
     const uint32_t eb = cb.x - 2u, ep = cp.x - 2u;
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
     kxi[s] = redc(mulw(nib, c2.x), cb.x, cb.y);
     // |N M^-1|_{m'_j} hat = REDC(hat(N) * hat(M^-1)); |N M^-1 (M'/m'_j)^-1| plain = REDC(hat(N) * ad)
     cmul[s] = redc(mulw(np[s], cp.w), cp.x, cp.y);
-    cd[s] = redc(mulw(np[s], sm.cp2(o).x), cp.x, cp.y);
+    cd[s] = redc(mulw(np[s], sm.cp2(t, s).x), cp.x, cp.y);
   }
   {
     const unsigned grp = C::TPI == 32 ? 0xffffffffu : (((1u << (C::TPI & 31)) - 1u) << (lane - t));
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
     for (int s = 0; s < NPT; s++) {
       const int o = t * NPT + s;
       if (live && o < K) {
-        const uint4 cp = sm.cp4(o);
+        const uint4 cp = sm.cp4(t, s);
         dg[4 + 2 * W + o] = kxi[s];
         dg[4 + 2 * W + K + o] = redc(mulw(cmul[s], 1u), cp.x, cp.y);
         dg[4 + 2 * W + 2 * K + o] = cd[s];
@@ -289,8 +289,7 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
     // y == 1: y~ + (N - M mod N) is a multiple of N
 #pragma unroll
     for (int s = 0; s < NPT; s++) {
-      const int o = t * NPT + s;
-      const uint32_t mb = sm.cb4(o).x, mp = sm.cp4(o).x;
+      const uint32_t mb = sm.cb4(t, s).x, mp = sm.cp4(t, s).x;
       uint32_t u = xb[s] + nmob[s];
       yb[s] = min(u, u - mb);
       u = xp[s] + nmop[s];
@@ -301,8 +300,7 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
     for (uint32_t i = 0;; i++) {
 #pragma unroll
       for (int s = 0; s < NPT; s++) {
-        const int o = t * NPT + s;
-        const uint32_t mb = sm.cb4(o).x, mp = sm.cp4(o).x;
+        const uint32_t mb = sm.cb4(t, s).x, mp = sm.cp4(t, s).x;
         uint32_t u = xb[s] + oneb[s];
         yb[s] = min(u, u - mb);
         u = xp[s] + onep[s];

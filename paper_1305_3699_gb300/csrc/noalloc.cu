@@ -118,9 +118,8 @@ __global__ void __launch_bounds__(C::THREADS) modexp_packed_kernel(PackedArgs a)
 
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
-    const int o = t * NPT + s;
-    yb[s] = sm.cb4(o).z;
-    yp[s] = sm.cp4(o).z;
+    yb[s] = sm.cb4(t, s).z;
+    yp[s] = sm.cp4(t, s).z;
   }
   mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
   from_rns_reduce<C>(xb, a.cls, key, sm, xib, t, out, (int)a.out_stride, live && !bad);

@@ -68,8 +68,12 @@ struct Cfg {
   static constexpr int NPT = (K + TPI - 1) / TPI; // channels per lane and base
   static constexpr int VEC = VEC_;                // words per shared-memory load of a matrix row (2 or 4)
   static constexpr int NPTP = (NPT + VEC - 1) / VEC * VEC;  // padded to whole vector loads
-  static constexpr int ROW = TPI * NPTP;          // words per extension-matrix row in smem
-  static constexpr int SL = TPI * NPT;            // slot-indexed constant arrays
+  // per-lane stride of a matrix row: an odd number of vectors, so that the distinct lanes of one
+  // shared-memory wavefront (8 for 16-byte loads, 16 for 8-byte loads) hit distinct banks
+  static constexpr int LS = ((NPTP / VEC) % 2 == 0) ? NPTP + VEC : NPTP;
+  static constexpr int ROW = TPI * LS;            // words per extension-matrix row in smem
+  static constexpr int NPTC = NPT | 1;            // per-lane stride of the channel-constant arrays (odd)
+  static constexpr int SL = TPI * NPTC;           // slots of the constant arrays
   static constexpr int KP = (K + 3) & ~3;         // xi / xi' buffer length
   static constexpr int XS = 2 * KP + 4;           // per-number stride of the two buffers: XS/4 odd
                                                   // keeps broadcast loads and stores bank-conflict free
@@ -97,10 +101,11 @@ struct Smem {
   uint32_t* base;
   __device__ const uint32_t* T1() const { return base + C::SM_T1; }
   __device__ const uint32_t* T2() const { return base + C::SM_T2; }
-  __device__ uint4 cb4(int o) const { return reinterpret_cast<const uint4*>(base + C::SM_CB4)[o]; }
-  __device__ uint4 cp4(int o) const { return reinterpret_cast<const uint4*>(base + C::SM_CP4)[o]; }
-  __device__ uint2 cb2(int o) const { return reinterpret_cast<const uint2*>(base + C::SM_CB2)[o]; }
-  __device__ uint2 cp2(int o) const { return reinterpret_cast<const uint2*>(base + C::SM_CP2)[o]; }
+  // constants of channel t*NPT + s (lane t of a group, its s-th channel)
+  __device__ uint4 cb4(int t, int s) const { return reinterpret_cast<const uint4*>(base + C::SM_CB4)[t * C::NPTC + s]; }
+  __device__ uint4 cp4(int t, int s) const { return reinterpret_cast<const uint4*>(base + C::SM_CP4)[t * C::NPTC + s]; }
+  __device__ uint2 cb2(int t, int s) const { return reinterpret_cast<const uint2*>(base + C::SM_CB2)[t * C::NPTC + s]; }
+  __device__ uint2 cp2(int t, int s) const { return reinterpret_cast<const uint2*>(base + C::SM_CP2)[t * C::NPTC + s]; }
   __device__ uint32_t* xi(int item_in_block) const { return base + C::SM_XI + item_in_block * C::XS; }
 };
 
@@ -111,18 +116,19 @@ __device__ void load_class_smem(const Smem<C>& sm, const uint32_t* cls) {
   uint32_t* s = sm.base;
   for (int idx = threadIdx.x; idx < C::K * C::ROW; idx += blockDim.x) {
     int row = idx / C::ROW, col = idx % C::ROW;
-    int t = col / C::NPTP, sl = col % C::NPTP;
+    int t = col / C::LS, sl = col % C::LS;
     int ch = t * C::NPT + sl;
     bool ok = sl < C::NPT && ch < C::K;
     s[C::SM_T1 + idx] = ok ? cls[o.T1 + row * C::K + ch] : 0u;
     s[C::SM_T2 + idx] = ok ? cls[o.T2 + row * C::K + ch] : 0u;
   }
-  for (int ch = threadIdx.x; ch < C::SL; ch += blockDim.x) {
-    bool ok = ch < C::K;
-    uint32_t* cb4 = s + C::SM_CB4 + 4 * ch;
-    uint32_t* cp4 = s + C::SM_CP4 + 4 * ch;
-    uint32_t* cb2 = s + C::SM_CB2 + 2 * ch;
-    uint32_t* cp2 = s + C::SM_CP2 + 2 * ch;
+  for (int q = threadIdx.x; q < C::SL; q += blockDim.x) {
+    const int ch = (q / C::NPTC) * C::NPT + q % C::NPTC;
+    bool ok = q % C::NPTC < C::NPT && ch < C::K;
+    uint32_t* cb4 = s + C::SM_CB4 + 4 * q;
+    uint32_t* cp4 = s + C::SM_CP4 + 4 * q;
+    uint32_t* cb2 = s + C::SM_CB2 + 2 * q;
+    uint32_t* cp2 = s + C::SM_CP2 + 2 * q;
     cb4[0] = ok ? cls[o.m + ch] : 0u;
     cb4[1] = ok ? cls[o.mi + ch] : 0u;
     cb4[2] = ok ? cls[o.r32 + ch] : 0u;
@@ -160,7 +166,7 @@ __device__ __forceinline__ void ext_dot(uint64_t (&acc)[C::NPT], const uint32_t*
     for (int q = 0; q < 4; q++) {
       if (i0 + q < K) {
         const uint32_t xv = q == 0 ? x4.x : q == 1 ? x4.y : q == 2 ? x4.z : x4.w;
-        const uint32_t* row = T + (i0 + q) * C::ROW + t * C::NPTP;
+        const uint32_t* row = T + (i0 + q) * C::ROW + t * C::LS;
         if constexpr (C::VEC == 4) {
 #pragma unroll
           for (int s4 = 0; s4 < C::NPTP; s4 += 4) {
@@ -203,11 +209,11 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
-    const uint4 cb = sm.cb4(o);
+    const uint4 cb = sm.cb4(t, s);
     uint32_t sb = redc(mulw(xb[s], yb[s]), cb.x, cb.y);
     uint32_t xi = redc(mulw(sb, kxi[s]), cb.x, cb.y);
     if (o < K) xib[o] = xi;
-    const uint4 cp = sm.cp4(o);
+    const uint4 cp = sm.cp4(t, s);
     sp[s] = redc(mulw(xp[s], yp[s]), cp.x, cp.y);
   }
   __syncwarp();
@@ -220,8 +226,8 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
-    const uint4 cp = sm.cp4(o);
-    const uint2 c2 = sm.cp2(o);
+    const uint4 cp = sm.cp4(t, s);
+    const uint2 c2 = sm.cp2(t, s);
     uint32_t qh = redc64(acc[s], cp.x, cp.y, cp.z);
     xp[s] = redc(madw(sp[s], cp.w, mulw(qh, cmul[s])), cp.x, cp.y);
     uint32_t xpj = redc(madw(sp[s], c2.x, mulw(qh, cd[s])), cp.x, cp.y);
@@ -235,8 +241,7 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
   // r_i = t_i - a' |M'|_{m_i}  (hat, the new B residues)
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
-    const int o = t * NPT + s;
-    const uint4 cb = sm.cb4(o);
+    const uint4 cb = sm.cb4(t, s);
     uint32_t th = redc64(acc[s], cb.x, cb.y, cb.z);
     uint32_t corr = redc(mulw(alpha, cb.w), cb.x, cb.y);
     uint32_t r = th + cb.x - corr;
@@ -269,8 +274,7 @@ __device__ __forceinline__ void to_rns(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C:
     if (w & 1) {  // keep the sums below 2^64: fold every two limbs
 #pragma unroll
       for (int s = 0; s < NPT; s++) {
-        const int o = t * NPT + s;
-        const uint32_t rb = sm.cb4(o).z, rp = sm.cp4(o).z;
+        const uint32_t rb = sm.cb4(t, s).z, rp = sm.cp4(t, s).z;
         ab[s] = madw(hi32(ab[s]), rb, lo32(ab[s]));
         ap[s] = madw(hi32(ap[s]), rp, lo32(ap[s]));
       }
@@ -278,8 +282,7 @@ __device__ __forceinline__ void to_rns(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C:
   }
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
-    const int o = t * NPT + s;
-    const uint4 cb = sm.cb4(o), cp = sm.cp4(o);
+    const uint4 cb = sm.cb4(t, s), cp = sm.cp4(t, s);
     xb[s] = redc64(ab[s], cb.x, cb.y, cb.z);
     xp[s] = redc64(ap[s], cp.x, cp.y, cp.z);
   }
@@ -302,8 +305,7 @@ __device__ __forceinline__ void add_vec(uint32_t (&ab)[C::NPT], uint32_t (&ap)[C
                                         const uint32_t (&bp)[C::NPT], const Smem<C>& sm, int t) {
 #pragma unroll
   for (int s = 0; s < C::NPT; s++) {
-    const int o = t * C::NPT + s;
-    const uint32_t mb = sm.cb4(o).x, mp = sm.cp4(o).x;
+    const uint32_t mb = sm.cb4(t, s).x, mp = sm.cp4(t, s).x;
     uint32_t u = ab[s] + bb[s];
     ab[s] = min(u, u - mb);
     uint32_t v = ap[s] + bp[s];
@@ -337,8 +339,8 @@ __device__ void from_rns_reduce(const uint32_t (&xb)[C::NPT], const uint32_t* cl
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
-    const uint4 cb = sm.cb4(o);
-    const uint2 c2 = sm.cb2(o);
+    const uint4 cb = sm.cb4(t, s);
+    const uint2 c2 = sm.cb2(t, s);
     uint32_t xi = redc(mulw(xb[s], c2.x), cb.x, cb.y);  // plain, [0, m)
     if (o < K) xib[o] = xi;
     kaw += hi32(mulw(xi, c2.y));
