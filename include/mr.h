@@ -314,6 +314,15 @@ mr_status mr_profile_read(mr_ctx *ctx, mr_kernel_time *times, uint32_t n_kinds);
  * Errors: MR_ERR_ARG (kind > 1, NULL pointer), MR_ERR_CUDA. */
 mr_status mr_imad_peak(mr_ctx *ctx, uint32_t kind, void *stream, double *per_second);
 
+/* Test hook of the large classes' bounded waits.  Later 8192/16384-bit calls on
+ * this context give up a wait between thread blocks after spin_limit polls
+ * (0 restores the default, about one second), and, when absent_slice >= 0, the
+ * blocks of that channel slice leave at once without arriving at any wait, so
+ * that the others time out: the call then completes, every item's status byte
+ * is MR_ERR_TIMEOUT and the context stays usable.  absent_slice = -1 turns the
+ * hook off.  Errors: MR_ERR_ARG. */
+mr_status mr_debug_big_wait(mr_ctx *ctx, uint32_t spin_limit, int32_t absent_slice);
+
 /* ------------------------------------------------------------ inspection -- */
 
 /* Copy one precomputed table of a size class (or of a key when key != NULL) to

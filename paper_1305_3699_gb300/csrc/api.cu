@@ -79,6 +79,8 @@ struct mr_ctx {
   std::vector<Span> spans;
   std::vector<cudaEvent_t> free_events;
   uint32_t* mr_dbg = nullptr;  // test hook of mr_debug_mr_setup
+  uint32_t big_spin_limit = 0;  // large-class barrier polls before giving up (0: the kernel default)
+  int32_t big_absent_slice = -1;  // test hook of mr_debug_big_wait
   std::vector<cudaStream_t> side;     // streams for concurrent groups of one-shot mixed calls
   std::vector<cudaEvent_t> side_join;
   cudaEvent_t side_fork = nullptr;
@@ -365,7 +367,8 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
       uint32_t* scr = reinterpret_cast<uint32_t*>(base + b.off_scratch);
       uint32_t* sync = scr + (size_t)b.slots * bk.slot_words(b.wbits);
       BigArgs a{b.ce->dev, b.ce->tslice, reinterpret_cast<const MxItem*>(base + b.off_mx), (uint32_t)b.mx.size(),
-                b.wbits, scr, status, sync, b.slots};
+                b.wbits, scr, status, sync, b.slots, ctx->big_spin_limit ? ctx->big_spin_limit : BIG_SPIN_POLLS,
+                ctx->big_absent_slice};
       e = cudaMemsetAsync(sync, 0, (b.slots + 1) * 4, stream);
       if (e == cudaSuccess) e = timed_launch(ctx, 0, stream, [&] { return bk.modexp(a, stream); });
       if (e != cudaSuccess) break;
@@ -1434,6 +1437,13 @@ mr_status mr_imad_peak(mr_ctx* ctx, uint32_t kind, void* stream, double* per_sec
   cudaSetDevice(ctx->device);
   cudaError_t e = mr::imad_stream_rate(ctx->device, (cudaStream_t)stream, kind == 0, per_second);
   return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "integer-multiply probe");
+}
+
+mr_status mr_debug_big_wait(mr_ctx* ctx, uint32_t spin_limit, int32_t absent_slice) {
+  if (!ctx || absent_slice < -1) return fail(ctx, MR_ERR_ARG, "bad arguments");
+  ctx->big_spin_limit = spin_limit;
+  ctx->big_absent_slice = absent_slice;
+  return MR_OK;
 }
 
 mr_status mr_debug_mr_setup(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs, size_t n, uint32_t* dev_out,

@@ -57,8 +57,6 @@ struct BigCfg {
   static_assert(K * 32 <= 2 * K * SC, "RNS -> binary stages all k rows in the matrix area");
 };
 
-constexpr uint32_t BIG_SPIN_LIMIT = 1u << 22;  // barrier polls (x ~0.1-1 us each) before giving up
-
 template <class C>
 struct BigGroup {
   uint32_t* s;         // shared memory
@@ -66,6 +64,7 @@ struct BigGroup {
   uint32_t* ctr;       // this slot's barrier counter
   uint32_t* abort;     // launch-wide abort flag
   uint32_t nbar;       // barriers passed so far (target = nbar * SLICES)
+  uint32_t spin_limit; // polls before a wait gives up
   int c, w, lane;
   __device__ uint4 a4(int q) const { return reinterpret_cast<const uint4*>(s + C::SM_C4A)[q]; }
   __device__ uint4 b4(int q) const { return reinterpret_cast<const uint4*>(s + C::SM_C4B)[q]; }
@@ -89,7 +88,7 @@ struct BigGroup {
           ok = 0;
           break;
         }
-        if (it >= BIG_SPIN_LIMIT) {
+        if (it >= spin_limit) {
           atomicExch(abort, 1u);
           ok = 0;
           break;
@@ -527,6 +526,8 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
   g.ctr = a.sync + slot_id;
   g.abort = a.sync + a.slots;
   g.nbar = 0;
+  g.spin_limit = a.spin_limit;
+  if (g.c == a.absent_slice) return;  // test hook: this slice never arrives; the others time out
   big_load_consts<C>(smem_raw, a.cls, g.c);
   const uint32_t n_groups = (a.n_items + 31) / 32;
   uint32_t grp = slot_id;
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
     __syncthreads();
     if (!big_modexp_group<C>(a, g, grp)) break;
   }
-  if (grp < n_groups && g.c == 0 && a.status) {
+  if (grp < n_groups && g.c == (a.absent_slice == 0 ? 1 : 0) && a.status) {
     // aborted: every unfinished item of this slot reports a timeout
     for (uint32_t r = grp; r < n_groups; r += a.slots) {
       const uint32_t i = r * 32 + threadIdx.x;

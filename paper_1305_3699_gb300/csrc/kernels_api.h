@@ -30,6 +30,9 @@ struct MRArgs {
   uint32_t* dbg;            // nullptr, or per candidate mr_debug_words(k, W) words of derived constants
 };
 
+// Barrier polls of the large-class kernel before a wait gives up (x 0.03-0.3 us each: about 1 s).
+constexpr uint32_t BIG_SPIN_POLLS = 1u << 22;
+
 // Exponentiation of a large size class (several CTAs per item group, cooperative launch).
 struct BigArgs {
   const uint32_t* cls;     // class table block (device)
@@ -41,6 +44,8 @@ struct BigArgs {
   uint8_t* status;         // per-item status bytes or nullptr
   uint32_t* sync;          // [slots] barrier counters, then the abort flag; zeroed before the launch
   uint32_t slots;          // item groups in flight (grid = slots * slices)
+  uint32_t spin_limit;     // barrier polls before a wait gives up
+  int32_t absent_slice;    // test hook: CTAs of this channel slice leave at once (-1: none)
 };
 
 // [special, s, nbits, 0][M mod N: W][M^2 mod N: W][kxi: k][N M^-1 (plain): k][cd: k][N^-1 mod m_i: k][N^-1 mod m'_j: k]

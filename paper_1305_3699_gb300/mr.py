@@ -29,7 +29,7 @@ EXPORTED = [
     "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
     "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant", "mr_debug_mr_setup",
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
-    "mr_imad_peak", "mr_autotune",
+    "mr_imad_peak", "mr_autotune", "mr_debug_big_wait",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -93,6 +93,7 @@ def _load() -> ctypes.CDLL:
         "mr_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelTime), U32]),
         "mr_imad_peak": (ctypes.c_int, [P, U32, P, ctypes.POINTER(ctypes.c_double)]),
         "mr_autotune": (ctypes.c_int, [P, U32, U32, U32, ctypes.POINTER(TuneResult)]),
+        "mr_debug_big_wait": (ctypes.c_int, [P, U32, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -371,6 +372,10 @@ class Context:
         self._check(lib.mr_autotune(self.handle, class_bits, n_items, exp_bits, ctypes.byref(r)))
         return {"variant": r.variant, "lanes_per_number": r.lanes_per_number, "window": r.window,
                 "configs": r.configs, "ms": r.ms, "ms_default": r.ms_default}
+
+    def mr_debug_big_wait(self, spin_limit: int = 0, absent_slice: int = -1):
+        """Test hook of the large classes' bounded waits (see mr.h)."""
+        self._check(lib.mr_debug_big_wait(self.handle, spin_limit, absent_slice))
 
     def mr_imad_peak(self, kind: int = 0, stream=None) -> float:
         """Measured multiply-adds per second: kind 0 mad.wide.u32, kind 1 mad.lo.u32."""

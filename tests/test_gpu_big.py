@@ -113,3 +113,24 @@ def test_large_class_unsupported_calls(mr, ctx):
     with pytest.raises(mr.MRError) as e:
         ctx.mr_rsa_mixed([h], [0], c, m)
     assert e.value.code == 4
+
+
+def test_bounded_wait_times_out_and_context_recovers(mr, ctx):
+    """One channel slice never arrives at the inter-block waits (test hook): the other blocks
+    give up after a short poll limit, every item reports MR_ERR_TIMEOUT, and the next call on
+    the same context computes correct results."""
+    r = SplitMix64(0x4D520033)
+    N = r.randbits(8192) | 1 | (1 << 8191)
+    h = ctx.mr_rns_setup(N)
+    xs = [r.below(N) for _ in range(32)]
+    es = [r.randbits(64) for _ in range(32)]
+    ctx.mr_debug_big_wait(spin_limit=1 << 14, absent_slice=3)
+    try:
+        _, st = _run(mr, ctx, [h] * 32, [N] * 32, xs, es, 256, 2)
+    finally:
+        ctx.mr_debug_big_wait(0, -1)
+    assert st == [8] * 32  # MR_ERR_TIMEOUT
+    got, st = _run(mr, ctx, [h] * 32, [N] * 32, xs, es, 256, 2)
+    assert st == [0] * 32
+    for j in range(32):
+        assert got[j] == plain.modexp(xs[j], es[j], N), j
