@@ -34,25 +34,26 @@ struct BigCfg {
   static constexpr int SC = NPT * NW;                 // channels per slice and base
   static constexpr int SLICES = (K + SC - 1) / SC;
   static constexpr int THREADS = NW * 32;
-  static constexpr int H = (K + 1) / 2;              // rows per staged half of xi
+  static constexpr int R = (K + 2) / 3;              // rows per staged third of xi
   // shared memory (words)
   static constexpr int SM_T1 = 0;                     // [K][SC] this slice's columns of T1
   static constexpr int SM_T2 = SM_T1 + K * SC;        // [K][SC] of T2
-  static constexpr int SM_X = SM_T2 + K * SC;         // [H][32] staged xi rows
-  static constexpr int SM_C4A = SM_X + H * 32;        // per slot uint4 {m, mi, r32, E}   B  (E = -M' 2^64 mod m)
+  static constexpr int SM_X = SM_T2 + K * SC;         // 2 x [R][32] staged xi rows (double buffer)
+  static constexpr int SM_C4A = SM_X + 2 * R * 32;    // per slot uint4 {m, mi, r32, E}   B  (E = -M' 2^64 mod m)
   static constexpr int SM_C4B = SM_C4A + 4 * SC;      // per slot uint4 {m, mi, r32, ahat} B'
   static constexpr int SM_C2A = SM_C4B + 4 * SC;      // per slot uint2 {mmiinv, ub}       B
   static constexpr int SM_C2B = SM_C2A + 2 * SC;      // per slot uint2 {ad, ubp}          B'
   static constexpr int SM_KAW = SM_C2B + 2 * SC;      // [NW][32] correction-factor partials
   static constexpr int SM_MISC = SM_KAW + NW * 32;    // [32]
-  static constexpr int SM_WORDS = SM_MISC + 32;
+  static constexpr int SM_MBAR = SM_MISC + 32;        // two mbarriers (8 bytes each) of the staging copies
+  static constexpr int SM_WORDS = SM_MBAR + 4;
   static constexpr int SMEM_BYTES = SM_WORDS * 4;
   // per-slot global scratch (words): xi, xi', slice partials, then the window table
   static constexpr size_t XG = 0, XPG = (size_t)K * 32, KAWG = (size_t)2 * K * 32;
   static constexpr size_t TAB = KAWG + (size_t)SLICES * 32;
   MR_HD static constexpr size_t slot_words(uint32_t wbits) { return TAB + ((size_t)1 << wbits) * 2 * K * 32; }
   static_assert(NPT == 4, "four channels per thread and base (one 16-byte matrix load per row)");
-  static_assert((SM_X % 4) == 0 && (SM_C4A % 4) == 0 && (SC % 4) == 0 && (H * 32) % 4 == 0, "alignment");
+  static_assert((SM_X % 4) == 0 && (SM_C4A % 4) == 0 && (SC % 4) == 0 && (SM_MBAR % 4) == 0, "alignment");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
   static_assert(K * 32 <= 2 * K * SC, "RNS -> binary stages all k rows in the matrix area");
 };
@@ -65,6 +66,7 @@ struct BigGroup {
   uint32_t* abort;     // launch-wide abort flag
   uint32_t nbar;       // barriers passed so far (target = nbar * SLICES)
   uint32_t spin_limit; // polls before a wait gives up
+  uint32_t ph;         // parity bits of the two staging mbarriers
   int c, w, lane;
   __device__ uint4 a4(int q) const { return reinterpret_cast<const uint4*>(s + C::SM_C4A)[q]; }
   __device__ uint4 b4(int q) const { return reinterpret_cast<const uint4*>(s + C::SM_C4B)[q]; }
@@ -101,13 +103,6 @@ struct BigGroup {
     return s[C::SM_MISC] != 0;
   }
 
-  // rows [r0, r1) of a global xi buffer into the staging area
-  __device__ void stage(const uint32_t* src, int r0, int r1) {
-    const uint4* g = reinterpret_cast<const uint4*>(src + (size_t)r0 * 32);
-    uint4* d = reinterpret_cast<uint4*>(s + C::SM_X);
-    const int n4 = (r1 - r0) * 8;
-    for (int i = threadIdx.x; i < n4; i += C::THREADS) d[i] = __ldcg(g + i);
-  }
 };
 
 // acc[s] += sum_{i in [r0, r1)} X[i - r0][lane] * T[i][w*NPT + s]   (X rows relative to r0)
@@ -127,16 +122,68 @@ __device__ __forceinline__ void big_dot(uint64_t (&acc)[C::NPT], const uint32_t*
   }
 }
 
-// One extension's dot products over all k rows of a global xi buffer, staged in two halves.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// One elected thread: copy `bytes` (a multiple of 16) of global memory to shared memory with the
+// tensor-memory-access unit; completion is counted on `mbar`.  The fences order this thread's view
+// of earlier generic accesses (the other blocks' stores seen through the slot barrier, this block's
+// reads of the buffer) before the asynchronous copy.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+
+// Wait for phase `parity` of `mbar` to complete; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// One extension's dot products over all k rows of a global xi buffer: the rows arrive in three
+// bulk copies into two shared-memory buffers, the copy of the next third overlapping the dot
+// products of the current one.  False (abort raised) when a copy does not complete in time.
 template <class C>
-__device__ __forceinline__ void big_ext(uint64_t (&acc)[C::NPT], BigGroup<C>& g, const uint32_t* src, const uint32_t* T) {
-  g.stage(src, 0, C::H);
-  __syncthreads();
-  big_dot<C>(acc, g.s + C::SM_X, T, 0, C::H, g.w, g.lane);
-  __syncthreads();
-  g.stage(src, C::H, C::K);
-  __syncthreads();
-  big_dot<C>(acc, g.s + C::SM_X, T, C::H, C::K, g.w, g.lane);
+__device__ bool big_ext(uint64_t (&acc)[C::NPT], BigGroup<C>& g, const uint32_t* src, const uint32_t* T) {
+  constexpr int R = C::R;
+  uint32_t* const buf0 = g.s + C::SM_X;
+  uint32_t* const buf1 = buf0 + R * 32;
+  uint64_t* const mb = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
+  if (threadIdx.x == 0) bulk_copy_g2s(buf0, src, (uint32_t)min(R, C::K) * 128u, &mb[0]);
+  for (int t = 0; t < 3; t++) {
+    const int r0 = t * R, r1 = min(C::K, r0 + R);
+    if (t < 2 && threadIdx.x == 0) {
+      const int n0 = r1, n1 = min(C::K, n0 + R);
+      if (n1 > n0) bulk_copy_g2s((t & 1) ? buf0 : buf1, src + (size_t)n0 * 32, (uint32_t)(n1 - n0) * 128u, &mb[(t + 1) & 1]);
+    }
+    const int b = t & 1;
+    bool ok = r1 <= r0 || mbar_wait(&mb[b], (g.ph >> b) & 1u, g.spin_limit);
+    if (r1 > r0) g.ph ^= 1u << b;
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(g.abort, 1u);
+        // the copy of the next third may still be in flight: give it a bounded chance to land
+        if (t < 2) mbar_wait(&mb[(t + 1) & 1], (g.ph >> ((t + 1) & 1)) & 1u, g.spin_limit);
+      }
+      __syncthreads();
+      return false;
+    }
+    if (r1 > r0) big_dot<C>(acc, b ? buf1 : buf0, T, r0, r1, g.w, g.lane);
+    __syncthreads();  // the buffer is refilled by the copy issued in the next iteration
+  }
+  return true;
 }
 
 // RNS Montgomery multiplication x <- x*y*M^-1 mod N (outputs below (k+1)N), this thread's channels.
@@ -165,7 +212,7 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
   uint64_t acc[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) acc[s] = 0;
-  big_ext<C>(acc, g, Xg, g.s + C::SM_T1);
+  if (!big_ext<C>(acc, g, Xg, g.s + C::SM_T1)) return false;
   // 4-5. new B' residues and xi'_j; partial correction-factor sums
   uint32_t kaw = 0;
 #pragma unroll
@@ -195,7 +242,7 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
   const uint32_t alpha = (ks + (1u << (KAW_Q - 2))) >> KAW_Q;
 #pragma unroll
   for (int s = 0; s < NPT; s++) acc[s] = mulw(alpha, g.a4(g.w * NPT + s).w);
-  big_ext<C>(acc, g, XPg, g.s + C::SM_T2);
+  if (!big_ext<C>(acc, g, XPg, g.s + C::SM_T2)) return false;
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const uint4 cb = g.a4(g.w * NPT + s);
@@ -527,7 +574,14 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
   g.abort = a.sync + a.slots;
   g.nbar = 0;
   g.spin_limit = a.spin_limit;
+  g.ph = 0;
   if (g.c == a.absent_slice) return;  // test hook: this slice never arrives; the others time out
+  if (threadIdx.x == 0) {
+    uint64_t* mb = reinterpret_cast<uint64_t*>(smem_raw + C::SM_MBAR);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mb[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mb[1])));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
   big_load_consts<C>(smem_raw, a.cls, g.c);
   const uint32_t n_groups = (a.n_items + 31) / 32;
   uint32_t grp = slot_id;
