@@ -1,14 +1,21 @@
-"""Benchmark: RSA-2048 CRT decryption throughput on the RNS exponentiation path.
+"""Benchmark of the RNS exponentiation library on synthetic, seeded workloads.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
-One step = one mr_rsa_decrypt_crt call over 4096 ciphertexts (uniform in [0, N))
-spread over 16 seeded RSA-2048 keys: 8192 RNS modular exponentiations of
-1024-bit numbers with full-length CRT exponents, plus 4096 Garner recombinations.
-The metric is modular exponentiations per second over all ranks; with N > 1
-(launched under torchrun) every rank runs its own batch (weak scaling, no
-collective on the data path).  `--impl reference` times the CPU oracle (plain
-Python integers, its own square-and-multiply) on the same workload instead.
+Workloads (--workload):
+  rsa2048_crt   (default) one step = one mr_rsa_decrypt_crt call over 4096 ciphertexts (uniform
+                in [0, N)) over 16 seeded RSA-2048 keys: 8192 RNS exponentiations of 1024-bit
+                numbers with full-length CRT exponents plus 4096 Garner recombinations
+  ragged        65,536 encrypt/decrypt requests over 256 keys of 1024-4096 bits (40/30/20/10%),
+                per-size plain launches against the persistent, graph-captured plan
+  serving       Poisson arrivals at 200k requests/s of the same mix: throughput, p50/p99 latency
+  modexp16384   256 exponentiations modulo 16384-bit RSA moduli with 16128-bit exponents
+  rsa1024_enc   64 RSA-1024 public encryptions (e = 65537), one graph replay per step
+  mr1024        Miller-Rabin: 4096 odd 1024-bit candidates x 8 seeded witnesses
+The metric is modular exponentiations per second over all ranks; with N > 1 (launched under
+torchrun) every rank runs its own batch (weak scaling, no collective on the data path).
+`--impl reference` times the CPU oracle (plain Python integers, its own square-and-multiply) on
+the same workload instead.
 
 Everything is printed on stderr except the single JSON result line (rank 0).
 """
@@ -452,6 +459,157 @@ def ragged_workload(rank: int = 0, n: int = N_RAGGED):
     return keys, idx, ops, xs
 
 
+def run_enc1024(args, rank, world, local_rank):
+    """RSA-1024 public encryption of 64 messages (one per key, e = 65537): the call is launch- and
+    latency-bound, so one step is one replay of a CUDA-graph-captured plan; reports throughput and
+    the per-call latency."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1305_3699_gb300 import mr
+    from synth import SplitMix64, load_keys
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    keys = load_keys("rsa1024_x64")
+    r = SplitMix64(0x4D520001 + 0x1000 * rank)
+    msgs = [r.below(k["N"]) for k in keys]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import plain
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 2.0:
+            for m, k in zip(msgs, keys):
+                plain.rsa_encrypt(m, k["e"], k["N"])
+            reps += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": reps * len(msgs) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{reps} passes over the 64 messages, oracle.plain.rsa_encrypt, one process"}
+    ctx = mr.Context(local_rank)
+    hk = [ctx.mr_rsa_key_setup(k["N"], k["e"]) for k in keys]
+    kl = mr.KeyList(hk)
+    m_dev = mr.to_tensor(msgs, 32, device=dev)
+    c_dev = torch.zeros_like(m_dev)
+    stream = torch.cuda.Stream(device=dev)
+    plan = ctx.mr_plan_create(kl, [mr.MR_OP_ENCRYPT] * len(msgs), m_dev, c_dev,
+                              flags=mr.MR_PLAN_GRAPH | mr.MR_PLAN_CONCURRENT)
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            plan.launch(stream)
+    torch.cuda.synchronize()
+    got = mr.from_tensor(c_dev[:2])
+    for j in range(2):
+        assert got[j] == pow(msgs[j], keys[j]["e"], keys[j]["N"]), "benchmark output mismatch"
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            evs[s][0].record(stream)
+            plan.launch(stream)
+            evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    value = len(msgs) * world * args.steps / (total_ms / 1e3)
+    # end to end: H2D of the messages, the graph replay, D2H of the ciphertexts
+    m_host, c_host = m_dev.cpu().pin_memory(), torch.empty_like(m_dev.cpu()).pin_memory()
+    e2e = []
+    with torch.cuda.stream(stream):
+        for _ in range(max(10, args.steps // 4)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m_dev.copy_(m_host, non_blocking=True)
+            plan.launch(stream)
+            c_host.copy_(c_dev, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e2e.append(a.elapsed_time(b))
+    info = plan.info()
+    plan.free()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded keys and messages)",
+                "config": {"workload": "rsa1024_encrypt_64", "messages": len(msgs), "keys": len(keys),
+                           "launch": "one CUDA-graph replay of a prepared plan per step",
+                           "latency_ms_p50": statistics.median(step_ms), "latency_ms_max": max(step_ms),
+                           "kernels_per_step": info["kernels"],
+                           "roofline": "not meaningful: 64 numbers occupy 16 warps of the GPU"},
+                "cpu_baseline": cpu,
+                "e2e": {"value": len(msgs) * world / (statistics.mean(e2e) / 1e3), "unit": UNIT,
+                        "h2d_bytes_per_step": int(m_host.numel() * 4), "d2h_bytes_per_step": int(c_host.numel() * 4),
+                        "latency_ms_p50": statistics.median(e2e)},
+                "gpu_launches": info["kernels"] * args.steps}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_mr1024(args, rank, world, local_rank):
+    """Miller-Rabin batch: 4096 odd 1024-bit candidates (the primes p, q of the 2048-bit keys and
+    seeded random odd numbers, half each) x 8 rounds with seeded witnesses in [2, n-2], one
+    mr_miller_rabin_batch call per step; a round is one exponentiation a^d mod n plus up to s-1
+    squarings."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1305_3699_gb300 import mr
+    from synth import SplitMix64, load_keys
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    rounds, n = 8, 4096
+    keys = load_keys(KEYSET)
+    primes = [k[h] for k in keys for h in ("p", "q")]
+    r = SplitMix64(0x4D520006 + 0x1000 * rank)
+    cands = [primes[i % len(primes)] if i % 2 == 0 else (r.randbits(1024) | 1 | (1 << 1023)) for i in range(n)]
+    wit = [[2 + r.below(c - 3) for _ in range(rounds)] for c in cands]
+    ctx = mr.Context(local_rank)
+    cand_t = mr.to_tensor(cands, 32, device=dev)
+    wit_t = mr.to_tensor([a for ws in wit for a in ws], 32, device=dev)
+    flags = torch.zeros(n, dtype=torch.uint8, device=dev)
+    mask = torch.zeros(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        ctx.mr_miller_rabin_batch(cand_t, wit_t, rounds, flags, mask, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    torch.cuda.synchronize()
+    f = flags.cpu().tolist()
+    assert all(f[i] == 1 for i in range(0, n, 2)), "a prime was reported composite"
+    from oracle import primality
+    for i in (1, 3, 5):
+        assert f[i] == (1 if all(primality.miller_rabin(cands[i], wit[i])) else 0)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            evs[s][0].record(stream)
+            step()
+            evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
+    value = n * rounds * world * args.steps / (total_ms / 1e3)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MR rounds/s (one exponentiation each)", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic (seeded candidates and witnesses)",
+                "config": {"workload": "miller_rabin_1024x4096x8", "candidates": n, "rounds": rounds,
+                           "composites_found": int(n - sum(f))}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_ragged(args, rank, world, local_rank):
     """Ragged batch: one prepared plan per launch mode over the same 65,536 requests."""
     import torch
@@ -656,10 +814,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="ragged workload: keep the default configurations")
+    ap.add_argument("--serve-capacity", type=int, default=4096, help="serving workload: requests per batch slot")
+    ap.add_argument("--serve-slots", type=int, default=3, help="serving workload: batch slots in flight")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ebits", type=int, default=BIG_EBITS,
                     help="exponent bits of the modexp16384 workload (smaller values for profiling runs)")
-    ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving", "modexp16384"])
+    ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving", "modexp16384", "rsa1024_enc", "mr1024"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -676,6 +836,10 @@ def main():
             return run_ragged(args, rank, world, local_rank)
         if args.workload == "modexp16384":
             return run_big(args, rank, world, local_rank)
+        if args.workload == "rsa1024_enc":
+            return run_enc1024(args, rank, world, local_rank)
+        if args.workload == "mr1024":
+            return run_mr1024(args, rank, world, local_rank)
         if args.workload == "serving":
             from paper_1305_3699_gb300.serve import run_serving_bench
             return run_serving_bench(args, rank, world, local_rank, METRIC, UNIT)

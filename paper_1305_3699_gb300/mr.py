@@ -189,6 +189,7 @@ class Key:
 
     def __init__(self, ctx: "Context", handle: int, N: int, e: Optional[int] = None, private: bool = False):
         self.ctx, self.handle, self.N, self.e, self.private = ctx, handle, N, e, private
+        self.half_bits = 0  # bit length of the larger RSA prime when the private CRT parts are set
 
     @property
     def limbs(self) -> int:
@@ -293,7 +294,9 @@ class Context:
         parts = [_limbs(v, hl) for v in (p, q, dp, dq, qinv)]
         self._check(lib.mr_rsa_key_setup(self.handle, _ptr(nl), len(nl), _ptr(el), len(el),
                                          *[_ptr(a) for a in parts], hl, ctypes.byref(h)))
-        return Key(self, h.value, N, e, True)
+        key = Key(self, h.value, N, e, True)
+        key.half_bits = max(p.bit_length(), q.bit_length())
+        return key
 
     # ---- batched calls (torch tensors: rows x limbs, 32-bit, contiguous, on this device)
     def mr_modexp_batch(self, keys, x, e, out, status=None, stream=None):

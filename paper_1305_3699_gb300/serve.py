@@ -61,11 +61,27 @@ class Server:
     """
 
     def __init__(self, ctx: "mr.Context", keys: Sequence["mr.Key"], capacity: int = 2048, slots: int = 3,
-                 row_limbs: int = 128, hbm_budget: int = 1 << 30, flags: int = mr.MR_PLAN_PERSISTENT):
+                 row_limbs: int = 128, hbm_budget: int = 1 << 30, flags: int = mr.MR_PLAN_PERSISTENT,
+                 latency_mappings: bool = True):
         import torch
         self.torch = torch
         self.ctx = ctx
         self.keys = list(keys)
+        self.mappings = {}
+        if latency_mappings:
+            # below full load, more lanes per number shorten each exponentiation's chain of
+            # multiplications: take the widest compiled lane mapping of every class in use
+            classes = set()
+            for k in self.keys:
+                classes.add(mr.mr_class_for_bits(k.N.bit_length())[0])
+                if getattr(k, "half_bits", 0):
+                    classes.add(mr.mr_class_for_bits(k.half_bits)[0])
+            for L in sorted(classes):
+                lanes = mr.mr_class_variants(L)
+                if lanes:
+                    v = max(range(len(lanes)), key=lambda i: lanes[i])
+                    ctx.mr_set_variant(L, v)
+                    self.mappings[L] = lanes[v]
         self.key_ptrs = np.array([k.handle for k in self.keys], dtype=np.uint64)
         self.key_bits = np.array([k.N.bit_length() for k in self.keys], dtype=np.int64)
         self.capacity, self.row_limbs, self.hbm_budget, self.flags = capacity, row_limbs, hbm_budget, flags
@@ -190,7 +206,7 @@ def run_serving_bench(args, rank, world, local_rank, metric, unit):
         rows[i] = np.frombuffer(x.to_bytes(512, "little"), dtype="<u4")
     rows = rows.view(np.int32)
     arrivals = poisson_arrivals(rate, n, 0x4D520005 + rank)
-    srv = Server(ctx, hk, capacity=4096, slots=3)
+    srv = Server(ctx, hk, capacity=args.serve_capacity, slots=args.serve_slots)
     # warm-up on a slice
     w = min(n, 8192)
     srv.run(arrivals[:w] - arrivals[0], np.array(idx[:w]), np.array(ops[:w]), rows[:w])
@@ -205,7 +221,9 @@ def run_serving_bench(args, rank, world, local_rank, metric, unit):
     line = {"metric": metric, "value": modexps / stats["wall_s"], "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded keys, inputs, arrivals)",
-            "config": {"workload": "serving_poisson_200k", "offered_req_per_s": rate, **stats}}
+            "config": {"workload": "serving_poisson_200k", "offered_req_per_s": rate, "slot_capacity": srv.capacity,
+                       "slots": len(srv.slots), "lanes_per_number": {str(L): t for L, t in srv.mappings.items()},
+                       **stats}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
