@@ -35,6 +35,7 @@ SETS = {
     "rsa2048_x16": dict(seed=SEED_BASE + 2, sizes=[2048] * 16),
     "mod16384_x4": dict(seed=SEED_BASE + 3, sizes=[16384] * 4),
     "mix_x256": dict(seed=SEED_BASE + 4, sizes=_mix_sizes()),
+    "rsa8192_x2": dict(seed=SEED_BASE + 7, sizes=[8192] * 2),
     "test_small": dict(seed=SEED_BASE + 99, sizes=[512] * 4 + [768] * 4),
 }
 

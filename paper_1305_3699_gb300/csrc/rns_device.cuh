@@ -45,6 +45,13 @@ __device__ __forceinline__ uint32_t redc(uint64_t v, uint32_t m, uint32_t mi) {
   uint32_t r = hi32(madw(q, m, v));
   return min(r, r - m);
 }
+// The same without the final conditional subtraction: for v < 2^32 m the result is in [0, 2m).
+// Used for temporaries that only feed further products: with m < 2^30 a product of such a value
+// with a residue below 2m stays below 2^32 m, so a later reduction still applies.
+__device__ __forceinline__ uint32_t redc_lazy(uint64_t v, uint32_t m, uint32_t mi) {
+  uint32_t q = lo32(v) * mi;
+  return hi32(madw(q, m, v));
+}
 // Any v < 2^64: fold the high word with r32 = 2^32 mod m, then reduce.  Result v 2^-32 mod m in [0, m].
 __device__ __forceinline__ uint32_t redc64(uint64_t v, uint32_t m, uint32_t mi, uint32_t r32) {
   return redc(madw(hi32(v), r32, lo32(v)), m, mi);
@@ -91,6 +98,7 @@ struct Cfg {
   static constexpr int SM_WORDS = SM_XI + IPB * XS;
   static constexpr int SMEM_BYTES = SM_WORDS * 4;
   static_assert(TPI == 1 || TPI == 2 || TPI == 4 || TPI == 8 || TPI == 16 || TPI == 32, "TPI must divide 32");
+  static_assert(K >= 16, "k >= 16 keeps every channel prime below isqrt(2^64/16) = 2^30 (lazy reductions)");
   static_assert(VEC == 2 || VEC == 4, "vector width");
   static_assert((SM_T2 % 4) == 0 && (SM_CB4 % 4) == 0 && (SM_CB2 % 2) == 0 && (SM_XI % 4) == 0, "alignment");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
@@ -210,11 +218,11 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
     const uint4 cb = sm.cb4(t, s);
-    uint32_t sb = redc(mulw(xb[s], yb[s]), cb.x, cb.y);
+    uint32_t sb = redc_lazy(mulw(xb[s], yb[s]), cb.x, cb.y);  // [0, 2m): only multiplied again
     uint32_t xi = redc(mulw(sb, kxi[s]), cb.x, cb.y);
     if (o < K) xib[o] = xi;
     const uint4 cp = sm.cp4(t, s);
-    sp[s] = redc(mulw(xp[s], yp[s]), cp.x, cp.y);
+    sp[s] = redc_lazy(mulw(xp[s], yp[s]), cp.x, cp.y);  // [0, 2m'): only multiplied again
   }
   __syncwarp();
   // 3. extension B -> B': qhat_j = sum_i xi_i |M/m_i|_{m'_j}   (k-term 64-bit dot products)
