@@ -201,11 +201,11 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
   for (int s = 0; s < NPT; s++) {
     const int q = g.w * NPT + s, o = g.c * C::SC + q;
     const uint4 cb = g.a4(q);
-    uint32_t sb = redc(mulw(xb[s], yb[s]), cb.x, cb.y);
+    uint32_t sb = redc_lazy(mulw(xb[s], yb[s]), cb.x, cb.y);  // [0, 2m): only multiplied again
     uint32_t xi = redc(mulw(sb, kxi[s]), cb.x, cb.y);
     if (o < K) Xg[(size_t)o * 32 + g.lane] = xi;
     const uint4 cp = g.b4(q);
-    sp[s] = redc(mulw(xp[s], yp[s]), cp.x, cp.y);
+    sp[s] = redc_lazy(mulw(xp[s], yp[s]), cp.x, cp.y);
   }
   if (!g.barrier()) return false;
   // 3. extension B -> B'
@@ -220,7 +220,7 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
     const int q = g.w * NPT + s, o = g.c * C::SC + q;
     const uint4 cp = g.b4(q);
     const uint2 c2 = g.b2(q);
-    uint32_t qh = redc64(acc[s], cp.x, cp.y, cp.z);
+    uint32_t qh = redc64_lazy(acc[s], cp.x, cp.y, cp.z);
     xp[s] = redc(madw(sp[s], cp.w, mulw(qh, cmul[s])), cp.x, cp.y);
     uint32_t xpj = redc(madw(sp[s], c2.x, mulw(qh, cd[s])), cp.x, cp.y);
     if (o < K) XPg[(size_t)o * 32 + g.lane] = xpj;

@@ -56,6 +56,10 @@ __device__ __forceinline__ uint32_t redc_lazy(uint64_t v, uint32_t m, uint32_t m
 __device__ __forceinline__ uint32_t redc64(uint64_t v, uint32_t m, uint32_t mi, uint32_t r32) {
   return redc(madw(hi32(v), r32, lo32(v)), m, mi);
 }
+// The same with a result in [0, 2m) (see redc_lazy).
+__device__ __forceinline__ uint32_t redc64_lazy(uint64_t v, uint32_t m, uint32_t mi, uint32_t r32) {
+  return redc_lazy(madw(hi32(v), r32, lo32(v)), m, mi);
+}
 
 // 96-bit accumulate (s2:s1:s0) += a*b (one-time conversions only)
 __device__ __forceinline__ void mac96(uint32_t& s0, uint32_t& s1, uint32_t& s2, uint32_t a, uint32_t b) {
@@ -236,7 +240,7 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
     const int o = t * NPT + s;
     const uint4 cp = sm.cp4(t, s);
     const uint2 c2 = sm.cp2(t, s);
-    uint32_t qh = redc64(acc[s], cp.x, cp.y, cp.z);
+    uint32_t qh = redc64_lazy(acc[s], cp.x, cp.y, cp.z);  // [0, 2m'): only multiplied again
     xp[s] = redc(madw(sp[s], cp.w, mulw(qh, cmul[s])), cp.x, cp.y);
     uint32_t xpj = redc(madw(sp[s], c2.x, mulw(qh, cd[s])), cp.x, cp.y);
     if (o < K) xpb[o] = xpj;
