@@ -134,3 +134,30 @@ def test_bounded_wait_times_out_and_context_recovers(mr, ctx):
     assert st == [0] * 32
     for j in range(32):
         assert got[j] == plain.modexp(xs[j], es[j], N), j
+
+
+def test_rsa8192_encrypt_decrypt_round_trip(mr, ctx):
+    """8192-bit RSA keys: encryption in the 8192-bit class (multi-block groups), CRT decryption on
+    4096-bit halves (lane-group class), both equal to the oracle, and decrypt(encrypt(m)) = m."""
+    keys = load_keys("rsa8192_x2")
+    hk = [ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]) for k in keys]
+    r = SplitMix64(0x4D520043)
+    idx = [j % 2 for j in range(10)]
+    msgs = [r.below(keys[i]["N"]) for i in idx]
+    msgs[0], msgs[1] = 0, keys[1]["N"] - 1
+    m = mr.to_tensor(msgs, 256)
+    c = torch.zeros_like(m)
+    ctx.mr_rsa_encrypt([hk[i] for i in idx], m, c)
+    m2 = torch.zeros_like(m)
+    st = torch.full((len(msgs),), 255, dtype=torch.uint8, device="cuda")
+    ctx.mr_rsa_decrypt_crt([hk[i] for i in idx], c, m2, st)
+    torch.cuda.synchronize()
+    cs, back = mr.from_tensor(c), mr.from_tensor(m2)
+    assert st.cpu().tolist() == [0] * len(msgs)
+    for j, i in enumerate(idx):
+        k = keys[i]
+        assert cs[j] == plain.rsa_encrypt(msgs[j], k["e"], k["N"]), j
+        assert back[j] == msgs[j], j
+    j = 3
+    k = keys[idx[j]]
+    assert back[j] == plain.rsa_decrypt_crt(cs[j], k["p"], k["q"], k["dp"], k["dq"], k["qinv"])
