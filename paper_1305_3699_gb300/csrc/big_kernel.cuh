@@ -11,9 +11,11 @@
 // shared memory for the whole launch.  The two base extensions exchange the
 // CRT coefficients xi / xi' of all channels through a per-slot buffer in global
 // memory (L2-resident): every CTA writes its slice, the CTAs of the slot meet at
-// a barrier, and each CTA stages the k rows into shared memory in two halves
-// for its dot products.  The fixed-point correction factor is summed from one
-// partial per slice.  Two barriers per multiplication.
+// a barrier, and each CTA brings the k rows into shared memory in thirds with
+// bulk copies (cp.async.bulk, completion on an mbarrier) into two buffers, the
+// copy of the next third overlapping the dot products of the current one.  The
+// fixed-point correction factor is summed from one partial per slice.  Two
+// barriers per multiplication.
 //
 // The CTAs of a slot wait on one another, so the kernel is started as one
 // cooperative launch (every CTA resident).  Each barrier wait is bounded: on

@@ -15,9 +15,11 @@
 //
 // Word arithmetic.  Channel primes m < 2^31 with k*m^2 < 2^64 (chosen at
 // setup), so a k-term dot product of residues accumulates exactly in one
-// 64-bit register with one mad.wide.u32 per term (full IMAD rate on sm_103)
-// and is reduced once.  Residues are kept in per-channel Montgomery form
-// x*2^32 mod m ("hat"); reductions use mad.wide (no mul.hi).
+// 64-bit register with one mad.wide.u32 per term (two issue slots of the
+// integer-multiply pipe, the cheapest exact 32x32->64 product; a carry-chain
+// accumulation costs more) and is reduced once.  Residues are kept in
+// per-channel Montgomery form x*2^32 mod m ("hat"); reductions use mad.wide
+// (no mul.hi).
 #pragma once
 #include <cstdint>
 
