@@ -31,6 +31,7 @@ struct ClassEntry {
   uint32_t variant = 0;  // selected lane mapping
   uint32_t wcap = 0;     // window-width cap chosen by mr_autotune (0 = the default rule)
   bool tuned = false;
+  bool pinned = false;   // lane mapping chosen by the caller (mr_set_variant, MR_VARIANT_<L>) or the tuner
   const KernelVariant& kv() const { return kern->var[variant]; }
   bool big() const { return kern && kern->big; }
 };
@@ -155,7 +156,10 @@ mr_status get_class(mr_ctx* ctx, uint32_t L, ClassEntry** out) {
     const char* v = getenv(ev.c_str());
     if (v) {
       unsigned idx = (unsigned)atoi(v);
-      if (idx < ce->kern->n_variants) ce->variant = idx;
+      if (idx < ce->kern->n_variants) {
+        ce->variant = idx;
+        ce->pinned = true;
+      }
     }
   }
   size_t bytes = ce->host.block.size() * 4;
@@ -746,6 +750,7 @@ mr_status autotune_class(mr_ctx* ctx, ClassEntry* ce, uint32_t n, uint32_t exp_b
   ce->variant = best_v;
   ce->wcap = best_w;
   ce->tuned = true;
+  ce->pinned = true;
   if (res) {
     res->variant = best_v;
     res->lanes_per_number = ce->big() ? 0u : ce->kern->var[best_v].tpi;
@@ -1159,7 +1164,22 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
     mr_status s = get_class(ctx, L, &ce);
     if (s) return s;
     if (ce->big()) return fail(ctx, MR_ERR_SIZE, "Miller-Rabin takes candidates of at most 4096 bits");
-    const KernelVariant& k = ce->kv();
+    // a candidate's rounds run one after another in its lane group: unless the caller chose a
+    // mapping, take the narrowest one that still gives at least 8 warps per SM for this batch
+    uint32_t vsel = ce->variant;
+    if (!ce->pinned) {
+      int sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+      vsel = 0;
+      for (uint32_t v = 0; v < ce->kern->n_variants; v++) {
+        if (ce->kern->var[v].tpi > ce->kern->var[vsel].tpi) vsel = v;  // the widest, unless a narrower one fills the GPU
+      }
+      for (uint32_t v = 0; v < ce->kern->n_variants; v++) {
+        const double warps = (double)n * ce->kern->var[v].tpi / 32.0;
+        if (warps >= 8.0 * sms && ce->kern->var[v].tpi < ce->kern->var[vsel].tpi) vsel = v;
+      }
+    }
+    const KernelVariant& k = ce->kern->var[vsel];
     const uint32_t wbits = choose_window(32 * n_limbs, 0, window_cap(ce));
     const size_t tab_words = modexp_scratch_words(k, (uint32_t)n, wbits);
     const size_t crow_words = n * 3 * (size_t)ce->host.W;
@@ -1486,6 +1506,7 @@ mr_status mr_set_variant(mr_ctx* ctx, uint32_t class_bits, uint32_t variant) {
     if (s) return s;
     if (variant >= ce->kern->n_variants) return fail(ctx, MR_ERR_ARG, "no such variant");
     ce->variant = variant;
+    ce->pinned = true;
     return MR_OK;
   });
 }
