@@ -210,3 +210,37 @@ def test_rsa2048_full_workload_sampled(mr, ctx):
         assert got[j] == plain.rsa_decrypt_crt(cts[j], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]), j
     for j in range(n):
         assert pow(got[j], 65537, keys[idx[j]]["N"]) == cts[j], j
+
+
+@pytest.mark.parametrize("bits", [512, 1024, 1536, 2048, 3072, 4096])
+def test_modexp_every_lane_mapping(mr, bits):
+    """Every compiled lane mapping of every class gives the oracle's results (the default mapping is
+    covered above; this selects each one explicitly on a fresh context)."""
+    lanes = mr.mr_class_variants(bits)
+    if bits == 512:
+        pool = load_keys("rsa1024_x64")
+    elif bits == 4096:
+        pool = load_keys("rsa8192_x2")
+    else:
+        pool = [k for k in load_keys("mix_x256") if k["bits"] == 2 * bits]
+    for v in range(len(lanes)):
+        c = mr.Context(0)
+        try:
+            c.mr_set_variant(bits, v)
+            _modexp_case(mr, c, [bits] * 41, [min(bits, 384)] * 41, 1000 + 10 * v + bits % 7)
+            if pool:  # CRT decryption: both halves and the recombination run in this class
+                keys = pool[:3]
+                nk = len(keys)
+                hk = [c.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]) for k in keys]
+                r = SplitMix64(2000 + v + bits)
+                cts = [r.below(keys[j % nk]["N"]) for j in range(9)]
+                ct = mr.to_tensor(cts, 2 * bits // 32)
+                m = torch.zeros_like(ct)
+                c.mr_rsa_decrypt_crt([hk[j % nk] for j in range(9)], ct, m)
+                torch.cuda.synchronize()
+                got = mr.from_tensor(m)
+                for j in range(9):
+                    k = keys[j % nk]
+                    assert got[j] == plain.rsa_decrypt_crt(cts[j], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]), (v, j)
+        finally:
+            c.close()
