@@ -618,6 +618,24 @@ mr_status guarded(mr_ctx* ctx, F&& f) {
   }
 }
 
+// Per-candidate verdicts from per-round items: probable prime when every round passed; bit r of
+// the mask set when round r (< 32) passed.
+__global__ void mr_combine_kernel(const uint8_t* item_pass, uint32_t n, uint32_t rounds, uint8_t* is_prime,
+                                  uint32_t* round_mask) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  uint32_t m = 0;
+  uint8_t all = 1;
+  for (uint32_t r = 0; r < rounds; r++) {
+    const uint8_t p = item_pass[(size_t)c * rounds + r];
+    all &= p;
+    if (p && r < 32) m |= 1u << r;
+  }
+  is_prime[c] = all;
+  if (round_mask) round_mask[c] = m;
+}
+
+
 // ------------------------------------------------------------- autotuning
 
 // Seeded host generator for the synthetic tuning batch (SplitMix64).
@@ -1164,34 +1182,47 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
     mr_status s = get_class(ctx, L, &ce);
     if (s) return s;
     if (ce->big()) return fail(ctx, MR_ERR_SIZE, "Miller-Rabin takes candidates of at most 4096 bits");
-    // a candidate's rounds run one after another in its lane group: unless the caller chose a
-    // mapping, take the narrowest one that still gives at least 8 warps per SM for this batch
+    // The rounds of a candidate are independent: each runs as its own work item (the setup of
+    // the candidate is repeated per round, a few hundredths of a round's cost) and a second
+    // kernel combines the verdicts.  The constant-dump hook keeps one item per candidate.
+    const uint32_t per = (rounds > 1 && !ctx->mr_dbg && (uint64_t)n * rounds <= 0xffffffffull) ? rounds : 1u;
+    const size_t items = n * (size_t)per;
+    // unless the caller chose a lane mapping, take the narrowest one that gives at least 8 warps per
+    // SM for this many items (the widest when none does)
     uint32_t vsel = ce->variant;
     if (!ce->pinned) {
       int sms = 0;
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
       vsel = 0;
+      for (uint32_t v = 0; v < ce->kern->n_variants; v++)
+        if (ce->kern->var[v].tpi > ce->kern->var[vsel].tpi) vsel = v;
       for (uint32_t v = 0; v < ce->kern->n_variants; v++) {
-        if (ce->kern->var[v].tpi > ce->kern->var[vsel].tpi) vsel = v;  // the widest, unless a narrower one fills the GPU
-      }
-      for (uint32_t v = 0; v < ce->kern->n_variants; v++) {
-        const double warps = (double)n * ce->kern->var[v].tpi / 32.0;
+        const double warps = (double)items * ce->kern->var[v].tpi / 32.0;
         if (warps >= 8.0 * sms && ce->kern->var[v].tpi < ce->kern->var[vsel].tpi) vsel = v;
       }
     }
     const KernelVariant& k = ce->kern->var[vsel];
     const uint32_t wbits = choose_window(32 * n_limbs, 0, window_cap(ce));
-    const size_t tab_words = modexp_scratch_words(k, (uint32_t)n, wbits);
-    const size_t crow_words = n * 3 * (size_t)ce->host.W;
+    const size_t tab_words = modexp_scratch_words(k, (uint32_t)items, wbits);
+    const size_t crow_words = items * 3 * (size_t)ce->host.W;
     const size_t off_crow = align256(tab_words * 4);
+    const size_t off_pass = align256(off_crow + crow_words * 4);
+    const size_t bytes = per > 1 ? off_pass + items : off_crow + crow_words * 4;
     void* dev = nullptr;
-    cudaError_t e = cudaMallocFromPoolAsync(&dev, off_crow + crow_words * 4, ctx->pool, (cudaStream_t)stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&dev, bytes, ctx->pool, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, std::string("scratch allocation failed: ") + cudaGetErrorString(e));
     char* base = static_cast<char*>(dev);
-    MRArgs a{ce->dev, cand, witness, dev_is_probable_prime, dev_round_mask, reinterpret_cast<uint32_t*>(base),
-             reinterpret_cast<uint32_t*>(base + off_crow), (uint32_t)n, n_limbs, rounds, wbits, ctx->mr_dbg};
-    unsigned grid = (unsigned)((n + k.ipb - 1) / k.ipb);
+    uint8_t* verdicts = per > 1 ? reinterpret_cast<uint8_t*>(base + off_pass) : dev_is_probable_prime;
+    MRArgs a{ce->dev, cand, witness, verdicts, per > 1 ? nullptr : dev_round_mask, reinterpret_cast<uint32_t*>(base),
+             reinterpret_cast<uint32_t*>(base + off_crow), (uint32_t)items, n_limbs, rounds, wbits, ctx->mr_dbg,
+             per};
+    unsigned grid = (unsigned)((items + k.ipb - 1) / k.ipb);
     e = timed_launch(ctx, 0, (cudaStream_t)stream, [&] { return k.mr(a, grid, (cudaStream_t)stream); });
+    if (e == cudaSuccess && per > 1) {
+      mr_combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+          verdicts, (uint32_t)n, rounds, dev_is_probable_prime, dev_round_mask);
+      e = cudaGetLastError();
+    }
     cudaError_t e2 = cudaFreeAsync(dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");

@@ -20,14 +20,16 @@ struct LaunchArgs {
 
 struct MRArgs {
   const uint32_t* cls;
-  const uint32_t* cand;     // n rows of n_limbs
-  const uint32_t* witness;  // n*rounds rows of n_limbs
-  uint8_t* is_prime;        // n
-  uint32_t* round_mask;     // n or nullptr
+  const uint32_t* cand;     // candidates, rows of n_limbs
+  const uint32_t* witness;  // candidates*rounds rows of n_limbs (candidate-major)
+  uint8_t* is_prime;        // per candidate (per = 1) or per item verdict bytes (per = rounds)
+  uint32_t* round_mask;     // per candidate or nullptr (only with per = 1)
   uint32_t* scratch;        // window tables, per warp (1 << wbits) x 2 NPT x 32 words
-  uint32_t* crow;           // per candidate 3W words: M mod N, M^2 mod N, N - (M mod N)
-  uint32_t n, n_limbs, rounds, wbits;
+  uint32_t* crow;           // per item 3W words: M mod N, M^2 mod N, N - (M mod N)
+  uint32_t n;               // work items: candidates * per
+  uint32_t n_limbs, rounds, wbits;
   uint32_t* dbg;            // nullptr, or per candidate mr_debug_words(k, W) words of derived constants
+  uint32_t per;             // items per candidate: 1 (an item runs all rounds) or rounds (one round each)
 };
 
 // Barrier polls of the large-class kernel before a wait gives up (x 0.03-0.3 us each: about 1 s).

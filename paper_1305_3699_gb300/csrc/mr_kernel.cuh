@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
   const bool live = g_raw < a.n;
   const uint32_t g = live ? g_raw : a.n - 1;
   const uint32_t nl = a.n_limbs;
-  const uint32_t* N = a.cand + (size_t)g * nl;
+  // item g: candidate g / per; rounds [r0, r1) (all of them when per = 1, round g % per otherwise)
+  const uint32_t cidx = g / a.per;
+  const uint32_t r0 = a.per == 1 ? 0u : g % a.per, r1 = a.per == 1 ? a.rounds : r0 + 1;
+  const uint32_t* N = a.cand + (size_t)cidx * nl;
   uint32_t* crow = a.crow + (size_t)g * 3 * W;
   uint32_t* xib = sm.xi(item_in_block);
   uint32_t* xpb = xib + C::KP;
@@ -254,8 +257,8 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
   const uint32_t nwin = __reduce_max_sync(0xffffffffu, (dbits + wb - 1) / wb);
   uint32_t mask = 0;
   bool all_pass = true;
-  for (uint32_t r = 0; r < a.rounds; r++) {
-    const uint32_t* wit = a.witness + ((size_t)g * a.rounds + r) * nl;
+  for (uint32_t r = r0; r < r1; r++) {
+    const uint32_t* wit = a.witness + ((size_t)cidx * a.rounds + r) * nl;
     uint32_t xb[NPT], xp[NPT], yb[NPT], yp[NPT];
     to_rns<C>(xb, xp, wit, special ? 0 : (int)min(nl, (uint32_t)W), a.cls, sm, t);
     mont_mul<C>(xb, xp, r2b, r2p, kxi, cmul, cd, sm, xib, xpb, t);  // a~ = a M mod N
@@ -318,7 +321,8 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
   if (live && t == 0) {
     uint8_t prime = all_pass ? 1 : 0;
     uint32_t m = mask;
-    const uint32_t all_rounds = a.rounds >= 32 ? 0xffffffffu : (1u << a.rounds) - 1u;
+    uint32_t all_rounds = 0;  // this item's rounds below 32
+    for (uint32_t r = r0; r < r1 && r < 32; r++) all_rounds |= 1u << r;
     if (special == 1u || special == 3u) {
       prime = 0;
       m = 0;
@@ -333,8 +337,8 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
       const uint64_t d5 = (n64 - 1) >> s5;
       prime = 1;
       m = 0;
-      for (uint32_t r = 0; r < a.rounds; r++) {
-        const uint32_t* wit = a.witness + ((size_t)g * a.rounds + r) * nl;
+      for (uint32_t r = r0; r < r1; r++) {
+        const uint32_t* wit = a.witness + ((size_t)cidx * a.rounds + r) * nl;
         uint64_t w = 0;
         for (int i = (int)nl - 1; i >= 0; i--) w = ((w << 32) | wit[i]) % n64;
         uint64_t y = 1 % n64, b = w, e = d5;
@@ -352,8 +356,8 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
         if (!pass) prime = 0;
       }
     }
-    a.is_prime[g] = prime;
-    if (a.round_mask) a.round_mask[g] = m;
+    a.is_prime[g] = prime;  // per = rounds: this round's verdict, combined per candidate afterwards
+    if (a.round_mask && a.per == 1) a.round_mask[g] = m;
   }
 }
 
