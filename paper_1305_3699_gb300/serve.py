@@ -187,44 +187,3 @@ def poisson_arrivals(rate: float, n: int, seed: int) -> np.ndarray:
         t += r.exponential(rate)
         out[i] = t
     return out
-
-
-def run_serving_bench(args, rank, world, local_rank, metric, unit):
-    """Serving workload: Poisson arrivals at 200k requests/s over the 256 mixed-size keys."""
-    import json
-    import torch
-    import bench as _bench  # the workload generator of the ragged mix
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    rate = 200_000.0
-    n = max(4096, int(rate * max(1.0, args.steps * 0.2)))
-    keys, idx, ops, xs = _bench.ragged_workload(rank, n)
-    ctx = mr.Context(local_rank)
-    hk = [ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]) for k in keys]
-    rows = np.zeros((n, 128), dtype=np.uint32)
-    for i, x in enumerate(xs):
-        rows[i] = np.frombuffer(x.to_bytes(512, "little"), dtype="<u4")
-    rows = rows.view(np.int32)
-    arrivals = poisson_arrivals(rate, n, 0x4D520005 + rank)
-    srv = Server(ctx, hk, capacity=args.serve_capacity, slots=args.serve_slots)
-    # warm-up on a slice
-    w = min(n, 8192)
-    srv.run(arrivals[:w] - arrivals[0], np.array(idx[:w]), np.array(ops[:w]), rows[:w])
-    out, status, lat, stats = srv.run(arrivals, np.array(idx), np.array(ops), rows)
-    modexps = sum((1 if ops[i] == 0 else 2) for i in range(n) if not np.isnan(lat[i]))
-    # results identical to the batched call on the same requests
-    check = list(range(0, n, max(1, n // 64)))
-    k0 = keys[idx[check[0]]]
-    want = pow(xs[check[0]], k0["e"] if ops[check[0]] == 0 else k0["d"], k0["N"])
-    got = int.from_bytes(out[check[0]].view(np.uint32).astype("<u4").tobytes(), "little")
-    assert got == want, "serving result mismatch"
-    line = {"metric": metric, "value": modexps / stats["wall_s"], "unit": unit, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded keys, inputs, arrivals)",
-            "config": {"workload": "serving_poisson_200k", "offered_req_per_s": rate, "slot_capacity": srv.capacity,
-                       "slots": len(srv.slots), "lanes_per_number": {str(L): t for L, t in srv.mappings.items()},
-                       **stats}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
-    return 0
