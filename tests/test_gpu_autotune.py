@@ -72,3 +72,27 @@ def test_plan_autotune_flag_same_results(mr):
             assert got[j] == want
     finally:
         ctx.close()
+
+
+def test_autotune_large_class_then_exact(mr):
+    """The tuner on a large class (one lane mapping; window widths up to 8) and exact results after."""
+    ctx = mr.Context(0)
+    try:
+        res = ctx.mr_autotune(8192, 40, 96)
+        assert res["variant"] == 0 and res["lanes_per_number"] == 0
+        assert 1 <= res["window"] <= 8 and res["ms"] > 0
+        r = SplitMix64(79)
+        N = r.randbits(8192) | 1 | (1 << 8191)
+        h = ctx.mr_rns_setup(N)
+        xs = [r.below(N) for _ in range(33)]
+        es = [r.randbits(96) for _ in range(33)]
+        x = mr.to_tensor(xs, 256)
+        e = mr.to_tensor(es, 3)
+        out = torch.zeros_like(x)
+        ctx.mr_modexp_batch([h] * 33, x, e, out)
+        torch.cuda.synchronize()
+        got = mr.from_tensor(out)
+        for j in range(33):
+            assert got[j] == plain.modexp(xs[j], es[j], N), j
+    finally:
+        ctx.close()
