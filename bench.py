@@ -254,6 +254,45 @@ def oracle_big_throughput(keys, idx, xs, es, steps: int = 1, warmup: int = 0):
     return value, cores, desc, times
 
 
+def _oracle_mixed_chunk(args):
+    from oracle import plain
+    t0 = time.perf_counter()
+    for op, x, k in args:
+        if op == 0:
+            plain.rsa_encrypt(x, k["e"], k["N"])
+        else:
+            plain.rsa_decrypt_crt(x, k["p"], k["q"], k["dp"], k["dq"], k["qinv"])
+    return time.perf_counter() - t0, len(args)
+
+
+def oracle_mixed_throughput(keys, idx, ops, xs, seconds: float = 10.0):
+    """The oracle on a bounded prefix of a mixed request list, on every host core: modexp/s
+    (an encryption counts one exponentiation, a CRT decryption two)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        probe = [[(ops[j], xs[j], keys[idx[j]])] for j in range(cores)]
+        t0 = time.perf_counter()
+        pool.map(_oracle_mixed_chunk, probe)
+        per = max(1e-4, time.perf_counter() - t0)
+        n = max(cores, min(len(xs), int(seconds / per) * cores))
+        tasks = [(ops[j], xs[j], keys[idx[j]]) for j in range(n)]
+        t0 = time.perf_counter()
+        pool.map(_oracle_mixed_chunk, [tasks[i::cores] for i in range(cores)])
+        dt = time.perf_counter() - t0
+    modexps = sum(1 if ops[j] == 0 else 2 for j in range(n))
+    desc = f"first {n} requests of the mix ({modexps} modexps), oracle.plain on {cores} processes"
+    return modexps / dt, cores, desc
+
+
+def _oracle_mr_chunk(args):
+    from oracle import primality
+    t0 = time.perf_counter()
+    for n, ws in args:
+        primality.miller_rabin(n, ws)
+    return time.perf_counter() - t0, len(args)
+
+
 # --------------------------------------------------------------- reference
 def run_reference(args, rank, world):
     if rank != 0:
@@ -598,13 +637,25 @@ def run_mr1024(args, rank, world, local_rank):
     torch.cuda.synchronize()
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
     value = n * rounds * world * args.steps / (total_ms / 1e3)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import multiprocessing as mpr
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        sample = [(cands[j], wit[j]) for j in range(min(n, 4 * cores))]
+        with mpr.get_context("spawn").Pool(cores) as pool:
+            t0 = time.perf_counter()
+            pool.map(_oracle_mr_chunk, [sample[i::cores] for i in range(cores)])
+            dt = time.perf_counter() - t0
+        cpu = {"value": len(sample) * rounds / dt, "unit": "MR rounds/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {len(sample)} candidates x {rounds} rounds, oracle.primality on {cores} processes"}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MR rounds/s (one exponentiation each)", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
                 "data": "synthetic (seeded candidates and witnesses)",
                 "config": {"workload": "miller_rabin_1024x4096x8", "candidates": n, "rounds": rounds,
-                           "composites_found": int(n - sum(f))}}
+                           "composites_found": int(n - sum(f))},
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -626,6 +677,11 @@ def run_ragged(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     modexps = sum(1 if o == 0 else 2 for o in ops)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        log("timing the CPU oracle on a bounded sample ...")
+        v, cores, desc = oracle_mixed_throughput(keys, idx, ops, xs)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     # every mode runs the same tuned kernels: tune each size class of the mix once, with its item
     # count and longest exponent in this workload
     per_class = {}
@@ -681,7 +737,8 @@ def run_ragged(args, rank, world, local_rank):
                        "keys": 256, "mix_bits": [b for b, _ in MIX], "mix_weights": [w for _, w in MIX],
                        "l2": "flushed between timed steps (512 MB write)", "modes": res,
                        "autotune": {str(L): v for L, v in tuning.items()},
-                       "speedup_vs_per_size_plain": res["per_size_plain"]["ms_per_step"] / rp["ms_per_step"]}}
+                       "speedup_vs_per_size_plain": res["per_size_plain"]["ms_per_step"] / rp["ms_per_step"]},
+            "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -819,6 +876,11 @@ def run_serving_bench(args, rank, world, local_rank):
     rate = 200_000.0
     n = max(4096, int(rate * max(1.0, args.steps * 0.2)))
     keys, idx, ops, xs = ragged_workload(rank, n)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        log("timing the CPU oracle on a bounded sample ...")
+        v, cores, desc = oracle_mixed_throughput(keys, idx, ops, xs)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     ctx = mr.Context(local_rank)
     hk = [ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]) for k in keys]
     rows = np.zeros((n, 128), dtype=np.uint32)
@@ -843,7 +905,8 @@ def run_serving_bench(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded keys, inputs, arrivals)",
             "config": {"workload": "serving_poisson_200k", "offered_req_per_s": rate, "slot_capacity": srv.capacity,
                        "slots": len(srv.slots), "lanes_per_number": {str(L): t for L, t in srv.mappings.items()},
-                       **stats}}
+                       **stats},
+            "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
