@@ -237,18 +237,22 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
     KAWg[g.c * 32 + g.lane] = v;
   }
   if (!g.barrier()) return false;
-  // 6. exact extension B' -> B with a' from the slice partials; the correction -a'|M'| enters
-  //    the accumulator before the dot product (E = -M' 2^64 mod m_i)
-  uint32_t ks = 0;
-  for (int u = 0; u < C::SLICES; u++) ks += __ldcg(KAWg + u * 32 + g.lane);
-  const uint32_t alpha = (ks + (1u << (KAW_Q - 2))) >> KAW_Q;
+  // 6. exact extension B' -> B with a' from the slice partials (loaded before the dot products,
+  //    summed after them); the correction -a'|M'| enters as a' E with E = -M' 2^64 mod m_i
+  uint32_t kp[C::SLICES];
 #pragma unroll
-  for (int s = 0; s < NPT; s++) acc[s] = mulw(alpha, g.a4(g.w * NPT + s).w);
+  for (int u = 0; u < C::SLICES; u++) kp[u] = __ldcg(KAWg + u * 32 + g.lane);
+#pragma unroll
+  for (int s = 0; s < NPT; s++) acc[s] = 0;
   if (!big_ext<C>(acc, g, XPg, g.s + C::SM_T2)) return false;
+  uint32_t ks = 0;
+#pragma unroll
+  for (int u = 0; u < C::SLICES; u++) ks += kp[u];
+  const uint32_t alpha = (ks + (1u << (KAW_Q - 2))) >> KAW_Q;
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const uint4 cb = g.a4(g.w * NPT + s);
-    xb[s] = redc64(acc[s], cb.x, cb.y, cb.z);
+    xb[s] = redc64(madw(alpha, cb.w, acc[s]), cb.x, cb.y, cb.z);
   }
   return true;
 }
