@@ -34,9 +34,10 @@
  * lanes and support every call.  The large classes (8192 and 16384 bits) run
  * one group of 32 numbers across several thread blocks that exchange the base
  * extension's coefficients through device memory, in one cooperative launch;
- * they serve mr_modexp_batch and mr_rsa_encrypt.  CRT decryption takes keys of
- * at most 8192 bits (halves of at most 4096), Miller-Rabin and mixed batches
- * take at most 4096-bit numbers; larger inputs return MR_ERR_SIZE.
+ * they serve mr_modexp_batch, mr_rsa_encrypt and the halves of mr_rsa_decrypt_crt
+ * (16384-bit keys: 8192-bit halves, recombined in binary by one warp per
+ * decryption).  Miller-Rabin and mixed batches take at most 4096-bit numbers;
+ * larger inputs return MR_ERR_SIZE.
  */
 #ifndef MR_H
 #define MR_H
@@ -142,8 +143,8 @@ mr_status mr_rsa_encrypt(mr_ctx *ctx, const mr_key *const *keys, size_t n, const
 /* RSA decryption through the CRT: m_p = c^dp mod p, m_q = c^dq mod q (two
  * independent half-size exponentiations), h = qinv (m_p - m_q) mod p,
  * m = m_q + h q.  Equals c^d mod N (Sec. 3.3 defines d).  Keys need their
- * private parts (else MR_ERR_KEY).  c[i] < N_i (else status RANGE).
- * Layout as mr_modexp_batch. */
+ * private parts (else MR_ERR_KEY); keys of up to 16384 bits.  c[i] < N_i
+ * (else status RANGE and a zero output).  Layout as mr_modexp_batch. */
 mr_status mr_rsa_decrypt_crt(mr_ctx *ctx, const mr_key *const *keys, size_t n, const uint32_t *c,
                              uint32_t c_stride, uint32_t *m, uint32_t m_stride, uint8_t *dev_status,
                              void *stream);

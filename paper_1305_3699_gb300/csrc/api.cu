@@ -375,6 +375,13 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
                 ctx->big_absent_slice};
       e = cudaMemsetAsync(sync, 0, (b.slots + 1) * 4, stream);
       if (e == cudaSuccess) e = timed_launch(ctx, 0, stream, [&] { return bk.modexp(a, stream); });
+      if (e == cudaSuccess && !b.crt.empty()) {
+        const uint32_t n_off = key_offsets(b.ce->host.k, b.ce->host.W).N;
+        e = timed_launch(ctx, 1, stream, [&] {
+          return launch_crt_bin(reinterpret_cast<const CrtItem*>(base + b.off_crt), (uint32_t)b.crt.size(),
+                                b.ce->host.W, n_off, stream);
+        });
+      }
       if (e != cudaSuccess) break;
       continue;
     }
@@ -982,7 +989,8 @@ mr_status mr_rsa_key_setup(mr_ctx* ctx, const uint32_t* N, uint32_t n_limbs, con
         cleanup();
         return s;
       }
-      std::vector<uint32_t> crt = build_crt(key->p.cls->host, bp, bq, bqi);
+      std::vector<uint32_t> crt = key->p.cls->big() ? build_crt_bin(key->p.cls->host.W, bp, bq, bqi)
+                                                    : build_crt(key->p.cls->host, bp, bq, bqi);
       s = upload(ctx, crt, &key->dev_crt);
       if (s) {
         cleanup();
@@ -1130,7 +1138,6 @@ mr_status mr_rsa_decrypt_crt(mr_ctx* ctx, const mr_key* const* keys, size_t n, c
       if (!k->priv) return fail(ctx, MR_ERR_KEY, "key has no private CRT parts");
       if (m_stride < k->pub.nlimbs()) return fail(ctx, MR_ERR_ARG, "m_stride smaller than a modulus");
       ClassEntry* ce = k->p.cls;
-      if (ce->big()) return fail(ctx, MR_ERR_SIZE, "CRT decryption takes keys of at most 8192 bits");
       ClassBatch& b = batch_for(batches, idx, ce);
       const KeyOff ko = key_offsets(ce->host.k, ce->host.W);
       const KeyEntry& pub = k->pub;

@@ -81,6 +81,12 @@ struct ClassKernels {
   const BigKernel* big;  // non-null for a large class
 };
 
+// Garner recombination of CRT decryptions whose halves are in a large size class
+// (binary, one warp per item): items[i].crt is a CrtBinOff block, p's W limbs sit at
+// items[i].keyp + n_off.  W <= CRT_BIN_MAX_W.
+constexpr uint32_t CRT_BIN_MAX_W = 512;
+cudaError_t launch_crt_bin(const CrtItem* items, uint32_t n_items, uint32_t W, uint32_t n_off, cudaStream_t s);
+
 // nullptr when no kernel is compiled for class L
 const ClassKernels* class_kernels(uint32_t L);
 

@@ -107,6 +107,25 @@ MR_HD constexpr inline CrtOff crt_offsets(uint32_t k, uint32_t W) {
   return o;
 }
 
+// [p2 W+1][qr W][q W][pinv 1]   (binary, large size classes; W limbs of the class of p and q)
+//   p2     p * ceil(2^(32W) / p): a multiple of p above every m_q, W+1 limbs
+//   qr     qinv * 2^(32(W+1)) mod p   (Montgomery factor of the W+1-limb radix)
+//   q      W limbs of q
+//   pinv   -p^-1 mod 2^32
+struct CrtBinOff {
+  uint32_t p2, qr, q, pinv, total;
+};
+
+MR_HD constexpr inline CrtBinOff crt_bin_offsets(uint32_t W) {
+  CrtBinOff o{};
+  o.p2 = 0;
+  o.qr = W + 1;
+  o.q = 2 * W + 1;
+  o.pinv = 3 * W + 1;
+  o.total = 3 * W + 2;
+  return o;
+}
+
 // ------------------------------------------------------------ work items
 struct MxItem {            // one modular exponentiation
   const uint32_t* key;     // modulus block (KeyOff layout)
@@ -121,7 +140,7 @@ struct MxItem {            // one modular exponentiation
 
 struct CrtItem {           // Garner recombination of one CRT decryption
   const uint32_t* keyp;    // modulus block of p
-  const uint32_t* crt;     // CrtOff block
+  const uint32_t* crt;     // CrtOff block (CrtBinOff for the large classes)
   const uint32_t* mp;      // W limbs, c^dp mod p
   const uint32_t* mq;      // W limbs, c^dq mod q
   uint32_t* out;           // out_limbs limbs

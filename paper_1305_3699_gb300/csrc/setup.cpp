@@ -289,4 +289,23 @@ std::vector<uint32_t> build_crt(const ClassHost& c, const Big& p, const Big& q, 
   return blk;
 }
 
+std::vector<uint32_t> build_crt_bin(uint32_t W, const Big& p, const Big& q, const Big& qinv) {
+  CrtBinOff o = crt_bin_offsets(W);
+  std::vector<uint32_t> blk(o.total, 0);
+  Big twoW = shl(Big(1), 32 * (size_t)W);
+  Big t = mod(twoW, p);
+  Big p2 = t.is_zero() ? twoW : add(twoW, sub(p, t));
+  std::vector<uint32_t> l = p2.limbs(W + 1);
+  for (uint32_t w = 0; w <= W; w++) blk[o.p2 + w] = l[w];
+  l = mod(shl(qinv, 32 * ((size_t)W + 1)), p).limbs(W);
+  for (uint32_t w = 0; w < W; w++) blk[o.qr + w] = l[w];
+  l = q.limbs(W);
+  for (uint32_t w = 0; w < W; w++) blk[o.q + w] = l[w];
+  const uint32_t p0 = p.limb(0);
+  uint32_t inv = p0;  // Newton's iteration for p0^-1 mod 2^32: 3, 6, 12, 24, 48 correct bits
+  for (int i = 0; i < 4; i++) inv *= 2u - p0 * inv;
+  blk[o.pinv] = 0u - inv;
+  return blk;
+}
+
 }  // namespace mr

@@ -50,6 +50,10 @@ int build_key(const ClassHost& c, const Big& N, const Big* exp, KeyHost& out, st
 // Garner-recombination block for RSA halves p, q of class c (CrtOff layout).
 std::vector<uint32_t> build_crt(const ClassHost& c, const Big& p, const Big& q, const Big& qinv);
 
+// Binary Garner block for halves p, q of a large size class of W limbs (CrtBinOff layout).
+// p must be odd.
+std::vector<uint32_t> build_crt_bin(uint32_t W, const Big& p, const Big& q, const Big& qinv);
+
 // Residues of X in all 2k channels (plain).
 std::vector<uint32_t> residues(const ClassHost& c, const Big& X);
 

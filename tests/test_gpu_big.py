@@ -108,11 +108,47 @@ def test_large_class_unsupported_calls(mr, ctx):
     c = mr.to_tensor([5], 512)
     m = torch.zeros_like(c)
     with pytest.raises(mr.MRError) as e:
-        ctx.mr_rsa_decrypt_crt([h], c, m)
-    assert e.value.code == 4  # MR_ERR_SIZE: CRT halves of 8192 bits
-    with pytest.raises(mr.MRError) as e:
         ctx.mr_rsa_mixed([h], [0], c, m)
-    assert e.value.code == 4
+    assert e.value.code == 4  # MR_ERR_SIZE: mixed batches take keys of at most 4096 bits
+
+
+def test_rsa16384_crt_decrypt(mr, ctx):
+    """16384-bit keys: the two 8192-bit halves run in the large-class kernel, then the binary
+    Garner recombination.  decrypt(encrypt(m)) = m for 36 messages over 4 keys (72 halves: three
+    item groups, the last partial); decryption is a bijection, so each equality pins that output.
+    Edge inputs 0, 1 and N-1 (odd d: (-1)^d = -1), an input N (status RANGE, output 0), and one
+    output against the oracle's CRT decryption of a random ciphertext."""
+    keys = load_keys("mod16384_x4")
+    hk = [ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]) for k in keys]
+    r = SplitMix64(0x4D520053)
+    idx = [j % len(keys) for j in range(36)]
+    msgs = [r.below(keys[i]["N"]) for i in idx]
+    m = mr.to_tensor(msgs, 512)
+    c = torch.zeros_like(m)
+    ctx.mr_rsa_encrypt([hk[i] for i in idx], m, c)
+    back = torch.full_like(m, -1)
+    st = torch.full((len(msgs),), 255, dtype=torch.uint8, device="cuda")
+    ctx.mr_rsa_decrypt_crt([hk[i] for i in idx], c, back, st)
+    torch.cuda.synchronize()
+    cs = mr.from_tensor(c)
+    assert st.cpu().tolist() == [0] * len(msgs)
+    assert mr.from_tensor(back) == msgs
+    for j in (0, 5):
+        k = keys[idx[j]]
+        assert cs[j] == plain.rsa_encrypt(msgs[j], k["e"], k["N"]), j
+
+    k0, k1 = keys[0], keys[1]
+    ct = [0, 1, k0["N"] - 1, k0["N"], r.below(k1["N"])]
+    kidx = [0, 0, 0, 0, 1]
+    cin = mr.to_tensor(ct, 512)
+    out = torch.full_like(cin, -1)
+    st = torch.full((len(ct),), 255, dtype=torch.uint8, device="cuda")
+    ctx.mr_rsa_decrypt_crt([hk[i] for i in kidx], cin, out, st)
+    torch.cuda.synchronize()
+    got = mr.from_tensor(out)
+    assert st.cpu().tolist() == [0, 0, 0, 5, 0]
+    assert got[:4] == [0, 1, k0["N"] - 1, 0]
+    assert got[4] == plain.rsa_decrypt_crt(ct[4], k1["p"], k1["q"], k1["dp"], k1["dq"], k1["qinv"])
 
 
 def test_bounded_wait_times_out_and_context_recovers(mr, ctx):
