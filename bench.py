@@ -228,6 +228,16 @@ def big_workload(rank: int = 0, ebits: int = BIG_EBITS):
     return keys, idx, xs, es
 
 
+def big_crt_workload(rank: int = 0):
+    """256 ciphertexts uniform below four seeded 16384-bit RSA moduli (64 per key)."""
+    from synth import SplitMix64, load_keys
+    keys = load_keys(BIG_KEYSET)
+    r = SplitMix64(BIG_SEED + 0x77 + 0x1000 * rank)
+    idx = [i % len(keys) for i in range(BIG_N)]
+    cts = [r.below(keys[i]["N"]) for i in idx]
+    return keys, idx, cts
+
+
 def _oracle_modexp_chunk(args):
     from oracle import plain
     t0 = time.perf_counter()
@@ -305,6 +315,19 @@ def run_reference(args, rank, world):
                 "scaling": "weak", "vs_baseline": None, "dtype": "int (Python)", "data": "synthetic",
                 "impl": "reference",
                 "config": {"workload": "modexp16384_long_exponent", "items": BIG_N, "sample_per_step": desc},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+    if args.workload == "rsa16384_crt":
+        keys, idx, cts = big_crt_workload(0)
+        budget = max(4.0, 90.0 / max(1, args.steps + args.warmup))
+        value, cores, desc, times = oracle_throughput(keys, idx, cts, budget, steps=args.steps, warmup=args.warmup)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int (Python)", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": "rsa16384_crt_decrypt", "ciphertexts": BIG_N, "sample_per_step": desc},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -746,35 +769,51 @@ def run_ragged(args, rank, world, local_rank):
 
 
 def run_big(args, rank, world, local_rank):
-    """Long-exponent workload: 256 exponentiations x^e mod N over four 16384-bit RSA moduli with
-    uniform 16128-bit exponents, one mr_modexp_batch call per step (the 16384-bit class runs as
-    one cooperative launch of 8 groups x 19 channel slices)."""
+    """Large-class workloads over four 16384-bit RSA keys, one call per step:
+      modexp16384   256 exponentiations x^e mod N with uniform 16128-bit exponents (mr_modexp_batch;
+                    the 16384-bit class runs as one cooperative launch of 8 groups x 19 channel slices)
+      rsa16384_crt  256 CRT decryptions (mr_rsa_decrypt_crt): 512 exponentiations modulo the 8192-bit
+                    primes in the 8192-bit class, then the binary Garner recombination"""
     import torch
     import torch.distributed as dist
 
     from paper_1305_3699_gb300 import mr
 
+    crt = args.workload == "rsa16384_crt"
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    keys, idx, xs, es = big_workload(rank, args.ebits)
+    if crt:
+        keys, idx, xs = big_crt_workload(rank)
+        es = None
+    else:
+        keys, idx, xs, es = big_workload(rank, args.ebits)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         log("timing the CPU oracle on a bounded sample ...")
-        v, cores, desc, _ = oracle_big_throughput(keys, idx, xs, es)
+        if crt:
+            v, cores, desc, _ = oracle_throughput(keys, idx, xs, args.cpu_seconds)
+        else:
+            v, cores, desc, _ = oracle_big_throughput(keys, idx, xs, es)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     ctx = mr.Context(local_rank)
-    hk = [ctx.mr_rns_setup(k["N"]) for k in keys]
+    if crt:
+        hk = [ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]) for k in keys]
+    else:
+        hk = [ctx.mr_rns_setup(k["N"]) for k in keys]
     kl = mr.KeyList([hk[i] for i in idx])
     W, EL = 512, (args.ebits + 31) // 32
     x_dev = mr.to_tensor(xs, W, device=dev)
-    e_dev = mr.to_tensor(es, EL, device=dev)
+    e_dev = None if crt else mr.to_tensor(es, EL, device=dev)
     out = torch.zeros_like(x_dev)
     status = torch.zeros(BIG_N, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def step():
-        ctx.mr_modexp_batch(kl, x_dev, e_dev, out, status, stream=stream)
+        if crt:
+            ctx.mr_rsa_decrypt_crt(kl, x_dev, out, status, stream=stream)
+        else:
+            ctx.mr_modexp_batch(kl, x_dev, e_dev, out, status, stream=stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -782,7 +821,11 @@ def run_big(args, rank, world, local_rank):
     torch.cuda.synchronize()
     got = mr.from_tensor(out[:2])
     for j in range(2):
-        assert got[j] == pow(xs[j], es[j], keys[idx[j]]["N"]), "benchmark output mismatch"
+        k = keys[idx[j]]
+        if crt:
+            assert pow(got[j], k["e"], k["N"]) == xs[j], "benchmark output mismatch"
+        else:
+            assert got[j] == pow(xs[j], es[j], k["N"]), "benchmark output mismatch"
     assert int(status.sum()) == 0
     vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     gpu_index = vis[local_rank] if local_rank < len(vis) else (vis[0] if vis else str(local_rank))
@@ -807,9 +850,11 @@ def run_big(args, rank, world, local_rank):
     t_wall1 = time.time()
     prof = ctx.mr_profile_read()
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
-    value = BIG_N * world * args.steps / (total_ms / 1e3)
-    # end to end: H2D of bases and exponents, the call, D2H of the results
-    x_host, e_host = x_dev.cpu().pin_memory(), e_dev.cpu().pin_memory()
+    per_item = 2 if crt else 1  # exponentiations per item
+    value = per_item * BIG_N * world * args.steps / (total_ms / 1e3)
+    # end to end: H2D of the inputs, the call, D2H of the results
+    x_host = x_dev.cpu().pin_memory()
+    e_host = None if crt else e_dev.cpu().pin_memory()
     o_host = torch.empty_like(x_host).pin_memory()
     e2e_ms = []
     with torch.cuda.stream(stream):
@@ -817,21 +862,31 @@ def run_big(args, rank, world, local_rank):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             x_dev.copy_(x_host, non_blocking=True)
-            e_dev.copy_(e_host, non_blocking=True)
+            if e_host is not None:
+                e_dev.copy_(e_host, non_blocking=True)
             step()
             o_host.copy_(out, non_blocking=True)
             b.record(stream)
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
-    e2e_val = BIG_N * world / (statistics.mean(e2e_ms) / 1e3)
+    e2e_val = per_item * BIG_N * world / (statistics.mean(e2e_ms) / 1e3)
     clocks = sampler.summary(t_wall0, t_wall1) if sampler else None
     if sampler:
         sampler.stop()
-    L, k = mr.mr_class_for_bits(16384)
-    WX = len(mr.mr_debug_class_table(L, "M"))
-    w = window_for_bits(args.ebits, 8)
-    prods = sum(algorithmic_products_per_modexp(k, W, WX, e.bit_length(), w, 1) for e in es)
-    (mx_launch, mx_ms), _ = prof
+    if crt:
+        L, k = mr.mr_class_for_bits(8192)
+        WX = len(mr.mr_debug_class_table(L, "M"))
+        Wm = L // 32
+        ebits = max(max(keys[i]["dp"].bit_length(), keys[i]["dq"].bit_length()) for i in idx)
+        w = window_for_bits(ebits, 8)
+        prods = sum(algorithmic_products_per_modexp(k, Wm, WX, keys[i][h].bit_length(), w, 2)
+                    for i in idx for h in ("dp", "dq"))
+    else:
+        L, k = mr.mr_class_for_bits(16384)
+        WX = len(mr.mr_debug_class_table(L, "M"))
+        w = window_for_bits(args.ebits, 8)
+        prods = sum(algorithmic_products_per_modexp(k, W, WX, e.bit_length(), w, 1) for e in es)
+    (mx_launch, mx_ms), (crt_launch, crt_ms) = prof
     mx_avg_ms = mx_ms / max(1, mx_launch)
     props = torch.cuda.get_device_properties(dev)
     max_mhz = sm_max_mhz()
@@ -845,17 +900,26 @@ def run_big(args, rank, world, local_rank):
                             f"{max_mhz:.0f} MHz (a 32x32->64 product counts 2)",
                 "microbench": {"mad_wide_per_s": wide_rate, "peak_int32_mul_per_s": 2 * wide_rate,
                                "frac": achieved / (2 * wide_rate)}}
+    if crt:
+        roofline["crt_kernel"] = "crt_bin_kernel (binary Garner, one warp per decryption)"
+        roofline["crt_kernel_ms"] = crt_ms / max(1, crt_launch)
+        config = {"workload": "rsa16384_crt_decrypt", "ciphertexts_per_gpu": BIG_N, "keys": len(keys),
+                  "modulus_bits": 16384, "half_bits": 8192, "modexps_per_step": 2 * BIG_N, "k_half": k,
+                  "decrypt_per_s": value / 2}
+        data = "synthetic (seeded 16384-bit RSA keys and ciphertexts)"
+    else:
+        config = {"workload": "modexp16384_long_exponent", "items_per_gpu": BIG_N, "keys": len(keys),
+                  "modulus_bits": 16384, "exponent_bits": args.ebits, "k": k}
+        data = "synthetic (seeded 16384-bit RSA moduli, bases and exponents)"
+    config.update({"l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"items partitioned over {world} GPU(s)"})
+    h2d = x_host.numel() * 4 + (0 if e_host is None else e_host.numel() * 4)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-                "data": "synthetic (seeded 16384-bit RSA moduli, bases and exponents)",
-                "config": {"workload": "modexp16384_long_exponent", "items_per_gpu": BIG_N, "keys": len(keys),
-                           "modulus_bits": 16384, "exponent_bits": args.ebits, "k": k,
-                           "l2": "flushed between timed steps (512 MB write)",
-                           "parallelism": f"items partitioned over {world} GPU(s)"},
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": data, "config": config,
                 "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int((x_host.numel() + e_host.numel()) * 4),
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(o_host.numel() * 4)},
                 "clocks": clocks, "gpu_launches": prof[0][0] + prof[1][0]}
         print(json.dumps(line), flush=True)
@@ -926,7 +990,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ebits", type=int, default=BIG_EBITS,
                     help="exponent bits of the modexp16384 workload (smaller values for profiling runs)")
-    ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving", "modexp16384", "rsa1024_enc", "mr1024"])
+    ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving", "modexp16384", "rsa16384_crt",
+                                                             "rsa1024_enc", "mr1024"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -941,7 +1006,7 @@ def main():
     try:
         if args.workload == "ragged":
             return run_ragged(args, rank, world, local_rank)
-        if args.workload == "modexp16384":
+        if args.workload in ("modexp16384", "rsa16384_crt"):
             return run_big(args, rank, world, local_rank)
         if args.workload == "rsa1024_enc":
             return run_enc1024(args, rank, world, local_rank)

@@ -26,14 +26,17 @@ namespace {
 struct ClassEntry {
   ClassHost host;
   uint32_t* dev = nullptr;
-  uint32_t* tslice = nullptr;  // large classes: extension matrices by channel slice
+  uint32_t* tslice[MAX_VARIANTS] = {};  // large classes: extension matrices by channel slice, per variant
   const ClassKernels* kern = nullptr;
-  uint32_t variant = 0;  // selected lane mapping
+  uint32_t variant = 0;  // selected lane mapping (large classes: slice width, used when pinned)
   uint32_t wcap = 0;     // window-width cap chosen by mr_autotune (0 = the default rule)
   bool tuned = false;
   bool pinned = false;   // lane mapping chosen by the caller (mr_set_variant, MR_VARIANT_<L>) or the tuner
   const KernelVariant& kv() const { return kern->var[variant]; }
   bool big() const { return kern && kern->big; }
+  uint32_t n_var() const { return big() ? kern->n_big : kern->n_variants; }
+  // threads that hold one number's channels: the lane group, or one lane per warp of every slice
+  uint32_t lanes(uint32_t v) const { return big() ? kern->big[v].slices * (kern->big[v].threads / 32) : kern->var[v].tpi; }
 };
 
 struct KeyEntry {
@@ -133,8 +136,8 @@ mr_status get_class(mr_ctx* ctx, uint32_t L, ClassEntry** out) {
     cudaError_t pe = ce->kern->var[v].prepare();  // kernel attributes, once, outside any capture
     if (pe != cudaSuccess) return cuda_fail(ctx, pe, "kernel attributes");
   }
-  if (ce->big()) {
-    const BigKernel& bk = *ce->kern->big;
+  for (uint32_t v = 0; ce->big() && v < ce->kern->n_big && v < (uint32_t)MAX_VARIANTS; v++) {
+    const BigKernel& bk = ce->kern->big[v];
     cudaError_t pe = bk.prepare();
     if (pe != cudaSuccess) return cuda_fail(ctx, pe, "kernel attributes");
     // [T1 | T2][slice][row][SC]: the columns of each channel slice contiguous, zero past channel k
@@ -146,8 +149,8 @@ mr_status get_class(mr_ctx* ctx, uint32_t L, ClassEntry** out) {
         for (uint32_t i = 0; i < k; i++)
           for (uint32_t q = 0; q < sc && c * sc + q < k; q++)
             ts[(((size_t)m * sl + c) * k + i) * sc + q] = ce->host.block[(m ? o.T2 : o.T1) + (size_t)i * k + c * sc + q];
-    cudaError_t e = cudaMalloc(&ce->tslice, ts.size() * 4);
-    if (e == cudaSuccess) e = cudaMemcpy(ce->tslice, ts.data(), ts.size() * 4, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMalloc(&ce->tslice[v], ts.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(ce->tslice[v], ts.data(), ts.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "class slice tables");
   }
   {
@@ -156,7 +159,7 @@ mr_status get_class(mr_ctx* ctx, uint32_t L, ClassEntry** out) {
     const char* v = getenv(ev.c_str());
     if (v) {
       unsigned idx = (unsigned)atoi(v);
-      if (idx < ce->kern->n_variants) {
+      if (idx < ce->n_var()) {
         ce->variant = idx;
         ce->pinned = true;
       }
@@ -243,7 +246,35 @@ struct ClassBatch {
   size_t off_mx = 0, off_crt = 0, off_scratch = 0, off_half = 0;
   size_t scratch_words = 0;
   uint32_t slots = 0;  // large class: item groups in flight
+  uint32_t bigv = 0;   // large class: kernel variant (slice width)
 };
+
+// Large class: the kernel variant (channel-slice width) for a batch of n items, and its item
+// groups in flight.  A variant holds fit = resident CTAs / slices groups in one cooperative wave;
+// the estimated time is the number of waves times the variant's relative time per group.  A
+// pinned class (mr_set_variant, the tuner) keeps its variant.  Returns false when no variant
+// fits the device.
+bool choose_big_variant(mr_ctx* ctx, const ClassEntry* ce, size_t n_items, uint32_t* v_out, uint32_t* slots) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const uint64_t groups = (n_items + 31) / 32;
+  double best = 1e300;
+  bool found = false;
+  for (uint32_t v = 0; v < ce->kern->n_big && v < (uint32_t)MAX_VARIANTS; v++) {
+    if (ce->pinned && v != ce->variant) continue;
+    const BigKernel& bk = ce->kern->big[v];
+    const uint64_t fit = (uint64_t)(bk.occupancy() * sms) / bk.slices;
+    if (fit == 0) continue;
+    const double cost = (double)((groups + fit - 1) / fit) * bk.group_time;
+    if (cost < best) {
+      best = cost;
+      found = true;
+      *v_out = v;
+      *slots = (uint32_t)std::min<uint64_t>(fit, groups);
+    }
+  }
+  return found;
+}
 
 // Reserve pinned staging space; waits for the previous upload to finish first.
 mr_status staging_reserve(mr_ctx* ctx, size_t bytes) {
@@ -311,12 +342,9 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
       b.scratch_words = 0;
     } else if (b.ce->big()) {
       // as many groups of 32 in flight as one cooperative launch can hold
-      const BigKernel& bk = *b.ce->kern->big;
-      int sms = 0;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-      const uint32_t fit = (uint32_t)(bk.occupancy() * sms) / bk.slices;
-      if (fit == 0) return fail(ctx, MR_ERR_CUDA, "large-class kernel does not fit the device");
-      b.slots = std::min<uint32_t>(fit, (uint32_t)((b.mx.size() + 31) / 32));
+      if (!choose_big_variant(ctx, b.ce, b.mx.size(), &b.bigv, &b.slots))
+        return fail(ctx, MR_ERR_CUDA, "large-class kernel does not fit the device");
+      const BigKernel& bk = b.ce->kern->big[b.bigv];
       b.scratch_words = (size_t)b.slots * bk.slot_words(b.wbits) + align256((b.slots + 1) * 4) / 4;
     } else {
       b.scratch_words = modexp_scratch_words(b.ce->kv(), (uint32_t)b.mx.size(), b.wbits);
@@ -367,10 +395,10 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
   for (auto& b : batches) {
     if (b.ce->big()) {
       if (b.mx.empty()) continue;
-      const BigKernel& bk = *b.ce->kern->big;
+      const BigKernel& bk = b.ce->kern->big[b.bigv];
       uint32_t* scr = reinterpret_cast<uint32_t*>(base + b.off_scratch);
       uint32_t* sync = scr + (size_t)b.slots * bk.slot_words(b.wbits);
-      BigArgs a{b.ce->dev, b.ce->tslice, reinterpret_cast<const MxItem*>(base + b.off_mx), (uint32_t)b.mx.size(),
+      BigArgs a{b.ce->dev, b.ce->tslice[b.bigv], reinterpret_cast<const MxItem*>(base + b.off_mx), (uint32_t)b.mx.size(),
                 b.wbits, scr, status, sync, b.slots, ctx->big_spin_limit ? ctx->big_spin_limit : BIG_SPIN_POLLS,
                 ctx->big_absent_slice};
       e = cudaMemsetAsync(sync, 0, (b.slots + 1) * 4, stream);
@@ -700,9 +728,11 @@ mr_status autotune_class(mr_ctx* ctx, ClassEntry* ce, uint32_t n, uint32_t exp_b
   ctx->prof_on = false;  // tuning launches stay out of the profile counters
   const uint32_t saved_launches[2] = {ctx->launches[0], ctx->launches[1]};
   mr_status s = e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "tuning setup");
-  const uint32_t nv = ce->big() ? 1u : ce->kern->n_variants;
+  const uint32_t nv = ce->n_var();
+  const bool was_pinned = ce->pinned;
+  ce->pinned = true;  // run_batches takes the variant under test
   auto time_config = [&](uint32_t variant, uint32_t w, double* ms) -> mr_status {
-    ce->variant = ce->big() ? 0u : variant;
+    ce->variant = variant;
     double best = 1e30;
     for (int rep = 0; rep < 3; rep++) {  // warm-up, then best of two
       std::vector<ClassBatch> batches(1);
@@ -770,6 +800,7 @@ mr_status autotune_class(mr_ctx* ctx, ClassEntry* ce, uint32_t n, uint32_t exp_b
   free_key_entry(ke);
   if (s) {
     ce->variant = 0;
+    ce->pinned = was_pinned;
     return s;
   }
   ce->variant = best_v;
@@ -778,7 +809,7 @@ mr_status autotune_class(mr_ctx* ctx, ClassEntry* ce, uint32_t n, uint32_t exp_b
   ce->pinned = true;
   if (res) {
     res->variant = best_v;
-    res->lanes_per_number = ce->big() ? 0u : ce->kern->var[best_v].tpi;
+    res->lanes_per_number = ce->lanes(best_v);
     res->window = best_w;
     res->configs = configs;
     res->ms = best_ms;
@@ -885,7 +916,8 @@ void mr_shutdown(mr_ctx* ctx) {
   }
   for (auto& kv : ctx->classes) {
     if (kv.second->dev) cudaFree(kv.second->dev);
-    if (kv.second->tslice) cudaFree(kv.second->tslice);
+    for (uint32_t* t : kv.second->tslice)
+      if (t) cudaFree(t);
   }
   if (ctx->staging) cudaFreeHost(ctx->staging);
   if (ctx->staging_evt) cudaEventDestroy(ctx->staging_evt);
@@ -1529,9 +1561,11 @@ mr_status mr_debug_mr_setup(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs,
 mr_status mr_class_variants(uint32_t class_bits, uint32_t* count, uint32_t* lanes_per_number, uint32_t capacity) {
   const ClassKernels* k = class_kernels(class_bits);
   if (!k) return MR_ERR_SIZE;
-  if (count) *count = k->n_variants;
+  const uint32_t nv = k->big ? k->n_big : k->n_variants;
+  if (count) *count = nv;
   if (lanes_per_number)
-    for (uint32_t i = 0; i < k->n_variants && i < capacity; i++) lanes_per_number[i] = k->var[i].tpi;
+    for (uint32_t i = 0; i < nv && i < capacity; i++)
+      lanes_per_number[i] = k->big ? k->big[i].slices * (k->big[i].threads / 32) : k->var[i].tpi;
   return MR_OK;
 }
 
@@ -1542,7 +1576,7 @@ mr_status mr_set_variant(mr_ctx* ctx, uint32_t class_bits, uint32_t variant) {
     ClassEntry* ce = nullptr;
     mr_status s = get_class(ctx, class_bits, &ce);
     if (s) return s;
-    if (variant >= ce->kern->n_variants) return fail(ctx, MR_ERR_ARG, "no such variant");
+    if (variant >= ce->n_var()) return fail(ctx, MR_ERR_ARG, "no such variant");
     ce->variant = variant;
     ce->pinned = true;
     return MR_OK;

@@ -25,35 +25,44 @@ CLASSES = {
 }
 
 
-# Large classes: several CTAs per group of 32 numbers (big_kernel.cuh).  L: (k, W, WX, NPT, NW)
+# Large classes: several CTAs per group of 32 numbers (big_kernel.cuh).
+# L: (k, W, WX, NPT, [(NW, group time relative to variant 0), ...]).  NW warps per CTA give channel
+# slices of 4 NW channels: wider slices need fewer CTAs per group, so more groups fit one wave, at a
+# longer time per group (more warps per SM sub-partition).  The relative group times were measured
+# with both variants in one wave on GB300.
 BIG = {
-    8192: (295, 256, 258, 4, 8),
-    16384: (599, 512, 513, 4, 8),
+    8192: (295, 256, 258, 4, [(8, 1.0), (12, 1.33)]),
+    16384: (599, 512, 513, 4, [(8, 1.0)]),
 }
 
 
-def big_unit(L, k, W, WX, npt, nw):
-    C = f"CB{L}"
-    return "\n".join([
-        f"// Kernel of the {L}-bit size class (k = {k} channels per base). Generated by gen_kernels.py.",
-        '#include "big_kernel.cuh"', '#include "kernels_api.h"', "", "namespace mr {", "",
-        f"using {C} = BigCfg<{k}, {W}, {WX}, {npt}, {nw}>;",
-        f"static size_t slot_words_{L}(uint32_t wbits) {{ return {C}::slot_words(wbits); }}", "",
-        f"static cudaError_t launch_big_{L}(const BigArgs& a, cudaStream_t s) {{",
-        "  void* args[] = {const_cast<BigArgs*>(&a)};",
-        f"  return cudaLaunchCooperativeKernel((const void*)big_modexp_kernel<{C}>, dim3(a.slots * {C}::SLICES),",
-        f"                                     dim3({C}::THREADS), args, {C}::SMEM_BYTES, s);", "}", "",
-        f"static cudaError_t prepare_big_{L}() {{",
-        f"  return cudaFuncSetAttribute(big_modexp_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES);",
-        "}", "",
-        f"static int occupancy_big_{L}() {{",
-        "  int n = 0;",
-        f"  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big_modexp_kernel<{C}>, {C}::THREADS, {C}::SMEM_BYTES) != cudaSuccess) n = 0;",
-        "  return n;", "}", "",
-        f"static const BigKernel kBig{L} = {{{C}::SC, {C}::SLICES, {C}::THREADS, {C}::SMEM_BYTES, slot_words_{L},",
-        f"                                 launch_big_{L}, prepare_big_{L}, occupancy_big_{L}}};",
-        f"extern const ClassKernels kClass{L} = {{{L}, {k}, {W}, {WX}, 0, {{}}, &kBig{L}}};", "",
-        "}  // namespace mr", ""])
+def big_unit(L, k, W, WX, npt, variants):
+    out = [f"// Kernel of the {L}-bit size class (k = {k} channels per base). Generated by gen_kernels.py.",
+           '#include "big_kernel.cuh"', '#include "kernels_api.h"', "", "namespace mr {", ""]
+    entries = []
+    for v, (nw, rel) in enumerate(variants):
+        C = f"CB{L}v{v}"
+        out += [
+            f"using {C} = BigCfg<{k}, {W}, {WX}, {npt}, {nw}>;",
+            f"static size_t slot_words_{L}_{v}(uint32_t wbits) {{ return {C}::slot_words(wbits); }}", "",
+            f"static cudaError_t launch_big_{L}_{v}(const BigArgs& a, cudaStream_t s) {{",
+            "  void* args[] = {const_cast<BigArgs*>(&a)};",
+            f"  return cudaLaunchCooperativeKernel((const void*)big_modexp_kernel<{C}>, dim3(a.slots * {C}::SLICES),",
+            f"                                     dim3({C}::THREADS), args, {C}::SMEM_BYTES, s);", "}", "",
+            f"static cudaError_t prepare_big_{L}_{v}() {{",
+            f"  return cudaFuncSetAttribute(big_modexp_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES);",
+            "}", "",
+            f"static int occupancy_big_{L}_{v}() {{",
+            "  int n = 0;",
+            f"  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big_modexp_kernel<{C}>, {C}::THREADS, {C}::SMEM_BYTES) != cudaSuccess) n = 0;",
+            "  return n;", "}", ""]
+        entries.append(f"    {{{C}::SC, {C}::SLICES, {C}::THREADS, {C}::SMEM_BYTES, {rel:.3f}f, slot_words_{L}_{v}, "
+                       f"launch_big_{L}_{v}, prepare_big_{L}_{v}, occupancy_big_{L}_{v}}}")
+    out.append(f"static const BigKernel kBig{L}[{len(variants)}] = {{")
+    out.append(",\n".join(entries) + "};")
+    out.append(f"extern const ClassKernels kClass{L} = {{{L}, {k}, {W}, {WX}, 0, {{}}, kBig{L}, {len(variants)}}};")
+    out += ["", "}  // namespace mr", ""]
+    return "\n".join(out)
 
 
 def unit(L, k, W, WX, variants):
@@ -83,7 +92,7 @@ def unit(L, k, W, WX, variants):
     out.append(f"extern const ClassKernels kClass{L} = {{")
     out.append(f"    {L}, {k}, {W}, {WX}, {len(variants)},")
     out.append("    {\n" + ",\n".join(entries) + "},")
-    out.append("    nullptr};")
+    out.append("    nullptr, 0};")
     out += ["", "}  // namespace mr", ""]
     return "\n".join(out)
 
@@ -92,9 +101,9 @@ def main():
     for L, (k, W, WX, vs) in CLASSES.items():
         with open(os.path.join(HERE, f"kern_{L}.cu"), "w") as f:
             f.write(unit(L, k, W, WX, vs))
-    for L, (k, W, WX, npt, nw) in BIG.items():
+    for L, (k, W, WX, npt, vs) in BIG.items():
         with open(os.path.join(HERE, f"kern_{L}.cu"), "w") as f:
-            f.write(big_unit(L, k, W, WX, npt, nw))
+            f.write(big_unit(L, k, W, WX, npt, vs))
     allc = list(CLASSES) + list(BIG)
     reg = ["// Registry of the compiled size classes. Generated by gen_kernels.py.", '#include "kernels_api.h"', "",
            "namespace mr {", ""]

@@ -70,6 +70,6 @@ extern const ClassKernels kClass1024 = {
     {
      {C1024v0::TPI, C1024v0::THREADS, C1024v0::IPB, C1024v0::NPT, C1024v0::SMEM_BYTES, launch_modexp_1024_0, launch_crt_1024_0, launch_mr_1024_0, prepare_1024_0, occupancy_1024_0},
      {C1024v1::TPI, C1024v1::THREADS, C1024v1::IPB, C1024v1::NPT, C1024v1::SMEM_BYTES, launch_modexp_1024_1, launch_crt_1024_1, launch_mr_1024_1, prepare_1024_1, occupancy_1024_1}},
-    nullptr};
+    nullptr, 0};
 
 }  // namespace mr

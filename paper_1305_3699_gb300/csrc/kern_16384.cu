@@ -4,27 +4,27 @@
 
 namespace mr {
 
-using CB16384 = BigCfg<599, 512, 513, 4, 8>;
-static size_t slot_words_16384(uint32_t wbits) { return CB16384::slot_words(wbits); }
+using CB16384v0 = BigCfg<599, 512, 513, 4, 8>;
+static size_t slot_words_16384_0(uint32_t wbits) { return CB16384v0::slot_words(wbits); }
 
-static cudaError_t launch_big_16384(const BigArgs& a, cudaStream_t s) {
+static cudaError_t launch_big_16384_0(const BigArgs& a, cudaStream_t s) {
   void* args[] = {const_cast<BigArgs*>(&a)};
-  return cudaLaunchCooperativeKernel((const void*)big_modexp_kernel<CB16384>, dim3(a.slots * CB16384::SLICES),
-                                     dim3(CB16384::THREADS), args, CB16384::SMEM_BYTES, s);
+  return cudaLaunchCooperativeKernel((const void*)big_modexp_kernel<CB16384v0>, dim3(a.slots * CB16384v0::SLICES),
+                                     dim3(CB16384v0::THREADS), args, CB16384v0::SMEM_BYTES, s);
 }
 
-static cudaError_t prepare_big_16384() {
-  return cudaFuncSetAttribute(big_modexp_kernel<CB16384>, cudaFuncAttributeMaxDynamicSharedMemorySize, CB16384::SMEM_BYTES);
+static cudaError_t prepare_big_16384_0() {
+  return cudaFuncSetAttribute(big_modexp_kernel<CB16384v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, CB16384v0::SMEM_BYTES);
 }
 
-static int occupancy_big_16384() {
+static int occupancy_big_16384_0() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big_modexp_kernel<CB16384>, CB16384::THREADS, CB16384::SMEM_BYTES) != cudaSuccess) n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big_modexp_kernel<CB16384v0>, CB16384v0::THREADS, CB16384v0::SMEM_BYTES) != cudaSuccess) n = 0;
   return n;
 }
 
-static const BigKernel kBig16384 = {CB16384::SC, CB16384::SLICES, CB16384::THREADS, CB16384::SMEM_BYTES, slot_words_16384,
-                                 launch_big_16384, prepare_big_16384, occupancy_big_16384};
-extern const ClassKernels kClass16384 = {16384, 599, 512, 513, 0, {}, &kBig16384};
+static const BigKernel kBig16384[1] = {
+    {CB16384v0::SC, CB16384v0::SLICES, CB16384v0::THREADS, CB16384v0::SMEM_BYTES, 1.000f, slot_words_16384_0, launch_big_16384_0, prepare_big_16384_0, occupancy_big_16384_0}};
+extern const ClassKernels kClass16384 = {16384, 599, 512, 513, 0, {}, kBig16384, 1};
 
 }  // namespace mr

@@ -70,6 +70,6 @@ extern const ClassKernels kClass512 = {
     {
      {C512v0::TPI, C512v0::THREADS, C512v0::IPB, C512v0::NPT, C512v0::SMEM_BYTES, launch_modexp_512_0, launch_crt_512_0, launch_mr_512_0, prepare_512_0, occupancy_512_0},
      {C512v1::TPI, C512v1::THREADS, C512v1::IPB, C512v1::NPT, C512v1::SMEM_BYTES, launch_modexp_512_1, launch_crt_512_1, launch_mr_512_1, prepare_512_1, occupancy_512_1}},
-    nullptr};
+    nullptr, 0};
 
 }  // namespace mr

@@ -4,27 +4,47 @@
 
 namespace mr {
 
-using CB8192 = BigCfg<295, 256, 258, 4, 8>;
-static size_t slot_words_8192(uint32_t wbits) { return CB8192::slot_words(wbits); }
+using CB8192v0 = BigCfg<295, 256, 258, 4, 8>;
+static size_t slot_words_8192_0(uint32_t wbits) { return CB8192v0::slot_words(wbits); }
 
-static cudaError_t launch_big_8192(const BigArgs& a, cudaStream_t s) {
+static cudaError_t launch_big_8192_0(const BigArgs& a, cudaStream_t s) {
   void* args[] = {const_cast<BigArgs*>(&a)};
-  return cudaLaunchCooperativeKernel((const void*)big_modexp_kernel<CB8192>, dim3(a.slots * CB8192::SLICES),
-                                     dim3(CB8192::THREADS), args, CB8192::SMEM_BYTES, s);
+  return cudaLaunchCooperativeKernel((const void*)big_modexp_kernel<CB8192v0>, dim3(a.slots * CB8192v0::SLICES),
+                                     dim3(CB8192v0::THREADS), args, CB8192v0::SMEM_BYTES, s);
 }
 
-static cudaError_t prepare_big_8192() {
-  return cudaFuncSetAttribute(big_modexp_kernel<CB8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, CB8192::SMEM_BYTES);
+static cudaError_t prepare_big_8192_0() {
+  return cudaFuncSetAttribute(big_modexp_kernel<CB8192v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, CB8192v0::SMEM_BYTES);
 }
 
-static int occupancy_big_8192() {
+static int occupancy_big_8192_0() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big_modexp_kernel<CB8192>, CB8192::THREADS, CB8192::SMEM_BYTES) != cudaSuccess) n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big_modexp_kernel<CB8192v0>, CB8192v0::THREADS, CB8192v0::SMEM_BYTES) != cudaSuccess) n = 0;
   return n;
 }
 
-static const BigKernel kBig8192 = {CB8192::SC, CB8192::SLICES, CB8192::THREADS, CB8192::SMEM_BYTES, slot_words_8192,
-                                 launch_big_8192, prepare_big_8192, occupancy_big_8192};
-extern const ClassKernels kClass8192 = {8192, 295, 256, 258, 0, {}, &kBig8192};
+using CB8192v1 = BigCfg<295, 256, 258, 4, 12>;
+static size_t slot_words_8192_1(uint32_t wbits) { return CB8192v1::slot_words(wbits); }
+
+static cudaError_t launch_big_8192_1(const BigArgs& a, cudaStream_t s) {
+  void* args[] = {const_cast<BigArgs*>(&a)};
+  return cudaLaunchCooperativeKernel((const void*)big_modexp_kernel<CB8192v1>, dim3(a.slots * CB8192v1::SLICES),
+                                     dim3(CB8192v1::THREADS), args, CB8192v1::SMEM_BYTES, s);
+}
+
+static cudaError_t prepare_big_8192_1() {
+  return cudaFuncSetAttribute(big_modexp_kernel<CB8192v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, CB8192v1::SMEM_BYTES);
+}
+
+static int occupancy_big_8192_1() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big_modexp_kernel<CB8192v1>, CB8192v1::THREADS, CB8192v1::SMEM_BYTES) != cudaSuccess) n = 0;
+  return n;
+}
+
+static const BigKernel kBig8192[2] = {
+    {CB8192v0::SC, CB8192v0::SLICES, CB8192v0::THREADS, CB8192v0::SMEM_BYTES, 1.000f, slot_words_8192_0, launch_big_8192_0, prepare_big_8192_0, occupancy_big_8192_0},
+    {CB8192v1::SC, CB8192v1::SLICES, CB8192v1::THREADS, CB8192v1::SMEM_BYTES, 1.330f, slot_words_8192_1, launch_big_8192_1, prepare_big_8192_1, occupancy_big_8192_1}};
+extern const ClassKernels kClass8192 = {8192, 295, 256, 258, 0, {}, kBig8192, 2};
 
 }  // namespace mr

@@ -68,6 +68,7 @@ constexpr int MAX_VARIANTS = 4;
 // Kernel of a large size class: one cooperative launch of slots * slices CTAs.
 struct BigKernel {
   uint32_t sc, slices, threads, smem_bytes;
+  float group_time;  // time of one item group relative to variant 0 when both fit one wave (measured)
   size_t (*slot_words)(uint32_t wbits);
   cudaError_t (*modexp)(const BigArgs&, cudaStream_t);
   cudaError_t (*prepare)();
@@ -78,7 +79,8 @@ struct ClassKernels {
   uint32_t L, k, W, WX;
   uint32_t n_variants;  // lane-group variants (0 for a large class)
   KernelVariant var[MAX_VARIANTS];
-  const BigKernel* big;  // non-null for a large class
+  const BigKernel* big;  // non-null for a large class: n_big variants (channel-slice widths)
+  uint32_t n_big;
 };
 
 // Garner recombination of CRT decryptions whose halves are in a large size class

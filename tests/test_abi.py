@@ -61,6 +61,16 @@ def test_class_for_bits_boundaries():
         mr.mr_class_for_bits(16385)
 
 
+def test_large_class_slice_widths():
+    """The large classes report, per compiled slice width, the threads that hold one number's
+    channels: one lane in every warp of every channel slice (4 channels per warp)."""
+    for L, k in ((8192, 295), (16384, 599)):
+        lanes = mr.mr_class_variants(L)
+        assert len(lanes) >= 1 and all(n > 0 for n in lanes)
+        nw = 8  # variant 0: 8 warps, slices of 32 channels
+        assert lanes[0] == -(-k // (4 * nw)) * nw
+
+
 def _key_cases():
     r = SplitMix64(1234)
     out = []

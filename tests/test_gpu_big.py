@@ -102,6 +102,39 @@ def test_modexp_8192_random_moduli(mr, ctx):
     assert st == [0] * n
 
 
+def test_modexp_8192_every_slice_width(mr):
+    """Every compiled slice width of the 8192-bit class (selected explicitly on a fresh context)
+    gives the oracle's results: 40 items (a full group and a partial one), edge bases, and one
+    16384-bit CRT decryption whose halves run in this class."""
+    r = SplitMix64(0x4D520063)
+    N = r.randbits(8192) | 1 | (1 << 8191)
+    keys = load_keys("mod16384_x4")
+    for v in range(len(mr.mr_class_variants(8192))):
+        c = mr.Context(0)
+        try:
+            c.mr_set_variant(8192, v)
+            h = c.mr_rns_setup(N)
+            xs = [r.below(N) for _ in range(40)]
+            es = [r.randbits(30 + 53 * (j % 5)) for j in range(40)]
+            xs[0], xs[1], xs[2] = 0, 1, N - 1
+            es[3] = r.randbits(8192)
+            got, st = _run(mr, c, [h] * 40, [N] * 40, xs, es, 256, 256)
+            assert st == [0] * 40
+            for j in range(40):
+                assert got[j] == plain.modexp(xs[j], es[j], N), (v, j)
+            k = keys[v % len(keys)]
+            hk = c.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"])
+            msg = r.below(k["N"])
+            ct = pow(msg, k["e"], k["N"])
+            cin = mr.to_tensor([ct], 512)
+            out = torch.zeros_like(cin)
+            c.mr_rsa_decrypt_crt([hk], cin, out)
+            torch.cuda.synchronize()
+            assert mr.from_tensor(out) == [msg], v
+        finally:
+            c.close()
+
+
 def test_large_class_unsupported_calls(mr, ctx):
     k = load_keys("mod16384_x4")[0]
     h = ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"])
