@@ -894,7 +894,7 @@ def run_big(args, rank, world, local_rank):
     achieved = 2 * prods / (mx_avg_ms / 1e3)
     wide_rate = ctx.mr_imad_peak(0, stream)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T int32-mul/s",
-                "frac": achieved / peak, "traffic": None, "kernel": f"big_modexp_kernel<k={k}, 8 warps x 4 channels>",
+                "frac": achieved / peak, "traffic": None, "kernel": f"big_modexp_kernel<k={k}> (channel-slice width: the variant with the fewest estimated waves)",
                 "kernel_ms": mx_avg_ms, "int32_mul_ops_per_launch": 2 * prods, "window": w,
                 "peak_def": f"{props.multi_processor_count} SMs x {IMAD_PER_CLK_PER_SM} int32-mul/clk x "
                             f"{max_mhz:.0f} MHz (a 32x32->64 product counts 2)",

@@ -255,7 +255,11 @@ mr_status mr_modexp_batch_noalloc(mr_ctx *ctx, const mr_key *key, size_t n, cons
 /* Lane mappings compiled for a size class, for autotuning.  Each class is
  * compiled for one or more numbers of GPU lanes per number; *count receives
  * how many, lanes_per_number[0..min(count, capacity)) their lane counts (may
- * be NULL).  Errors: MR_ERR_SIZE (no such class). */
+ * be NULL).  For the large classes a variant is a channel-slice width and its
+ * lane count is the threads holding one number's channels (one lane in each
+ * warp of each of the number's thread blocks); unless a variant is selected,
+ * each call picks the one that needs the fewest estimated cooperative waves.
+ * Errors: MR_ERR_SIZE (no such class). */
 mr_status mr_class_variants(uint32_t class_bits, uint32_t *count, uint32_t *lanes_per_number, uint32_t capacity);
 
 /* Select the lane mapping later calls on this context use for a size class
@@ -265,8 +269,8 @@ mr_status mr_set_variant(mr_ctx *ctx, uint32_t class_bits, uint32_t variant);
 
 /* Result of mr_autotune. */
 typedef struct {
-  uint32_t variant;          /* chosen lane mapping (as for mr_set_variant; 0 for the large classes) */
-  uint32_t lanes_per_number; /* its lanes per number (0 for the large classes) */
+  uint32_t variant;          /* chosen lane mapping (as for mr_set_variant) */
+  uint32_t lanes_per_number; /* its lanes per number (as mr_class_variants reports) */
   uint32_t window;           /* chosen window-width cap */
   uint32_t configs;          /* configurations timed */
   double ms;                 /* device time of one call with the chosen configuration */

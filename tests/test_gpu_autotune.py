@@ -75,11 +75,14 @@ def test_plan_autotune_flag_same_results(mr):
 
 
 def test_autotune_large_class_then_exact(mr):
-    """The tuner on a large class (one lane mapping; window widths up to 8) and exact results after."""
+    """The tuner on a large class (its channel-slice widths; window widths up to 8) and exact results
+    after."""
     ctx = mr.Context(0)
     try:
+        lanes = mr.mr_class_variants(8192)
         res = ctx.mr_autotune(8192, 40, 96)
-        assert res["variant"] == 0 and res["lanes_per_number"] == 0
+        assert 0 <= res["variant"] < len(lanes) and res["lanes_per_number"] == lanes[res["variant"]]
+        assert res["configs"] >= len(lanes)
         assert 1 <= res["window"] <= 8 and res["ms"] > 0
         r = SplitMix64(79)
         N = r.randbits(8192) | 1 | (1 << 8191)
