@@ -684,6 +684,105 @@ def run_mr1024(args, rank, world, local_rank):
     return 0
 
 
+def _oracle_prime_chunk(args):
+    from oracle import primality
+    t0 = time.perf_counter()
+    for n, ws in args:
+        primality.prime_test_verdict(n, ws)
+    return time.perf_counter() - t0, len(args)
+
+
+def run_primegen1024(args, rank, world, local_rank):
+    """Key-generation primality search: 16384 seeded random odd 1024-bit candidates, each sieved by
+    trial division with the first 10,000 primes and, when it survives, tested with 8 Miller-Rabin
+    rounds (seeded witnesses in [2, n-2]); one mr_prime_test_batch call per step.  The same
+    candidates through mr_miller_rabin_batch alone (no sieve) are timed beside it."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1305_3699_gb300 import mr
+    from synth import SplitMix64
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    rounds, n = 8, 16384
+    r = SplitMix64(0x4D520007 + 0x1000 * rank)
+    cands = [r.randbits(1024) | 1 | (1 << 1023) for _ in range(n)]
+    wit = [[2 + r.below(c - 3) for _ in range(rounds)] for c in cands]
+    ctx = mr.Context(local_rank)
+    cand_t = mr.to_tensor(cands, 32, device=dev)
+    wit_t = mr.to_tensor([a for ws in wit for a in ws], 32, device=dev)
+    verdict = torch.zeros(n, dtype=torch.uint8, device=dev)
+    surv = torch.zeros(1, dtype=torch.int32, device=dev)
+    flags = torch.zeros(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        ctx.mr_prime_test_batch(cand_t, wit_t, rounds, verdict, survivors=surv, stream=stream)
+
+    def step_mr_only():
+        ctx.mr_miller_rabin_batch(cand_t, wit_t, rounds, flags, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+            step_mr_only()
+    torch.cuda.synchronize()
+    v = verdict.cpu().tolist()
+    from oracle import primality
+    for i in range(0, n, n // 16):
+        assert v[i] == primality.prime_test_verdict(cands[i], wit[i]), "benchmark output mismatch"
+    f = flags.cpu().tolist()
+    assert all((v[i] == 2) == (f[i] == 1) for i in range(n) if v[i] > 0), "sieve and Miller-Rabin disagree"
+
+    def timed(fn):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for s_ in range(args.steps):
+                evs[s_][0].record(stream)
+                fn()
+                evs[s_][1].record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
+
+    ctx.mr_profile_enable(True)
+    ctx.mr_profile_read()
+    total_ms = timed(step)
+    prof = ctx.mr_profile_read()
+    mr_only_ms = timed(step_mr_only)
+    value = n * world * args.steps / (total_ms / 1e3)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import multiprocessing as mpr
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        sample = [(cands[j], wit[j]) for j in range(min(n, 64 * cores))]
+        with mpr.get_context("spawn").Pool(cores) as pool:
+            t0 = time.perf_counter()
+            pool.map(_oracle_prime_chunk, [sample[i::cores] for i in range(cores)])
+            dt = time.perf_counter() - t0
+        cpu = {"value": len(sample) / dt, "unit": "candidates/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {len(sample)} candidates, oracle.primality.prime_test_verdict on {cores} processes"}
+    if rank == 0:
+        (mx_n, mx_ms), (tr_n, tr_ms) = prof
+        line = {"metric": METRIC, "value": value, "unit": "candidates/s (trial division + Miller-Rabin)",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic (seeded random odd candidates and witnesses)",
+                "config": {"workload": "primegen_1024x16384x8", "candidates": n, "rounds": rounds,
+                           "trial_primes": 10000, "survivors": int(surv.item()),
+                           "probable_primes": sum(1 for x in v if x == 2),
+                           "trial_kernel_ms": tr_ms / max(1, tr_n), "mr_kernel_ms": mx_ms / max(1, mx_n),
+                           "miller_rabin_only_ms": mr_only_ms / args.steps,
+                           "sieve_speedup": mr_only_ms / total_ms},
+                "cpu_baseline": cpu, "gpu_launches": int(mx_n + tr_n)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_ragged(args, rank, world, local_rank):
     """Ragged batch: one prepared plan per launch mode over the same 65,536 requests."""
     import torch
@@ -991,7 +1090,7 @@ def main():
     ap.add_argument("--ebits", type=int, default=BIG_EBITS,
                     help="exponent bits of the modexp16384 workload (smaller values for profiling runs)")
     ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving", "modexp16384", "rsa16384_crt",
-                                                             "rsa1024_enc", "mr1024"])
+                                                             "rsa1024_enc", "mr1024", "primegen1024"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -1012,6 +1111,8 @@ def main():
             return run_enc1024(args, rank, world, local_rank)
         if args.workload == "mr1024":
             return run_mr1024(args, rank, world, local_rank)
+        if args.workload == "primegen1024":
+            return run_primegen1024(args, rank, world, local_rank)
         if args.workload == "serving":
             return run_serving_bench(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)

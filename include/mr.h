@@ -229,6 +229,26 @@ mr_status mr_miller_rabin_batch(mr_ctx *ctx, const uint32_t *cand, uint32_t n_li
                                 const uint32_t *witness, uint32_t rounds, uint8_t *dev_is_probable_prime,
                                 uint32_t *dev_round_mask, void *stream);
 
+/* Primality test of n candidates as key generation runs it: trial division by
+ * the first n_primes primes (Sec. 4.3: the first 10,000 primes), then
+ * Miller-Rabin rounds (Sec. 3.2, as mr_miller_rabin_batch) on the candidates
+ * that pass it only; the rest skip the exponentiations.  A candidate passes
+ * trial division when it is at least 2 and no listed prime other than itself
+ * divides it.
+ *   cand, n_limbs, n, witness, rounds   as mr_miller_rabin_batch
+ *   n_primes       1..10000 (2, 3, 5, ... in order; the 10,000th is 104729)
+ *   dev_verdict    device, n bytes: 0 = fails trial division, 1 = passes it and
+ *                  some Miller-Rabin round fails (composite), 2 = passes both
+ *                  (probable prime)
+ *   dev_survivors  device, one uint32 or NULL: the number of candidates that
+ *                  passed trial division
+ * The trial-division tables (5.2 MB) are built and uploaded on the first call
+ * of a context.  Errors: MR_ERR_ARG (n_primes out of range, n * rounds >= 2^32,
+ * a NULL pointer), MR_ERR_SIZE, MR_ERR_OOM, MR_ERR_CUDA. */
+mr_status mr_prime_test_batch(mr_ctx *ctx, const uint32_t *cand, uint32_t n_limbs, size_t n,
+                              const uint32_t *witness, uint32_t rounds, uint32_t n_primes,
+                              uint8_t *dev_verdict, uint32_t *dev_survivors, void *stream);
+
 /* Allocation-free exponentiation: out[i] = x[i]^e[i] mod N for i < n, one
  * modulus per call.  The paper has no counterpart; this entry point exists for
  * callers that cannot allocate device memory when they call it -- an engine that
@@ -353,6 +373,15 @@ mr_status mr_debug_table(mr_ctx *ctx, uint32_t class_bits, const mr_key *key, co
  * N^-1 mod m'_j (k).  Synchronises the stream.  Errors as mr_miller_rabin_batch. */
 mr_status mr_debug_mr_setup(mr_ctx *ctx, const uint32_t *cand, uint32_t n_limbs, size_t n, uint32_t *dev_out,
                             void *stream);
+
+/* The trial-division tables of mr_prime_test_batch as built on the host (no
+ * context, no device): 131 rows of 10,016 words: rows w < 128 hold
+ * 2^(32w) mod p_j for the first 10,000 primes p_j (column j), row 128 the
+ * primes (columns past 10,000 zero in these rows), then from row 129 on the
+ * factors floor((2^64-1)/p_j) as consecutive little-endian word pairs.  *count
+ * receives the word count; out may be NULL to query
+ * it.  Errors: MR_ERR_ARG (out too small). */
+mr_status mr_debug_trial_table(uint32_t *out, size_t capacity, size_t *count);
 
 /* As mr_debug_table for the key tables of modulus N (host, n_limbs limbs),
  * computed on the host only (no context, no device).  Errors as mr_rns_setup. */

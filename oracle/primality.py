@@ -91,3 +91,14 @@ def miller_rabin_round(n: int, a: int) -> bool:
 def miller_rabin(n: int, witnesses: Sequence[int]) -> List[bool]:
     """Per-witness verdicts; n is a probable prime when all are True."""
     return [miller_rabin_round(n, a) for a in witnesses]
+
+
+def prime_test_verdict(n: int, witnesses: Sequence[int], count: int = 10000) -> int:
+    """The key-generation primality test: trial division by the first ``count`` primes
+    (Sec. 4.3), then the Miller-Rabin rounds (Sec. 3.2) for candidates that pass it.
+
+    0 = fails trial division, 1 = passes it and some round fails, 2 = passes every round.
+    """
+    if not trial_division_passes(n, count):
+        return 0
+    return 2 if all(miller_rabin(n, witnesses)) else 1

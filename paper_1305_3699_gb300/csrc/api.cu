@@ -88,6 +88,7 @@ struct mr_ctx {
   std::vector<cudaStream_t> side;     // streams for concurrent groups of one-shot mixed calls
   std::vector<cudaEvent_t> side_join;
   cudaEvent_t side_fork = nullptr;
+  uint32_t* trial_tab = nullptr;  // trial-division tables (mr_prime_test_batch), built on first use
 };
 
 struct mr_plan;
@@ -655,6 +656,40 @@ mr_status guarded(mr_ctx* ctx, F&& f) {
 
 // Per-candidate verdicts from per-round items: probable prime when every round passed; bit r of
 // the mask set when round r (< 32) passed.
+// Size class of Miller-Rabin candidates of n_limbs limbs (lane-group classes only).
+mr_status mr_class(mr_ctx* ctx, uint32_t n_limbs, ClassEntry** out) {
+  uint32_t L = class_for_bits(32 * n_limbs);
+  if (!L) return fail(ctx, MR_ERR_SIZE, "candidates longer than the largest size class");
+  mr_status s = get_class(ctx, L, out);
+  if (s) return s;
+  if ((*out)->big()) return fail(ctx, MR_ERR_SIZE, "Miller-Rabin takes candidates of at most 4096 bits");
+  return MR_OK;
+}
+
+// Lane mapping of a Miller-Rabin launch of `items` work items: the caller's choice when pinned,
+// else the narrowest mapping that gives at least 8 warps per SM (the widest when none does).
+uint32_t mr_variant(mr_ctx* ctx, const ClassEntry* ce, size_t items) {
+  if (ce->pinned) return ce->variant;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  uint32_t vsel = 0;
+  for (uint32_t v = 0; v < ce->kern->n_variants; v++)
+    if (ce->kern->var[v].tpi > ce->kern->var[vsel].tpi) vsel = v;
+  for (uint32_t v = 0; v < ce->kern->n_variants; v++) {
+    const double warps = (double)items * ce->kern->var[v].tpi / 32.0;
+    if (warps >= 8.0 * sms && ce->kern->var[v].tpi < ce->kern->var[vsel].tpi) vsel = v;
+  }
+  return vsel;
+}
+
+// Device scratch bytes of mr_launch with lane mapping v: window tables per warp, then per item 3W
+// words of constants.
+size_t mr_scratch_bytes(const ClassEntry* ce, uint32_t v, uint32_t n_limbs, size_t items) {
+  const KernelVariant& k = ce->kern->var[v];
+  const uint32_t wbits = choose_window(32 * n_limbs, 0, window_cap(ce));
+  return align256(modexp_scratch_words(k, (uint32_t)items, wbits) * 4) + items * 3 * (size_t)ce->host.W * 4;
+}
+
 __global__ void mr_combine_kernel(const uint8_t* item_pass, uint32_t n, uint32_t rounds, uint8_t* is_prime,
                                   uint32_t* round_mask) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -919,6 +954,7 @@ void mr_shutdown(mr_ctx* ctx) {
     for (uint32_t* t : kv.second->tslice)
       if (t) cudaFree(t);
   }
+  if (ctx->trial_tab) cudaFree(ctx->trial_tab);
   if (ctx->staging) cudaFreeHost(ctx->staging);
   if (ctx->staging_evt) cudaEventDestroy(ctx->staging_evt);
   for (auto& sp : ctx->spans) {
@@ -1204,6 +1240,27 @@ mr_status mr_rsa_decrypt_crt(mr_ctx* ctx, const mr_key* const* keys, size_t n, c
   });
 }
 
+// Miller-Rabin launch shared by mr_miller_rabin_batch and mr_prime_test_batch: n candidates (or the
+// *n_sel of them listed in sel), one work item per (candidate, round) when per = rounds.  With
+// per > 1 the item verdicts go to `item_pass` (n * per bytes) and the caller combines them.
+mr_status mr_launch(mr_ctx* ctx, ClassEntry* ce, uint32_t v, const uint32_t* cand, uint32_t n_limbs, size_t n,
+                    const uint32_t* witness, uint32_t rounds, uint32_t per, uint8_t* item_pass,
+                    uint32_t* dev_round_mask, const uint32_t* sel, const uint32_t* n_sel, void* scratch,
+                    cudaStream_t stream) {
+  const size_t items = n * (size_t)per;
+  const KernelVariant& k = ce->kern->var[v];
+  const uint32_t wbits = choose_window(32 * n_limbs, 0, window_cap(ce));
+  const size_t tab_words = modexp_scratch_words(k, (uint32_t)items, wbits);
+  const size_t off_crow = align256(tab_words * 4);
+  char* base = static_cast<char*>(scratch);
+  MRArgs a{ce->dev, cand, witness, item_pass, dev_round_mask, reinterpret_cast<uint32_t*>(base),
+           reinterpret_cast<uint32_t*>(base + off_crow), (uint32_t)items, n_limbs, rounds, wbits, ctx->mr_dbg,
+           per, sel, n_sel};
+  unsigned grid = (unsigned)((items + k.ipb - 1) / k.ipb);
+  cudaError_t e = timed_launch(ctx, 0, stream, [&] { return k.mr(a, grid, stream); });
+  return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "kernel launch");
+}
+
 mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs, size_t n, const uint32_t* witness,
                                 uint32_t rounds, uint8_t* dev_is_probable_prime, uint32_t* dev_round_mask,
                                 void* stream) {
@@ -1215,55 +1272,94 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
   if (n > 0xffffffffull) return fail(ctx, MR_ERR_ARG, "batch too large");
   return guarded(ctx, [&]() -> mr_status {
     cudaSetDevice(ctx->device);
-    uint32_t L = class_for_bits(32 * n_limbs);
-    if (!L) return fail(ctx, MR_ERR_SIZE, "candidates longer than the largest size class");
+    cudaStream_t st = (cudaStream_t)stream;
     ClassEntry* ce = nullptr;
-    mr_status s = get_class(ctx, L, &ce);
+    mr_status s = mr_class(ctx, n_limbs, &ce);
     if (s) return s;
-    if (ce->big()) return fail(ctx, MR_ERR_SIZE, "Miller-Rabin takes candidates of at most 4096 bits");
     // The rounds of a candidate are independent: each runs as its own work item (the setup of
     // the candidate is repeated per round, a few hundredths of a round's cost) and a second
     // kernel combines the verdicts.  The constant-dump hook keeps one item per candidate.
     const uint32_t per = (rounds > 1 && !ctx->mr_dbg && (uint64_t)n * rounds <= 0xffffffffull) ? rounds : 1u;
     const size_t items = n * (size_t)per;
-    // unless the caller chose a lane mapping, take the narrowest one that gives at least 8 warps per
-    // SM for this many items (the widest when none does)
-    uint32_t vsel = ce->variant;
-    if (!ce->pinned) {
-      int sms = 0;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-      vsel = 0;
-      for (uint32_t v = 0; v < ce->kern->n_variants; v++)
-        if (ce->kern->var[v].tpi > ce->kern->var[vsel].tpi) vsel = v;
-      for (uint32_t v = 0; v < ce->kern->n_variants; v++) {
-        const double warps = (double)items * ce->kern->var[v].tpi / 32.0;
-        if (warps >= 8.0 * sms && ce->kern->var[v].tpi < ce->kern->var[vsel].tpi) vsel = v;
-      }
-    }
-    const KernelVariant& k = ce->kern->var[vsel];
-    const uint32_t wbits = choose_window(32 * n_limbs, 0, window_cap(ce));
-    const size_t tab_words = modexp_scratch_words(k, (uint32_t)items, wbits);
-    const size_t crow_words = items * 3 * (size_t)ce->host.W;
-    const size_t off_crow = align256(tab_words * 4);
-    const size_t off_pass = align256(off_crow + crow_words * 4);
-    const size_t bytes = per > 1 ? off_pass + items : off_crow + crow_words * 4;
+    const uint32_t v = mr_variant(ctx, ce, items);
+    const size_t sbytes = mr_scratch_bytes(ce, v, n_limbs, items);
+    const size_t off_pass = align256(sbytes);
+    const size_t bytes = per > 1 ? off_pass + items : sbytes;
     void* dev = nullptr;
-    cudaError_t e = cudaMallocFromPoolAsync(&dev, bytes, ctx->pool, (cudaStream_t)stream);
+    cudaError_t e = cudaMallocFromPoolAsync(&dev, bytes, ctx->pool, st);
     if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, std::string("scratch allocation failed: ") + cudaGetErrorString(e));
     char* base = static_cast<char*>(dev);
     uint8_t* verdicts = per > 1 ? reinterpret_cast<uint8_t*>(base + off_pass) : dev_is_probable_prime;
-    MRArgs a{ce->dev, cand, witness, verdicts, per > 1 ? nullptr : dev_round_mask, reinterpret_cast<uint32_t*>(base),
-             reinterpret_cast<uint32_t*>(base + off_crow), (uint32_t)items, n_limbs, rounds, wbits, ctx->mr_dbg,
-             per};
-    unsigned grid = (unsigned)((items + k.ipb - 1) / k.ipb);
-    e = timed_launch(ctx, 0, (cudaStream_t)stream, [&] { return k.mr(a, grid, (cudaStream_t)stream); });
-    if (e == cudaSuccess && per > 1) {
-      mr_combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-          verdicts, (uint32_t)n, rounds, dev_is_probable_prime, dev_round_mask);
+    s = mr_launch(ctx, ce, v, cand, n_limbs, n, witness, rounds, per, verdicts, per > 1 ? nullptr : dev_round_mask,
+                  nullptr, nullptr, dev, st);
+    if (!s && per > 1) {
+      mr_combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(verdicts, (uint32_t)n, rounds,
+                                                                     dev_is_probable_prime, dev_round_mask);
       e = cudaGetLastError();
+      if (e != cudaSuccess) s = cuda_fail(ctx, e, "kernel launch");
     }
-    cudaError_t e2 = cudaFreeAsync(dev, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    cudaError_t e2 = cudaFreeAsync(dev, st);
+    if (s) return s;
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");
+    return MR_OK;
+  });
+}
+
+mr_status mr_prime_test_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs, size_t n, const uint32_t* witness,
+                              uint32_t rounds, uint32_t n_primes, uint8_t* dev_verdict, uint32_t* dev_survivors,
+                              void* stream) {
+  if (!ctx) return MR_ERR_ARG;
+  if (n == 0) return dev_survivors ? (cudaMemsetAsync(dev_survivors, 0, 4, (cudaStream_t)stream) == cudaSuccess
+                                          ? MR_OK
+                                          : cuda_fail(ctx, cudaErrorInvalidValue, "cudaMemsetAsync"))
+                                   : MR_OK;
+  if (!cand || !n_limbs || !witness || !rounds || !dev_verdict)
+    return fail(ctx, MR_ERR_ARG, "null argument, zero limbs or zero rounds");
+  if (n_primes == 0 || n_primes > TRIAL_MAX_PRIMES) return fail(ctx, MR_ERR_ARG, "n_primes must be 1..10000");
+  if ((uint64_t)n * rounds > 0xffffffffull) return fail(ctx, MR_ERR_ARG, "batch too large");
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    ClassEntry* ce = nullptr;
+    mr_status s = mr_class(ctx, n_limbs, &ce);
+    if (s) return s;
+    if (n_limbs > TRIAL_MAX_LIMBS) return fail(ctx, MR_ERR_SIZE, "candidates longer than 4096 bits");
+    if (!ctx->trial_tab) {
+      std::vector<uint32_t> t = trial_tables_host();
+      s = upload(ctx, t, &ctx->trial_tab);
+      if (s) return s;
+    }
+    // device scratch: [count][sel n][slot n][Miller-Rabin scratch][item verdicts n * rounds]
+    const uint32_t per = rounds;
+    const size_t items = n * (size_t)per;
+    // the lane mapping is chosen for the expected survivors (about one random odd candidate in ten
+    // passes the first 10,000 primes; one in eight is assumed); scratch holds every candidate
+    const uint32_t v = mr_variant(ctx, ce, (items + 7) / 8);
+    const size_t off_sel = 256, off_slot = align256(off_sel + n * 4), off_mr = align256(off_slot + n * 4);
+    const size_t off_pass = align256(off_mr + mr_scratch_bytes(ce, v, n_limbs, items));
+    const size_t bytes = off_pass + items;
+    void* dev = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&dev, bytes, ctx->pool, st);
+    if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, std::string("scratch allocation failed: ") + cudaGetErrorString(e));
+    char* base = static_cast<char*>(dev);
+    uint32_t* count = reinterpret_cast<uint32_t*>(base);
+    uint32_t* sel = reinterpret_cast<uint32_t*>(base + off_sel);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(base + off_slot);
+    uint8_t* pass = reinterpret_cast<uint8_t*>(base + off_pass);
+    e = cudaMemsetAsync(count, 0, 4, st);
+    if (e == cudaSuccess)
+      e = timed_launch(ctx, 1, st, [&] { return launch_trial(cand, n_limbs, (uint32_t)n, ctx->trial_tab, n_primes,
+                                                             sel, slot, count, st); });
+    s = e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "trial division launch");
+    if (!s)
+      s = mr_launch(ctx, ce, v, cand, n_limbs, n, witness, rounds, per, pass, nullptr, sel, count, base + off_mr, st);
+    if (!s) {
+      e = launch_prime_combine(pass, slot, (uint32_t)n, per, dev_verdict, st);
+      if (e == cudaSuccess && dev_survivors) e = cudaMemcpyAsync(dev_survivors, count, 4, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) s = cuda_fail(ctx, e, "kernel launch");
+    }
+    cudaError_t e2 = cudaFreeAsync(dev, st);
+    if (s) return s;
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");
     return MR_OK;
   });
@@ -1644,6 +1740,19 @@ mr_status mr_debug_table(mr_ctx* ctx, uint32_t class_bits, const mr_key* key, co
     mr_status s = debug_class_table(*c, nm, out, capacity, count);
     return s ? fail(ctx, s, "unknown table or buffer too small") : MR_OK;
   });
+}
+
+mr_status mr_debug_trial_table(uint32_t* out, size_t capacity, size_t* count) {
+  try {
+    if (count) *count = trial_table_words();
+    if (!out) return MR_OK;
+    if (capacity < trial_table_words()) return MR_ERR_ARG;
+    std::vector<uint32_t> t = trial_tables_host();
+    std::copy(t.begin(), t.end(), out);
+    return MR_OK;
+  } catch (...) {
+    return MR_ERR_ARG;
+  }
 }
 
 mr_status mr_debug_key_table_host(const uint32_t* N, uint32_t n_limbs, const char* name, uint32_t* out,

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "layout.h"
 
@@ -30,6 +31,8 @@ struct MRArgs {
   uint32_t n_limbs, rounds, wbits;
   uint32_t* dbg;            // nullptr, or per candidate mr_debug_words(k, W) words of derived constants
   uint32_t per;             // items per candidate: 1 (an item runs all rounds) or rounds (one round each)
+  const uint32_t* sel;      // nullptr, or the candidates to test: item g takes candidate sel[g / per]
+  const uint32_t* n_sel;    // with sel: device word, the number of selected candidates (items = it * per)
 };
 
 // Barrier polls of the large-class kernel before a wait gives up (x 0.03-0.3 us each: about 1 s).
@@ -88,6 +91,21 @@ struct ClassKernels {
 // items[i].keyp + n_off.  W <= CRT_BIN_MAX_W.
 constexpr uint32_t CRT_BIN_MAX_W = 512;
 cudaError_t launch_crt_bin(const CrtItem* items, uint32_t n_items, uint32_t W, uint32_t n_off, cudaStream_t s);
+
+// Trial division by the first primes ahead of Miller-Rabin (trial.cu).  Device table layout
+// (words): [limb w][prime j] 2^(32w) mod p_j (TRIAL_MAX_LIMBS rows of TRIAL_STRIDE), then the
+// primes (TRIAL_STRIDE), then the Barrett factors floor((2^64-1)/p_j) as uint64 (2 TRIAL_STRIDE).
+constexpr uint32_t TRIAL_MAX_PRIMES = 10000, TRIAL_STRIDE = 10016, TRIAL_MAX_LIMBS = 128;
+constexpr uint32_t TRIAL_NONE = 0xffffffffu;
+constexpr size_t trial_table_words() { return (size_t)(TRIAL_MAX_LIMBS + 3) * TRIAL_STRIDE; }
+std::vector<uint32_t> trial_tables_host();
+// Candidates passing trial division by the first np primes are appended to sel (count: *count,
+// zeroed by the caller), slot[c] = their position; the others get slot[c] = TRIAL_NONE.
+cudaError_t launch_trial(const uint32_t* cand, uint32_t nl, uint32_t n, const uint32_t* tab, uint32_t np,
+                         uint32_t* sel, uint32_t* slot, uint32_t* count, cudaStream_t s);
+// verdict[c] = 0 (slot NONE), else 2 when the per item verdicts of slot[c] all pass, else 1.
+cudaError_t launch_prime_combine(const uint8_t* item_pass, const uint32_t* slot, uint32_t n, uint32_t per,
+                                 uint8_t* verdict, cudaStream_t s);
 
 // nullptr when no kernel is compiled for class L
 const ClassKernels* class_kernels(uint32_t L);

@@ -115,11 +115,15 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
   const int t = threadIdx.x % TPI;
   const int item_in_block = threadIdx.x / TPI;
   const uint32_t g_raw = blockIdx.x * C::IPB + item_in_block;
-  const bool live = g_raw < a.n;
-  const uint32_t g = live ? g_raw : a.n - 1;
+  // with a selection the item count is on the device (candidates that passed trial division)
+  const uint32_t n_items = a.sel ? min(a.n, *a.n_sel * a.per) : a.n;
+  if (n_items == 0) return;  // uniform: every thread of the launch reads the same count
+  const bool live = g_raw < n_items;
+  const uint32_t g = live ? g_raw : n_items - 1;
   const uint32_t nl = a.n_limbs;
-  // item g: candidate g / per; rounds [r0, r1) (all of them when per = 1, round g % per otherwise)
-  const uint32_t cidx = g / a.per;
+  // item g: candidate g / per (or sel[g / per]); rounds [r0, r1) (all of them when per = 1, round
+  // g % per otherwise)
+  const uint32_t cidx = a.sel ? a.sel[g / a.per] : g / a.per;
   const uint32_t r0 = a.per == 1 ? 0u : g % a.per, r1 = a.per == 1 ? a.rounds : r0 + 1;
   const uint32_t* N = a.cand + (size_t)cidx * nl;
   uint32_t* crow = a.crow + (size_t)g * 3 * W;

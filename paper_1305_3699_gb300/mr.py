@@ -29,7 +29,7 @@ EXPORTED = [
     "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
     "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant", "mr_debug_mr_setup",
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
-    "mr_imad_peak", "mr_autotune", "mr_debug_big_wait",
+    "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -78,6 +78,8 @@ def _load() -> ctypes.CDLL:
         "mr_rsa_encrypt": (ctypes.c_int, [P, P, SZ, P, U32, P, U32, P, P]),
         "mr_rsa_decrypt_crt": (ctypes.c_int, [P, P, SZ, P, U32, P, U32, P, P]),
         "mr_miller_rabin_batch": (ctypes.c_int, [P, P, U32, SZ, P, U32, P, P, P]),
+        "mr_prime_test_batch": (ctypes.c_int, [P, P, U32, SZ, P, U32, U32, P, P, P]),
+        "mr_debug_trial_table": (ctypes.c_int, [PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_debug_table": (ctypes.c_int, [P, U32, P, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_debug_key_table_host": (ctypes.c_int, [PU32, U32, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
@@ -170,6 +172,19 @@ def mr_debug_key_table_host(N: int, name: str) -> List[int]:
     if rc:
         raise MRError(rc, f"table {name}")
     return [int(v) for v in out]
+
+
+def mr_debug_trial_table() -> np.ndarray:
+    """The trial-division tables as built on the host: 131 rows of 10,016 words (see mr.h)."""
+    cnt = ctypes.c_size_t()
+    rc = lib.mr_debug_trial_table(None, 0, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, "trial table")
+    out = np.zeros(cnt.value, dtype=np.uint32)
+    rc = lib.mr_debug_trial_table(_ptr(out), cnt.value, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, "trial table")
+    return out.reshape(131, -1)
 
 
 def mr_debug_class_table(class_bits: int, name: str) -> List[int]:
@@ -352,6 +367,13 @@ class Context:
         n, nl = _rows(cand)
         self._check(lib.mr_miller_rabin_batch(self.handle, _dev(cand), nl, n, _dev(witness), rounds, _dev(is_prime),
                                               _dev(round_mask), _stream(stream)))
+
+    def mr_prime_test_batch(self, cand, witness, rounds: int, verdict, n_primes: int = 10000, survivors=None,
+                            stream=None):
+        """verdict[i] = 0 (fails trial division), 1 (a Miller-Rabin round fails), 2 (probable prime)."""
+        n, nl = _rows(cand)
+        self._check(lib.mr_prime_test_batch(self.handle, _dev(cand), nl, n, _dev(witness), rounds, n_primes,
+                                            _dev(verdict), _dev(survivors), _stream(stream)))
 
     def mr_debug_mr_setup(self, cand, out, stream=None):
         n, nl = _rows(cand)

@@ -71,6 +71,25 @@ def test_large_class_slice_widths():
         assert lanes[0] == -(-k // (4 * nw)) * nw
 
 
+def test_trial_table_matches_oracle():
+    """Trial-division tables built by the library's host code: the first 10,000 primes (the
+    oracle's sieve), 2^(32w) mod p for every limb w < 128 (Python's pow), Barrett factors."""
+    from oracle import primality
+    t = mr.mr_debug_trial_table()
+    ps = primality.first_primes(10000)
+    assert t.shape == (131, 10016)
+    assert [int(v) for v in t[128, :10000]] == list(ps)
+    assert not t[:129, 10000:].any()
+    r = SplitMix64(4321)
+    for _ in range(300):
+        j, w = r.below(10000), r.below(128)
+        assert int(t[w, j]) == pow(2, 32 * w, ps[j]), (w, j)
+    mu_words = t[129:131].reshape(-1)  # rows 129-130: the uint64 factors, low word first
+    for j in (0, 1, 2, 4999, 9999):
+        mu = int(mu_words[2 * j]) | (int(mu_words[2 * j + 1]) << 32)
+        assert mu == ((1 << 64) - 1) // ps[j], j
+
+
 def _key_cases():
     r = SplitMix64(1234)
     out = []

@@ -25,6 +25,44 @@ def test_trial_division_matches_brute_force():
         assert primality.trial_division_passes(n) == primality.is_prime_by_trial(n) or n < 2
 
 
+def _smallest_factor(n):
+    f = 2
+    while f * f <= n:
+        if n % f == 0:
+            return f
+        f += 1
+    return n
+
+
+def test_trial_division_short_lists_brute_force():
+    """With the first `count` primes only, n passes exactly when n >= 2 and its smallest prime
+    factor is n itself or exceeds the count-th prime (smallest factors found by brute force)."""
+    for count, last in ((1, 2), (10, 29), (100, 541)):
+        assert primality.first_primes(count)[-1] == last
+        for n in range(0, 3000):
+            want = n >= 2 and (_smallest_factor(n) == n or _smallest_factor(n) > last)
+            assert primality.trial_division_passes(n, count) == want, (count, n)
+
+
+def test_prime_test_verdict_cases():
+    """Verdict 0 for small factors, 1 for composites without listed factors that a round
+    catches, 2 for primes; primes above the list pass trial division."""
+    w = [2, 3, 5, 7, 11, 13]
+    assert [primality.prime_test_verdict(n, w) for n in (0, 1, 2, 17, 4, 9, 104729)] == [0, 0, 2, 2, 0, 0, 2]
+    p10001 = 104743  # the 10,001st prime: not in the list
+    assert primality.prime_test_verdict(p10001, w) == 2
+    assert primality.prime_test_verdict(p10001 * p10001, w) == 1        # no listed factor
+    assert primality.prime_test_verdict(p10001 * 104759, w) == 1
+    assert primality.prime_test_verdict(104729 * p10001, w) == 0        # a listed factor
+    assert primality.prime_test_verdict(p10001 * p10001, w, count=1) == 1
+    assert primality.prime_test_verdict(3 * p10001, w, count=1) == 1    # 3 is not listed with count 1
+    assert primality.prime_test_verdict(3 * p10001, w, count=2) == 0
+    # 3215031751 = 151 * 751 * 28351 is a strong pseudoprime to bases 2, 3, 5, 7 (published):
+    # Miller-Rabin alone passes it, the trial division (151 is listed) does not
+    assert all(primality.miller_rabin(3215031751, [2, 3, 5, 7]))
+    assert primality.prime_test_verdict(3215031751, [2, 3, 5, 7]) == 0
+
+
 def test_miller_rabin_exhaustive_below_2_16():
     # Bases {2,3,5,7} decide primality exactly below 3,215,031,751 (published bound).
     # (n > 7 so that no base is a multiple of n)
