@@ -82,6 +82,40 @@ def algorithmic_products_per_modexp(k: int, W: int, WX: int, ebits: int, w: int,
     return mms * per_mm + chunks * W * 2 * k + k * WX
 
 
+def mms_sliding(e: int, w: int, chunks: int) -> int:
+    """RNS Montgomery multiplications of one exponentiation on the sliding-window schedule the
+    lane-group kernel runs when every number of a warp has the same exponent e (windows of up to
+    w + 1 bits that start and end on a set bit; table of the 2^w odd powers, built with x^2):
+    `chunks` entry products, 2^w table products, the squarings and window products, one exit."""
+    ws = w + 1
+    mms = chunks + (1 << w) + 1
+    top = e.bit_length() - 1
+    lo = max(top - ws + 1, 0)
+    while not (e >> lo) & 1:
+        lo += 1
+    pos = lo
+    while pos > 0:
+        i, z = pos - 1, 0
+        while i - z >= 0 and not (e >> (i - z)) & 1:
+            z += 1
+        if i - z < 0:
+            mms += z
+            pos = 0
+        else:
+            t = i - z
+            lo = max(t - ws + 1, 0)
+            while not (e >> lo) & 1:
+                lo += 1
+            mms += z + (t - lo + 1) + 1
+            pos = lo
+    return mms
+
+
+def algorithmic_products_sliding(k: int, W: int, WX: int, e: int, w: int, chunks: int) -> int:
+    """As algorithmic_products_per_modexp, on the sliding-window schedule (mms_sliding)."""
+    return mms_sliding(e, w, chunks) * (2 * k * k + 7 * k) + chunks * W * 2 * k + k * WX
+
+
 # ------------------------------------------------------------- clock sampler
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -94,7 +128,7 @@ class ClockSampler:
         self.mark = None
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", gpu_index], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -124,6 +158,10 @@ class ClockSampler:
 
     def summary(self, t0, t1):
         rows = self.window(t0, t1)
+        note = None
+        if not rows:  # a timed region shorter than the sampling interval: the samples next to it
+            rows = self.window(t0 - 0.2, t1 + 0.2)
+            note = "no sample inside the timed region; samples within 0.2 s of it"
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples in the timed region"], "samples": 0}
 
@@ -136,9 +174,12 @@ class ClockSampler:
         mx = [num(r[2]) for r in rows if num(r[2]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max((num(r[3]) or 0) for r in rows)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": reasons, "samples": len(rows),
+               "power_w_max": max((num(r[3]) or 0) for r in rows)}
+        if note:
+            out["note"] = note
+        return out
 
 
 # --------------------------------------------------------- CPU oracle timing
@@ -445,10 +486,15 @@ def run_ours(args, rank, world, local_rank):
     W = 32
     WX = len(mr.mr_debug_class_table(L_half, "M"))
     w = window_for_bits(max(max(keys[i]["dp"].bit_length(), keys[i]["dq"].bit_length()) for i in idx))
+    # every warp holds halves of one key (256 ciphertexts per key, items ordered by exponent), so
+    # the kernel runs the sliding-window schedule (w >= 4) for all of them
     prods = 0
     for i in idx:
         for dpq in (keys[i]["dp"], keys[i]["dq"]):
-            prods += algorithmic_products_per_modexp(k, W, WX, dpq.bit_length(), w, 2)
+            if w >= 4:
+                prods += algorithmic_products_sliding(k, W, WX, dpq, w, 2)
+            else:
+                prods += algorithmic_products_per_modexp(k, W, WX, dpq.bit_length(), w, 2)
     ops_per_launch = 2 * prods  # one exponentiation launch per step covers all 8192 halves
     max_mhz = sm_max_mhz()
     peak = props.multi_processor_count * IMAD_PER_CLK_PER_SM * max_mhz * 1e6

@@ -376,6 +376,11 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
       b.mx[2 * i + 1].out = mq;
     }
   }
+  // items with the same exponent next to each other: warps of the lane-group kernel whose numbers
+  // share one exponent run the sliding-window schedule
+  for (auto& b : batches)
+    if (!b.ce->big())
+      std::stable_sort(b.mx.begin(), b.mx.end(), [](const MxItem& x, const MxItem& y) { return x.e < y.e; });
   mr_status s = staging_reserve(ctx, upload_bytes);
   if (s) {
     cudaFreeAsync(dev, stream);
@@ -544,10 +549,13 @@ size_t layout_groups(mr_ctx* ctx, std::vector<GroupLaunch>& groups, uint32_t fla
   for (auto& g : groups) {
     const KernelVariant& kv = g.ce->kv();
     g.persistent = (flags & MR_PLAN_PERSISTENT) != 0;
-    // items in decreasing exponent length: long items first, groups of a warp homogeneous
+    // items in decreasing exponent length: long items first, groups of a warp homogeneous; equal
+    // lengths ordered by exponent, so that the halves of one key share warps (one schedule)
     std::vector<size_t> ord(g.mx.size());
     for (size_t i = 0; i < ord.size(); i++) ord[i] = i;
-    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return g.ebits[a] > g.ebits[b]; });
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+      return g.ebits[a] != g.ebits[b] ? g.ebits[a] > g.ebits[b] : g.mx[a].e < g.mx[b].e;
+    });
     std::vector<MxItem> mx(g.mx.size());
     std::vector<uint32_t> eb(g.mx.size());
     for (size_t i = 0; i < ord.size(); i++) {

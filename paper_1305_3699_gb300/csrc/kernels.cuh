@@ -93,39 +93,116 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
     add_vec<C>(xb, xp, hb, hp, sm, t);
   }
 
-  // window table: entry 0 = 1 (Montgomery form M mod N), entry j = x~^j
+  // Exponent schedule.  Groups of a warp run in lockstep, so the schedule must be the same for
+  // all of them.  When every number of the warp has the same exponent (the halves of one RSA key,
+  // sorted together by the host) and windows are long (wb >= 4), sliding windows of up to wb + 1
+  // bits are used (left to right: a run of zero bits costs squarings only, a window starts and
+  // ends on a set bit, so only odd powers are tabulated; about 4% fewer multiplications than fixed
+  // windows for 1024-bit exponents, same table size).  Otherwise fixed wb-bit windows.
   const int wb = (int)a.wbits, E = 1 << wb;
-  load_vec<C>(yb, yp, key + ko.one, t);
-  tab_store<C>(wt, 0, yb, yp, lane);
-  tab_store<C>(wt, 1, xb, xp, lane);
+  const uint32_t el = it.e_limbs;
+  uint32_t ebits = 0;
+  if (t == 0) ebits = bad ? 0u : exp_bits(it.e, el);
+  ebits = __shfl_sync(0xffffffffu, ebits, lane - t);
+  bool uni = false;
+  if (wb >= 4) {
+    const uint32_t* e0 = reinterpret_cast<const uint32_t*>(
+        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(it.e), 0));
+    const uint32_t eb0 = __shfl_sync(0xffffffffu, ebits, 0);
+    int eq = ebits == eb0 && eb0 != 0u;
+    if (eq && t == 0)
+      for (uint32_t w = 0; w < (ebits + 31) / 32; w++)
+        if (it.e[w] != e0[w]) {
+          eq = 0;
+          break;
+        }
+    eq = __shfl_sync(0xffffffffu, eq, lane - t);
+    uni = __all_sync(0xffffffffu, eq);
+  }
+
+  // window table.  Fixed windows: entry j = x~^j, entry 0 = 1 (Montgomery form M mod N).
+  // Sliding windows: entry i = x~^(2i+1).  One multiplication site: the multiplier (y) is x~, or
+  // x~^2 once the first product has formed it.
+  if (!uni) {
+    load_vec<C>(yb, yp, key + ko.one, t);
+    tab_store<C>(wt, 0, yb, yp, lane);
+  }
+  tab_store<C>(wt, uni ? 0 : 1, xb, xp, lane);
   {
     uint32_t cb[NPT], cp[NPT];
 #pragma unroll
     for (int s = 0; s < NPT; s++) {
       cb[s] = xb[s];
       cp[s] = xp[s];
+      yb[s] = xb[s];
+      yp[s] = xp[s];
     }
-    for (int j = 2; j < E; j++) {
-      mont_mul<C>(cb, cp, xb, xp, kxi, cmul, cd, sm, xib, xpb, t);
-      tab_store<C>(wt, j, cb, cp, lane);
+    const int iters = uni ? E : E - 2;
+    for (int j = 0; j < iters; j++) {
+      mont_mul<C>(cb, cp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
+      if (uni && j == 0) {
+#pragma unroll
+        for (int s = 0; s < NPT; s++) {  // y = x~^2; restart the products from x~
+          yb[s] = cb[s];
+          yp[s] = cp[s];
+          cb[s] = xb[s];
+          cp[s] = xp[s];
+        }
+      } else {
+        tab_store<C>(wt, uni ? j : j + 2, cb, cp, lane);
+      }
     }
   }
 
-  // exponent: fixed windows from the top; groups of a warp run in lockstep
-  const uint32_t el = it.e_limbs;
-  uint32_t ebits = 0;
-  if (t == 0) ebits = bad ? 0u : exp_bits(it.e, el);
-  ebits = __shfl_sync(0xffffffffu, ebits, lane - t);
-  const uint32_t nwin = __reduce_max_sync(0xffffffffu, (ebits + wb - 1) / wb);
-  uint32_t d = (nwin && !bad) ? exp_digit(it.e, el, (nwin - 1) * wb, wb) : 0u;
+  const int ws = wb + 1;  // sliding window width
+  int pos = 0;            // sliding: bits below the current window still to process
+  int widx = 0;           // fixed: next window index
+  uint32_t d;
+  if (uni) {
+    const int top = (int)ebits - 1;
+    int lo = max(top - ws + 1, 0);
+    while (!exp_digit(it.e, el, (uint32_t)lo, 1)) lo++;
+    d = (exp_digit(it.e, el, (uint32_t)lo, (uint32_t)(top - lo + 1)) - 1u) >> 1;
+    pos = lo;
+  } else {
+    const uint32_t nwin = __reduce_max_sync(0xffffffffu, (ebits + wb - 1) / wb);
+    d = (nwin && !bad) ? exp_digit(it.e, el, (nwin - 1) * wb, wb) : 0u;
+    widx = (int)nwin - 2;
+  }
   __syncwarp();
   tab_load<C>(wt, d, xb, xp, lane);
-  // per window: wb squarings, then (when any number of the warp has a non-zero digit) one
-  // multiplication by the table entry; a squaring passes x as both operands
-  for (int widx = (int)nwin - 2; widx >= 0; widx--) {
-    for (int q = 0; q < wb; q++) mont_mul<C>(xb, xp, xb, xp, kxi, cmul, cd, sm, xib, xpb, t);
-    d = bad ? 0u : exp_digit(it.e, el, (uint32_t)widx * wb, wb);
-    if (__any_sync(0xffffffffu, d != 0)) {
+  // each step: nsq squarings (a squaring passes x as both operands), then, when the step has a
+  // window (fixed: any number of the warp has a non-zero digit), one multiplication by its entry
+  for (;;) {
+    int nsq;
+    bool mul;
+    if (uni) {
+      if (pos <= 0) break;
+      const int i = pos - 1;
+      int z = 0;
+      while (i - z >= 0 && !exp_digit(it.e, el, (uint32_t)(i - z), 1)) z++;
+      if (i - z < 0) {
+        nsq = z;
+        mul = false;
+        pos = 0;
+      } else {
+        const int top = i - z;
+        int lo = max(top - ws + 1, 0);
+        while (!exp_digit(it.e, el, (uint32_t)lo, 1)) lo++;
+        nsq = z + (top - lo + 1);
+        d = (exp_digit(it.e, el, (uint32_t)lo, (uint32_t)(top - lo + 1)) - 1u) >> 1;
+        mul = true;
+        pos = lo;
+      }
+    } else {
+      if (widx < 0) break;
+      nsq = wb;
+      d = bad ? 0u : exp_digit(it.e, el, (uint32_t)widx * wb, wb);
+      mul = __any_sync(0xffffffffu, d != 0);
+      widx--;
+    }
+    for (int q = 0; q < nsq; q++) mont_mul<C>(xb, xp, xb, xp, kxi, cmul, cd, sm, xib, xpb, t);
+    if (mul) {
       tab_load<C>(wt, d, yb, yp, lane);
       mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
     }

@@ -118,6 +118,39 @@ def test_modexp_full_length_exponents(mr, ctx):
     _modexp_case(mr, ctx, [2048] * 3, [2048] * 3, 6)
 
 
+@pytest.mark.parametrize("bits", [512, 1024, 2048, 4096])
+def test_modexp_shared_exponent_sliding_windows(mr, ctx, bits):
+    """Warps whose numbers share one exponent run the sliding-window schedule: every item of a
+    block of 40 (several warps, a ragged tail) has the same exponent, moduli and bases differ.
+    Exponents: random, single bit, all ones, long zero runs inside and at the bottom, a last
+    window ending on bit 0, one set bit in each of the top and bottom positions."""
+    r = SplitMix64(0x51 + bits)
+    eb = min(bits, 1024)
+    exps = [r.randbits(eb) | (1 << (eb - 1)), 1 << (eb - 1), (1 << eb) - 1,
+            (r.randbits(eb // 2) << (eb // 2)) | 1, (r.randbits(64) | (1 << 63)) << (eb - 64),
+            (1 << (eb - 1)) | 1, (1 << (eb - 1)) | (0b1011 << 200) | 0b110001]
+    el = (eb + 31) // 32
+    for j, e in enumerate(exps):
+        n = 40
+        mods = [r.randbits(bits) | 1 | (1 << (bits - 1)) for _ in range(3)]
+        hk = [ctx.mr_rns_setup(N) for N in mods]
+        idx = [i % 3 for i in range(n)]
+        xs = [r.below(mods[i]) for i in idx]
+        xs[0], xs[1] = 1, mods[idx[1]] - 1
+        x = mr.to_tensor(xs, bits // 32)
+        et = mr.to_tensor([e] * n, el)
+        out = torch.zeros_like(x)
+        st = _status(n)
+        ctx.mr_modexp_batch([hk[i] for i in idx], x, et, out, st)
+        torch.cuda.synchronize()
+        got = mr.from_tensor(out)
+        for i in range(n):
+            assert got[i] == plain.modexp(xs[i], e, mods[idx[i]]), (bits, j, i)
+        assert st.cpu().tolist() == [0] * n
+        for h in hk:
+            h.free()
+
+
 def test_modexp_mixed_sizes_one_call(mr, ctx):
     bits = [512, 1024, 2048, 3072, 4096, 1024, 768, 1536] * 5
     _modexp_case(mr, ctx, bits, [96] * len(bits), 9)
