@@ -26,6 +26,27 @@ __device__ __forceinline__ uint32_t exp_digit(const uint32_t* e, uint32_t el, ui
   return (uint32_t)(v >> b) & ((1u << wb) - 1u);
 }
 
+// Bits [i-31, i] of e (bit i in bit 31); positions below 0 read as zero.
+__device__ __forceinline__ uint32_t exp_top32(const uint32_t* e, uint32_t el, int i) {
+  const int lo = i - 31;
+  const uint32_t p = (uint32_t)(lo > 0 ? lo : 0);
+  const uint32_t l = p >> 5, b = p & 31;
+  const uint64_t v = (l < el ? e[l] : 0u) | ((uint64_t)(l + 1 < el ? e[l + 1] : 0u) << 32);
+  const uint32_t f = (uint32_t)(v >> b);  // bits [p, p + 32)
+  return lo >= 0 ? f : f << (31 - i);
+}
+
+// Sliding window whose top bit is the set bit `top`: the up to ws bits [lo, top] trimmed to end
+// on a set bit.  Returns the table index (value - 1) / 2 of the odd window value; *lo_out = lo.
+__device__ __forceinline__ uint32_t slide_window(const uint32_t* e, uint32_t el, int top, int ws, int* lo_out) {
+  int lo = max(top - ws + 1, 0);
+  uint32_t v = exp_digit(e, el, (uint32_t)lo, (uint32_t)(top - lo + 1));
+  const int tz = __ffs(v) - 1;  // v != 0: bit top is set
+  v >>= tz;
+  *lo_out = lo + tz;
+  return (v - 1u) >> 1;
+}
+
 template <class C>
 __device__ __forceinline__ void tab_store(uint32_t* wt, int ent, const uint32_t (&b)[C::NPT], const uint32_t (&p)[C::NPT],
                                           int lane) {
@@ -120,14 +141,20 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
     uni = __all_sync(0xffffffffu, eq);
   }
 
+  // The schedule flag is passed through an empty asm at each place it steers (the table, the
+  // first window, the loop), so that the compiler cannot duplicate the code between them per
+  // value of the flag (each copy would hold another inlined multiplication).
+  int uni_t = uni ? 1 : 0, uni_f = uni ? 1 : 0;
+  asm volatile("" : "+r"(uni_t), "+r"(uni_f));
+
   // window table.  Fixed windows: entry j = x~^j, entry 0 = 1 (Montgomery form M mod N).
   // Sliding windows: entry i = x~^(2i+1).  One multiplication site: the multiplier (y) is x~, or
   // x~^2 once the first product has formed it.
-  if (!uni) {
+  if (!uni_t) {
     load_vec<C>(yb, yp, key + ko.one, t);
     tab_store<C>(wt, 0, yb, yp, lane);
   }
-  tab_store<C>(wt, uni ? 0 : 1, xb, xp, lane);
+  tab_store<C>(wt, uni_t ? 0 : 1, xb, xp, lane);
   {
     uint32_t cb[NPT], cp[NPT];
 #pragma unroll
@@ -137,10 +164,13 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
       yb[s] = xb[s];
       yp[s] = xp[s];
     }
-    const int iters = uni ? E : E - 2;
+    const int iters = uni_t ? E : E - 2;
     for (int j = 0; j < iters; j++) {
       mont_mul<C>(cb, cp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
-      if (uni && j == 0) {
+      // opaque to the compiler: keeps one copy of the loop (no peeled first iteration)
+      int first = (uni_t && j == 0) ? 1 : 0;
+      asm volatile("" : "+r"(first));
+      if (first) {
 #pragma unroll
         for (int s = 0; s < NPT; s++) {  // y = x~^2; restart the products from x~
           yb[s] = cb[s];
@@ -149,26 +179,22 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
           cp[s] = xp[s];
         }
       } else {
-        tab_store<C>(wt, uni ? j : j + 2, cb, cp, lane);
+        tab_store<C>(wt, uni_t ? j : j + 2, cb, cp, lane);
       }
     }
   }
 
+  // first window.  cur: sliding: bits below the current window still to process; fixed: index of
+  // the next window.  Both schedules' values are formed and one is selected (no branch here, so
+  // that the compiler keeps a single copy of the loop below).
   const int ws = wb + 1;  // sliding window width
-  int pos = 0;            // sliding: bits below the current window still to process
-  int widx = 0;           // fixed: next window index
-  uint32_t d;
-  if (uni) {
-    const int top = (int)ebits - 1;
-    int lo = max(top - ws + 1, 0);
-    while (!exp_digit(it.e, el, (uint32_t)lo, 1)) lo++;
-    d = (exp_digit(it.e, el, (uint32_t)lo, (uint32_t)(top - lo + 1)) - 1u) >> 1;
-    pos = lo;
-  } else {
-    const uint32_t nwin = __reduce_max_sync(0xffffffffu, (ebits + wb - 1) / wb);
-    d = (nwin && !bad) ? exp_digit(it.e, el, (nwin - 1) * wb, wb) : 0u;
-    widx = (int)nwin - 2;
-  }
+  const uint32_t nwin = __reduce_max_sync(0xffffffffu, (ebits + wb - 1) / wb);
+  const uint32_t d_fixed = (nwin && !bad) ? exp_digit(it.e, el, (nwin - 1) * wb, wb) : 0u;
+  int lo_first = 0;
+  const uint32_t d_slide = uni_f ? slide_window(it.e, el, (int)ebits - 1, ws, &lo_first) : 0u;
+  uint32_t d = uni_f ? d_slide : d_fixed;
+  int cur = uni_f ? lo_first : (int)nwin - 2;
+  asm volatile("" : "+r"(cur), "+r"(d));  // opaque start values: the loop is not peeled
   __syncwarp();
   tab_load<C>(wt, d, xb, xp, lane);
   // each step: nsq squarings (a squaring passes x as both operands), then, when the step has a
@@ -176,34 +202,54 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   for (;;) {
     int nsq;
     bool mul;
-    if (uni) {
-      if (pos <= 0) break;
-      const int i = pos - 1;
-      int z = 0;
-      while (i - z >= 0 && !exp_digit(it.e, el, (uint32_t)(i - z), 1)) z++;
-      if (i - z < 0) {
-        nsq = z;
+    // opaque to the compiler: one copy of the loop body (no unswitched copy per schedule)
+    int slide = uni ? 1 : 0;
+    asm volatile("" : "+r"(slide));
+    if (slide) {
+      if (cur <= 0) break;
+      const int i = cur - 1;
+      int z = 0;  // zero bits from i down, 32 at a time
+      for (;;) {
+        if (i - z < 0) break;
+        const uint32_t u = exp_top32(it.e, el, i - z);
+        if (u) {
+          z += __clz(u);
+          break;
+        }
+        z += 32;
+      }
+      if (i - z < 0) {  // only zeros left: squarings
+        nsq = cur;
         mul = false;
-        pos = 0;
+        cur = 0;
       } else {
         const int top = i - z;
-        int lo = max(top - ws + 1, 0);
-        while (!exp_digit(it.e, el, (uint32_t)lo, 1)) lo++;
+        int lo;
+        d = slide_window(it.e, el, top, ws, &lo);
         nsq = z + (top - lo + 1);
-        d = (exp_digit(it.e, el, (uint32_t)lo, (uint32_t)(top - lo + 1)) - 1u) >> 1;
         mul = true;
-        pos = lo;
+        cur = lo;
       }
     } else {
-      if (widx < 0) break;
+      if (cur < 0) break;
       nsq = wb;
-      d = bad ? 0u : exp_digit(it.e, el, (uint32_t)widx * wb, wb);
+      d = bad ? 0u : exp_digit(it.e, el, (uint32_t)cur * wb, wb);
       mul = __any_sync(0xffffffffu, d != 0);
-      widx--;
+      cur--;
     }
-    for (int q = 0; q < nsq; q++) mont_mul<C>(xb, xp, xb, xp, kxi, cmul, cd, sm, xib, xpb, t);
-    if (mul) {
-      tab_load<C>(wt, d, yb, yp, lane);
+    // one multiplication site for the squarings and the window product (the second operand is a
+    // copy of x, or the table entry), so the loop holds a single copy of the multiplication code
+    const int nmm = nsq + (mul ? 1 : 0);
+    for (int q = 0; q < nmm; q++) {
+      if (q < nsq) {
+#pragma unroll
+        for (int s = 0; s < NPT; s++) {
+          yb[s] = xb[s];
+          yp[s] = xp[s];
+        }
+      } else {
+        tab_load<C>(wt, d, yb, yp, lane);
+      }
       mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
     }
   }
