@@ -44,7 +44,7 @@ SEED = 0x4D520002
 IMAD_PER_CLK_PER_SM = 64   # int32 multiplies per clock per SM (integer multiply pipe)
 # DRAM bytes (read + write) of one exponentiation launch of the RSA-2048 CRT workload, from an ncu
 # capture of the current kernel on this workload (dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_BYTES_PER_LAUNCH = 2_844_416 + 24_651_776
+TRAFFIC_BYTES_PER_LAUNCH = 2_862_848 + 24_692_736
 # long-exponent workload: 256 exponentiations modulo 16384-bit RSA moduli with 16128-bit exponents
 BIG_KEYSET = "mod16384_x4"
 BIG_N = 256
