@@ -249,6 +249,35 @@ mr_status mr_prime_test_batch(mr_ctx *ctx, const uint32_t *cand, uint32_t n_limb
                               const uint32_t *witness, uint32_t rounds, uint32_t n_primes,
                               uint8_t *dev_verdict, uint32_t *dev_survivors, void *stream);
 
+/* RSA key generation on the device from candidate pools (Sec. 3.3: N = pq,
+ * d = e^-1 mod (p-1)(q-1); Sec. 3.1: Arazi's inversion; the primes pass the
+ * test of mr_prime_test_batch with the first 10,000 primes).  For key k, p is
+ * the first candidate of its p pool that is a probable prime with
+ * gcd(e, p-1) = 1, q the first such candidate of its q pool with q != p;
+ * then N = pq, d = Arazi(e, (p-1)(q-1)), dp = Arazi(e, p-1),
+ * dq = Arazi(e, q-1) (so dp = d mod (p-1), dq = d mod (q-1)) and
+ * qinv = q^-1 mod p; Arazi(e, f) = (1 + f t) / e with t = -f^-1 mod e.  The
+ * private parts are written to device memory only.
+ *   half_limbs  limbs of each candidate (2..64: primes of up to 2048 bits)
+ *   n_keys, pool
+ *   cand        device, n_keys * 2 * pool rows of half_limbs limbs: rows
+ *               [2k pool, 2k pool + pool) are key k's p candidates, the next
+ *               pool rows its q candidates (odd candidates of the wanted size;
+ *               the caller supplies the randomness)
+ *   witness, rounds   Miller-Rabin witnesses, `rounds` rows per candidate
+ *               (row c * rounds + r), as mr_miller_rabin_batch
+ *   e           public exponent, odd, 3 <= e < 2^32
+ *   out         device, n_keys rows of 9 * half_limbs limbs: N (2H), d (2H),
+ *               p, q, dp, dq, qinv (H each)
+ *   dev_status  device, n_keys bytes or NULL: 0, MR_ERR_RANGE (a pool holds no
+ *               usable prime; the row is zero) or MR_ERR_NOT_COPRIME (an
+ *               inverse does not exist: a candidate passed the test but is
+ *               not prime)
+ * Errors: MR_ERR_ARG, MR_ERR_SIZE, MR_ERR_OOM, MR_ERR_CUDA. */
+mr_status mr_rsa_keygen_batch(mr_ctx *ctx, uint32_t half_limbs, size_t n_keys, uint32_t pool,
+                              const uint32_t *cand, const uint32_t *witness, uint32_t rounds, uint32_t e,
+                              uint32_t *out, uint8_t *dev_status, void *stream);
+
 /* Allocation-free exponentiation: out[i] = x[i]^e[i] mod N for i < n, one
  * modulus per call.  The paper has no counterpart; this entry point exists for
  * callers that cannot allocate device memory when they call it -- an engine that

@@ -38,6 +38,34 @@ def gen_prime(rng: SplitMix64, bits: int, rounds: int = 40, e: int | None = None
             return n
 
 
+def first_usable_prime(pool, witnesses, e: int, count: int = 10000, exclude: int | None = None):
+    """The first candidate of ``pool`` that passes trial division by the first ``count`` primes
+    and every Miller-Rabin round with its witnesses (Sec. 4.3, Sec. 3.2), has gcd(e, n-1) = 1
+    and differs from ``exclude``; None when there is none."""
+    from .primality import prime_test_verdict
+    for n, ws in zip(pool, witnesses):
+        if n == exclude or gcd(e, n - 1) != 1:
+            continue
+        if prime_test_verdict(n, ws, count) == 2:
+            return n
+    return None
+
+
+def rsa_key_from_pools(p_pool, p_witnesses, q_pool, q_witnesses, e: int = 65537, count: int = 10000):
+    """RSA key from given candidate pools (Sec. 3.3): p is the first usable prime of the p pool, q
+    the first of the q pool other than p; N = pq and the private parts by Arazi's inversion
+    (rsa_private_parts).  None when a pool holds no usable prime."""
+    p = first_usable_prime(p_pool, p_witnesses, e, count)
+    if p is None:
+        return None
+    q = first_usable_prime(q_pool, q_witnesses, e, count, exclude=p)
+    if q is None:
+        return None
+    key = {"N": p * q, "e": e, "p": p, "q": q}
+    key.update(rsa_private_parts(p, q, e))
+    return key
+
+
 def gen_rsa_key(rng: SplitMix64, bits: int, e: int = 65537, rounds: int = 40) -> dict:
     """A seeded RSA key of exactly ``bits`` bits with primes of bits/2 bits each."""
     half = bits // 2

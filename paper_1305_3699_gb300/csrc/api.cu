@@ -1374,6 +1374,39 @@ mr_status mr_prime_test_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limb
 }
 
 
+mr_status mr_rsa_keygen_batch(mr_ctx* ctx, uint32_t half_limbs, size_t n_keys, uint32_t pool, const uint32_t* cand,
+                              const uint32_t* witness, uint32_t rounds, uint32_t e, uint32_t* out, uint8_t* dev_status,
+                              void* stream) {
+  if (!ctx) return MR_ERR_ARG;
+  if (n_keys == 0) return MR_OK;
+  if (!cand || !witness || !out || !rounds || !pool) return fail(ctx, MR_ERR_ARG, "null argument, zero pool or rounds");
+  if (half_limbs < 2 || half_limbs > KEYGEN_MAX_HALF_LIMBS)
+    return fail(ctx, MR_ERR_SIZE, "prime candidates must have 2 to 64 limbs");
+  if (e < 3 || !(e & 1u)) return fail(ctx, MR_ERR_ARG, "the public exponent must be odd and at least 3");
+  const uint64_t n = (uint64_t)n_keys * 2 * pool;
+  if (n * rounds > 0xffffffffull) return fail(ctx, MR_ERR_ARG, "batch too large");
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    void* dev = nullptr;
+    cudaError_t e1 = cudaMallocFromPoolAsync(&dev, align256((size_t)n), ctx->pool, st);
+    if (e1 != cudaSuccess)
+      return fail(ctx, MR_ERR_OOM, std::string("scratch allocation failed: ") + cudaGetErrorString(e1));
+    uint8_t* verdict = static_cast<uint8_t*>(dev);
+    // verdicts of every candidate (trial division, then Miller-Rabin on the survivors)
+    mr_status s = mr_prime_test_batch(ctx, cand, half_limbs, (size_t)n, witness, rounds, TRIAL_MAX_PRIMES, verdict,
+                                      nullptr, stream);
+    if (!s) {
+      cudaError_t e2 = launch_keygen(cand, verdict, (uint32_t)n_keys, pool, half_limbs, e, out, dev_status, st);
+      if (e2 != cudaSuccess) s = cuda_fail(ctx, e2, "key assembly launch");
+    }
+    cudaError_t e3 = cudaFreeAsync(dev, st);
+    if (s) return s;
+    if (e3 != cudaSuccess) return cuda_fail(ctx, e3, "cudaFreeAsync");
+    return MR_OK;
+  });
+}
+
 mr_status mr_rsa_mixed(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, size_t n, const uint32_t* in,
                        uint32_t in_stride, uint32_t* out, uint32_t out_stride, uint8_t* dev_status, uint32_t flags,
                        void* stream) {

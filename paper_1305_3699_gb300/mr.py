@@ -30,6 +30,7 @@ EXPORTED = [
     "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant", "mr_debug_mr_setup",
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
     "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
+    "mr_rsa_keygen_batch",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -80,6 +81,7 @@ def _load() -> ctypes.CDLL:
         "mr_miller_rabin_batch": (ctypes.c_int, [P, P, U32, SZ, P, U32, P, P, P]),
         "mr_prime_test_batch": (ctypes.c_int, [P, P, U32, SZ, P, U32, U32, P, P, P]),
         "mr_debug_trial_table": (ctypes.c_int, [PU32, SZ, ctypes.POINTER(SZ)]),
+        "mr_rsa_keygen_batch": (ctypes.c_int, [P, U32, SZ, U32, P, P, U32, U32, P, P, P]),
         "mr_debug_table": (ctypes.c_int, [P, U32, P, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_debug_key_table_host": (ctypes.c_int, [PU32, U32, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
@@ -374,6 +376,15 @@ class Context:
         n, nl = _rows(cand)
         self._check(lib.mr_prime_test_batch(self.handle, _dev(cand), nl, n, _dev(witness), rounds, n_primes,
                                             _dev(verdict), _dev(survivors), _stream(stream)))
+
+    def mr_rsa_keygen_batch(self, cand, witness, rounds: int, n_keys: int, pool: int, out, e: int = 65537,
+                            status=None, stream=None):
+        """Keys from candidate pools: out rows of 9 * half_limbs limbs (N, d, p, q, dp, dq, qinv)."""
+        n, nl = _rows(cand)
+        if n != n_keys * 2 * pool:
+            raise ValueError("cand must hold n_keys * 2 * pool rows")
+        self._check(lib.mr_rsa_keygen_batch(self.handle, nl, n_keys, pool, _dev(cand), _dev(witness), rounds, e,
+                                            _dev(out), _dev(status), _stream(stream)))
 
     def mr_debug_mr_setup(self, cand, out, stream=None):
         n, nl = _rows(cand)

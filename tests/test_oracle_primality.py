@@ -63,6 +63,31 @@ def test_prime_test_verdict_cases():
     assert primality.prime_test_verdict(3215031751, [2, 3, 5, 7]) == 0
 
 
+def test_key_from_pools_selection_and_identities():
+    """Pool selection: composites, a prime with e | p-1 and a repeat of p are skipped; the key's
+    parts satisfy the RSA identities (e d = 1 mod (p-1)(q-1), dp/dq, q qinv = 1 mod p, and
+    decryption inverts encryption)."""
+    ws = lambda pool: [[2, 3, 5, 7] for _ in pool]
+    e = 3
+    # 7: 3 | 7-1 (skipped for e = 3); 9, 15: composite; 11: first usable p; q pool: 11 repeats p, 13: 3 | 12
+    key = keygen.rsa_key_from_pools([9, 7, 15, 11, 23], ws(range(5)), [11, 13, 17, 29], ws(range(4)), e)
+    assert (key["p"], key["q"]) == (11, 17)
+    assert keygen.rsa_key_from_pools([9, 15, 21], ws(range(3)), [17], ws(range(1)), e) is None
+    r = SplitMix64(0x6B65)
+    pool_p = [r.randbits(256) | (3 << 254) | 1 for _ in range(400)]
+    pool_q = [r.randbits(256) | (3 << 254) | 1 for _ in range(400)]
+    wp = [[r.between(2, n - 2) for _ in range(8)] for n in pool_p]
+    wq = [[r.between(2, n - 2) for _ in range(8)] for n in pool_q]
+    k = keygen.rsa_key_from_pools(pool_p, wp, pool_q, wq, 65537)
+    assert k is not None
+    p, q, d = k["p"], k["q"], k["d"]
+    assert primality.is_prime_by_trial(p) if p < 1 << 40 else pow(2, p - 1, p) == 1
+    assert k["N"] == p * q and (k["e"] * d) % ((p - 1) * (q - 1)) == 1
+    assert k["dp"] == d % (p - 1) and k["dq"] == d % (q - 1) and (k["qinv"] * q) % p == 1
+    m = r.below(k["N"])
+    assert pow(pow(m, 65537, k["N"]), d, k["N"]) == m
+
+
 def test_miller_rabin_exhaustive_below_2_16():
     # Bases {2,3,5,7} decide primality exactly below 3,215,031,751 (published bound).
     # (n > 7 so that no base is a multiple of n)
