@@ -829,6 +829,93 @@ def run_primegen1024(args, rank, world, local_rank):
     return 0
 
 
+def _oracle_keygen_chunk(args):
+    from oracle import keygen
+    t0 = time.perf_counter()
+    for pp, wp, pq, wq in args:
+        keygen.rsa_key_from_pools(pp, wp, pq, wq, 65537)
+    return time.perf_counter() - t0, len(args)
+
+
+def run_keygen2048(args, rank, world, local_rank):
+    """RSA-2048 key generation on the device: 16 keys, each from pools of 2048 seeded random odd
+    1024-bit candidates for p and for q (top two bits set), 4 Miller-Rabin rounds with seeded
+    witnesses; one mr_rsa_keygen_batch call per step (trial division and Miller-Rabin on every
+    candidate, then the key assembly with Arazi's inversion)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1305_3699_gb300 import mr
+    from synth import SplitMix64
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n_keys, pool, rounds, H = 16, 2048, 4, 32
+    r = SplitMix64(0x4D520008 + 0x1000 * rank)
+    pools = [[r.randbits(1024) | (3 << 1022) | 1 for _ in range(pool)] for _ in range(2 * n_keys)]
+    wits = [[[r.between(2, c - 2) for _ in range(rounds)] for c in pl] for pl in pools]
+    ctx = mr.Context(local_rank)
+    cand_t = mr.to_tensor([c for pl in pools for c in pl], H, device=dev)
+    wit_t = mr.to_tensor([w for wl in wits for ws in wl for w in ws], H, device=dev)
+    out = torch.zeros((n_keys, 9 * H), dtype=torch.int32, device=dev)
+    st = torch.zeros(n_keys, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        ctx.mr_rsa_keygen_batch(cand_t, wit_t, rounds, n_keys, pool, out, status=st, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    torch.cuda.synchronize()
+    from oracle import keygen
+    rows = out.cpu().numpy().astype("int64") & 0xFFFFFFFF
+    for k in (0, n_keys - 1):
+        want = keygen.rsa_key_from_pools(pools[2 * k], wits[2 * k], pools[2 * k + 1], wits[2 * k + 1], 65537)
+        got_n = sum(int(v) << (32 * i) for i, v in enumerate(rows[k][:2 * H]))
+        assert (want is None and int(st[k]) == 5) or (want is not None and got_n == want["N"]), "keygen mismatch"
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.mr_profile_enable(True)
+    ctx.mr_profile_read()
+    with torch.cuda.stream(stream):
+        for s_ in range(args.steps):
+            evs[s_][0].record(stream)
+            step()
+            evs[s_][1].record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.mr_profile_read()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
+    made = int((st == 0).sum())
+    value = made * world * args.steps / (total_ms / 1e3)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import multiprocessing as mpr
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        sample = [(pools[2 * k], wits[2 * k], pools[2 * k + 1], wits[2 * k + 1]) for k in range(n_keys)]
+        with mpr.get_context("spawn").Pool(cores) as pool_:
+            t0 = time.perf_counter()
+            pool_.map(_oracle_keygen_chunk, [sample[i::cores] for i in range(cores) if sample[i::cores]])
+            dt = time.perf_counter() - t0
+        cpu = {"value": n_keys / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
+               "sample": f"all {n_keys} keys, oracle.keygen.rsa_key_from_pools on {cores} processes"}
+    if rank == 0:
+        (mx_n, mx_ms), (tr_n, tr_ms) = prof
+        line = {"metric": METRIC, "value": value, "unit": "RSA-2048 keys/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic (seeded candidate pools and witnesses)",
+                "config": {"workload": "keygen_rsa2048_16x2x2048", "keys": n_keys, "pool": pool, "rounds": rounds,
+                           "keys_made": made, "mr_kernel_ms": mx_ms / max(1, mx_n),
+                           "trial_kernel_ms": tr_ms / max(1, tr_n)},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_ragged(args, rank, world, local_rank):
     """Ragged batch: one prepared plan per launch mode over the same 65,536 requests."""
     import torch
@@ -1136,7 +1223,7 @@ def main():
     ap.add_argument("--ebits", type=int, default=BIG_EBITS,
                     help="exponent bits of the modexp16384 workload (smaller values for profiling runs)")
     ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving", "modexp16384", "rsa16384_crt",
-                                                             "rsa1024_enc", "mr1024", "primegen1024"])
+                                                             "rsa1024_enc", "mr1024", "primegen1024", "keygen2048"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -1159,6 +1246,8 @@ def main():
             return run_mr1024(args, rank, world, local_rank)
         if args.workload == "primegen1024":
             return run_primegen1024(args, rank, world, local_rank)
+        if args.workload == "keygen2048":
+            return run_keygen2048(args, rank, world, local_rank)
         if args.workload == "serving":
             return run_serving_bench(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
