@@ -3,9 +3,12 @@
 // primes are the candidates that pass trial division and the Miller-Rabin rounds, whose verdicts
 // this kernel reads).  The private parts never leave the device.
 //
-// One thread per key, serial multi-limb arithmetic in local memory: the work per key (a few
-// multi-limb products, two short divisions, one binary inversion of about 4 * 32H steps) is a
-// small fraction of the primality tests that precede it.
+// One warp per key.  Lane 0 picks the primes and forms N, d, dp, dq with serial multi-limb code
+// (a few products and three exact divisions by e); the binary inversion for qinv, about 4 * 32H
+// dependent steps, runs on the whole warp with one limb per lane and register (limb i in lane
+// i mod 32, register i / 32): carries of an addition are resolved for all limbs at once from
+// two ballots (generate and propagate masks, added as integers), shifts move one bit between
+// neighbouring lanes.
 //   p     first candidate of the key's p pool with verdict 2 and gcd(e, p - 1) = 1
 //   q     the same in the q pool, q != p
 //   N     p q;   d = Arazi(e, (p-1)(q-1));   dp = Arazi(e, p - 1);   dq = Arazi(e, q - 1)
@@ -19,14 +22,6 @@ namespace mr {
 namespace {
 
 constexpr int KG_MAX = 2 * KEYGEN_MAX_HALF_LIMBS;  // limbs of N
-
-__device__ bool kg_is_zero(const uint32_t* a, int n) {
-  for (int i = 0; i < n; i++)
-    if (a[i]) return false;
-  return true;
-}
-
-__device__ bool kg_is_one(const uint32_t* a, int n) { return a[0] == 1u && kg_is_zero(a + 1, n - 1); }
 
 __device__ int kg_cmp(const uint32_t* a, const uint32_t* b, int n) {
   for (int i = n - 1; i >= 0; i--)
@@ -43,25 +38,6 @@ __device__ uint32_t kg_sub(uint32_t* r, const uint32_t* a, const uint32_t* b, in
     br = (uint32_t)(d >> 32) ? 1u : 0u;
   }
   return br;
-}
-
-// r = a + b (n limbs); returns the carry
-__device__ uint32_t kg_add(uint32_t* r, const uint32_t* a, const uint32_t* b, int n) {
-  uint64_t c = 0;
-  for (int i = 0; i < n; i++) {
-    c += (uint64_t)a[i] + b[i];
-    r[i] = (uint32_t)c;
-    c >>= 32;
-  }
-  return (uint32_t)c;
-}
-
-// a = (top:a) / 2
-__device__ void kg_shr1(uint32_t* a, int n, uint32_t top) {
-  for (int i = 0; i < n; i++) {
-    const uint32_t hi = i + 1 < n ? a[i + 1] : top;
-    a[i] = (a[i] >> 1) | (hi << 31);
-  }
 }
 
 // r (2n limbs) = a b
@@ -134,60 +110,137 @@ __device__ bool kg_arazi(uint32_t* d, const uint32_t* f, int n, uint32_t e) {
   return rem == 0;
 }
 
-// r = a mod p (n limbs each), binary long division
-__device__ void kg_mod(uint32_t* r, const uint32_t* a, const uint32_t* p, int n) {
-  uint32_t t[KG_MAX / 2 + 1], pe[KG_MAX / 2 + 1];
-  for (int i = 0; i <= n; i++) {
-    t[i] = 0;
-    pe[i] = i < n ? p[i] : 0u;
-  }
-  for (int bit = 32 * n - 1; bit >= 0; bit--) {
-    uint32_t cy = (a[bit >> 5] >> (bit & 31)) & 1u;  // t = 2 t + bit
-    for (int i = 0; i <= n; i++) {
-      const uint32_t nc = t[i] >> 31;
-      t[i] = (t[i] << 1) | cy;
-      cy = nc;
-    }
-    if (kg_cmp(t, pe, n + 1) >= 0) kg_sub(t, t, pe, n + 1);
-  }
-  for (int i = 0; i < n; i++) r[i] = t[i];
+// ---- warp-cooperative multi-limb arithmetic: limb i = 32 j + lane (j = 0, 1), n <= 64 limbs;
+// limbs at or above n are zero.  Every lane of the warp calls these together.
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint64_t w_ballot64(bool b0, bool b1) {
+  return (uint64_t)__ballot_sync(FULL, b0) | ((uint64_t)__ballot_sync(FULL, b1) << 32);
 }
 
-// r = u^-1 mod p (p odd), binary extended Euclid with a bounded step count; false when u has no
-// inverse (or the bound ran out)
-__device__ bool kg_inv(uint32_t* r, const uint32_t* u, const uint32_t* p, int n) {
-  uint32_t a[KG_MAX / 2], b[KG_MAX / 2], x1[KG_MAX / 2], x2[KG_MAX / 2];
-  kg_mod(a, u, p, n);
-  for (int i = 0; i < n; i++) {
-    b[i] = p[i];
-    x1[i] = i == 0 ? 1u : 0u;
-    x2[i] = 0;
+// r = a + b + cin over n limbs; returns the carry out of limb n-1
+__device__ uint32_t w_add(uint32_t (&r)[2], const uint32_t (&a)[2], const uint32_t (&b)[2], uint32_t cin, int n,
+                          int lane) {
+  uint32_t sm[2];
+  bool g[2], pr[2];
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    sm[j] = a[j] + b[j];
+    g[j] = sm[j] < a[j];          // the limb generates a carry
+    pr[j] = sm[j] == 0xffffffffu;  // the limb passes an incoming carry on
   }
-  if (kg_is_zero(a, n)) return false;
+  // carry into limb i = carry into bit i of the integer sum G + (G | P) + cin
+  const uint64_t G = w_ballot64(g[0], g[1]), X = G | w_ballot64(pr[0], pr[1]);
+  const uint64_t s1 = G + X;
+  const bool o1 = s1 < G;
+  const uint64_t s2 = s1 + cin;
+  const bool o2 = s2 < s1;
+  const uint64_t C = s2 ^ G ^ X;
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const int i = 32 * j + lane;
+    r[j] = i < n ? sm[j] + (uint32_t)((C >> i) & 1u) : 0u;
+  }
+  return n < 64 ? (uint32_t)((C >> n) & 1u) : (uint32_t)(o1 || o2);
+}
+
+// r = a - b over n limbs; returns the borrow
+__device__ uint32_t w_sub(uint32_t (&r)[2], const uint32_t (&a)[2], const uint32_t (&b)[2], int n, int lane) {
+  uint32_t nb[2];
+#pragma unroll
+  for (int j = 0; j < 2; j++) nb[j] = 32 * j + lane < n ? ~b[j] : 0u;
+  return 1u - w_add(r, a, nb, 1u, n, lane);
+}
+
+// v = (top : v) / 2, top in {0, 1} being limb n
+__device__ void w_shr1(uint32_t (&v)[2], uint32_t top, int n, int lane) {
+  const uint32_t up0 = __shfl_down_sync(FULL, v[0], 1), up1 = __shfl_down_sync(FULL, v[1], 1);
+  const uint32_t w10 = __shfl_sync(FULL, v[1], 0);
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const int i = 32 * j + lane;
+    const uint32_t nb = i + 1 == n ? top : (lane < 31 ? (j ? up1 : up0) : (j ? 0u : w10));
+    v[j] = i < n ? (v[j] >> 1) | (nb << 31) : 0u;
+  }
+}
+
+// v = 2 v + bit0 over n limbs
+__device__ void w_shl1(uint32_t (&v)[2], uint32_t bit0, int n, int lane) {
+  const uint32_t dn0 = __shfl_up_sync(FULL, v[0], 1), dn1 = __shfl_up_sync(FULL, v[1], 1);
+  const uint32_t w031 = __shfl_sync(FULL, v[0], 31);
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const int i = 32 * j + lane;
+    const uint32_t lo = i == 0 ? (bit0 << 31) : (lane > 0 ? (j ? dn1 : dn0) : w031);
+    v[j] = i < n ? (v[j] << 1) | (lo >> 31) : 0u;
+  }
+}
+
+__device__ __forceinline__ bool w_is_zero(const uint32_t (&v)[2]) { return !__any_sync(FULL, (v[0] | v[1]) != 0u); }
+
+__device__ __forceinline__ bool w_is_one(const uint32_t (&v)[2], int lane) {
+  return __all_sync(FULL, v[1] == 0u && v[0] == (lane == 0 ? 1u : 0u));
+}
+
+__device__ __forceinline__ uint32_t w_low_bit(const uint32_t (&v)[2]) { return __shfl_sync(FULL, v[0], 0) & 1u; }
+
+// bit `bit` of v (uniform)
+__device__ __forceinline__ uint32_t w_bit(const uint32_t (&v)[2], int bit) {
+  const int li = bit >> 5;
+  const uint32_t word = __shfl_sync(FULL, (li >> 5) ? v[1] : v[0], li & 31);
+  return (word >> (bit & 31)) & 1u;
+}
+
+// r = u mod p by binary long division (32n steps)
+__device__ void w_mod(uint32_t (&r)[2], const uint32_t (&u)[2], const uint32_t (&p)[2], int n, int lane) {
+  r[0] = r[1] = 0u;
+  for (int bit = 32 * n - 1; bit >= 0; bit--) {
+    const uint32_t t = w_bit(r, 32 * n - 1);  // the bit shifted out of limb n-1
+    w_shl1(r, w_bit(u, bit), n, lane);
+    uint32_t d[2];
+    const uint32_t br = w_sub(d, r, p, n, lane);
+    if (t || !br) {  // 2r + bit >= p (the value is below 2p)
+      r[0] = d[0];
+      r[1] = d[1];
+    }
+  }
+}
+
+// r = u^-1 mod p (p odd) by the binary extended Euclidean algorithm, with a bounded step count;
+// false when u has no inverse (or the bound ran out)
+__device__ bool w_inv(uint32_t (&r)[2], const uint32_t (&u)[2], const uint32_t (&p)[2], int n, int lane) {
+  uint32_t a[2], b[2] = {p[0], p[1]}, x1[2] = {lane == 0 ? 1u : 0u, 0u}, x2[2] = {0u, 0u};
+  w_mod(a, u, p, n, lane);
+  if (w_is_zero(a)) return false;
   const int limit = 8 * 32 * n + 64;
   int steps = 0;
-  while (!kg_is_one(a, n) && !kg_is_one(b, n)) {
-    if (kg_is_zero(a, n) || kg_is_zero(b, n) || ++steps > limit) return false;
-    while ((a[0] & 1u) == 0 && steps++ <= limit) {
-      kg_shr1(a, n, 0);
-      const uint32_t cy = (x1[0] & 1u) ? kg_add(x1, x1, p, n) : 0u;
-      kg_shr1(x1, n, cy);
+  while (!w_is_one(a, lane) && !w_is_one(b, lane)) {
+    if (w_is_zero(a) || w_is_zero(b) || ++steps > limit) return false;
+    while (!w_low_bit(a) && steps++ <= limit) {
+      w_shr1(a, 0u, n, lane);
+      uint32_t cy = 0u;
+      if (w_low_bit(x1)) cy = w_add(x1, x1, p, 0u, n, lane);
+      w_shr1(x1, cy, n, lane);
     }
-    while ((b[0] & 1u) == 0 && steps++ <= limit) {
-      kg_shr1(b, n, 0);
-      const uint32_t cy = (x2[0] & 1u) ? kg_add(x2, x2, p, n) : 0u;
-      kg_shr1(x2, n, cy);
+    while (!w_low_bit(b) && steps++ <= limit) {
+      w_shr1(b, 0u, n, lane);
+      uint32_t cy = 0u;
+      if (w_low_bit(x2)) cy = w_add(x2, x2, p, 0u, n, lane);
+      w_shr1(x2, cy, n, lane);
     }
-    if (kg_cmp(a, b, n) >= 0) {
-      kg_sub(a, a, b, n);
-      if (kg_sub(x1, x1, x2, n)) kg_add(x1, x1, p, n);
+    uint32_t d[2];
+    if (!w_sub(d, a, b, n, lane)) {  // a >= b
+      a[0] = d[0];
+      a[1] = d[1];
+      if (w_sub(x1, x1, x2, n, lane)) w_add(x1, x1, p, 0u, n, lane);
     } else {
-      kg_sub(b, b, a, n);
-      if (kg_sub(x2, x2, x1, n)) kg_add(x2, x2, p, n);
+      w_sub(b, b, a, n, lane);
+      if (w_sub(x2, x2, x1, n, lane)) w_add(x2, x2, p, 0u, n, lane);
     }
   }
-  const uint32_t* x = kg_is_one(a, n) ? x1 : x2;
-  for (int i = 0; i < n; i++) r[i] = x[i];
+  const bool one_a = w_is_one(a, lane);
+  r[0] = one_a ? x1[0] : x2[0];
+  r[1] = one_a ? x1[1] : x2[1];
   return true;
 }
 
@@ -206,56 +259,70 @@ __device__ int kg_pick(const uint32_t* cand, const uint8_t* verdict, uint32_t fi
   return -1;
 }
 
-__global__ void keygen_kernel(const uint32_t* cand, const uint8_t* verdict, uint32_t n_keys, uint32_t pool, int H,
-                              uint32_t e, uint32_t* out, uint8_t* status) {
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_keys) return;
+__global__ void __launch_bounds__(32) keygen_kernel(const uint32_t* cand, const uint8_t* verdict, uint32_t pool,
+                                                    int H, uint32_t e, uint32_t* out, uint8_t* status) {
+  __shared__ uint32_t sp[KEYGEN_MAX_HALF_LIMBS], sq[KEYGEN_MAX_HALF_LIMBS];
+  __shared__ uint32_t sst;
+  const uint32_t k = blockIdx.x;  // one warp per key
+  const int lane = (int)threadIdx.x;
   uint32_t* o = out + (size_t)k * 9 * H;  // N 2H | d 2H | p | q | dp | dq | qinv
-  uint32_t* oN = o;
-  uint32_t* od = o + 2 * H;
-  uint32_t* op = o + 4 * H;
-  uint32_t* oq = o + 5 * H;
-  uint32_t* odp = o + 6 * H;
-  uint32_t* odq = o + 7 * H;
-  uint32_t* oqi = o + 8 * H;
-  uint8_t st = 0;
-  const uint32_t base = k * 2 * pool;
-  const int jp = kg_pick(cand, verdict, base, pool, H, e, nullptr);
-  const int jq = jp < 0 ? -1 : kg_pick(cand, verdict, base + pool, pool, H, e, cand + (size_t)(base + jp) * H);
-  uint32_t p[KG_MAX / 2], q[KG_MAX / 2], pm1[KG_MAX / 2], qm1[KG_MAX / 2], one[KG_MAX / 2];
-  uint32_t N[KG_MAX], phi[KG_MAX], t[KG_MAX];
-  if (jp < 0 || jq < 0) {
-    st = 5;  // MR_ERR_RANGE: a pool holds no usable prime
-  } else {
-    for (int i = 0; i < H; i++) {
-      p[i] = cand[(size_t)(base + jp) * H + i];
-      q[i] = cand[(size_t)(base + pool + jq) * H + i];
-      one[i] = i == 0 ? 1u : 0u;
+  if (lane == 0) {
+    uint32_t st = 0;
+    const uint32_t base = k * 2 * pool;
+    const int jp = kg_pick(cand, verdict, base, pool, H, e, nullptr);
+    const int jq = jp < 0 ? -1 : kg_pick(cand, verdict, base + pool, pool, H, e, cand + (size_t)(base + jp) * H);
+    if (jp < 0 || jq < 0) {
+      st = 5;  // MR_ERR_RANGE: a pool holds no usable prime
+    } else {
+      uint32_t p[KG_MAX / 2], q[KG_MAX / 2], pm1[KG_MAX / 2], qm1[KG_MAX / 2], one[KG_MAX / 2];
+      uint32_t N[KG_MAX], phi[KG_MAX], t[KG_MAX];
+      for (int i = 0; i < H; i++) {
+        p[i] = cand[(size_t)(base + jp) * H + i];
+        q[i] = cand[(size_t)(base + pool + jq) * H + i];
+        one[i] = i == 0 ? 1u : 0u;
+        sp[i] = p[i];
+        sq[i] = q[i];
+        o[4 * H + i] = p[i];
+        o[5 * H + i] = q[i];
+      }
+      kg_sub(pm1, p, one, H);
+      kg_sub(qm1, q, one, H);
+      kg_mul(N, p, q, H);
+      kg_mul(phi, pm1, qm1, H);
+      bool ok = kg_arazi(t, phi, 2 * H, e);
+      for (int i = 0; i < 2 * H; i++) {
+        o[i] = N[i];
+        o[2 * H + i] = ok ? t[i] : 0u;
+      }
+      ok = ok && kg_arazi(t, pm1, H, e);
+      for (int i = 0; i < H; i++) o[6 * H + i] = ok ? t[i] : 0u;
+      ok = ok && kg_arazi(t, qm1, H, e);
+      for (int i = 0; i < H; i++) o[7 * H + i] = ok ? t[i] : 0u;
+      if (!ok) st = 3;  // MR_ERR_NOT_COPRIME: gcd(e, p-1) = gcd(e, q-1) = 1 was checked; not reached
     }
-    kg_sub(pm1, p, one, H);
-    kg_sub(qm1, q, one, H);
-    kg_mul(N, p, q, H);
-    kg_mul(phi, pm1, qm1, H);
-    bool ok = kg_arazi(t, phi, 2 * H, e);
-    for (int i = 0; i < 2 * H; i++) {
-      oN[i] = N[i];
-      od[i] = ok ? t[i] : 0u;
-    }
-    ok = ok && kg_arazi(t, pm1, H, e);
-    for (int i = 0; i < H; i++) odp[i] = ok ? t[i] : 0u;
-    ok = ok && kg_arazi(t, qm1, H, e);
-    for (int i = 0; i < H; i++) odq[i] = ok ? t[i] : 0u;
-    ok = ok && kg_inv(t, q, p, H);
-    for (int i = 0; i < H; i++) {
-      oqi[i] = ok ? t[i] : 0u;
-      op[i] = p[i];
-      oq[i] = q[i];
-    }
-    if (!ok) st = 3;  // MR_ERR_NOT_COPRIME: an inverse does not exist (not a prime after all)
+    sst = st;
   }
-  if (st == 5)
-    for (int i = 0; i < 9 * H; i++) o[i] = 0u;
-  if (status) status[k] = st;
+  __syncwarp();
+  uint32_t st = sst;
+  if (st == 0) {  // qinv = q^-1 mod p on the whole warp
+    uint32_t pw[2], qw[2], r[2];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int i = 32 * j + lane;
+      pw[j] = i < H ? sp[i] : 0u;
+      qw[j] = i < H ? sq[i] : 0u;
+    }
+    const bool ok = w_inv(r, qw, pw, H, lane);
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int i = 32 * j + lane;
+      if (i < H) o[8 * H + i] = ok ? r[j] : 0u;
+    }
+    if (!ok) st = 3;  // MR_ERR_NOT_COPRIME: q has no inverse mod p (p not prime after all)
+  } else if (st == 5) {
+    for (int i = lane; i < 9 * H; i += 32) o[i] = 0u;
+  }
+  if (lane == 0 && status) status[k] = (uint8_t)st;
 }
 
 }  // namespace
@@ -265,7 +332,7 @@ cudaError_t launch_keygen(const uint32_t* cand, const uint8_t* verdict, uint32_t
   if (n_keys == 0) return cudaSuccess;
   if (half_limbs < 2 || half_limbs > KEYGEN_MAX_HALF_LIMBS || pool == 0 || e < 3 || !(e & 1u))
     return cudaErrorInvalidValue;
-  keygen_kernel<<<(n_keys + 31) / 32, 32, 0, s>>>(cand, verdict, n_keys, pool, (int)half_limbs, e, out, status);
+  keygen_kernel<<<n_keys, 32, 0, s>>>(cand, verdict, pool, (int)half_limbs, e, out, status);
   return cudaGetLastError();
 }
 
