@@ -149,6 +149,29 @@ mr_status mr_rsa_decrypt_crt(mr_ctx *ctx, const mr_key *const *keys, size_t n, c
                              uint32_t c_stride, uint32_t *m, uint32_t m_stride, uint8_t *dev_status,
                              void *stream);
 
+/* Message-level RSA (Sec. 3.3: a message is split into blocks of the key's
+ * length, all blocks encrypted or decrypted in one pass).  A byte string of
+ * len bytes is read as n_blocks = ceil(len / B) blocks of
+ * B = (bits(N) - 1) / 8 bytes (the last one shorter), each block a
+ * little-endian integer below N.  mr_rsa_message_blocks gives n_blocks, B and
+ * the limbs per ciphertext row W = ceil(bits(N) / 32); needs no device.
+ * Errors: MR_ERR_ARG (NULL key), MR_ERR_SIZE (N below 2^9). */
+mr_status mr_rsa_message_blocks(const mr_key *key, size_t len, size_t *n_blocks, uint32_t *block_bytes,
+                                uint32_t *row_limbs);
+
+/* c (device, n_blocks rows of W limbs) = the blocks of msg (device, len
+ * bytes) each raised to e mod N.  dev_status: n_blocks bytes or NULL.
+ * Errors as mr_rsa_encrypt. */
+mr_status mr_rsa_encrypt_message(mr_ctx *ctx, const mr_key *key, const uint8_t *msg, size_t len, uint32_t *c,
+                                 uint8_t *dev_status, void *stream);
+
+/* msg (device, len bytes) = the CRT decryptions of c (device, n_blocks rows
+ * of W limbs, n_blocks as mr_rsa_message_blocks gives for len), written back
+ * as bytes.  The key needs its private parts.  Errors as mr_rsa_decrypt_crt,
+ * and MR_ERR_ARG when n_blocks does not match len. */
+mr_status mr_rsa_decrypt_message(mr_ctx *ctx, const mr_key *key, const uint32_t *c, size_t n_blocks, uint8_t *msg,
+                                 size_t len, uint8_t *dev_status, void *stream);
+
 /* ------------------------------------------------------- mixed batches -- */
 
 /* Operations of a mixed batch. */

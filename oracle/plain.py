@@ -95,6 +95,29 @@ def rsa_decrypt_crt(c: int, p: int, q: int, dp: int, dq: int, qinv: int) -> int:
     return mq + h * q
 
 
+def message_block_bytes(N: int) -> int:
+    """Bytes per message block for modulus N: the largest whole number of bytes whose values all
+    lie below N, (bits(N) - 1) // 8 (Sec. 3.3 splits messages into blocks of the key's length;
+    the paper does not say how a block is kept below N: this is our reading)."""
+    return (N.bit_length() - 1) // 8
+
+
+def message_blocks(msg: bytes, N: int) -> list:
+    """A byte string as integers below N: consecutive blocks of message_block_bytes(N) bytes (the
+    last one shorter), each read little-endian (the library's limb order)."""
+    B = message_block_bytes(N)
+    if B < 1:
+        raise ValueError("modulus too small")
+    return [int.from_bytes(msg[i:i + B], "little") for i in range(0, len(msg), B)]
+
+
+def message_from_blocks(blocks, N: int, length: int) -> bytes:
+    """Inverse of message_blocks for a message of `length` bytes."""
+    B = message_block_bytes(N)
+    out = b"".join(int(v).to_bytes(B, "little") for v in blocks)
+    return out[:length]
+
+
 def rsa_private_parts(p: int, q: int, e: int) -> dict:
     """d = e^-1 mod (p-1)(q-1) (Sec. 3.3), by Arazi's formula (Sec. 3.1), and the CRT parts."""
     phi = (p - 1) * (q - 1)

@@ -1407,6 +1407,76 @@ mr_status mr_rsa_keygen_batch(mr_ctx* ctx, uint32_t half_limbs, size_t n_keys, u
   });
 }
 
+mr_status mr_rsa_message_blocks(const mr_key* key, size_t len, size_t* n_blocks, uint32_t* block_bytes,
+                                uint32_t* row_limbs) {
+  if (!key) return MR_ERR_ARG;
+  const uint32_t B = (key->pub.host.nbits - 1) / 8;
+  if (B == 0) return MR_ERR_SIZE;
+  if (n_blocks) *n_blocks = (len + B - 1) / B;
+  if (block_bytes) *block_bytes = B;
+  if (row_limbs) *row_limbs = key->pub.nlimbs();
+  return MR_OK;
+}
+
+mr_status mr_rsa_encrypt_message(mr_ctx* ctx, const mr_key* key, const uint8_t* msg, size_t len, uint32_t* c,
+                                 uint8_t* dev_status, void* stream) {
+  if (!ctx) return MR_ERR_ARG;
+  if (!key || key->ctx != ctx) return fail(ctx, MR_ERR_ARG, "invalid key handle");
+  if (len == 0) return MR_OK;
+  if (!msg || !c) return fail(ctx, MR_ERR_ARG, "null argument");
+  size_t nb = 0;
+  uint32_t B = 0, W = 0;
+  if (mr_rsa_message_blocks(key, len, &nb, &B, &W)) return fail(ctx, MR_ERR_SIZE, "modulus below 2^9");
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    void* dev = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&dev, nb * W * 4, ctx->pool, st);
+    if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, std::string("scratch allocation failed: ") + cudaGetErrorString(e));
+    uint32_t* rows = static_cast<uint32_t*>(dev);
+    e = launch_pack_message(msg, len, B, W, nb, rows, st);
+    mr_status s = e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "message packing");
+    if (!s) {
+      std::vector<const mr_key*> keys(nb, key);
+      s = mr_rsa_encrypt(ctx, keys.data(), nb, rows, W, c, W, dev_status, stream);
+    }
+    cudaError_t e2 = cudaFreeAsync(dev, st);
+    if (s) return s;
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");
+    return MR_OK;
+  });
+}
+
+mr_status mr_rsa_decrypt_message(mr_ctx* ctx, const mr_key* key, const uint32_t* c, size_t n_blocks, uint8_t* msg,
+                                 size_t len, uint8_t* dev_status, void* stream) {
+  if (!ctx) return MR_ERR_ARG;
+  if (!key || key->ctx != ctx) return fail(ctx, MR_ERR_ARG, "invalid key handle");
+  size_t nb = 0;
+  uint32_t B = 0, W = 0;
+  if (mr_rsa_message_blocks(key, len, &nb, &B, &W)) return fail(ctx, MR_ERR_SIZE, "modulus below 2^9");
+  if (nb != n_blocks) return fail(ctx, MR_ERR_ARG, "n_blocks does not match the message length");
+  if (len == 0) return MR_OK;
+  if (!msg || !c) return fail(ctx, MR_ERR_ARG, "null argument");
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    void* dev = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&dev, nb * W * 4, ctx->pool, st);
+    if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, std::string("scratch allocation failed: ") + cudaGetErrorString(e));
+    uint32_t* rows = static_cast<uint32_t*>(dev);
+    std::vector<const mr_key*> keys(nb, key);
+    mr_status s = mr_rsa_decrypt_crt(ctx, keys.data(), nb, c, W, rows, W, dev_status, stream);
+    if (!s) {
+      e = launch_unpack_message(rows, B, W, len, msg, st);
+      if (e != cudaSuccess) s = cuda_fail(ctx, e, "message unpacking");
+    }
+    cudaError_t e2 = cudaFreeAsync(dev, st);
+    if (s) return s;
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");
+    return MR_OK;
+  });
+}
+
 mr_status mr_rsa_mixed(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, size_t n, const uint32_t* in,
                        uint32_t in_stride, uint32_t* out, uint32_t out_stride, uint8_t* dev_status, uint32_t flags,
                        void* stream) {

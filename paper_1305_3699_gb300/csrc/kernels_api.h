@@ -115,6 +115,12 @@ constexpr uint32_t KEYGEN_MAX_HALF_LIMBS = 64;
 cudaError_t launch_keygen(const uint32_t* cand, const uint8_t* verdict, uint32_t n_keys, uint32_t pool,
                           uint32_t half_limbs, uint32_t e, uint32_t* out, uint8_t* status, cudaStream_t s);
 
+// Message blocks (message.cu): rows of W limbs, block i = bytes [i B, i B + B) of the message,
+// little-endian; unpack writes the first len bytes back from such rows.
+cudaError_t launch_pack_message(const uint8_t* msg, size_t len, uint32_t B, uint32_t W, size_t n_blocks, uint32_t* rows,
+                                cudaStream_t s);
+cudaError_t launch_unpack_message(const uint32_t* rows, uint32_t B, uint32_t W, size_t len, uint8_t* msg, cudaStream_t s);
+
 // nullptr when no kernel is compiled for class L
 const ClassKernels* class_kernels(uint32_t L);
 

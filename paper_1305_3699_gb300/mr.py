@@ -30,7 +30,7 @@ EXPORTED = [
     "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant", "mr_debug_mr_setup",
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
     "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
-    "mr_rsa_keygen_batch",
+    "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -82,6 +82,9 @@ def _load() -> ctypes.CDLL:
         "mr_prime_test_batch": (ctypes.c_int, [P, P, U32, SZ, P, U32, U32, P, P, P]),
         "mr_debug_trial_table": (ctypes.c_int, [PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_rsa_keygen_batch": (ctypes.c_int, [P, U32, SZ, U32, P, P, U32, U32, P, P, P]),
+        "mr_rsa_message_blocks": (ctypes.c_int, [P, SZ, ctypes.POINTER(SZ), PU32, PU32]),
+        "mr_rsa_encrypt_message": (ctypes.c_int, [P, P, P, SZ, P, P, P]),
+        "mr_rsa_decrypt_message": (ctypes.c_int, [P, P, P, SZ, P, SZ, P, P]),
         "mr_debug_table": (ctypes.c_int, [P, U32, P, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_debug_key_table_host": (ctypes.c_int, [PU32, U32, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
@@ -385,6 +388,22 @@ class Context:
             raise ValueError("cand must hold n_keys * 2 * pool rows")
         self._check(lib.mr_rsa_keygen_batch(self.handle, nl, n_keys, pool, _dev(cand), _dev(witness), rounds, e,
                                             _dev(out), _dev(status), _stream(stream)))
+
+    def mr_rsa_message_blocks(self, key: Key, length: int):
+        """(n_blocks, bytes per block, limbs per ciphertext row) of a `length`-byte message."""
+        nb, B, W = ctypes.c_size_t(), ctypes.c_uint32(), ctypes.c_uint32()
+        self._check(lib.mr_rsa_message_blocks(key.handle, length, ctypes.byref(nb), ctypes.byref(B), ctypes.byref(W)))
+        return nb.value, B.value, W.value
+
+    def mr_rsa_encrypt_message(self, key: Key, msg, c, status=None, stream=None):
+        """msg: contiguous uint8 CUDA tensor; c: n_blocks rows of W limbs."""
+        self._check(lib.mr_rsa_encrypt_message(self.handle, key.handle, _dev(msg), msg.numel(), _dev(c), _dev(status),
+                                               _stream(stream)))
+
+    def mr_rsa_decrypt_message(self, key: Key, c, msg, status=None, stream=None):
+        n, _ = _rows(c)
+        self._check(lib.mr_rsa_decrypt_message(self.handle, key.handle, _dev(c), n, _dev(msg), msg.numel(),
+                                               _dev(status), _stream(stream)))
 
     def mr_debug_mr_setup(self, cand, out, stream=None):
         n, nl = _rows(cand)

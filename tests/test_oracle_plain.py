@@ -134,3 +134,21 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     monkeypatch.setattr(plain, "modexp", wrong)
     with pytest.raises(AssertionError):
         test_modexp_matches_library_pow(64)
+
+
+def test_message_blocks_round_trip_and_bounds():
+    """Blocks are below N, cover the message in order, the last one shorter; the byte string comes
+    back from the blocks; RSA on the blocks round-trips; the empty message has no blocks."""
+    from synth import SplitMix64
+    r = SplitMix64(0x6D7367)
+    for bits in (17, 64, 1024, 2051):
+        N = r.randbits(bits) | 1 | (1 << (bits - 1))
+        B = plain.message_block_bytes(N)
+        assert 256 ** B <= N < 256 ** (B + 2)
+        for length in (0, 1, B - 1, B, B + 1, 5 * B + 3):
+            msg = bytes(r.below(256) for _ in range(length))
+            blocks = plain.message_blocks(msg, N)
+            assert len(blocks) == -(-length // B)
+            assert all(0 <= v < N for v in blocks)
+            assert plain.message_from_blocks(blocks, N, length) == msg
+    assert plain.message_blocks(b"\x01\x02\x03", (1 << 17) + 1) == [0x0201, 0x03]
