@@ -101,12 +101,16 @@ __device__ bool kg_arazi(uint32_t* d, const uint32_t* f, int n, uint32_t e) {
   }
   num[n] = (uint32_t)c;
   uint64_t rem = 0;
+  bool f_is_one = f[0] == 1u;
   for (int i = n; i >= 0; i--) {
     const uint64_t cur = (rem << 32) | num[i];
     const uint64_t qd = cur / e;
     rem = cur - qd * e;
-    if (i < n) d[i] = (uint32_t)qd;  // the quotient is below f: its limb n is zero
+    if (i < n) d[i] = (uint32_t)qd;  // the quotient is below f for f > 1: its limb n is zero
+    if (i > 0 && i < n && f[i]) f_is_one = false;
   }
+  if (f_is_one)  // e^-1 mod 1 = 0 (the formula gives 1)
+    for (int i = 0; i < n; i++) d[i] = 0u;
   return rem == 0;
 }
 

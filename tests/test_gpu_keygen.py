@@ -92,6 +92,19 @@ def test_keygen_small_primes_exponent_3_and_empty_pool(mr, ctx):
     assert st[2] == 5 and st.count(0) >= 3
 
 
+def test_keygen_degenerate_prime_two(mr, ctx):
+    """A pool whose first candidate is 2: it passes the prime test and gcd(e, 1) = 1, so p = 2;
+    dp = e^-1 mod 1 = 0 and qinv = 1, as the oracle has them."""
+    q_pool = [(1 << 61) - 1, 18446744073709551557]  # primes (2^61 - 1; the largest 64-bit prime)
+    p_pool = [2, 9]
+    wits = [[1, 1], [2, 3]], [[2, 3], [2, 3]]
+    got, st = _run(mr, ctx, [p_pool, q_pool], list(wits), 1, 2, 2, 2, 3)
+    want = keygen.rsa_key_from_pools(p_pool, wits[0], q_pool, wits[1], 3)
+    assert st == [0] and want["p"] == 2 and want["dp"] == 0
+    for part in ("N", "d", "p", "q", "dp", "dq", "qinv"):
+        assert got[0][part] == want[part], part
+
+
 def test_keygen_2048_bit_primes(mr, ctx):
     """The largest size: 2048-bit primes (4096-bit N), one key."""
     _check(mr, ctx, n_keys=1, pool=1536, bits=2048, rounds=3, e=65537, seed=0x4B4A)
