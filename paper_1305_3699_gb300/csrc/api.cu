@@ -1317,10 +1317,11 @@ mr_status mr_prime_test_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limb
                               uint32_t rounds, uint32_t n_primes, uint8_t* dev_verdict, uint32_t* dev_survivors,
                               void* stream) {
   if (!ctx) return MR_ERR_ARG;
-  if (n == 0) return dev_survivors ? (cudaMemsetAsync(dev_survivors, 0, 4, (cudaStream_t)stream) == cudaSuccess
-                                          ? MR_OK
-                                          : cuda_fail(ctx, cudaErrorInvalidValue, "cudaMemsetAsync"))
-                                   : MR_OK;
+  if (n == 0) {  // no candidates: no survivors
+    if (!dev_survivors) return MR_OK;
+    const cudaError_t e = cudaMemsetAsync(dev_survivors, 0, 4, (cudaStream_t)stream);
+    return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "cudaMemsetAsync");
+  }
   if (!cand || !n_limbs || !witness || !rounds || !dev_verdict)
     return fail(ctx, MR_ERR_ARG, "null argument, zero limbs or zero rounds");
   if (n_primes == 0 || n_primes > TRIAL_MAX_PRIMES) return fail(ctx, MR_ERR_ARG, "n_primes must be 1..10000");
