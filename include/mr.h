@@ -363,6 +363,20 @@ typedef struct {
  * exp_bits > 65536), MR_ERR_SIZE, MR_ERR_OOM, MR_ERR_CUDA. */
 mr_status mr_autotune(mr_ctx *ctx, uint32_t class_bits, uint32_t n_items, uint32_t exp_bits, mr_tune_result *res);
 
+/* Tuning state of a size class on this context (class_bits: a class size as
+ * mr_class_for_bits returns it): *variant = its lane mapping (as
+ * mr_set_variant), *window_cap = the window-width cap (0: the default rule),
+ * *tuned = 1 when mr_autotune or mr_set_tuning chose them.  Any pointer may be
+ * NULL.  Errors: MR_ERR_ARG, MR_ERR_SIZE. */
+mr_status mr_get_tuning(mr_ctx *ctx, uint32_t class_bits, uint32_t *variant, uint32_t *window_cap, uint32_t *tuned);
+
+/* Install a tuning state (for instance one saved from mr_autotune on an earlier
+ * context): variant < count of mr_class_variants, window_cap 0 (the default
+ * rule) or up to 6 (8 for the large classes).  The class then counts as tuned
+ * (MR_PLAN_AUTOTUNE leaves it alone).  Results do not depend on it, only speed
+ * does.  Errors: MR_ERR_ARG, MR_ERR_SIZE. */
+mr_status mr_set_tuning(mr_ctx *ctx, uint32_t class_bits, uint32_t variant, uint32_t window_cap);
+
 /* --------------------------------------------------------- instrumentation -- */
 
 /* Per-kernel timing.  While enabled, every batched call records a pair of CUDA

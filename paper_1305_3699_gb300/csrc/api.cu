@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mr.h"
 #include "kernels_api.h"
 #include "noalloc.h"
@@ -106,6 +108,14 @@ struct mr_key {
 };
 
 namespace {
+
+// NVTX range around a public call (shown by Nsight tools; no cost without a tool attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 mr_status fail(mr_ctx* ctx, mr_status code, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -991,6 +1001,7 @@ mr_status mr_class_for_bits(uint32_t bits, uint32_t* class_bits, uint32_t* k) {
 }
 
 mr_status mr_rns_setup(mr_ctx* ctx, const uint32_t* N, uint32_t n_limbs, mr_key** out) {
+  NvtxRange nvtx_("mr_rns_setup");
   if (!ctx || !N || !n_limbs || !out) return fail(ctx, MR_ERR_ARG, "null argument");
   return guarded(ctx, [&]() -> mr_status {
     cudaSetDevice(ctx->device);
@@ -1014,6 +1025,7 @@ mr_status mr_rns_setup(mr_ctx* ctx, const uint32_t* N, uint32_t n_limbs, mr_key*
 mr_status mr_rsa_key_setup(mr_ctx* ctx, const uint32_t* N, uint32_t n_limbs, const uint32_t* e, uint32_t e_limbs,
                            const uint32_t* p, const uint32_t* q, const uint32_t* dp, const uint32_t* dq,
                            const uint32_t* qinv, uint32_t half_limbs, mr_key** out) {
+  NvtxRange nvtx_("mr_rsa_key_setup");
   if (!ctx || !N || !n_limbs || !e || !e_limbs || !out) return fail(ctx, MR_ERR_ARG, "null argument");
   return guarded(ctx, [&]() -> mr_status {
     cudaSetDevice(ctx->device);
@@ -1113,6 +1125,7 @@ static mr_status check_keys(mr_ctx* ctx, const mr_key* const* keys, size_t n) {
 mr_status mr_modexp_batch(mr_ctx* ctx, const mr_key* const* keys, size_t n, const uint32_t* x, uint32_t x_stride,
                           const uint32_t* e, uint32_t e_stride, uint32_t* out, uint32_t out_stride,
                           uint8_t* dev_status, void* stream) {
+  NvtxRange nvtx_("mr_modexp_batch");
   if (!ctx) return MR_ERR_ARG;
   if (n == 0) return MR_OK;
   if (!keys || !x || !e || !out || !x_stride || !e_stride || !out_stride) return fail(ctx, MR_ERR_ARG, "null argument or zero stride");
@@ -1150,6 +1163,7 @@ mr_status mr_modexp_batch(mr_ctx* ctx, const mr_key* const* keys, size_t n, cons
 
 mr_status mr_rsa_encrypt(mr_ctx* ctx, const mr_key* const* keys, size_t n, const uint32_t* m, uint32_t m_stride,
                          uint32_t* c, uint32_t c_stride, uint8_t* dev_status, void* stream) {
+  NvtxRange nvtx_("mr_rsa_encrypt");
   if (!ctx) return MR_ERR_ARG;
   if (n == 0) return MR_OK;
   if (!keys || !m || !c || !m_stride || !c_stride) return fail(ctx, MR_ERR_ARG, "null argument or zero stride");
@@ -1191,6 +1205,7 @@ mr_status mr_rsa_encrypt(mr_ctx* ctx, const mr_key* const* keys, size_t n, const
 
 mr_status mr_rsa_decrypt_crt(mr_ctx* ctx, const mr_key* const* keys, size_t n, const uint32_t* c, uint32_t c_stride,
                              uint32_t* m, uint32_t m_stride, uint8_t* dev_status, void* stream) {
+  NvtxRange nvtx_("mr_rsa_decrypt_crt");
   if (!ctx) return MR_ERR_ARG;
   if (n == 0) return MR_OK;
   if (!keys || !c || !m || !c_stride || !m_stride) return fail(ctx, MR_ERR_ARG, "null argument or zero stride");
@@ -1272,6 +1287,7 @@ mr_status mr_launch(mr_ctx* ctx, ClassEntry* ce, uint32_t v, const uint32_t* can
 mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs, size_t n, const uint32_t* witness,
                                 uint32_t rounds, uint8_t* dev_is_probable_prime, uint32_t* dev_round_mask,
                                 void* stream) {
+  NvtxRange nvtx_("mr_miller_rabin_batch");
   if (!ctx) return MR_ERR_ARG;
   if (n == 0) return MR_OK;
   if (!cand || !n_limbs || !witness || !rounds || !dev_is_probable_prime)
@@ -1316,6 +1332,7 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
 mr_status mr_prime_test_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs, size_t n, const uint32_t* witness,
                               uint32_t rounds, uint32_t n_primes, uint8_t* dev_verdict, uint32_t* dev_survivors,
                               void* stream) {
+  NvtxRange nvtx_("mr_prime_test_batch");
   if (!ctx) return MR_ERR_ARG;
   if (n == 0) {  // no candidates: no survivors
     if (!dev_survivors) return MR_OK;
@@ -1378,6 +1395,7 @@ mr_status mr_prime_test_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limb
 mr_status mr_rsa_keygen_batch(mr_ctx* ctx, uint32_t half_limbs, size_t n_keys, uint32_t pool, const uint32_t* cand,
                               const uint32_t* witness, uint32_t rounds, uint32_t e, uint32_t* out, uint8_t* dev_status,
                               void* stream) {
+  NvtxRange nvtx_("mr_rsa_keygen_batch");
   if (!ctx) return MR_ERR_ARG;
   if (n_keys == 0) return MR_OK;
   if (!cand || !witness || !out || !rounds || !pool) return fail(ctx, MR_ERR_ARG, "null argument, zero pool or rounds");
@@ -1421,6 +1439,7 @@ mr_status mr_rsa_message_blocks(const mr_key* key, size_t len, size_t* n_blocks,
 
 mr_status mr_rsa_encrypt_message(mr_ctx* ctx, const mr_key* key, const uint8_t* msg, size_t len, uint32_t* c,
                                  uint8_t* dev_status, void* stream) {
+  NvtxRange nvtx_("mr_rsa_encrypt_message");
   if (!ctx) return MR_ERR_ARG;
   if (!key || key->ctx != ctx) return fail(ctx, MR_ERR_ARG, "invalid key handle");
   if (len == 0) return MR_OK;
@@ -1450,6 +1469,7 @@ mr_status mr_rsa_encrypt_message(mr_ctx* ctx, const mr_key* key, const uint8_t* 
 
 mr_status mr_rsa_decrypt_message(mr_ctx* ctx, const mr_key* key, const uint32_t* c, size_t n_blocks, uint8_t* msg,
                                  size_t len, uint8_t* dev_status, void* stream) {
+  NvtxRange nvtx_("mr_rsa_decrypt_message");
   if (!ctx) return MR_ERR_ARG;
   if (!key || key->ctx != ctx) return fail(ctx, MR_ERR_ARG, "invalid key handle");
   size_t nb = 0;
@@ -1481,6 +1501,7 @@ mr_status mr_rsa_decrypt_message(mr_ctx* ctx, const mr_key* key, const uint32_t*
 mr_status mr_rsa_mixed(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, size_t n, const uint32_t* in,
                        uint32_t in_stride, uint32_t* out, uint32_t out_stride, uint8_t* dev_status, uint32_t flags,
                        void* stream) {
+  NvtxRange nvtx_("mr_rsa_mixed");
   if (!ctx) return MR_ERR_ARG;
   if (n == 0) return MR_OK;
   if (!keys || !ops || !in || !out || !in_stride || !out_stride) return fail(ctx, MR_ERR_ARG, "null argument or zero stride");
@@ -1548,6 +1569,7 @@ mr_status mr_rsa_mixed(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* op
 mr_status mr_plan_create(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, size_t n, const uint32_t* in,
                          uint32_t in_stride, uint32_t* out, uint32_t out_stride, uint8_t* dev_status, uint32_t flags,
                          mr_plan** out_plan) {
+  NvtxRange nvtx_("mr_plan_create");
   if (!ctx || !out_plan) return MR_ERR_ARG;
   *out_plan = nullptr;
   if (!n || !keys || !ops || !in || !out || !in_stride || !out_stride)
@@ -1619,6 +1641,7 @@ mr_status mr_plan_create(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* 
 }
 
 mr_status mr_plan_launch(mr_plan* plan, void* stream) {
+  NvtxRange nvtx_("mr_plan_launch");
   if (!plan) return MR_ERR_ARG;
   mr_ctx* ctx = plan->ctx;
   return guarded(ctx, [&]() -> mr_status {
@@ -1791,7 +1814,39 @@ mr_status mr_set_variant(mr_ctx* ctx, uint32_t class_bits, uint32_t variant) {
   });
 }
 
+mr_status mr_get_tuning(mr_ctx* ctx, uint32_t class_bits, uint32_t* variant, uint32_t* window_cap, uint32_t* tuned) {
+  if (!ctx) return MR_ERR_ARG;
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    ClassEntry* ce = nullptr;
+    mr_status s = get_class(ctx, class_bits, &ce);
+    if (s) return s;
+    if (variant) *variant = ce->variant;
+    if (window_cap) *window_cap = ce->wcap;
+    if (tuned) *tuned = ce->tuned ? 1u : 0u;
+    return MR_OK;
+  });
+}
+
+mr_status mr_set_tuning(mr_ctx* ctx, uint32_t class_bits, uint32_t variant, uint32_t window_cap) {
+  if (!ctx) return MR_ERR_ARG;
+  return guarded(ctx, [&]() -> mr_status {
+    cudaSetDevice(ctx->device);
+    ClassEntry* ce = nullptr;
+    mr_status s = get_class(ctx, class_bits, &ce);
+    if (s) return s;
+    if (variant >= ce->n_var()) return fail(ctx, MR_ERR_ARG, "no such variant");
+    if (window_cap > (ce->big() ? 8u : 6u)) return fail(ctx, MR_ERR_ARG, "window cap out of range");
+    ce->variant = variant;
+    ce->wcap = window_cap;
+    ce->pinned = true;
+    ce->tuned = true;
+    return MR_OK;
+  });
+}
+
 mr_status mr_autotune(mr_ctx* ctx, uint32_t class_bits, uint32_t n_items, uint32_t exp_bits, mr_tune_result* res) {
+  NvtxRange nvtx_("mr_autotune");
   if (!ctx) return MR_ERR_ARG;
   if (!n_items || !exp_bits || n_items > (1u << 20) || exp_bits > 65536)
     return fail(ctx, MR_ERR_ARG, "n_items and exp_bits must be positive (n_items <= 2^20, exp_bits <= 65536)");

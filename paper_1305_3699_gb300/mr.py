@@ -31,6 +31,7 @@ EXPORTED = [
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
     "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
     "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
+    "mr_get_tuning", "mr_set_tuning",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -83,6 +84,8 @@ def _load() -> ctypes.CDLL:
         "mr_debug_trial_table": (ctypes.c_int, [PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_rsa_keygen_batch": (ctypes.c_int, [P, U32, SZ, U32, P, P, U32, U32, P, P, P]),
         "mr_rsa_message_blocks": (ctypes.c_int, [P, SZ, ctypes.POINTER(SZ), PU32, PU32]),
+        "mr_get_tuning": (ctypes.c_int, [P, U32, PU32, PU32, PU32]),
+        "mr_set_tuning": (ctypes.c_int, [P, U32, U32, U32]),
         "mr_rsa_encrypt_message": (ctypes.c_int, [P, P, P, SZ, P, P, P]),
         "mr_rsa_decrypt_message": (ctypes.c_int, [P, P, P, SZ, P, SZ, P, P]),
         "mr_debug_table": (ctypes.c_int, [P, U32, P, ctypes.c_char_p, PU32, SZ, ctypes.POINTER(SZ)]),
@@ -404,6 +407,35 @@ class Context:
         n, _ = _rows(c)
         self._check(lib.mr_rsa_decrypt_message(self.handle, key.handle, _dev(c), n, _dev(msg), msg.numel(),
                                                _dev(status), _stream(stream)))
+
+    def mr_get_tuning(self, class_bits: int) -> dict:
+        v, w, t = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        self._check(lib.mr_get_tuning(self.handle, class_bits, ctypes.byref(v), ctypes.byref(w), ctypes.byref(t)))
+        return {"variant": v.value, "window_cap": w.value, "tuned": bool(t.value)}
+
+    def mr_set_tuning(self, class_bits: int, variant: int, window_cap: int = 0):
+        self._check(lib.mr_set_tuning(self.handle, class_bits, variant, window_cap))
+
+    def save_tuning(self, path: str, classes: Sequence[int] = (512, 1024, 1536, 2048, 3072, 4096, 8192, 16384)):
+        """Write the tuned classes' (variant, window cap) to a JSON file (an autotune cache)."""
+        import json
+        state = {}
+        for L in classes:
+            t = self.mr_get_tuning(L)
+            if t["tuned"]:
+                state[str(L)] = {"variant": t["variant"], "window_cap": t["window_cap"]}
+        with open(path, "w") as f:
+            json.dump({"mr_tuning": 1, "classes": state}, f, indent=1, sort_keys=True)
+        return state
+
+    def load_tuning(self, path: str) -> dict:
+        """Install the tuning saved by save_tuning."""
+        import json
+        with open(path) as f:
+            d = json.load(f)
+        for L, t in d.get("classes", {}).items():
+            self.mr_set_tuning(int(L), int(t["variant"]), int(t["window_cap"]))
+        return d.get("classes", {})
 
     def mr_debug_mr_setup(self, cand, out, stream=None):
         n, nl = _rows(cand)

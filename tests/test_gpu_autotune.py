@@ -99,3 +99,37 @@ def test_autotune_large_class_then_exact(mr):
             assert got[j] == plain.modexp(xs[j], es[j], N), j
     finally:
         ctx.close()
+
+
+def test_tuning_saved_and_loaded(mr, tmp_path):
+    """An autotune result written to JSON and installed on a new context: the same lane mapping and
+    window cap, the class counts as tuned, and results stay exact."""
+    c1 = mr.Context(0)
+    try:
+        res = c1.mr_autotune(2048, 256, 1024)
+        state = c1.save_tuning(str(tmp_path / "tune.json"))
+        assert state["2048"] == {"variant": res["variant"], "window_cap": res["window"]}
+    finally:
+        c1.close()
+    c2 = mr.Context(0)
+    try:
+        assert not c2.mr_get_tuning(2048)["tuned"]
+        c2.load_tuning(str(tmp_path / "tune.json"))
+        t = c2.mr_get_tuning(2048)
+        assert t == {"variant": res["variant"], "window_cap": res["window"], "tuned": True}
+        with pytest.raises(mr.MRError):
+            c2.mr_set_tuning(2048, 99, 0)
+        keys = load_keys("mix_x256")
+        ks = [k for k in keys if k["bits"] == 2048][:3]
+        hk = [c2.mr_rsa_key_setup(k["N"], k["e"]) for k in ks]
+        r = SplitMix64(81)
+        msgs = [r.below(k["N"]) for k in ks]
+        m = mr.to_tensor(msgs, 64)
+        c = torch.zeros_like(m)
+        c2.mr_rsa_encrypt(hk, m, c)
+        torch.cuda.synchronize()
+        got = mr.from_tensor(c)
+        for i, k in enumerate(ks):
+            assert got[i] == plain.rsa_encrypt(msgs[i], k["e"], k["N"])
+    finally:
+        c2.close()
