@@ -440,6 +440,15 @@ mr_status mr_debug_table(mr_ctx *ctx, uint32_t class_bits, const mr_key *key, co
 mr_status mr_debug_mr_setup(mr_ctx *ctx, const uint32_t *cand, uint32_t n_limbs, size_t n, uint32_t *dev_out,
                             void *stream);
 
+/* The binary Garner block that CRT keys with halves in a large size class carry
+ * (host only, no context): for primes p, q and qinv = q^-1 mod p (n_limbs limbs
+ * each) and the class's limb count W: [P2: W+1 limbs][qr: W][q: W][pinv: 1] with
+ * P2 = p * ceil(2^(32W) / p), qr = qinv * 2^(32(W+1)) mod p, pinv = -p^-1 mod 2^32.
+ * *count receives the word count (3W + 2); out may be NULL to query it.
+ * Errors: MR_ERR_ARG, MR_ERR_EVEN_MODULUS (p even). */
+mr_status mr_debug_crt_bin_host(const uint32_t *p, const uint32_t *q, const uint32_t *qinv, uint32_t n_limbs,
+                                uint32_t W, uint32_t *out, size_t capacity, size_t *count);
+
 /* The trial-division tables of mr_prime_test_batch as built on the host (no
  * context, no device): 131 rows of 10,016 words: rows w < 128 hold
  * 2^(32w) mod p_j for the first 10,000 primes p_j (column j), row 128 the

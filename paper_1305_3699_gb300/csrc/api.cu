@@ -1909,6 +1909,23 @@ mr_status mr_debug_table(mr_ctx* ctx, uint32_t class_bits, const mr_key* key, co
   });
 }
 
+mr_status mr_debug_crt_bin_host(const uint32_t* p, const uint32_t* q, const uint32_t* qinv, uint32_t n_limbs,
+                                uint32_t W, uint32_t* out, size_t capacity, size_t* count) {
+  if (!p || !q || !qinv || !n_limbs || W < n_limbs || W > CRT_BIN_MAX_W) return MR_ERR_ARG;
+  try {
+    const Big bp = big_from(p, n_limbs), bq = big_from(q, n_limbs), bqi = big_from(qinv, n_limbs);
+    if (!bp.bit(0)) return MR_ERR_EVEN_MODULUS;
+    std::vector<uint32_t> blk = build_crt_bin(W, bp, bq, bqi);
+    if (count) *count = blk.size();
+    if (!out) return MR_OK;
+    if (capacity < blk.size()) return MR_ERR_ARG;
+    std::copy(blk.begin(), blk.end(), out);
+    return MR_OK;
+  } catch (...) {
+    return MR_ERR_ARG;
+  }
+}
+
 mr_status mr_debug_trial_table(uint32_t* out, size_t capacity, size_t* count) {
   try {
     if (count) *count = trial_table_words();

@@ -31,7 +31,7 @@ EXPORTED = [
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
     "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
     "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
-    "mr_get_tuning", "mr_set_tuning",
+    "mr_get_tuning", "mr_set_tuning", "mr_debug_crt_bin_host",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -85,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "mr_rsa_keygen_batch": (ctypes.c_int, [P, U32, SZ, U32, P, P, U32, U32, P, P, P]),
         "mr_rsa_message_blocks": (ctypes.c_int, [P, SZ, ctypes.POINTER(SZ), PU32, PU32]),
         "mr_get_tuning": (ctypes.c_int, [P, U32, PU32, PU32, PU32]),
+        "mr_debug_crt_bin_host": (ctypes.c_int, [PU32, PU32, PU32, U32, U32, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_set_tuning": (ctypes.c_int, [P, U32, U32, U32]),
         "mr_rsa_encrypt_message": (ctypes.c_int, [P, P, P, SZ, P, P, P]),
         "mr_rsa_decrypt_message": (ctypes.c_int, [P, P, P, SZ, P, SZ, P, P]),
@@ -193,6 +194,21 @@ def mr_debug_trial_table() -> np.ndarray:
     if rc:
         raise MRError(rc, "trial table")
     return out.reshape(131, -1)
+
+
+def mr_debug_crt_bin_host(p: int, q: int, qinv: int, W: int) -> List[int]:
+    """The binary Garner block of CRT halves p, q in a class of W limbs (see mr.h)."""
+    nl = max(1, (max(p.bit_length(), q.bit_length()) + 31) // 32)
+    a, b, c = _limbs(p, nl), _limbs(q, nl), _limbs(qinv % p, nl)
+    cnt = ctypes.c_size_t()
+    rc = lib.mr_debug_crt_bin_host(_ptr(a), _ptr(b), _ptr(c), nl, W, None, 0, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, "crt block")
+    out = np.zeros(cnt.value, dtype=np.uint32)
+    rc = lib.mr_debug_crt_bin_host(_ptr(a), _ptr(b), _ptr(c), nl, W, _ptr(out), cnt.value, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, "crt block")
+    return [int(v) for v in out]
 
 
 def mr_debug_class_table(class_bits: int, name: str) -> List[int]:

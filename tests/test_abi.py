@@ -90,6 +90,27 @@ def test_trial_table_matches_oracle():
         assert mu == ((1 << 64) - 1) // ps[j], j
 
 
+def test_crt_bin_block_matches_definition():
+    """The binary Garner block of 16384-bit keys (8192-bit halves, W = 256) built by the library's
+    host code: P2 is the least multiple of p not below 2^(32W), qr = qinv 2^(32(W+1)) mod p,
+    q's limbs, pinv p = -1 mod 2^32; also for unbalanced halves."""
+    keys = load_keys("mod16384_x4")[:2]
+    cases = [(k["p"], k["q"], k["qinv"]) for k in keys]
+    r = SplitMix64(0x43)
+    p_small = keys[0]["p"] >> 200 | 1  # an odd number below the class size (the block does not need a prime)
+    cases.append((p_small, keys[0]["q"], r.below(p_small)))
+    W = 256
+    for p, q, qinv in cases:
+        blk = mr.mr_debug_crt_bin_host(p, q, qinv, W)
+        assert len(blk) == 3 * W + 2
+        val = lambda a, b: sum(v << (32 * i) for i, v in enumerate(blk[a:b]))
+        P2 = val(0, W + 1)
+        assert P2 % p == 0 and P2 >= 1 << (32 * W) and P2 - p < 1 << (32 * W)
+        assert val(W + 1, 2 * W + 1) == (qinv * (1 << (32 * (W + 1)))) % p
+        assert val(2 * W + 1, 3 * W + 1) == q
+        assert (blk[3 * W + 1] * p) % (1 << 32) == (1 << 32) - 1
+
+
 def _key_cases():
     r = SplitMix64(1234)
     out = []
