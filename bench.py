@@ -345,9 +345,95 @@ def _oracle_mr_chunk(args):
 
 
 # --------------------------------------------------------------- reference
+def _reference_line(args, workload, value, unit, cores, desc, times, config=None):
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int (Python)", "data": "synthetic",
+            "impl": "reference", "config": dict({"workload": workload, "sample_per_step": desc}, **(config or {})),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _pool_steps(fn, chunks, steps, warmup):
+    """Run fn over chunks on every host core, `warmup + steps` times; per-step seconds of the timed ones."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    times = []
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for s_ in range(warmup + max(1, steps)):
+            t0 = time.perf_counter()
+            pool.map(fn, [chunks[i::cores] for i in range(cores) if chunks[i::cores]])
+            if s_ >= warmup:
+                times.append(time.perf_counter() - t0)
+    return cores, times
+
+
+def run_reference_extra(args):
+    """The oracle on the other workloads' inputs (same seeds as the GPU arm), bounded samples."""
+    from synth import SplitMix64, load_keys
+    if args.workload in ("ragged", "serving"):
+        keys, idx, ops, xs = ragged_workload(0)
+        times, value, cores, desc = [], 0.0, 1, ""
+        for _ in range(max(1, args.steps)):
+            t0 = time.perf_counter()
+            value, cores, desc = oracle_mixed_throughput(keys, idx, ops, xs, seconds=min(10.0, args.cpu_seconds))
+            times.append(time.perf_counter() - t0)
+        return _reference_line(args, "ragged_mix_65536" if args.workload == "ragged" else "serving_poisson_200k",
+                               value, UNIT, cores, desc, times)
+    if args.workload == "rsa1024_enc":
+        from oracle import plain
+        keys = load_keys("rsa1024_x64")
+        r = SplitMix64(0x4D520001)
+        msgs = [r.below(k["N"]) for k in keys]
+        times = []
+        for _ in range(args.warmup + max(1, args.steps)):
+            t0 = time.perf_counter()
+            for m, k in zip(msgs, keys):
+                plain.rsa_encrypt(m, k["e"], k["N"])
+            times.append(time.perf_counter() - t0)
+        times = times[args.warmup:]
+        return _reference_line(args, "rsa1024_encrypt_64", len(msgs) / statistics.mean(times), UNIT, 1,
+                               "the 64 messages, oracle.plain.rsa_encrypt, one process", times)
+    if args.workload == "mr1024":
+        rounds, n = 8, 4096
+        keys = load_keys(KEYSET)
+        primes = [k[h] for k in keys for h in ("p", "q")]
+        r = SplitMix64(0x4D520006)
+        cands = [primes[i % len(primes)] if i % 2 == 0 else (r.randbits(1024) | 1 | (1 << 1023)) for i in range(n)]
+        wit = [[2 + r.below(c - 3) for _ in range(rounds)] for c in cands]
+        sample = [(cands[j], wit[j]) for j in range(min(n, 256))]
+        cores, times = _pool_steps(_oracle_mr_chunk, sample, args.steps, args.warmup)
+        return _reference_line(args, "miller_rabin_1024x4096x8", len(sample) * rounds / statistics.mean(times),
+                               "MR rounds/s", cores, f"first {len(sample)} candidates x {rounds} rounds", times)
+    if args.workload == "primegen1024":
+        rounds, n = 8, 16384
+        r = SplitMix64(0x4D520007)
+        cands = [r.randbits(1024) | 1 | (1 << 1023) for _ in range(n)]
+        wit = [[2 + r.below(c - 3) for _ in range(rounds)] for c in cands]
+        sample = [(cands[j], wit[j]) for j in range(1024)]
+        cores, times = _pool_steps(_oracle_prime_chunk, sample, args.steps, args.warmup)
+        return _reference_line(args, "primegen_1024x16384x8", len(sample) / statistics.mean(times), "candidates/s",
+                               cores, f"first {len(sample)} candidates, prime_test_verdict", times)
+    if args.workload == "keygen2048":
+        n_keys, pool, rounds = 16, 2048, 4
+        r = SplitMix64(0x4D520008)
+        pools = [[r.randbits(1024) | (3 << 1022) | 1 for _ in range(pool)] for _ in range(2 * n_keys)]
+        wits = [[[r.between(2, c - 2) for _ in range(rounds)] for c in pl] for pl in pools]
+        sample = [(pools[2 * k], wits[2 * k], pools[2 * k + 1], wits[2 * k + 1]) for k in range(n_keys)]
+        cores, times = _pool_steps(_oracle_keygen_chunk, sample, args.steps, args.warmup)
+        return _reference_line(args, "keygen_rsa2048_16x2x2048", n_keys / statistics.mean(times), "RSA-2048 keys/s",
+                               cores, f"all {n_keys} keys, rsa_key_from_pools", times)
+    return None
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
+    extra = run_reference_extra(args)
+    if extra is not None:
+        return extra
     if args.workload == "modexp16384":
         keys, idx, xs, es = big_workload(0)
         value, cores, desc, times = oracle_big_throughput(keys, idx, xs, es, steps=args.steps, warmup=args.warmup)
