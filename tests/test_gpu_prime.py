@@ -98,3 +98,20 @@ def test_argument_errors(mr, ctx):
     with pytest.raises(mr.MRError) as e:
         ctx.mr_prime_test_batch(big, big, 1, v[:1])
     assert e.value.code == 4
+
+
+def test_empty_inputs_of_the_key_generation_calls(mr, ctx):
+    """Zero candidates, zero keys and an empty message are no-ops (the survivor count reads 0)."""
+    none = torch.zeros((0, 32), dtype=torch.int32, device="cuda")
+    v = torch.zeros(0, dtype=torch.uint8, device="cuda")
+    surv = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    ctx.mr_prime_test_batch(none, none, 4, v, survivors=surv)
+    out = torch.zeros((0, 9 * 32), dtype=torch.int32, device="cuda")
+    ctx.mr_rsa_keygen_batch(none, none, 4, 0, 16, out)
+    k = load_keys("rsa1024_x64")[0]
+    h = ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"])
+    empty = torch.zeros(0, dtype=torch.uint8, device="cuda")
+    ctx.mr_rsa_encrypt_message(h, empty, none)
+    ctx.mr_rsa_decrypt_message(h, none, empty)
+    torch.cuda.synchronize()
+    assert int(surv.item()) == 0
