@@ -2,7 +2,9 @@
  * mr.h -- C ABI of the GB300 RNS modular-exponentiation library (libmrmod.so).
  *
  * What it computes.  Batched x^e mod N for odd moduli of up to 16384 bits, RSA
- * encryption, RSA decryption through the CRT, and Miller-Rabin rounds.  Numbers
+ * encryption, RSA decryption through the CRT, Miller-Rabin rounds, the
+ * primality test of key generation (trial division, then Miller-Rabin), RSA key
+ * generation from candidate pools, and message-level encryption.  Numbers
  * are held in a Residue Number System (RNS): residues modulo pairwise coprime
  * primes below 2^31, one base B of k primes plus a second base B' of k primes.
  * Multiplication modulo N is the RNS Montgomery
@@ -36,8 +38,9 @@
  * extension's coefficients through device memory, in one cooperative launch;
  * they serve mr_modexp_batch, mr_rsa_encrypt and the halves of mr_rsa_decrypt_crt
  * (16384-bit keys: 8192-bit halves, recombined in binary by one warp per
- * decryption).  Miller-Rabin and mixed batches take at most 4096-bit numbers;
- * larger inputs return MR_ERR_SIZE.
+ * decryption).  Miller-Rabin, the prime test and mixed batches take at most
+ * 4096-bit numbers, key generation primes of at most 2048 bits; larger inputs
+ * return MR_ERR_SIZE.
  */
 #ifndef MR_H
 #define MR_H
