@@ -13,10 +13,12 @@ Contents, each function citing the passage of "Secrets from the GPU"
                     x^e mod N by the oracle's own left-to-right square-and-multiply
                     (Sec. 3.1), RSA encryption / decryption (Sec. 3.3), the CRT
                     (Garner) decryption, modular inverse and Arazi's inversion
-                    formula (Sec. 3.1).
-* ``primality``  -- trial division by the first 10,000 primes (Sec. 4.3) and the
-                    Miller-Rabin test with caller-chosen witnesses (Sec. 3.2).
-* ``keygen``     -- seeded RSA key generation for the synthetic workloads (Sec. 3.3).
+                    formula (Sec. 3.1), message blocks (Sec. 3.3).
+* ``primality``  -- trial division by the first 10,000 primes (Sec. 4.3), the
+                    Miller-Rabin test with caller-chosen witnesses (Sec. 3.2) and the
+                    two composed (prime_test_verdict).
+* ``keygen``     -- seeded RSA key generation for the synthetic workloads, and keys
+                    from given candidate pools (rsa_key_from_pools) (Sec. 3.3).
 * ``rns``        -- a slow, step-by-step model of the RNS Montgomery
                     multiplication with base extension (Sec. 3.1), used to pin the
                     base choice, the precomputed constants and intermediate residues.

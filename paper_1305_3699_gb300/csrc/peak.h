@@ -1,3 +1,4 @@
+// Host interface of the integer-multiply throughput probe (peak.cu) behind mr_imad_peak.
 #pragma once
 #include <cuda_runtime.h>
 
