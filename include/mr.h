@@ -443,6 +443,15 @@ mr_status mr_debug_table(mr_ctx *ctx, uint32_t class_bits, const mr_key *key, co
 mr_status mr_debug_mr_setup(mr_ctx *ctx, const uint32_t *cand, uint32_t n_limbs, size_t n, uint32_t *dev_out,
                             void *stream);
 
+/* The large classes' choice of slice width (host only, no context): for a batch
+ * of n_items exponentiations of class class_bits (8192 or 16384) on a GPU of
+ * `sms` SMs holding ctas_per_sm blocks of every variant per SM, *variant is the
+ * variant with the fewest estimated cooperative waves (waves x the variant's
+ * relative time per group of 32 numbers) and *slots the groups it runs at once.
+ * Errors: MR_ERR_ARG, MR_ERR_SIZE (not a large class, or nothing fits). */
+mr_status mr_debug_big_variant(uint32_t class_bits, size_t n_items, uint32_t sms, uint32_t ctas_per_sm,
+                               uint32_t *variant, uint32_t *slots);
+
 /* The binary Garner block that CRT keys with halves in a large size class carry
  * (host only, no context): for primes p, q and qinv = q^-1 mod p (n_limbs limbs
  * each) and the class's limb count W: [P2: W+1 limbs][qr: W][q: W][pinv: 1] with

@@ -265,16 +265,15 @@ struct ClassBatch {
 // the estimated time is the number of waves times the variant's relative time per group.  A
 // pinned class (mr_set_variant, the tuner) keeps its variant.  Returns false when no variant
 // fits the device.
-bool choose_big_variant(mr_ctx* ctx, const ClassEntry* ce, size_t n_items, uint32_t* v_out, uint32_t* slots) {
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  const uint64_t groups = (n_items + 31) / 32;
+// The policy itself, on given resident CTAs per SM of each variant (pinned < 0: any variant).
+bool pick_big_variant(const ClassKernels* kern, uint64_t groups, int sms, const int* ctas_per_sm, int pinned,
+                      uint32_t* v_out, uint32_t* slots) {
   double best = 1e300;
   bool found = false;
-  for (uint32_t v = 0; v < ce->kern->n_big && v < (uint32_t)MAX_VARIANTS; v++) {
-    if (ce->pinned && v != ce->variant) continue;
-    const BigKernel& bk = ce->kern->big[v];
-    const uint64_t fit = (uint64_t)(bk.occupancy() * sms) / bk.slices;
+  for (uint32_t v = 0; v < kern->n_big && v < (uint32_t)MAX_VARIANTS; v++) {
+    if (pinned >= 0 && v != (uint32_t)pinned) continue;
+    const BigKernel& bk = kern->big[v];
+    const uint64_t fit = (uint64_t)(ctas_per_sm[v] * sms) / bk.slices;
     if (fit == 0) continue;
     const double cost = (double)((groups + fit - 1) / fit) * bk.group_time;
     if (cost < best) {
@@ -285,6 +284,14 @@ bool choose_big_variant(mr_ctx* ctx, const ClassEntry* ce, size_t n_items, uint3
     }
   }
   return found;
+}
+
+bool choose_big_variant(mr_ctx* ctx, const ClassEntry* ce, size_t n_items, uint32_t* v_out, uint32_t* slots) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  int occ[MAX_VARIANTS] = {};
+  for (uint32_t v = 0; v < ce->kern->n_big && v < (uint32_t)MAX_VARIANTS; v++) occ[v] = ce->kern->big[v].occupancy();
+  return pick_big_variant(ce->kern, (n_items + 31) / 32, sms, occ, ce->pinned ? (int)ce->variant : -1, v_out, slots);
 }
 
 // Reserve pinned staging space; waits for the previous upload to finish first.
@@ -1907,6 +1914,16 @@ mr_status mr_debug_table(mr_ctx* ctx, uint32_t class_bits, const mr_key* key, co
     mr_status s = debug_class_table(*c, nm, out, capacity, count);
     return s ? fail(ctx, s, "unknown table or buffer too small") : MR_OK;
   });
+}
+
+mr_status mr_debug_big_variant(uint32_t class_bits, size_t n_items, uint32_t sms, uint32_t ctas_per_sm,
+                               uint32_t* variant, uint32_t* slots) {
+  const ClassKernels* kern = class_kernels(class_bits);
+  if (!kern) return MR_ERR_SIZE;
+  if (!kern->big || !sms || !ctas_per_sm || !n_items || !variant || !slots) return MR_ERR_ARG;
+  int occ[MAX_VARIANTS];
+  for (int v = 0; v < MAX_VARIANTS; v++) occ[v] = (int)ctas_per_sm;
+  return pick_big_variant(kern, (n_items + 31) / 32, (int)sms, occ, -1, variant, slots) ? MR_OK : MR_ERR_SIZE;
 }
 
 mr_status mr_debug_crt_bin_host(const uint32_t* p, const uint32_t* q, const uint32_t* qinv, uint32_t n_limbs,

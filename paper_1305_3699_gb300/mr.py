@@ -31,7 +31,7 @@ EXPORTED = [
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
     "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
     "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
-    "mr_get_tuning", "mr_set_tuning", "mr_debug_crt_bin_host",
+    "mr_get_tuning", "mr_set_tuning", "mr_debug_crt_bin_host", "mr_debug_big_variant",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -85,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "mr_rsa_keygen_batch": (ctypes.c_int, [P, U32, SZ, U32, P, P, U32, U32, P, P, P]),
         "mr_rsa_message_blocks": (ctypes.c_int, [P, SZ, ctypes.POINTER(SZ), PU32, PU32]),
         "mr_get_tuning": (ctypes.c_int, [P, U32, PU32, PU32, PU32]),
+        "mr_debug_big_variant": (ctypes.c_int, [U32, SZ, U32, U32, PU32, PU32]),
         "mr_debug_crt_bin_host": (ctypes.c_int, [PU32, PU32, PU32, U32, U32, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_set_tuning": (ctypes.c_int, [P, U32, U32, U32]),
         "mr_rsa_encrypt_message": (ctypes.c_int, [P, P, P, SZ, P, P, P]),
@@ -194,6 +195,15 @@ def mr_debug_trial_table() -> np.ndarray:
     if rc:
         raise MRError(rc, "trial table")
     return out.reshape(131, -1)
+
+
+def mr_debug_big_variant(class_bits: int, n_items: int, sms: int = 152, ctas_per_sm: int = 1):
+    """(variant, slots) the large-class launch picks for n_items numbers (see mr.h)."""
+    v, sl = ctypes.c_uint32(), ctypes.c_uint32()
+    rc = lib.mr_debug_big_variant(class_bits, n_items, sms, ctas_per_sm, ctypes.byref(v), ctypes.byref(sl))
+    if rc:
+        raise MRError(rc, "big variant")
+    return v.value, sl.value
 
 
 def mr_debug_crt_bin_host(p: int, q: int, qinv: int, W: int) -> List[int]:

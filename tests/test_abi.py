@@ -90,6 +90,22 @@ def test_trial_table_matches_oracle():
         assert mu == ((1 << 64) - 1) // ps[j], j
 
 
+def test_large_class_wave_policy():
+    """The slice width a large-class launch picks on 152 SMs with one block per SM: the 8192-bit
+    class fits 15 groups per wave at 32 channels per block and 21 at 48 (1.33x the time per group):
+    8 and 15 groups stay on the narrow slices, 16-21 groups take one wide wave, 30 groups two
+    narrow waves, 42 groups two wide waves (2.66 against 3); the 16384-bit class has one width
+    (8 groups per wave)."""
+    cases = {256: (0, 8), 480: (0, 15), 512: (1, 16), 672: (1, 21), 960: (0, 15), 1344: (1, 21)}
+    for n, want in cases.items():
+        assert mr.mr_debug_big_variant(8192, n) == want, n
+    assert mr.mr_debug_big_variant(16384, 256) == (0, 8)
+    assert mr.mr_debug_big_variant(16384, 1000) == (0, 8)
+    with pytest.raises(mr.MRError) as e:
+        mr.mr_debug_big_variant(1024, 100)
+    assert e.value.code == 1  # not a large class
+
+
 def test_crt_bin_block_matches_definition():
     """The binary Garner block of 16384-bit keys (8192-bit halves, W = 256) built by the library's
     host code: P2 is the least multiple of p not below 2^(32W), qr = qinv 2^(32(W+1)) mod p,
