@@ -316,8 +316,11 @@ mr_status mr_rsa_keygen_batch(mr_ctx *ctx, uint32_t half_limbs, size_t n_keys, u
  *   key     modulus of at most 2048 bits (else MR_ERR_SIZE)
  *   x, e, out, dev_status   as mr_modexp_batch (device rows), n items
  * A batch whose window tables exceed the 16 MiB array is refused with
- * MR_ERR_SIZE (about 1,700 items of a 1024-bit modulus with a long exponent);
- * split it.  The first call on a device looks up the array's device address;
+ * MR_ERR_SIZE, and the message gives the largest batch that fits (1,792 items
+ * of a 1024-bit modulus with a 32-limb exponent stride); split it.  The window
+ * width follows from 32 * e_stride, not from the exponents' values (they are
+ * in device memory): pass short exponents with the smallest stride that holds
+ * them (one limb for e = 65537), which keeps both the tables and the work small.  The first call on a device looks up the array's device address;
  * make that first call before any stream capture.  All calls share the array
  * (it keeps the previous call's contents, which no call reads before writing),
  * so calls that overlap on the GPU -- on different streams, or from different
@@ -402,11 +405,36 @@ mr_status mr_profile_read(mr_ctx *ctx, mr_kernel_time *times, uint32_t n_kinds);
  * 32x32 multiply-adds in every lane of every SM, timed with CUDA events on
  * `stream` (NULL = the default stream).  kind 0: mad.wide.u32 (64-bit product
  * added to a 64-bit accumulator, the instruction of the channel products and
- * base-extension dot products); kind 1: mad.lo.u32.  *per_second receives
- * instructions per second summed over all lanes.  Takes a few milliseconds of
- * device time; allocates 8 bytes of device memory for the duration.
- * Errors: MR_ERR_ARG (kind > 1, NULL pointer), MR_ERR_CUDA. */
+ * base-extension dot products); kind 1: mad.lo.u32; kind 2: the same 64-bit
+ * accumulation as a carry pair, mad.lo.cc.u32 + madc.hi.u32 (rate in products,
+ * two instructions each); kind 3: mad.hi.u32.  *per_second receives
+ * instructions (kind 2: products) per second summed over all lanes.  Takes a
+ * few milliseconds of device time; allocates 8 bytes of device memory for the
+ * duration.  Errors: MR_ERR_ARG (kind > 3, NULL pointer), MR_ERR_CUDA. */
 mr_status mr_imad_peak(mr_ctx *ctx, uint32_t kind, void *stream, double *per_second);
+
+/* Measured tensor-core throughput of this GPU (Sec. 3.1: the base extensions
+ * are products with constant matrices, the one dense contraction of the path),
+ * in operations (2 per multiply-add) per second over all SMs, timed with CUDA
+ * events on `stream`.  kind 0: tcgen05.mma kind::f16 (fp16 operands in shared
+ * memory, fp32 accumulator in tensor memory, M = 128, N = 256, K = 16, one CTA
+ * per SM); kind 1: mma.sync m16n8k32 s8 -> s32 (the integer tensor path that
+ * sm_103a offers: tcgen05 has no kind::i8 there); kind 2: mma.sync m16n8k16
+ * f16 -> f32.  Allocates 64 bytes of device memory for the duration.  Errors:
+ * MR_ERR_ARG, MR_ERR_TIMEOUT (a bounded completion wait ran out; the tensor
+ * memory was released), MR_ERR_CUDA. */
+mr_status mr_tensor_peak(mr_ctx *ctx, uint32_t kind, void *stream, double *ops_per_second);
+
+/* Test hook of the tensor-core operand layout: one CTA computes the exact fp32
+ * product D = A * B^T with tcgen05 (A: 128 x kdim fp16, B: n x kdim fp16, both
+ * row-major host arrays; D: 128 x n fp32 host array, row-major), staging both
+ * operands in the K-major shared-memory layout of the tensor-core extension.
+ * swap_strides = 1 exchanges the descriptor's two byte offsets (diagnosis
+ * only; kdim must then be 16).  16 <= n <= 128 and 16 <= kdim <= 64, both
+ * multiples of 16.
+ * Synchronises `stream`.  Errors: MR_ERR_ARG, MR_ERR_TIMEOUT, MR_ERR_CUDA. */
+mr_status mr_debug_tc_mma(mr_ctx *ctx, const uint16_t *a, const uint16_t *b, uint32_t n, uint32_t kdim,
+                          uint32_t swap_strides, float *d, void *stream);
 
 /* Test hook of the large classes' bounded waits.  Later 8192/16384-bit calls on
  * this context give up a wait between thread blocks after spin_limit polls

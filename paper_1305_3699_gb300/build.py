@@ -19,7 +19,7 @@ LIB = os.path.join(LIB_DIR, "libmrmod.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["api.cu", "registry.cu", "kern_512.cu", "kern_1024.cu", "kern_1536.cu", "kern_2048.cu",
-                "kern_3072.cu", "kern_4096.cu", "noalloc.cu", "peak.cu", "kern_8192.cu", "kern_16384.cu",
+                "kern_3072.cu", "kern_4096.cu", "noalloc.cu", "peak.cu", "tc_peak.cu", "kern_8192.cu", "kern_16384.cu",
                 "crt_bin.cu", "trial.cu", "keygen.cu", "message.cu"]
 CXX_SOURCES = ["setup.cpp"]
 

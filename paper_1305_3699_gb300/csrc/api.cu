@@ -1761,10 +1761,31 @@ mr_status mr_profile_read(mr_ctx* ctx, mr_kernel_time* times, uint32_t n_kinds) 
 }
 
 mr_status mr_imad_peak(mr_ctx* ctx, uint32_t kind, void* stream, double* per_second) {
-  if (!ctx || !per_second || kind > 1) return fail(ctx, MR_ERR_ARG, "bad arguments");
+  if (!ctx || !per_second || kind > 3) return fail(ctx, MR_ERR_ARG, "bad arguments");
   cudaSetDevice(ctx->device);
-  cudaError_t e = mr::imad_stream_rate(ctx->device, (cudaStream_t)stream, kind == 0, per_second);
+  cudaError_t e = mr::imad_stream_rate(ctx->device, (cudaStream_t)stream, (int)kind, per_second);
   return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "integer-multiply probe");
+}
+
+mr_status mr_tensor_peak(mr_ctx* ctx, uint32_t kind, void* stream, double* ops_per_second) {
+  if (!ctx || !ops_per_second || kind > 2) return fail(ctx, MR_ERR_ARG, "bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = mr::tensor_rate(ctx->device, (cudaStream_t)stream, (int)kind, ops_per_second);
+  if (e == cudaErrorLaunchTimeout) return fail(ctx, MR_ERR_TIMEOUT, "tensor probe: completion wait ran out");
+  return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "tensor probe");
+}
+
+mr_status mr_debug_tc_mma(mr_ctx* ctx, const uint16_t* a, const uint16_t* b, uint32_t n, uint32_t kdim,
+                          uint32_t swap_strides, float* d, void* stream) {
+  // with exchanged offsets the tensor core reads up to 16 x 16 * rows bytes past each operand's start:
+  // inside the 32 KB operand regions only for a single K step
+  if (!ctx || !a || !b || !d || n < 16 || n > 128 || n % 16 || kdim < 16 || kdim > 64 || kdim % 16 ||
+      (swap_strides && kdim != 16))
+    return fail(ctx, MR_ERR_ARG, "bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = mr::tensor_debug_mma(a, b, n, kdim, swap_strides, d, (cudaStream_t)stream);
+  if (e == cudaErrorLaunchTimeout) return fail(ctx, MR_ERR_TIMEOUT, "tensor product: completion wait ran out");
+  return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "tensor product");
 }
 
 mr_status mr_debug_big_wait(mr_ctx* ctx, uint32_t spin_limit, int32_t absent_slice) {

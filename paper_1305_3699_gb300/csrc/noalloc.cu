@@ -19,6 +19,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "kernels.cuh"
 #include "noalloc.h"
@@ -134,6 +135,7 @@ namespace {
 
 std::mutex g_mu;
 std::map<int, uint32_t*> g_scratch_addr;  // device ordinal -> device address of g_noalloc_scratch
+std::map<std::pair<int, int>, bool> g_smem_set;  // (device, channels per base) -> shared-memory limit raised
 
 // Device address of the static scratch array on the current device (looked up once per device).
 cudaError_t scratch_address(int device, uint32_t** out) {
@@ -151,14 +153,29 @@ cudaError_t scratch_address(int device, uint32_t** out) {
   return cudaSuccess;
 }
 
+// Raise the kernel's dynamic shared-memory limit on the current device (a per-device setting: done
+// once per device and class; a failure is not remembered, the next call tries again).
+template <class C>
+cudaError_t prepare_packed(int device) {
+  std::lock_guard<std::mutex> g(g_mu);
+  const auto key = std::make_pair(device, C::K);
+  if (g_smem_set.count(key)) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(modexp_packed_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       C::SMEM_BYTES);
+  if (e == cudaSuccess) g_smem_set[key] = true;
+  return e;
+}
+
 template <class C>
 int launch_packed(const NoallocCall& c, std::string& err) {
-  size_t grid = (c.n + C::IPB - 1) / C::IPB;
-  size_t bytes = grid * (C::THREADS / 32) * ((size_t)1 << c.wbits) * 2 * C::NPT * 32 * 4;
-  if (bytes > NOALLOC_SCRATCH_BYTES) {
-    err = "batch needs " + std::to_string(bytes) + " bytes of window tables; the allocation-free entry point has " +
-          std::to_string(NOALLOC_SCRATCH_BYTES) + " (at most " +
-          std::to_string(NOALLOC_SCRATCH_BYTES / (bytes / c.n + 1)) + " items of this size): split the batch";
+  // window tables: one per warp of the grid, 2^w entries of 2 NPT words per lane
+  const size_t per_block = (size_t)(C::THREADS / 32) * ((size_t)1 << c.wbits) * 2 * C::NPT * 32 * 4;
+  const size_t grid = (c.n + C::IPB - 1) / C::IPB;
+  if (grid * per_block > NOALLOC_SCRATCH_BYTES) {
+    const size_t max_items = NOALLOC_SCRATCH_BYTES / per_block * C::IPB;
+    err = "batch needs " + std::to_string(grid * per_block) +
+          " bytes of window tables; the allocation-free entry point has " + std::to_string(NOALLOC_SCRATCH_BYTES) +
+          " (at most " + std::to_string(max_items) + " items of this modulus size and exponent stride): split the batch";
     return 4;  // MR_ERR_SIZE
   }
   uint32_t* scratch = nullptr;
@@ -167,10 +184,8 @@ int launch_packed(const NoallocCall& c, std::string& err) {
     err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
     return 7;  // MR_ERR_CUDA
   }
-  static const cudaError_t attr = cudaFuncSetAttribute(modexp_packed_kernel<C>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
-  if (attr != cudaSuccess) {
-    err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(attr);
+  if ((e = prepare_packed<C>(c.device)) != cudaSuccess) {
+    err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
     return 7;
   }
   PackedArgs a{c.cls, c.key, c.x, c.e, c.out, c.status, scratch, c.n, c.x_stride, c.e_stride, c.out_stride, c.wbits};

@@ -32,6 +32,7 @@ EXPORTED = [
     "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
     "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
     "mr_get_tuning", "mr_set_tuning", "mr_debug_crt_bin_host", "mr_debug_big_variant",
+    "mr_tensor_peak", "mr_debug_tc_mma",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -104,6 +105,8 @@ def _load() -> ctypes.CDLL:
         "mr_plan_free": (None, [P]),
         "mr_profile_read": (ctypes.c_int, [P, ctypes.POINTER(KernelTime), U32]),
         "mr_imad_peak": (ctypes.c_int, [P, U32, P, ctypes.POINTER(ctypes.c_double)]),
+        "mr_tensor_peak": (ctypes.c_int, [P, U32, P, ctypes.POINTER(ctypes.c_double)]),
+        "mr_debug_tc_mma": (ctypes.c_int, [P, P, P, U32, U32, U32, P, P]),
         "mr_autotune": (ctypes.c_int, [P, U32, U32, U32, ctypes.POINTER(TuneResult)]),
         "mr_debug_big_wait": (ctypes.c_int, [P, U32, ctypes.c_int32]),
     }
@@ -491,10 +494,26 @@ class Context:
         self._check(lib.mr_debug_big_wait(self.handle, spin_limit, absent_slice))
 
     def mr_imad_peak(self, kind: int = 0, stream=None) -> float:
-        """Measured multiply-adds per second: kind 0 mad.wide.u32, kind 1 mad.lo.u32."""
+        """Measured multiply-adds per second: kind 0 mad.wide.u32, 1 mad.lo.u32, 2 carry pair, 3 mad.hi.u32."""
         v = ctypes.c_double()
         self._check(lib.mr_imad_peak(self.handle, kind, _stream(stream), ctypes.byref(v)))
         return v.value
+
+    def mr_tensor_peak(self, kind: int = 0, stream=None) -> float:
+        """Measured tensor operations per second: kind 0 tcgen05 kind::f16, 1 mma.sync s8, 2 mma.sync f16."""
+        v = ctypes.c_double()
+        self._check(lib.mr_tensor_peak(self.handle, kind, _stream(stream), ctypes.byref(v)))
+        return v.value
+
+    def mr_debug_tc_mma(self, a: np.ndarray, b: np.ndarray, swap_strides: int = 0, stream=None) -> np.ndarray:
+        """D = A B^T (fp16 in, fp32 out) through one tcgen05 CTA (layout test hook, see mr.h)."""
+        a = np.ascontiguousarray(a, dtype=np.float16)
+        b = np.ascontiguousarray(b, dtype=np.float16)
+        n, kdim = b.shape
+        d = np.zeros((a.shape[0], n), dtype=np.float32)
+        self._check(lib.mr_debug_tc_mma(self.handle, a.ctypes.data, b.ctypes.data, n, kdim, swap_strides,
+                                        d.ctypes.data, _stream(stream)))
+        return d
 
     def mr_debug_table(self, name: str, key: Optional[Key] = None, class_bits: int = 0) -> List[int]:
         cnt = ctypes.c_size_t()

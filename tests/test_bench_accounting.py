@@ -68,3 +68,41 @@ def test_multiplication_counts():
             assert got == pow(x, e, N)
             assert bench.algorithmic_products_per_modexp(k, W, WX, e.bit_length(), w, 2) == \
                 mms * per_mm + 2 * W * 2 * k + k * WX
+
+
+def _primes_below_2_31(count):
+    """The `count` largest primes below 2^31, by trial division (exact for 31-bit numbers)."""
+    out, x = [], (1 << 31) - 1
+    while len(out) < count:
+        if x % 2:
+            d, p = 3, True
+            while d * d <= x:
+                if x % d == 0:
+                    p = False
+                    break
+                d += 2
+            if p:
+                out.append(x)
+        x -= 1
+    return out
+
+
+def test_k31_is_the_closure_bound():
+    """K31[L] is the smallest k with M >= (k+1)^2 2^L and M' >= (k+1) 2^L over the largest primes
+    below 2^31 (B the first k, B' the next k)."""
+    import math
+    primes = _primes_below_2_31(2 * 530 + 2)
+    for L, k in bench.K31.items():
+        def ok(kk):
+            M, Mp = math.prod(primes[:kk]), math.prod(primes[kk:2 * kk])
+            return M >= (kk + 1) ** 2 * 2 ** L and Mp >= (kk + 1) * 2 ** L
+        assert ok(k) and not ok(k - 1), L
+
+
+def test_31bit_count_values():
+    """One RSA-2048 CRT half (1024-bit, |e| = 1024, w = 5): 1263 multiplications of 5304 operations
+    plus 13,320 operations of conversions; one 16384-bit exponentiation with |e| = 16128, w = 8:
+    18,402 multiplications of 1,134,200 operations."""
+    assert bench.ops_31bit_count(1024, 1024, 5) == 1263 * 5304 + 13320
+    assert bench.ops_31bit_count(16384, 16128, 8) == 18402 * 1134200 + 2 * (2 * 512 * 1061 + 2 * 530 * 513)
+    assert bench.tensor_ops_31bit_count(16384, 256, 16128, 8) == 18402 * 2 * 16 * 2 * 256 * 530 * 531

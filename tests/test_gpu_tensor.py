@@ -1,0 +1,68 @@
+"""Tensor-core building blocks of the base extension (Sec. 3.1: the extensions are products with
+constant matrices): the tcgen05 operand layout gives exact products of small integers, and the
+throughput probes report plausible rates."""
+import numpy as np
+import pytest
+
+from synth import SplitMix64
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _ints(r, rows, cols, hi):
+    return np.array([[r.below(hi) for _ in range(cols)] for _ in range(rows)], dtype=np.float64)
+
+
+@pytest.mark.parametrize("n,kdim", [(128, 64), (16, 16), (64, 32), (128, 16)])
+def test_tc_mma_exact_small_integers(n, kdim):
+    """7-bit integers (the slice width of the extension): every partial sum stays below 2^24, so
+    fp32 accumulation is exact and D must equal the integer product A B^T exactly."""
+    _need_gpu()
+    from paper_1305_3699_gb300 import mr
+
+    r = SplitMix64(n * 1000 + kdim)
+    a = _ints(r, 128, kdim, 128)
+    b = _ints(r, n, kdim, 128)
+    with mr.Context(0) as ctx:
+        d = ctx.mr_debug_tc_mma(a, b)
+    want = a @ b.T
+    assert np.array_equal(d.astype(np.float64), want), np.argwhere(d != want)[:8]
+
+
+def test_tc_mma_distinguishes_rows_and_columns():
+    """A one-hot pattern: row i of A and row j of B share exactly one non-zero column, so each
+    output names the pair it came from (a transposed or shifted operand would move the values)."""
+    _need_gpu()
+    from paper_1305_3699_gb300 import mr
+
+    kdim, n = 64, 128
+    a = np.zeros((128, kdim))
+    b = np.zeros((n, kdim))
+    for i in range(128):
+        a[i, i % kdim] = 1 + i // kdim
+    for j in range(n):
+        b[j, (3 * j) % kdim] = 1 + j % 7
+    with mr.Context(0) as ctx:
+        d = ctx.mr_debug_tc_mma(a, b)
+    assert np.array_equal(d.astype(np.float64), a @ b.T)
+
+
+def test_tensor_peaks_plausible():
+    """Every probe completes and reports a rate between 1 TOP/s and 10 POP/s."""
+    _need_gpu()
+    from paper_1305_3699_gb300 import mr
+
+    with mr.Context(0) as ctx:
+        for kind in (0, 1, 2):
+            v = ctx.mr_tensor_peak(kind)
+            assert 1e12 < v < 1e16, (kind, v)
+        for kind in (0, 1, 2, 3):
+            v = ctx.mr_imad_peak(kind)
+            assert 1e11 < v < 1e14, (kind, v)
