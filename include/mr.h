@@ -425,6 +425,18 @@ mr_status mr_imad_peak(mr_ctx *ctx, uint32_t kind, void *stream, double *per_sec
  * memory was released), MR_ERR_CUDA. */
 mr_status mr_tensor_peak(mr_ctx *ctx, uint32_t kind, void *stream, double *ops_per_second);
 
+/* The tensor-core operand table of a size class's base extensions, built on the
+ * host (no device needed): for each channel slice of 32 output channels c and
+ * each extension matrix (T1 = |M/m_i|_{m'_j} 2^64 mod m'_j, then T2 =
+ * |M'/m'_j|_{m_i} 2^64 mod m_i; row = input channel, 4 x 7-bit slices of
+ * every entry), the fp16 values of slice b of column j at row 32 b + j of a
+ * 128-row K-major tile, in chunks of 64 input channels; layout
+ * [slice][matrix][chunk][16 KB].  *count receives the number of 32-bit words
+ * (two fp16 values each, the lower address in the low half); out may be NULL
+ * to query it.  Errors: MR_ERR_SIZE (no such class, or an entry above 28
+ * bits), MR_ERR_ARG (capacity too small). */
+mr_status mr_debug_tc_slices(uint32_t class_bits, uint32_t *out, size_t capacity, size_t *count);
+
 /* Test hook of the tensor-core operand layout: one CTA computes the exact fp32
  * product D = A * B^T with tcgen05 (A: 128 x kdim fp16, B: n x kdim fp16, both
  * row-major host arrays; D: 128 x n fp32 host array, row-major), staging both

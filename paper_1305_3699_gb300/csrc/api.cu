@@ -151,15 +151,20 @@ mr_status get_class(mr_ctx* ctx, uint32_t L, ClassEntry** out) {
     const BigKernel& bk = ce->kern->big[v];
     cudaError_t pe = bk.prepare();
     if (pe != cudaSuccess) return cuda_fail(ctx, pe, "kernel attributes");
-    // [T1 | T2][slice][row][SC]: the columns of each channel slice contiguous, zero past channel k
     const uint32_t k = ce->host.k, sc = bk.sc, sl = bk.slices;
     const ClassOff o = class_offsets(k, ce->host.W, ce->host.WX);
-    std::vector<uint32_t> ts((size_t)2 * sl * k * sc, 0);
-    for (uint32_t m = 0; m < 2; m++)
-      for (uint32_t c = 0; c < sl; c++)
-        for (uint32_t i = 0; i < k; i++)
-          for (uint32_t q = 0; q < sc && c * sc + q < k; q++)
-            ts[(((size_t)m * sl + c) * k + i) * sc + q] = ce->host.block[(m ? o.T2 : o.T1) + (size_t)i * k + c * sc + q];
+    std::vector<uint32_t> ts;
+    if (!bk.tc) {
+      // [T1 | T2][slice][row][SC]: the columns of each channel slice contiguous, zero past channel k
+      ts.assign((size_t)2 * sl * k * sc, 0);
+      for (uint32_t m = 0; m < 2; m++)
+        for (uint32_t c = 0; c < sl; c++)
+          for (uint32_t i = 0; i < k; i++)
+            for (uint32_t q = 0; q < sc && c * sc + q < k; q++)
+              ts[(((size_t)m * sl + c) * k + i) * sc + q] = ce->host.block[(m ? o.T2 : o.T1) + (size_t)i * k + c * sc + q];
+    } else if (!tc_slice_table(ce->host.block.data() + o.T1, ce->host.block.data() + o.T2, k, sc, sl, ts)) {
+      return fail(ctx, MR_ERR_SIZE, "extension matrix entries exceed the 28 bits of four 7-bit slices");
+    }
     cudaError_t e = cudaMalloc(&ce->tslice[v], ts.size() * 4);
     if (e == cudaSuccess) e = cudaMemcpy(ce->tslice[v], ts.data(), ts.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "class slice tables");
@@ -1935,6 +1940,25 @@ mr_status mr_debug_table(mr_ctx* ctx, uint32_t class_bits, const mr_key* key, co
     mr_status s = debug_class_table(*c, nm, out, capacity, count);
     return s ? fail(ctx, s, "unknown table or buffer too small") : MR_OK;
   });
+}
+
+mr_status mr_debug_tc_slices(uint32_t class_bits, uint32_t* out, size_t capacity, size_t* count) {
+  try {
+    std::string err;
+    const ClassHost* c = host_class(class_bits, err);
+    if (!c) return MR_ERR_SIZE;
+    const ClassOff o = class_offsets(c->k, c->W, c->WX);
+    std::vector<uint32_t> ts;
+    if (!tc_slice_table(c->block.data() + o.T1, c->block.data() + o.T2, c->k, 32, (c->k + 31) / 32, ts))
+      return MR_ERR_SIZE;
+    if (count) *count = ts.size();
+    if (!out) return MR_OK;
+    if (capacity < ts.size()) return MR_ERR_ARG;
+    std::copy(ts.begin(), ts.end(), out);
+    return MR_OK;
+  } catch (...) {
+    return MR_ERR_ARG;
+  }
 }
 
 mr_status mr_debug_big_variant(uint32_t class_bits, size_t n_items, uint32_t sms, uint32_t ctas_per_sm,

@@ -27,11 +27,13 @@
 #include "kernels.cuh"
 #include "kernels_api.h"
 #include "rns_device.cuh"
+#include "tc_device.cuh"
 
 namespace mr {
 
 template <int K_, int W_, int WX_, int NPT_, int NW_>
 struct BigCfg {
+  static constexpr bool TC = false;                   // base extensions on the integer pipe
   static constexpr int K = K_, W = W_, WX = WX_, NPT = NPT_, NW = NW_;
   static constexpr int SC = NPT * NW;                 // channels per slice and base
   static constexpr int SLICES = (K + SC - 1) / SC;
@@ -60,6 +62,64 @@ struct BigCfg {
   static_assert(K * 32 <= 2 * K * SC, "RNS -> binary stages all k rows in the matrix area");
 };
 
+// Tensor-core form of the same kernel.  The two base extensions of a slice's CTA are the product
+// D (32 numbers x 32 channels) = X (32 x k) T (k x 32) of the CRT coefficients with its columns of
+// the class's extension matrix, every entry below 2^28 and the exact sum below 2^64.  Both factors
+// are split into four 7-bit slices, X = sum_a 2^(7a) X_a and T = sum_b 2^(7b) T_b, stacked as
+// A = [X_0; X_1; X_2; X_3] (128 x k) and B = [T_0 T_1 T_2 T_3] (k x 128), and multiplied on the
+// tensor cores in fp16 with fp32 accumulation: every entry of A B is a sum of k products below
+// 127^2, exact in fp32 for k <= 1040.  The recombination D = sum_{a,b} 2^(7(a+b)) (A B)[a, b] is
+// exact in 64 bits.  A is written by the slot's CTAs (each its 32 channels, as fp16 slices in the
+// shared-memory operand layout of tc_device.cuh) into a per-slot buffer in global memory; B is a
+// class table in the same layout.  Each CTA streams both through a ring of STAGES shared-memory
+// stages, 64 columns of k per stage, with bulk copies completed on mbarriers; one thread issues the
+// copies and the tcgen05 products (128 x 128 x 16 each) into a 128-column tensor-memory
+// accumulator, the tensor core's completion frees each stage; the epilogue reads the accumulator
+// back (warp w: lanes of slice a = w % 4), combines the slices and hands every thread the same
+// 64-bit dot products the integer form computes.  Everything else is the integer kernel's.
+template <int K_, int W_, int WX_>
+struct BigTcCfg {
+  static constexpr bool TC = true;
+  static constexpr int K = K_, W = W_, WX = WX_, NPT = 4, NW = 8;
+  static constexpr int SC = NPT * NW;                 // 32 channels per slice and base
+  static constexpr int SLICES = (K + SC - 1) / SC;
+  static constexpr int THREADS = NW * 32;
+  static constexpr int KC = 64;                       // columns of k per staged chunk
+  static constexpr int NCH = (K + KC - 1) / KC;       // chunks per extension
+  static constexpr int KP = NCH * KC;                 // padded k
+  static constexpr int STAGES = 4;
+  static constexpr uint32_t CHUNK_BYTES = 128u * KC * 2u;  // one operand chunk: 128 rows x 64 fp16
+  static constexpr uint32_t TMEM_COLS = 128;
+  static constexpr int EX_LS = 17;                    // exchange: 64-bit words per lane (16 + 1 pad)
+  // shared memory (words)
+  static constexpr int SM_RING = 0;                   // STAGES x [A chunk | B chunk]
+  static constexpr int SM_T1 = SM_RING;               // staging area of the RNS -> binary conversion
+  static constexpr int SM_EX = SM_RING + STAGES * 2 * (int)CHUNK_BYTES / 4;  // [4 a][2 halves][32][EX_LS] u64
+  static constexpr int SM_C4A = SM_EX + 4 * 2 * 32 * EX_LS * 2;
+  static constexpr int SM_C4B = SM_C4A + 4 * SC;
+  static constexpr int SM_C2A = SM_C4B + 4 * SC;
+  static constexpr int SM_C2B = SM_C2A + 2 * SC;
+  static constexpr int SM_KAW = SM_C2B + 2 * SC;
+  static constexpr int SM_MISC = SM_KAW + NW * 32;
+  static constexpr int SM_MBAR = SM_MISC + 32;        // full[STAGES], empty[STAGES], done (8 bytes each)
+  static constexpr int SM_TMEM = SM_MBAR + 2 * (2 * STAGES + 1);
+  static constexpr int SM_WORDS = SM_TMEM + 4;
+  static constexpr int SMEM_BYTES = SM_WORDS * 4;
+  // per-slot global scratch (words): the A operands of the two extensions, the plain CRT coefficients
+  // of the exit conversion, slice partials, then the window table
+  static constexpr size_t AOP_WORDS = (size_t)NCH * CHUNK_BYTES / 4;
+  static constexpr size_t AG1 = 0, AG2 = AOP_WORDS, XG = 2 * AOP_WORDS, KAWG = XG + (size_t)K * 32;
+  static constexpr size_t TAB = KAWG + (size_t)SLICES * 32;
+  MR_HD static constexpr size_t slot_words(uint32_t wbits) { return TAB + ((size_t)1 << wbits) * 2 * K * 32; }
+  // class table: [slice][extension][chunk] operand chunks of B
+  static constexpr size_t BTAB_BYTES = (size_t)2 * SLICES * NCH * CHUNK_BYTES;
+  static_assert(K * 32 <= STAGES * 2 * (int)CHUNK_BYTES / 4, "RNS -> binary staging fits the ring");
+  static_assert(SLICES * SC <= KP, "every slice's columns lie inside the padded operand");
+  static_assert((SM_MBAR % 2) == 0 && (SM_C4A % 4) == 0 && (SM_EX % 2) == 0, "alignment");
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+  static_assert(K <= 1040, "7-bit slices: k * 127^2 < 2^24 keeps every fp32 partial sum exact");
+};
+
 template <class C>
 struct BigGroup {
   uint32_t* s;         // shared memory
@@ -69,6 +129,9 @@ struct BigGroup {
   uint32_t nbar;       // barriers passed so far (target = nbar * SLICES)
   uint32_t spin_limit; // polls before a wait gives up
   uint32_t ph;         // parity bits of the two staging mbarriers
+  uint32_t chunk;      // tensor-core form: operand chunks staged so far (ring position and parities)
+  uint32_t done_ph;    // tensor-core form: parity of the accumulator-complete mbarrier
+  const uint8_t* btab; // tensor-core form: this slice's B operand chunks [extension][chunk]
   int c, w, lane;
   __device__ uint4 a4(int q) const { return reinterpret_cast<const uint4*>(s + C::SM_C4A)[q]; }
   __device__ uint4 b4(int q) const { return reinterpret_cast<const uint4*>(s + C::SM_C4B)[q]; }
@@ -188,45 +251,185 @@ __device__ bool big_ext(uint64_t (&acc)[C::NPT], BigGroup<C>& g, const uint32_t*
   return true;
 }
 
+// Tensor-core form: this thread's four CRT coefficients (channels o0 .. o0+3 of number `lane`) as four
+// 7-bit fp16 slices into the A operand `aop` of an extension: row 32a + lane, columns o0 .. o0+3 of
+// slice a (one 8-byte store per slice; o0 is a multiple of 4).
+template <class C>
+__device__ __forceinline__ void tc_put_slices(uint8_t* aop, const uint32_t (&v)[4], int o0, int lane) {
+  uint8_t* chunk = aop + (size_t)(o0 / C::KC) * C::CHUNK_BYTES;
+  const uint32_t col = (uint32_t)(o0 % C::KC);
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    uint32_t h[4];
+#pragma unroll
+    for (int s = 0; s < 4; s++) h[s] = __half_as_ushort(__uint2half_rn((v[s] >> (7 * a)) & 127u));
+    const uint2 pk = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+    *reinterpret_cast<uint2*>(chunk + tc::tile_off(128, 32u * a + lane, col)) = pk;
+  }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) completing on `mbar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+
+// One base extension on the tensor cores (see BigTcCfg): acc[s] = sum_i X[lane][i] T[i][4w + s], exact,
+// from the slot's A operand `aop` (all slices written, the slot barrier passed) and this slice's B
+// operand `bop`.  False (abort raised) when a copy or the tensor core does not complete in time.
+template <class C>
+__device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, const uint8_t* bop) {
+  constexpr int S = C::STAGES, NCH = C::NCH;
+  constexpr uint32_t CB = C::CHUNK_BYTES;
+  uint8_t* const ring = reinterpret_cast<uint8_t*>(g.s + C::SM_RING);
+  uint64_t* const full = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
+  uint64_t* const empty = full + S;
+  uint64_t* const done = empty + S;
+  const uint32_t taddr = g.s[C::SM_TMEM];
+  // earlier generic accesses of the ring (the exit conversion stages through it) before the copies
+  tc::fence_smem_async();
+  __syncthreads();
+  uint32_t ok = 1;
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");  // the slot's A stores, seen through its barrier
+    const uint32_t g0 = g.chunk;
+    auto load = [&](int c) {
+      const uint32_t st = (g0 + c) % S;
+      uint8_t* dst = ring + (size_t)st * 2 * CB;
+      mbar_expect_tx(&full[st], 2 * CB);
+      bulk_g2s(dst, aop + (size_t)c * CB, CB, &full[st]);
+      bulk_g2s(dst + CB, bop + (size_t)c * CB, CB, &full[st]);
+    };
+    for (int c = 0; c < S - 1 && c < NCH; c++) load(c);
+    constexpr uint32_t idesc = tc::idesc_f16_f32(128, 128);
+    for (int c = 0; c < NCH; c++) {
+      const uint32_t gc = g0 + c, st = gc % S;
+      if (!mbar_wait(&full[st], (gc / S) & 1u, g.spin_limit)) {
+        ok = 0;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t a0 = smem_u32(ring + (size_t)st * 2 * CB), b0 = a0 + CB;
+#pragma unroll
+      for (int ks = 0; ks < C::KC / 16; ks++) {
+        // K step: column groups 2ks, 2ks + 1 (leading offset 16 x 128 rows, stride offset 128 bytes)
+        const uint64_t ad = tc::sdesc(a0 + ks * 4096u, 2048u, 128u);
+        const uint64_t bd = tc::sdesc(b0 + ks * 4096u, 2048u, 128u);
+        tc::mma_f16(taddr, ad, bd, idesc, (c | ks) ? 1u : 0u);
+      }
+      tc::mma_commit(&empty[st]);
+      const int cn = c + S - 1;  // refill the stage of chunk c - 1 once its products are done
+      if (cn < NCH) {
+        if (c >= 1 && !mbar_wait(&empty[(gc - 1) % S], ((gc - 1) / S) & 1u, g.spin_limit)) {
+          ok = 0;
+          break;
+        }
+        load(cn);
+      }
+    }
+    tc::mma_commit(done);
+    // on failure, still give the issued products a bounded chance to finish before tensor memory is reused
+    if (!mbar_wait(done, g.done_ph, g.spin_limit)) ok = 0;
+    if (!ok) atomicExch(g.abort, 1u);
+  }
+  g.chunk += NCH;
+  g.done_ph ^= 1u;
+  if (__syncthreads_or(!ok)) return false;
+  tc::fence_after_sync();
+  // epilogue: warp w reads the lanes of slice a = w % 4 (its number = lane), columns of the channels
+  // 16h .. 16h+15 (h = w / 4) of all four matrix slices; combines the matrix slices, then the four
+  // warps of each half combine the data slices through shared memory
+  const int qa = g.w & 3, h = g.w >> 2;
+  uint64_t part[16];
+#pragma unroll
+  for (int j = 0; j < 16; j++) part[j] = 0;
+#pragma unroll
+  for (int b = 0; b < 4; b++) {
+    uint32_t v[16];
+    tc::tmem_ld16(taddr + ((uint32_t)(32 * qa) << 16) + 32u * b + 16u * h, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 16; j++) part[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) << (7 * b);
+  }
+  uint64_t* ex = reinterpret_cast<uint64_t*>(g.s + C::SM_EX);
+#pragma unroll
+  for (int j = 0; j < 16; j++) ex[((qa * 2 + h) * 32 + g.lane) * C::EX_LS + j] = part[j] << (7 * qa);
+  tc::fence_before_sync();
+  __syncthreads();
+  const int jb = 4 * g.w - 16 * h;  // this thread's channels 4w .. 4w+3 within half h
+#pragma unroll
+  for (int s = 0; s < 4; s++) {
+    uint64_t v = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) v += ex[((q * 2 + h) * 32 + g.lane) * C::EX_LS + jb + s];
+    acc[s] = v;
+  }
+  return true;
+}
+
 // RNS Montgomery multiplication x <- x*y*M^-1 mod N (outputs below (k+1)N), this thread's channels.
 template <class C>
 __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], const uint32_t (&yb)[C::NPT],
                              const uint32_t (&yp)[C::NPT], const uint32_t (&kxi)[C::NPT],
                              const uint32_t (&cmul)[C::NPT], const uint32_t (&cd)[C::NPT], BigGroup<C>& g) {
   constexpr int NPT = C::NPT, K = C::K;
-  uint32_t* Xg = g.slot + C::XG;
-  uint32_t* XPg = g.slot + C::XPG;
   uint32_t* KAWg = g.slot + C::KAWG;
   uint32_t sp[NPT];
-  // 1-2. s = x*y in both bases; xi_i = s_i |-N^-1 (M/m_i)^-1| to the exchange buffer
+  uint32_t xv[NPT];
+  // 1-2. s = x*y in both bases; xi_i = s_i |-N^-1 (M/m_i)^-1| to the exchange buffer (zero on padding slots)
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
-    const int q = g.w * NPT + s, o = g.c * C::SC + q;
+    const int q = g.w * NPT + s;
     const uint4 cb = g.a4(q);
     uint32_t sb = redc_lazy(mulw(xb[s], yb[s]), cb.x, cb.y);  // [0, 2m): only multiplied again
-    uint32_t xi = redc(mulw(sb, kxi[s]), cb.x, cb.y);
-    if (o < K) Xg[(size_t)o * 32 + g.lane] = xi;
+    xv[s] = redc(mulw(sb, kxi[s]), cb.x, cb.y);
     const uint4 cp = g.b4(q);
     sp[s] = redc_lazy(mulw(xp[s], yp[s]), cp.x, cp.y);
+  }
+  if constexpr (C::TC) {
+    tc_put_slices<C>(reinterpret_cast<uint8_t*>(g.slot + C::AG1), xv, g.c * C::SC + g.w * NPT, g.lane);
+  } else {
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      const int o = g.c * C::SC + g.w * NPT + s;
+      if (o < K) g.slot[C::XG + (size_t)o * 32 + g.lane] = xv[s];
+    }
   }
   if (!g.barrier()) return false;
   // 3. extension B -> B'
   uint64_t acc[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) acc[s] = 0;
-  if (!big_ext<C>(acc, g, Xg, g.s + C::SM_T1)) return false;
+  if constexpr (C::TC) {
+    if (!tc_ext<C>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG1), g.btab)) return false;
+  } else {
+    if (!big_ext<C>(acc, g, g.slot + C::XG, g.s + C::SM_T1)) return false;
+  }
   // 4-5. new B' residues and xi'_j; partial correction-factor sums
   uint32_t kaw = 0;
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
-    const int q = g.w * NPT + s, o = g.c * C::SC + q;
+    const int q = g.w * NPT + s;
     const uint4 cp = g.b4(q);
     const uint2 c2 = g.b2(q);
     uint32_t qh = redc64_lazy(acc[s], cp.x, cp.y, cp.z);
     xp[s] = redc(madw(sp[s], cp.w, mulw(qh, cmul[s])), cp.x, cp.y);
-    uint32_t xpj = redc(madw(sp[s], c2.x, mulw(qh, cd[s])), cp.x, cp.y);
-    if (o < K) XPg[(size_t)o * 32 + g.lane] = xpj;
-    kaw += hi32(mulw(xpj, c2.y));  // zero on padding slots (ubp = 0)
+    xv[s] = redc(madw(sp[s], c2.x, mulw(qh, cd[s])), cp.x, cp.y);  // xi'_j, zero on padding slots
+    kaw += hi32(mulw(xv[s], c2.y));  // zero on padding slots (ubp = 0)
+  }
+  if constexpr (C::TC) {
+    tc_put_slices<C>(reinterpret_cast<uint8_t*>(g.slot + C::AG2), xv, g.c * C::SC + g.w * NPT, g.lane);
+  } else {
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      const int o = g.c * C::SC + g.w * NPT + s;
+      if (o < K) g.slot[C::XPG + (size_t)o * 32 + g.lane] = xv[s];
+    }
   }
   g.s[C::SM_KAW + g.w * 32 + g.lane] = kaw;
   __syncthreads();
@@ -244,7 +447,12 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
   for (int u = 0; u < C::SLICES; u++) kp[u] = __ldcg(KAWg + u * 32 + g.lane);
 #pragma unroll
   for (int s = 0; s < NPT; s++) acc[s] = 0;
-  if (!big_ext<C>(acc, g, XPg, g.s + C::SM_T2)) return false;
+  if constexpr (C::TC) {
+    if (!tc_ext<C>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG2), g.btab + (size_t)C::NCH * C::CHUNK_BYTES))
+      return false;
+  } else {
+    if (!big_ext<C>(acc, g, g.slot + C::XPG, g.s + C::SM_T2)) return false;
+  }
   uint32_t ks = 0;
 #pragma unroll
   for (int u = 0; u < C::SLICES; u++) ks += kp[u];
@@ -581,20 +789,50 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
   g.nbar = 0;
   g.spin_limit = a.spin_limit;
   g.ph = 0;
+  g.chunk = 0;
+  g.done_ph = 0;
+  g.btab = nullptr;
   if (g.c == a.absent_slice) return;  // test hook: this slice never arrives; the others time out
   if (threadIdx.x == 0) {
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem_raw + C::SM_MBAR);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mb[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mb[1])));
+    int nmb = 2;  // staging copies of the integer form
+    if constexpr (C::TC) nmb = 2 * C::STAGES + 1;  // full and empty per stage, accumulator complete
+    for (int i = 0; i < nmb; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mb[i])));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if constexpr (C::TC) {
+    g.btab = reinterpret_cast<const uint8_t*>(a.tslice) + (size_t)g.c * 2 * C::NCH * C::CHUNK_BYTES;
+    if (threadIdx.x < 32) {
+      tc::tmem_alloc(smem_raw + C::SM_TMEM, C::TMEM_COLS);
+      tc::tmem_relinquish();
+    }
+    // columns of k beyond the last slice are never written: zero them once in both A operands
+    if (g.c == 0 && C::KP > C::SLICES * C::SC) {
+      constexpr uint32_t tail_col = C::SLICES * C::SC % C::KC;  // first padding column in the last chunk
+      constexpr uint32_t tail_off = tail_col / 8 * 16 * 128, tail_bytes = C::CHUNK_BYTES - tail_off;
+      for (int e = 0; e < 2; e++) {
+        uint4* t = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(g.slot + (e ? C::AG2 : C::AG1)) +
+                                            (size_t)(C::NCH - 1) * C::CHUNK_BYTES + tail_off);
+        for (uint32_t i = threadIdx.x; i < tail_bytes / 16; i += C::THREADS) t[i] = make_uint4(0, 0, 0, 0);
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
   }
   big_load_consts<C>(smem_raw, a.cls, g.c);
   const uint32_t n_groups = (a.n_items + 31) / 32;
   uint32_t grp = slot_id;
   for (; grp < n_groups; grp += a.slots) {
-    big_load_smem<C>(smem_raw, a.cls, a.tslice, g.c);
+    if constexpr (!C::TC) big_load_smem<C>(smem_raw, a.cls, a.tslice, g.c);
     __syncthreads();
     if (!big_modexp_group<C>(a, g, grp)) break;
+  }
+  if constexpr (C::TC) {
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x < 32) tc::tmem_dealloc(smem_raw[C::SM_TMEM], C::TMEM_COLS);
   }
   if (grp < n_groups && g.c == (a.absent_slice == 0 ? 1 : 0) && a.status) {
     // aborted: every unfinished item of this slot reports a timeout

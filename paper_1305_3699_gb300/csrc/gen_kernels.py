@@ -26,13 +26,14 @@ CLASSES = {
 
 
 # Large classes: several CTAs per group of 32 numbers (big_kernel.cuh).
-# L: (k, W, WX, NPT, [(NW, group time relative to variant 0), ...]).  NW warps per CTA give channel
-# slices of 4 NW channels: wider slices need fewer CTAs per group, so more groups fit one wave, at a
-# longer time per group (more warps per SM sub-partition).  The relative group times were measured
-# with both variants in one wave on GB300.
+# L: (k, W, WX, NPT, [(NW, group time relative to variant 0, tensor), ...]).  NW warps per CTA give
+# channel slices of 4 NW channels: wider slices need fewer CTAs per group, so more groups fit one
+# wave, at a longer time per group (more warps per SM sub-partition).  tensor = 1: the base
+# extensions run on the tensor cores (BigTcCfg: 8 warps, 32-channel slices).  The relative group
+# times were measured with the variants in one wave on GB300.
 BIG = {
-    8192: (295, 256, 258, 4, [(8, 1.0), (12, 1.33)]),
-    16384: (599, 512, 513, 4, [(8, 1.0)]),
+    8192: (295, 256, 258, 4, [(8, 1.0, 0), (12, 1.33, 0)]),
+    16384: (599, 512, 513, 4, [(8, 1.0, 0), (8, 0.434, 1)]),
 }
 
 
@@ -40,10 +41,11 @@ def big_unit(L, k, W, WX, npt, variants):
     out = [f"// Kernel of the {L}-bit size class (k = {k} channels per base). Generated by gen_kernels.py.",
            '#include "big_kernel.cuh"', '#include "kernels_api.h"', "", "namespace mr {", ""]
     entries = []
-    for v, (nw, rel) in enumerate(variants):
+    for v, (nw, rel, tc) in enumerate(variants):
         C = f"CB{L}v{v}"
+        cfg = f"BigTcCfg<{k}, {W}, {WX}>" if tc else f"BigCfg<{k}, {W}, {WX}, {npt}, {nw}>"
         out += [
-            f"using {C} = BigCfg<{k}, {W}, {WX}, {npt}, {nw}>;",
+            f"using {C} = {cfg};",
             f"static size_t slot_words_{L}_{v}(uint32_t wbits) {{ return {C}::slot_words(wbits); }}", "",
             f"static cudaError_t launch_big_{L}_{v}(const BigArgs& a, cudaStream_t s) {{",
             "  void* args[] = {const_cast<BigArgs*>(&a)};",
@@ -56,7 +58,7 @@ def big_unit(L, k, W, WX, npt, variants):
             "  int n = 0;",
             f"  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, big_modexp_kernel<{C}>, {C}::THREADS, {C}::SMEM_BYTES) != cudaSuccess) n = 0;",
             "  return n;", "}", ""]
-        entries.append(f"    {{{C}::SC, {C}::SLICES, {C}::THREADS, {C}::SMEM_BYTES, {rel:.3f}f, slot_words_{L}_{v}, "
+        entries.append(f"    {{{C}::SC, {C}::SLICES, {C}::THREADS, {C}::SMEM_BYTES, {tc}, {rel:.3f}f, slot_words_{L}_{v}, "
                        f"launch_big_{L}_{v}, prepare_big_{L}_{v}, occupancy_big_{L}_{v}}}")
     out.append(f"static const BigKernel kBig{L}[{len(variants)}] = {{")
     out.append(",\n".join(entries) + "};")

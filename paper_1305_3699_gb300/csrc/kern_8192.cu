@@ -43,8 +43,8 @@ static int occupancy_big_8192_1() {
 }
 
 static const BigKernel kBig8192[2] = {
-    {CB8192v0::SC, CB8192v0::SLICES, CB8192v0::THREADS, CB8192v0::SMEM_BYTES, 1.000f, slot_words_8192_0, launch_big_8192_0, prepare_big_8192_0, occupancy_big_8192_0},
-    {CB8192v1::SC, CB8192v1::SLICES, CB8192v1::THREADS, CB8192v1::SMEM_BYTES, 1.330f, slot_words_8192_1, launch_big_8192_1, prepare_big_8192_1, occupancy_big_8192_1}};
+    {CB8192v0::SC, CB8192v0::SLICES, CB8192v0::THREADS, CB8192v0::SMEM_BYTES, 0, 1.000f, slot_words_8192_0, launch_big_8192_0, prepare_big_8192_0, occupancy_big_8192_0},
+    {CB8192v1::SC, CB8192v1::SLICES, CB8192v1::THREADS, CB8192v1::SMEM_BYTES, 0, 1.330f, slot_words_8192_1, launch_big_8192_1, prepare_big_8192_1, occupancy_big_8192_1}};
 extern const ClassKernels kClass8192 = {8192, 295, 256, 258, 0, {}, kBig8192, 2};
 
 }  // namespace mr

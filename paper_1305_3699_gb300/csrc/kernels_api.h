@@ -41,7 +41,8 @@ constexpr uint32_t BIG_SPIN_POLLS = 1u << 22;
 // Exponentiation of a large size class (several CTAs per item group, cooperative launch).
 struct BigArgs {
   const uint32_t* cls;     // class table block (device)
-  const uint32_t* tslice;  // extension matrices by channel slice: [T1 | T2][slice][k][SC]
+  const uint32_t* tslice;  // extension matrices by channel slice: [T1 | T2][slice][k][SC] (u32), or for a
+                           // tensor-core variant the fp16 slice operands [T1 | T2][slice][chunk] (big_kernel.cuh)
   const MxItem* items;
   uint32_t n_items;
   uint32_t wbits;          // window width, 1..8
@@ -71,6 +72,7 @@ constexpr int MAX_VARIANTS = 4;
 // Kernel of a large size class: one cooperative launch of slots * slices CTAs.
 struct BigKernel {
   uint32_t sc, slices, threads, smem_bytes;
+  uint32_t tc;       // 1: base extensions on the tensor cores (slice table in fp16, big_kernel.cuh)
   float group_time;  // time of one item group relative to variant 0 when both fit one wave (measured)
   size_t (*slot_words)(uint32_t wbits);
   cudaError_t (*modexp)(const BigArgs&, cudaStream_t);

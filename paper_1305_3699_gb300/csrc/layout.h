@@ -39,6 +39,15 @@ struct ClassOff {
   uint32_t m, mi, r32, ahat, ad, ubp, mphh, mmiinv, ub, T1, T2, P, MD, ML, total;
 };
 
+// Tensor-core operand layout in shared memory (K-major, no swizzling; tc_device.cuh): byte offset
+// of element (r, k) of an R-row tile of fp16 values.  The unit is the core matrix of 8 rows x 16
+// bytes (8 values of k), stored row after row; core matrix (r / 8, k / 8) sits at
+// (k / 8) * (R / 8) * 128 + (r / 8) * 128.  The large classes' tensor-core slice table is built on the
+// host in this layout.
+MR_HD constexpr inline uint32_t tc_tile_off(uint32_t R, uint32_t r, uint32_t k) {
+  return (k >> 3) * (R >> 3) * 128u + (r >> 3) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
+}
+
 MR_HD constexpr inline ClassOff class_offsets(uint32_t k, uint32_t W, uint32_t WX) {
   ClassOff o{};
   o.m = 0;

@@ -308,4 +308,35 @@ std::vector<uint32_t> build_crt_bin(uint32_t W, const Big& p, const Big& q, cons
   return blk;
 }
 
+uint16_t half_bits(uint32_t v) {
+  if (v == 0) return 0;
+  uint32_t e = 0;
+  while ((v >> (e + 1)) != 0) e++;  // v in [2^e, 2^(e+1))
+  const uint32_t mant = (v << (10 - e)) & 0x3FFu;
+  return (uint16_t)(((e + 15u) << 10) | mant);
+}
+
+bool tc_slice_table(const uint32_t* T1, const uint32_t* T2, uint32_t k, uint32_t sc, uint32_t slices,
+                    std::vector<uint32_t>& out) {
+  if (sc != 32) return false;
+  const uint32_t KC = 64, nch = (k + KC - 1) / KC, chunk_bytes = 128u * KC * 2u;
+  std::vector<uint16_t> h((size_t)slices * 2 * nch * chunk_bytes / 2, 0);
+  for (uint32_t c = 0; c < slices; c++)
+    for (uint32_t e = 0; e < 2; e++) {
+      const uint32_t* T = e ? T2 : T1;
+      for (uint32_t i = 0; i < k; i++)
+        for (uint32_t j = 0; j < sc && c * sc + j < k; j++) {
+          const uint32_t t = T[(size_t)i * k + c * sc + j];
+          if (t >> 28) return false;
+          for (uint32_t b = 0; b < 4; b++) {
+            const size_t byte = (((size_t)c * 2 + e) * nch + i / KC) * chunk_bytes + tc_tile_off(128, 32 * b + j, i % KC);
+            h[byte / 2] = half_bits((t >> (7 * b)) & 127u);
+          }
+        }
+    }
+  out.assign(h.size() / 2, 0);
+  for (size_t w = 0; w < out.size(); w++) out[w] = (uint32_t)h[2 * w] | ((uint32_t)h[2 * w + 1] << 16);
+  return true;
+}
+
 }  // namespace mr

@@ -54,6 +54,19 @@ std::vector<uint32_t> build_crt(const ClassHost& c, const Big& p, const Big& q, 
 // p must be odd.
 std::vector<uint32_t> build_crt_bin(uint32_t W, const Big& p, const Big& q, const Big& qinv);
 
+// Operands B of the tensor-core base extensions of a large class (big_kernel.cuh, BigTcCfg): for
+// each channel slice of sc = 32 columns and each extension matrix T (T1, then T2; k x k, row i =
+// input channel, column j = output channel, entries below 2^28), the four 7-bit slices of the
+// slice's columns as fp16 values, row 32 b + j of slice b, in chunks of 64 values of i in the
+// tensor-core tile layout (tc_tile_off, 128 rows), zero past channel k.  Layout
+// [slice][extension][chunk]; `out` receives the bytes as 32-bit words.  False when an entry needs
+// more than 28 bits.
+bool tc_slice_table(const uint32_t* T1, const uint32_t* T2, uint32_t k, uint32_t sc, uint32_t slices,
+                    std::vector<uint32_t>& out);
+
+// fp16 bit pattern of an integer 0 <= v < 2048 (exact).
+uint16_t half_bits(uint32_t v);
+
 // Residues of X in all 2k channels (plain).
 std::vector<uint32_t> residues(const ClassHost& c, const Big& X);
 

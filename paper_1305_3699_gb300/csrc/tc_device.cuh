@@ -15,7 +15,11 @@
 // (between row groups) 128 bytes.  tile_off() gives the byte offset of one
 // element.
 #pragma once
+#include <cuda_fp16.h>
+
 #include <cstdint>
+
+#include "layout.h"
 
 namespace mr {
 namespace tc {
@@ -23,9 +27,7 @@ namespace tc {
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Byte offset of element (r, k) of an R-row K-major tile (layout above).
-__host__ __device__ constexpr uint32_t tile_off(uint32_t R, uint32_t r, uint32_t k) {
-  return (k >> 3) * (R >> 3) * 128u + (r >> 3) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
-}
+__host__ __device__ constexpr uint32_t tile_off(uint32_t R, uint32_t r, uint32_t k) { return tc_tile_off(R, r, k); }
 
 // Shared-memory matrix descriptor: start address, leading- and stride-dimension byte offsets
 // (all multiples of 16 bytes), descriptor version 1 (bits 46-47), no swizzling, base offset 0.

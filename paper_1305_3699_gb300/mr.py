@@ -32,7 +32,7 @@ EXPORTED = [
     "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
     "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
     "mr_get_tuning", "mr_set_tuning", "mr_debug_crt_bin_host", "mr_debug_big_variant",
-    "mr_tensor_peak", "mr_debug_tc_mma",
+    "mr_tensor_peak", "mr_debug_tc_mma", "mr_debug_tc_slices",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -107,6 +107,7 @@ def _load() -> ctypes.CDLL:
         "mr_imad_peak": (ctypes.c_int, [P, U32, P, ctypes.POINTER(ctypes.c_double)]),
         "mr_tensor_peak": (ctypes.c_int, [P, U32, P, ctypes.POINTER(ctypes.c_double)]),
         "mr_debug_tc_mma": (ctypes.c_int, [P, P, P, U32, U32, U32, P, P]),
+        "mr_debug_tc_slices": (ctypes.c_int, [U32, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_autotune": (ctypes.c_int, [P, U32, U32, U32, ctypes.POINTER(TuneResult)]),
         "mr_debug_big_wait": (ctypes.c_int, [P, U32, ctypes.c_int32]),
     }
@@ -523,6 +524,19 @@ class Context:
         self._check(lib.mr_debug_table(self.handle, class_bits, kh, name.encode(), _ptr(out), cnt.value,
                                        ctypes.byref(cnt)))
         return [int(v) for v in out]
+
+
+def mr_debug_tc_slices(class_bits: int) -> np.ndarray:
+    """The tensor-core operand table of a size class as fp16 values (see mr.h), host-built."""
+    cnt = ctypes.c_size_t()
+    rc = lib.mr_debug_tc_slices(class_bits, None, 0, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, f"no tensor-core table for class {class_bits}")
+    out = np.zeros(cnt.value, dtype=np.uint32)
+    rc = lib.mr_debug_tc_slices(class_bits, _ptr(out), cnt.value, ctypes.byref(cnt))
+    if rc:
+        raise MRError(rc, "tensor-core table")
+    return out.view(np.float16)
 
 
 def to_tensor(values: Iterable[int], n_limbs: int, device="cuda"):

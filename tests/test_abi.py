@@ -95,12 +95,13 @@ def test_large_class_wave_policy():
     class fits 15 groups per wave at 32 channels per block and 21 at 48 (1.33x the time per group):
     8 and 15 groups stay on the narrow slices, 16-21 groups take one wide wave, 30 groups two
     narrow waves, 42 groups two wide waves (2.66 against 3); the 16384-bit class has one width
-    (8 groups per wave)."""
+    (8 groups per wave) in two forms and picks the tensor-core form of the base extensions (less
+    time per group)."""
     cases = {256: (0, 8), 480: (0, 15), 512: (1, 16), 672: (1, 21), 960: (0, 15), 1344: (1, 21)}
     for n, want in cases.items():
         assert mr.mr_debug_big_variant(8192, n) == want, n
-    assert mr.mr_debug_big_variant(16384, 256) == (0, 8)
-    assert mr.mr_debug_big_variant(16384, 1000) == (0, 8)
+    assert mr.mr_debug_big_variant(16384, 256) == (1, 8)
+    assert mr.mr_debug_big_variant(16384, 1000) == (1, 8)
     with pytest.raises(mr.MRError) as e:
         mr.mr_debug_big_variant(1024, 100)
     assert e.value.code == 1  # not a large class
@@ -163,3 +164,46 @@ def test_key_setup_errors():
     with pytest.raises(mr.MRError) as e:
         mr.mr_debug_key_table_host(12345679, "no_such_table")
     assert e.value.code == 1
+
+
+def _tile_off(R, r, k):
+    """Byte offset of element (r, k) of an R-row tensor-core tile: 8-row x 16-byte core matrices,
+    column groups of 8 outermost (the K-major layout without swizzling)."""
+    return (k // 8) * (R // 8) * 128 + (r // 8) * 128 + (r % 8) * 16 + (k % 8) * 2
+
+
+@pytest.mark.parametrize("L", [8192, 16384])
+def test_tc_slice_table_recombines_to_scaled_matrices(L):
+    """The tensor-core operand table: at a seeded sample of (slice, matrix, input channel, column),
+    the four fp16 slices at their tile positions are integers in [0, 127] and recombine,
+    sum_b 2^(7b) s_b, to the extension matrix entry times 2^64 mod its prime (the device's scaled
+    form); past channel k every slice is zero."""
+    from synth import SplitMix64
+    k = mr.mr_class_for_bits(L)[1]
+    B = mr.mr_debug_class_table(L, "B")
+    Bp = mr.mr_debug_class_table(L, "Bp")
+    T1 = mr.mr_debug_class_table(L, "M_mi_Bp")  # row i, column j
+    T2 = mr.mr_debug_class_table(L, "Mp_mj_B")  # row j, column i
+    t = mr.mr_debug_tc_slices(L)
+    slices, nch = (k + 31) // 32, (k + 63) // 64
+    assert t.size == slices * 2 * nch * 128 * 64
+    r = SplitMix64(L)
+
+    def at(c, e, i, j, b):
+        byte = ((c * 2 + e) * nch + i // 64) * 16384 + _tile_off(128, 32 * b + j, i % 64)
+        return float(t[byte // 2])
+
+    for _ in range(400):
+        c, e, i, j = r.below(slices), r.below(2), r.below(nch * 64), r.below(32)
+        vals = [at(c, e, i, j, b) for b in range(4)]
+        assert all(v == int(v) and 0 <= v <= 127 for v in vals)
+        col = 32 * c + j
+        if i >= k or col >= k:
+            assert vals == [0.0] * 4
+            continue
+        got = sum(int(v) << (7 * b) for b, v in enumerate(vals))
+        if e == 0:
+            want = T1[i * k + col] * (1 << 64) % Bp[col]
+        else:
+            want = T2[i * k + col] * (1 << 64) % B[col]
+        assert got == want, (c, e, i, j)

@@ -59,6 +59,36 @@ def test_modexp_16384_ragged_groups_and_edges(mr, ctx):
     assert st == [0] * n
 
 
+@pytest.mark.parametrize("variant", [0, 1], ids=["integer", "tensor"])
+def test_modexp_16384_both_forms_of_the_extension(mr, variant):
+    """The same batch with the base extensions on the integer pipe (variant 0) and on the tensor
+    cores (variant 1, fp16 slices, Sec. 3.1's constant-matrix products): every output equals the
+    oracle's.  Three groups of 32, the last partial, edge values, one full-length exponent."""
+    keys = load_keys("mod16384_x4")
+    c = mr.Context(0)
+    try:
+        c.mr_set_variant(16384, variant)
+        handles = [c.mr_rns_setup(k["N"]) for k in keys]
+        r = SplitMix64(0x7C16384 + variant)
+        n = 70
+        idx = [(3 * i) % len(keys) for i in range(n)]
+        Ns = [keys[i]["N"] for i in idx]
+        xs = [r.below(N) for N in Ns]
+        es = [r.randbits(40 + 37 * (j % 5)) for j in range(n)]
+        xs[0], es[0] = 0, 9
+        xs[1], es[1] = 1, r.randbits(200)
+        xs[2], es[2] = Ns[2] - 1, 5
+        xs[3], es[3] = r.below(Ns[3]), 0
+        xs[33], es[33] = Ns[33] - 1, 2
+        es[40] = r.randbits(16128) | (1 << 16127)
+        got, st = _run(mr, c, [handles[i] for i in idx], Ns, xs, es, 512, 504)
+        for j in range(n):
+            assert got[j] == plain.modexp(xs[j], es[j], Ns[j]), j
+        assert st == [0] * n
+    finally:
+        c.close()
+
+
 def test_modexp_16384_range_status(mr, ctx):
     keys = load_keys("mod16384_x4")
     h = ctx.mr_rns_setup(keys[0]["N"])
