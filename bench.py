@@ -268,6 +268,24 @@ def sm_max_mhz() -> float:
         return 2070.0
 
 
+def measured_peak(key: str, default: float) -> float:
+    """A figure of MEASURED_PEAKS.json (measured on this machine's GPUs), else `default`."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get(key, default))
+    except (OSError, ValueError):
+        return default
+
+
+def big_variant_used(mr, L: int, n_items: int) -> int:
+    """The variant a large-class call of n_items runs: MR_VARIANT_<L> when set, else the library's
+    wave policy on this GPU (one block per SM)."""
+    env = os.environ.get(f"MR_VARIANT_{L}")
+    if env is not None and env.isdigit():
+        return int(env)
+    return mr.mr_debug_big_variant(L, n_items)[0]
+
+
 def window_for_bits(bits: int, max_w: int = 5) -> int:
     """The library's window width for an exponent of `bits` bits: minimises squarings +
     multiplications + table entries over w = 1..max_w (5 for the lane-group classes, 8 for the
@@ -1328,6 +1346,8 @@ def run_big(args, rank, world, local_rank, emit=True):
     max_mhz = sm_max_mhz()
     peak = props.multi_processor_count * IMAD_PER_CLK_PER_SM * max_mhz * 1e6
     achieved = 2 * prods / (mx_avg_ms / 1e3)
+    variant = big_variant_used(mr, L, len(idx) * (2 if crt else 1))
+    vinfo = mr.mr_big_variant_info(L, variant)
     wide_rate = ctx.mr_imad_peak(0, stream)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T int32-mul/s",
                 "frac": achieved / peak, "traffic": None, "kernel": f"big_modexp_kernel<k={k}> (channel-slice width: the variant with the fewest estimated waves)",
@@ -1343,6 +1363,39 @@ def run_big(args, rank, world, local_rank, emit=True):
                 "int32_mul_ops_per_launch_31bit_count": ops31,
                 "count_31bit": f"k = {K31[L]} channels of primes below 2^31, 2[2k(k+1)+8k] per multiplication, "
                                "|e|+ceil(|e|/w)+2^w+2 multiplications, conversions"}
+    if vinfo["tensor"]:
+        # the base extensions ran on the tensor cores: the dominant unit is the tensor pipe.  Algorithmic
+        # work: per multiplication 2 extensions x 16 fp16 slice pairs x 2 n k^2 (n numbers, k channels);
+        # executed: the padded products the kernel issues (128 x 128 x 16 per step, 19 blocks per group)
+        nums = len(idx) * (2 if crt else 1)
+        ebits_all = ([keys[i][h].bit_length() for i in idx for h in ("dp", "dq")] if crt else
+                     [e.bit_length() for e in es])
+        mms = [1 + (2 ** w - 2) + (w + 1) * (max(1, math.ceil(b / w)) - 1) + 1 + (1 if crt else 0) for b in ebits_all]
+        tensor_alg = sum(m * 2 * 16 * 2 * k * k for m in mms)
+        groups = math.ceil(nums / 32)
+        kp = math.ceil(k / 64) * 64
+        tensor_exec = max(mms) * groups * vinfo["slices"] * 2 * (kp // 16) * 2 * 128 * 128 * 16
+        tensor31 = sum(mm31 * 2 * 16 * 2 * K31[L] * (K31[L] + 1) for mm31 in
+                       (b + math.ceil(b / w) + 2 ** w + 2 for b in ebits_all))
+        t_s = mx_avg_ms / 1e3
+        tpeak = measured_peak("bf16_tflops_sustained", 1700.0) * 1e12
+        tc_probe = ctx.mr_tensor_peak(0, stream)
+        imad = {k2: roofline[k2] for k2 in ("bound", "achieved", "peak", "unit", "frac", "frac_31bit_count")}
+        roofline = {"bound": "tensor", "achieved": tensor_alg / t_s / 1e12, "peak": tpeak / 1e12, "unit": "TFLOP/s",
+                    "frac": tensor_alg / t_s / tpeak, "traffic": None,
+                    "kernel": f"big_modexp_kernel<k={k}, base extensions on tcgen05 (fp16 slices)>",
+                    "kernel_ms": mx_avg_ms, "window": w,
+                    "tensor_ops_per_launch": tensor_alg,
+                    "count": f"2 extensions x 16 slice pairs x 2 n k^2 per multiplication, k = {k}",
+                    "executed_tensor_ops_per_launch": tensor_exec, "frac_executed": tensor_exec / t_s / tpeak,
+                    "frac_31bit_count": tensor31 / t_s / tpeak, "tensor_ops_per_launch_31bit_count": tensor31,
+                    "count_31bit": f"2 x 16 x 2 n k(k+1) per multiplication, k = {K31[L]}, "
+                                   "|e|+ceil(|e|/w)+2^w+2 multiplications",
+                    "peak_def": "MEASURED_PEAKS bf16 sustained (a seconds-long kernel; fp16 and bf16 share the "
+                                "tensor rate)",
+                    "tcgen05_f16_probe_tflops": tc_probe / 1e12, "frac_of_probe": tensor_alg / t_s / tc_probe,
+                    "integer_pipe_equivalent": imad}
+    roofline["variant"] = {"index": variant, **vinfo}
     if crt:
         roofline["crt_kernel"] = "crt_bin_kernel (binary Garner, one warp per decryption)"
         roofline["crt_kernel_ms"] = crt_ms / max(1, crt_launch)

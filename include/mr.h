@@ -425,6 +425,15 @@ mr_status mr_imad_peak(mr_ctx *ctx, uint32_t kind, void *stream, double *per_sec
  * memory was released), MR_ERR_CUDA. */
 mr_status mr_tensor_peak(mr_ctx *ctx, uint32_t kind, void *stream, double *ops_per_second);
 
+/* One compiled variant of a large size class (8192, 16384 bits): channels per
+ * thread block and base, thread blocks per group of 32 numbers, and whether its
+ * two base extensions run on the tensor cores (1: fp16 slices with fp32
+ * accumulation in tensor memory, exact; 0: the integer pipe).  Results do not
+ * depend on the variant.  Any output pointer may be NULL.  Errors: MR_ERR_SIZE
+ * (no such class), MR_ERR_ARG (not a large class, or no such variant). */
+mr_status mr_big_variant_info(uint32_t class_bits, uint32_t variant, uint32_t *slice_channels, uint32_t *slices,
+                              uint32_t *tensor);
+
 /* The tensor-core operand table of a size class's base extensions, built on the
  * host (no device needed): for each channel slice of 32 output channels c and
  * each extension matrix (T1 = |M/m_i|_{m'_j} 2^64 mod m'_j, then T2 =
@@ -447,6 +456,20 @@ mr_status mr_debug_tc_slices(uint32_t class_bits, uint32_t *out, size_t capacity
  * Synchronises `stream`.  Errors: MR_ERR_ARG, MR_ERR_TIMEOUT, MR_ERR_CUDA. */
 mr_status mr_debug_tc_mma(mr_ctx *ctx, const uint16_t *a, const uint16_t *b, uint32_t n, uint32_t kdim,
                           uint32_t swap_strides, float *d, void *stream);
+
+/* Phase counters of the tensor-core form of the large classes (instrumentation,
+ * off by default).  on != 0: later calls on this context add, per thread block
+ * (its thread 0), the SM clock cycles spent in each phase of every RNS
+ * Montgomery multiplication: 0 channel work up to the first exchange, 1 the
+ * first barrier between the blocks of an item group, 2 the first extension's
+ * copies and tensor-core products, 3 its epilogue, 4 channel work up to the
+ * second exchange, 5 the second barrier, 6 the second extension's copies and
+ * products, 7 its epilogue and the final channel work.  When out is not NULL
+ * it receives the 8 sums and then the number of blocks counted (9 words),
+ * after a device synchronisation, and the counters restart from zero.
+ * on == 0 releases them (after reading into out, if given).  Allocates 72
+ * bytes of device memory while on.  Errors: MR_ERR_ARG, MR_ERR_CUDA. */
+mr_status mr_debug_big_phases(mr_ctx *ctx, int on, uint64_t *out);
 
 /* Test hook of the large classes' bounded waits.  Later 8192/16384-bit calls on
  * this context give up a wait between thread blocks after spin_limit polls

@@ -87,6 +87,7 @@ struct mr_ctx {
   uint32_t* mr_dbg = nullptr;  // test hook of mr_debug_mr_setup
   uint32_t big_spin_limit = 0;  // large-class barrier polls before giving up (0: the kernel default)
   int32_t big_absent_slice = -1;  // test hook of mr_debug_big_wait
+  unsigned long long* big_phases = nullptr;  // mr_debug_big_phases: device counters, or nullptr (off)
   std::vector<cudaStream_t> side;     // streams for concurrent groups of one-shot mixed calls
   std::vector<cudaEvent_t> side_join;
   cudaEvent_t side_fork = nullptr;
@@ -428,7 +429,7 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
       uint32_t* sync = scr + (size_t)b.slots * bk.slot_words(b.wbits);
       BigArgs a{b.ce->dev, b.ce->tslice[b.bigv], reinterpret_cast<const MxItem*>(base + b.off_mx), (uint32_t)b.mx.size(),
                 b.wbits, scr, status, sync, b.slots, ctx->big_spin_limit ? ctx->big_spin_limit : BIG_SPIN_POLLS,
-                ctx->big_absent_slice};
+                ctx->big_absent_slice, ctx->big_phases};
       e = cudaMemsetAsync(sync, 0, (b.slots + 1) * 4, stream);
       if (e == cudaSuccess) e = timed_launch(ctx, 0, stream, [&] { return bk.modexp(a, stream); });
       if (e == cudaSuccess && !b.crt.empty()) {
@@ -985,6 +986,7 @@ void mr_shutdown(mr_ctx* ctx) {
       if (t) cudaFree(t);
   }
   if (ctx->trial_tab) cudaFree(ctx->trial_tab);
+  if (ctx->big_phases) cudaFree(ctx->big_phases);
   if (ctx->staging) cudaFreeHost(ctx->staging);
   if (ctx->staging_evt) cudaEventDestroy(ctx->staging_evt);
   for (auto& sp : ctx->spans) {
@@ -1793,6 +1795,30 @@ mr_status mr_debug_tc_mma(mr_ctx* ctx, const uint16_t* a, const uint16_t* b, uin
   return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "tensor product");
 }
 
+mr_status mr_debug_big_phases(mr_ctx* ctx, int on, uint64_t* out) {
+  if (!ctx) return MR_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaSuccess;
+  if (out) {
+    std::vector<unsigned long long> h(BIG_PHASES + 1, 0);
+    if (ctx->big_phases) {
+      e = cudaDeviceSynchronize();
+      if (e == cudaSuccess) e = cudaMemcpy(h.data(), ctx->big_phases, h.size() * 8, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemset(ctx->big_phases, 0, h.size() * 8);
+    }
+    for (size_t i = 0; i < h.size(); i++) out[i] = h[i];
+  }
+  if (e == cudaSuccess && on && !ctx->big_phases) {
+    e = cudaMalloc(&ctx->big_phases, (BIG_PHASES + 1) * 8);
+    if (e == cudaSuccess) e = cudaMemset(ctx->big_phases, 0, (BIG_PHASES + 1) * 8);
+  } else if (e == cudaSuccess && !on && ctx->big_phases) {
+    e = cudaDeviceSynchronize();
+    cudaFree(ctx->big_phases);
+    ctx->big_phases = nullptr;
+  }
+  return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "phase counters");
+}
+
 mr_status mr_debug_big_wait(mr_ctx* ctx, uint32_t spin_limit, int32_t absent_slice) {
   if (!ctx || absent_slice < -1) return fail(ctx, MR_ERR_ARG, "bad arguments");
   ctx->big_spin_limit = spin_limit;
@@ -1940,6 +1966,18 @@ mr_status mr_debug_table(mr_ctx* ctx, uint32_t class_bits, const mr_key* key, co
     mr_status s = debug_class_table(*c, nm, out, capacity, count);
     return s ? fail(ctx, s, "unknown table or buffer too small") : MR_OK;
   });
+}
+
+mr_status mr_big_variant_info(uint32_t class_bits, uint32_t variant, uint32_t* slice_channels, uint32_t* slices,
+                              uint32_t* tensor) {
+  const ClassKernels* kern = class_kernels(class_bits);
+  if (!kern) return MR_ERR_SIZE;
+  if (!kern->big || variant >= kern->n_big) return MR_ERR_ARG;
+  const BigKernel& bk = kern->big[variant];
+  if (slice_channels) *slice_channels = bk.sc;
+  if (slices) *slices = bk.slices;
+  if (tensor) *tensor = bk.tc;
+  return MR_OK;
 }
 
 mr_status mr_debug_tc_slices(uint32_t class_bits, uint32_t* out, size_t capacity, size_t* count) {

@@ -87,7 +87,8 @@ struct BigTcCfg {
   static constexpr int KC = 64;                       // columns of k per staged chunk
   static constexpr int NCH = (K + KC - 1) / KC;       // chunks per extension
   static constexpr int KP = NCH * KC;                 // padded k
-  static constexpr int STAGES = 4;
+  static constexpr int STAGES = 5;
+  static constexpr int PRE = (STAGES - 1 < NCH) ? STAGES - 1 : NCH;  // chunks whose B is fetched at the barrier
   static constexpr uint32_t CHUNK_BYTES = 128u * KC * 2u;  // one operand chunk: 128 rows x 64 fp16
   static constexpr uint32_t TMEM_COLS = 128;
   static constexpr int EX_LS = 17;                    // exchange: 64-bit words per lane (16 + 1 pad)
@@ -103,7 +104,8 @@ struct BigTcCfg {
   static constexpr int SM_MISC = SM_KAW + NW * 32;
   static constexpr int SM_MBAR = SM_MISC + 32;        // full[STAGES], empty[STAGES], done (8 bytes each)
   static constexpr int SM_TMEM = SM_MBAR + 2 * (2 * STAGES + 1);
-  static constexpr int SM_WORDS = SM_TMEM + 4;
+  static constexpr int SM_PH = SM_TMEM + 4;           // phase counters: BIG_PHASES sums, last time stamp (u64)
+  static constexpr int SM_WORDS = SM_PH + 2 * (BIG_PHASES + 1);
   static constexpr int SMEM_BYTES = SM_WORDS * 4;
   // per-slot global scratch (words): the A operands of the two extensions, the plain CRT coefficients
   // of the exit conversion, slice partials, then the window table
@@ -115,7 +117,7 @@ struct BigTcCfg {
   static constexpr size_t BTAB_BYTES = (size_t)2 * SLICES * NCH * CHUNK_BYTES;
   static_assert(K * 32 <= STAGES * 2 * (int)CHUNK_BYTES / 4, "RNS -> binary staging fits the ring");
   static_assert(SLICES * SC <= KP, "every slice's columns lie inside the padded operand");
-  static_assert((SM_MBAR % 2) == 0 && (SM_C4A % 4) == 0 && (SM_EX % 2) == 0, "alignment");
+  static_assert((SM_MBAR % 2) == 0 && (SM_C4A % 4) == 0 && (SM_EX % 2) == 0 && (SM_PH % 2) == 0, "alignment");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
   static_assert(K <= 1040, "7-bit slices: k * 127^2 < 2^24 keeps every fp32 partial sum exact");
 };
@@ -132,41 +134,31 @@ struct BigGroup {
   uint32_t chunk;      // tensor-core form: operand chunks staged so far (ring position and parities)
   uint32_t done_ph;    // tensor-core form: parity of the accumulator-complete mbarrier
   const uint8_t* btab; // tensor-core form: this slice's B operand chunks [extension][chunk]
+  unsigned long long* phases;  // tensor-core form: phase counters of the launch, or nullptr
   int c, w, lane;
+  // Phase counters: thread 0 closes the interval since the previous mark into phase i.
+  __device__ __forceinline__ void mark(int i) {
+    if constexpr (C::TC) {
+      if (phases && threadIdx.x == 0) {
+        unsigned long long* ph = reinterpret_cast<unsigned long long*>(s + C::SM_PH);
+        const unsigned long long t = clock64();
+        ph[i] += t - ph[BIG_PHASES];
+        ph[BIG_PHASES] = t;
+      }
+    }
+  }
   __device__ uint4 a4(int q) const { return reinterpret_cast<const uint4*>(s + C::SM_C4A)[q]; }
   __device__ uint4 b4(int q) const { return reinterpret_cast<const uint4*>(s + C::SM_C4B)[q]; }
   __device__ uint2 a2(int q) const { return reinterpret_cast<const uint2*>(s + C::SM_C2A)[q]; }
   __device__ uint2 b2(int q) const { return reinterpret_cast<const uint2*>(s + C::SM_C2B)[q]; }
 
   // All CTAs of the slot meet; false when the wait ran out or another CTA aborted.
-  __device__ bool barrier() {
-    nbar++;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const uint32_t target = nbar * (uint32_t)C::SLICES;
-      __threadfence();
-      atomicAdd(ctr, 1u);
-      uint32_t ok = 1;
-      for (uint32_t it = 0;; it++) {
-        uint32_t v;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
-        if ((int32_t)(v - target) >= 0) break;
-        if (*(volatile uint32_t*)abort) {
-          ok = 0;
-          break;
-        }
-        if (it >= spin_limit) {
-          atomicExch(abort, 1u);
-          ok = 0;
-          break;
-        }
-        __nanosleep(it < 64 ? 32 : 256);
-      }
-      s[C::SM_MISC] = ok;
-    }
-    __syncthreads();
-    return s[C::SM_MISC] != 0;
-  }
+  // Tensor-core form: `prefetch_b` (non-null) names the B operand of the extension that follows the
+  // barrier; thread 0 starts its first chunks' copies between arriving and waiting (B does not depend
+  // on the other CTAs), so their latency hides behind the wait.
+  // prefetch_a: the A operand of that extension, used only to complete the prefetched stages (and wait
+  // for them, bounded) when the barrier gives up, so that no copy is left in flight.
+  __device__ bool barrier(const uint8_t* prefetch_b = nullptr, const uint8_t* prefetch_a = nullptr);
 
 };
 
@@ -279,11 +271,43 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
+// Thread 0: the B halves of the first PRE chunks of the next extension into their ring stages, each stage's
+// mbarrier expecting both halves (the A halves follow in tc_ext once the slot barrier has passed).  The
+// stages are free: every product of the previous extension has completed.
+template <class C>
+__device__ __forceinline__ void tc_prefetch_b(BigGroup<C>& g, const uint8_t* bop) {
+  constexpr uint32_t CB = C::CHUNK_BYTES;
+  uint8_t* const ring = reinterpret_cast<uint8_t*>(g.s + C::SM_RING);
+  uint64_t* const full = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
+  for (int c = 0; c < C::PRE; c++) {
+    const uint32_t st = (g.chunk + c) % C::STAGES;
+    mbar_expect_tx(&full[st], 2 * CB);
+    bulk_g2s(ring + (size_t)st * 2 * CB + CB, bop + (size_t)c * CB, CB, &full[st]);
+  }
+}
+
+// Thread 0, abort path after tc_prefetch_b: issue the matching A halves (readable memory, whatever it holds)
+// so that every prefetched stage completes, and wait for them (bounded) before the block can exit.
+template <class C>
+__device__ void tc_drain_prefetch(BigGroup<C>& g, const uint8_t* aop) {
+  constexpr uint32_t CB = C::CHUNK_BYTES;
+  uint8_t* const ring = reinterpret_cast<uint8_t*>(g.s + C::SM_RING);
+  uint64_t* const full = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
+  for (int c = 0; c < C::PRE; c++) {
+    const uint32_t st = (g.chunk + c) % C::STAGES;
+    bulk_g2s(ring + (size_t)st * 2 * CB, aop + (size_t)c * CB, CB, &full[st]);
+  }
+  for (int c = 0; c < C::PRE; c++) {
+    const uint32_t gc = g.chunk + c;
+    mbar_wait(&full[gc % C::STAGES], (gc / C::STAGES) & 1u, g.spin_limit);
+  }
+}
+
 // One base extension on the tensor cores (see BigTcCfg): acc[s] = sum_i X[lane][i] T[i][4w + s], exact,
 // from the slot's A operand `aop` (all slices written, the slot barrier passed) and this slice's B
 // operand `bop`.  False (abort raised) when a copy or the tensor core does not complete in time.
 template <class C>
-__device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, const uint8_t* bop) {
+__device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, const uint8_t* bop, int ph0) {
   constexpr int S = C::STAGES, NCH = C::NCH;
   constexpr uint32_t CB = C::CHUNK_BYTES;
   uint8_t* const ring = reinterpret_cast<uint8_t*>(g.s + C::SM_RING);
@@ -291,9 +315,6 @@ __device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, c
   uint64_t* const empty = full + S;
   uint64_t* const done = empty + S;
   const uint32_t taddr = g.s[C::SM_TMEM];
-  // earlier generic accesses of the ring (the exit conversion stages through it) before the copies
-  tc::fence_smem_async();
-  __syncthreads();
   uint32_t ok = 1;
   if (threadIdx.x == 0) {
     asm volatile("fence.proxy.async.global;" ::: "memory");  // the slot's A stores, seen through its barrier
@@ -301,11 +322,14 @@ __device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, c
     auto load = [&](int c) {
       const uint32_t st = (g0 + c) % S;
       uint8_t* dst = ring + (size_t)st * 2 * CB;
-      mbar_expect_tx(&full[st], 2 * CB);
+      if (c >= C::PRE) {  // the first PRE chunks' B halves were started at the barrier (tc_prefetch_b)
+        mbar_expect_tx(&full[st], 2 * CB);
+        bulk_g2s(dst + CB, bop + (size_t)c * CB, CB, &full[st]);
+      }
       bulk_g2s(dst, aop + (size_t)c * CB, CB, &full[st]);
-      bulk_g2s(dst + CB, bop + (size_t)c * CB, CB, &full[st]);
     };
-    for (int c = 0; c < S - 1 && c < NCH; c++) load(c);
+    int issued = 0, consumed = 0;
+    for (int c = 0; c < S - 1 && c < NCH; c++, issued++) load(c);
     constexpr uint32_t idesc = tc::idesc_f16_f32(128, 128);
     for (int c = 0; c < NCH; c++) {
       const uint32_t gc = g0 + c, st = gc % S;
@@ -313,6 +337,7 @@ __device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, c
         ok = 0;
         break;
       }
+      consumed = c + 1;
       tc::fence_after_sync();
       const uint32_t a0 = smem_u32(ring + (size_t)st * 2 * CB), b0 = a0 + CB;
 #pragma unroll
@@ -330,12 +355,19 @@ __device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, c
           break;
         }
         load(cn);
+        issued++;
       }
     }
     tc::mma_commit(done);
-    // on failure, still give the issued products a bounded chance to finish before tensor memory is reused
+    // on failure, still give the issued products and copies a bounded chance to finish before the
+    // tensor memory is reused or the block exits
     if (!mbar_wait(done, g.done_ph, g.spin_limit)) ok = 0;
-    if (!ok) atomicExch(g.abort, 1u);
+    if (!ok) {
+      atomicExch(g.abort, 1u);
+      for (int c = consumed; c < issued; c++)
+        mbar_wait(&full[(g0 + c) % S], ((g0 + c) / S) & 1u, g.spin_limit);
+    }
+    g.mark(ph0);
   }
   g.chunk += NCH;
   g.done_ph ^= 1u;
@@ -369,7 +401,46 @@ __device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, c
     for (int q = 0; q < 4; q++) v += ex[((q * 2 + h) * 32 + g.lane) * C::EX_LS + jb + s];
     acc[s] = v;
   }
+  g.mark(ph0 + 1);
   return true;
+}
+
+template <class C>
+__device__ bool BigGroup<C>::barrier(const uint8_t* prefetch_b, const uint8_t* prefetch_a) {
+  nbar++;
+  // the ring's generic accesses (the exit conversion stages through it) before any copy into it
+  if constexpr (C::TC) tc::fence_smem_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t target = nbar * (uint32_t)C::SLICES;
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    if constexpr (C::TC) {
+      if (prefetch_b) tc_prefetch_b<C>(*this, prefetch_b);
+    }
+    uint32_t ok = 1;
+    for (uint32_t it = 0;; it++) {
+      uint32_t v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if ((int32_t)(v - target) >= 0) break;
+      if (*(volatile uint32_t*)abort) {
+        ok = 0;
+        break;
+      }
+      if (it >= spin_limit) {
+        atomicExch(abort, 1u);
+        ok = 0;
+        break;
+      }
+      if (it >= 2048) __nanosleep(128);  // poll at L2 latency first, then back off
+    }
+    if constexpr (C::TC) {
+      if (!ok && prefetch_b) tc_drain_prefetch<C>(*this, prefetch_a);
+    }
+    s[C::SM_MISC] = ok;
+  }
+  __syncthreads();
+  return s[C::SM_MISC] != 0;
 }
 
 // RNS Montgomery multiplication x <- x*y*M^-1 mod N (outputs below (k+1)N), this thread's channels.
@@ -381,6 +452,7 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
   uint32_t* KAWg = g.slot + C::KAWG;
   uint32_t sp[NPT];
   uint32_t xv[NPT];
+  g.mark(7);  // the previous multiplication's tail and the work between multiplications
   // 1-2. s = x*y in both bases; xi_i = s_i |-N^-1 (M/m_i)^-1| to the exchange buffer (zero on padding slots)
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
@@ -391,8 +463,11 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
     const uint4 cp = g.b4(q);
     sp[s] = redc_lazy(mulw(xp[s], yp[s]), cp.x, cp.y);
   }
+  const uint8_t *pre1 = nullptr, *pa1 = nullptr;
   if constexpr (C::TC) {
     tc_put_slices<C>(reinterpret_cast<uint8_t*>(g.slot + C::AG1), xv, g.c * C::SC + g.w * NPT, g.lane);
+    pre1 = g.btab;
+    pa1 = reinterpret_cast<const uint8_t*>(g.slot + C::AG1);
   } else {
 #pragma unroll
     for (int s = 0; s < NPT; s++) {
@@ -400,13 +475,15 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
       if (o < K) g.slot[C::XG + (size_t)o * 32 + g.lane] = xv[s];
     }
   }
-  if (!g.barrier()) return false;
+  g.mark(0);
+  if (!g.barrier(pre1, pa1)) return false;
+  g.mark(1);
   // 3. extension B -> B'
   uint64_t acc[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) acc[s] = 0;
   if constexpr (C::TC) {
-    if (!tc_ext<C>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG1), g.btab)) return false;
+    if (!tc_ext<C>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG1), g.btab, 2)) return false;
   } else {
     if (!big_ext<C>(acc, g, g.slot + C::XG, g.s + C::SM_T1)) return false;
   }
@@ -439,7 +516,14 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
     for (int u = 0; u < C::NW; u++) v += g.s[C::SM_KAW + u * 32 + g.lane];
     KAWg[g.c * 32 + g.lane] = v;
   }
-  if (!g.barrier()) return false;
+  const uint8_t *pre2 = nullptr, *pa2 = nullptr;
+  if constexpr (C::TC) {
+    pre2 = g.btab + (size_t)C::NCH * C::CHUNK_BYTES;
+    pa2 = reinterpret_cast<const uint8_t*>(g.slot + C::AG2);
+  }
+  g.mark(4);
+  if (!g.barrier(pre2, pa2)) return false;
+  g.mark(5);
   // 6. exact extension B' -> B with a' from the slice partials (loaded before the dot products,
   //    summed after them); the correction -a'|M'| enters as a' E with E = -M' 2^64 mod m_i
   uint32_t kp[C::SLICES];
@@ -448,7 +532,8 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
 #pragma unroll
   for (int s = 0; s < NPT; s++) acc[s] = 0;
   if constexpr (C::TC) {
-    if (!tc_ext<C>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG2), g.btab + (size_t)C::NCH * C::CHUNK_BYTES))
+    if (!tc_ext<C>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG2), g.btab + (size_t)C::NCH * C::CHUNK_BYTES,
+                   6))
       return false;
   } else {
     if (!big_ext<C>(acc, g, g.slot + C::XPG, g.s + C::SM_T2)) return false;
@@ -792,6 +877,7 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
   g.chunk = 0;
   g.done_ph = 0;
   g.btab = nullptr;
+  g.phases = a.phases;
   if (g.c == a.absent_slice) return;  // test hook: this slice never arrives; the others time out
   if (threadIdx.x == 0) {
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem_raw + C::SM_MBAR);
@@ -816,6 +902,11 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
         for (uint32_t i = threadIdx.x; i < tail_bytes / 16; i += C::THREADS) t[i] = make_uint4(0, 0, 0, 0);
       }
     }
+    if (g.phases && threadIdx.x == 0) {
+      unsigned long long* ph = reinterpret_cast<unsigned long long*>(smem_raw + C::SM_PH);
+      for (int i = 0; i < BIG_PHASES; i++) ph[i] = 0;
+      ph[BIG_PHASES] = clock64();
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -833,6 +924,11 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
     __syncthreads();
     tc::fence_after_sync();
     if (threadIdx.x < 32) tc::tmem_dealloc(smem_raw[C::SM_TMEM], C::TMEM_COLS);
+    if (g.phases && threadIdx.x == 0) {
+      const unsigned long long* ph = reinterpret_cast<const unsigned long long*>(smem_raw + C::SM_PH);
+      for (int i = 0; i < BIG_PHASES; i++) atomicAdd(&g.phases[i], ph[i]);
+      atomicAdd(&g.phases[BIG_PHASES], 1ull);
+    }
   }
   if (grp < n_groups && g.c == (a.absent_slice == 0 ? 1 : 0) && a.status) {
     // aborted: every unfinished item of this slot reports a timeout

@@ -52,7 +52,15 @@ struct BigArgs {
   uint32_t slots;          // item groups in flight (grid = slots * slices)
   uint32_t spin_limit;     // barrier polls before a wait gives up
   int32_t absent_slice;    // test hook: CTAs of this channel slice leave at once (-1: none)
+  unsigned long long* phases;  // nullptr, or BIG_PHASES + 1 counters: SM cycles per phase summed over the
+                               // CTAs (thread 0 of each), then the number of CTAs (tensor-core form only)
 };
+
+// Phases of one RNS Montgomery multiplication timed by the large-class kernel's phase counters: channel work
+// up to the first exchange, first barrier, first extension's copies and products, its epilogue, channel work
+// up to the second exchange, second barrier, second extension's copies and products, its epilogue and the
+// final channel work.
+constexpr int BIG_PHASES = 8;
 
 // [special, s, nbits, 0][M mod N: W][M^2 mod N: W][kxi: k][N M^-1 (plain): k][cd: k][N^-1 mod m_i: k][N^-1 mod m'_j: k]
 MR_HD inline uint32_t mr_debug_words(uint32_t k, uint32_t W) { return 4 + 2 * W + 5 * k; }

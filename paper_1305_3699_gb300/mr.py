@@ -32,7 +32,7 @@ EXPORTED = [
     "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
     "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
     "mr_get_tuning", "mr_set_tuning", "mr_debug_crt_bin_host", "mr_debug_big_variant",
-    "mr_tensor_peak", "mr_debug_tc_mma", "mr_debug_tc_slices",
+    "mr_tensor_peak", "mr_debug_tc_mma", "mr_debug_tc_slices", "mr_big_variant_info", "mr_debug_big_phases",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -108,6 +108,8 @@ def _load() -> ctypes.CDLL:
         "mr_tensor_peak": (ctypes.c_int, [P, U32, P, ctypes.POINTER(ctypes.c_double)]),
         "mr_debug_tc_mma": (ctypes.c_int, [P, P, P, U32, U32, U32, P, P]),
         "mr_debug_tc_slices": (ctypes.c_int, [U32, PU32, SZ, ctypes.POINTER(SZ)]),
+        "mr_big_variant_info": (ctypes.c_int, [U32, U32, PU32, PU32, PU32]),
+        "mr_debug_big_phases": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
         "mr_autotune": (ctypes.c_int, [P, U32, U32, U32, ctypes.POINTER(TuneResult)]),
         "mr_debug_big_wait": (ctypes.c_int, [P, U32, ctypes.c_int32]),
     }
@@ -490,6 +492,13 @@ class Context:
         return {"variant": r.variant, "lanes_per_number": r.lanes_per_number, "window": r.window,
                 "configs": r.configs, "ms": r.ms, "ms_default": r.ms_default}
 
+    def mr_debug_big_phases(self, on: bool = True) -> List[int]:
+        """Phase cycle counters of the large classes' tensor-core form (see mr.h): returns the 8 sums
+        and the block count accumulated so far, then restarts them (on) or releases them (off)."""
+        buf = (ctypes.c_uint64 * 9)()
+        self._check(lib.mr_debug_big_phases(self.handle, 1 if on else 0, buf))
+        return [int(v) for v in buf]
+
     def mr_debug_big_wait(self, spin_limit: int = 0, absent_slice: int = -1):
         """Test hook of the large classes' bounded waits (see mr.h)."""
         self._check(lib.mr_debug_big_wait(self.handle, spin_limit, absent_slice))
@@ -524,6 +533,15 @@ class Context:
         self._check(lib.mr_debug_table(self.handle, class_bits, kh, name.encode(), _ptr(out), cnt.value,
                                        ctypes.byref(cnt)))
         return [int(v) for v in out]
+
+
+def mr_big_variant_info(class_bits: int, variant: int) -> dict:
+    """Channels per block, blocks per group and tensor-core flag of a large-class variant (see mr.h)."""
+    sc, sl, tc = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    rc = lib.mr_big_variant_info(class_bits, variant, ctypes.byref(sc), ctypes.byref(sl), ctypes.byref(tc))
+    if rc:
+        raise MRError(rc, f"no variant {variant} of large class {class_bits}")
+    return {"slice_channels": sc.value, "slices": sl.value, "tensor": bool(tc.value)}
 
 
 def mr_debug_tc_slices(class_bits: int) -> np.ndarray:

@@ -207,3 +207,15 @@ def test_tc_slice_table_recombines_to_scaled_matrices(L):
         else:
             want = T2[i * k + col] * (1 << 64) % B[col]
         assert got == want, (c, e, i, j)
+
+
+def test_big_variant_info():
+    """The 16384-bit class compiles the integer form (variant 0) and the tensor-core form (variant 1)
+    of its base extensions, both with 32-channel slices (19 blocks per group); the 8192-bit class's
+    integer variants have 32- and 48-channel slices."""
+    assert mr.mr_big_variant_info(16384, 0) == {"slice_channels": 32, "slices": 19, "tensor": False}
+    assert mr.mr_big_variant_info(16384, 1) == {"slice_channels": 32, "slices": 19, "tensor": True}
+    assert mr.mr_big_variant_info(8192, 0)["slice_channels"] == 32
+    assert mr.mr_big_variant_info(8192, 1)["slice_channels"] == 48
+    with pytest.raises(mr.MRError):
+        mr.mr_big_variant_info(1024, 0)
