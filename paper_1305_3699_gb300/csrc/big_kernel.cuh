@@ -65,18 +65,21 @@ struct BigCfg {
 // Tensor-core form of the same kernel.  The two base extensions of a slice's CTA are the product
 // D (32 numbers x 32 channels) = X (32 x k) T (k x 32) of the CRT coefficients with its columns of
 // the class's extension matrix, every entry below 2^28 and the exact sum below 2^64.  Both factors
-// are split into four 7-bit slices, X = sum_a 2^(7a) X_a and T = sum_b 2^(7b) T_b, stacked as
-// A = [X_0; X_1; X_2; X_3] (128 x k) and B = [T_0 T_1 T_2 T_3] (k x 128), and multiplied on the
-// tensor cores in fp16 with fp32 accumulation: every entry of A B is a sum of k products below
-// 127^2, exact in fp32 for k <= 1040.  The recombination D = sum_{a,b} 2^(7(a+b)) (A B)[a, b] is
-// exact in 64 bits.  A is written by the slot's CTAs (each its 32 channels, as fp16 slices in the
-// shared-memory operand layout of tc_device.cuh) into a per-slot buffer in global memory; B is a
-// class table in the same layout.  Each CTA streams both through a ring of STAGES shared-memory
-// stages, 64 columns of k per stage, with bulk copies completed on mbarriers; one thread issues the
-// copies and the tcgen05 products (128 x 128 x 16 each) into a 128-column tensor-memory
-// accumulator, the tensor core's completion frees each stage; the epilogue reads the accumulator
-// back (warp w: lanes of slice a = w % 4), combines the slices and hands every thread the same
-// 64-bit dot products the integer form computes.  Everything else is the integer kernel's.
+// are split into four 7-bit slices, X = sum_a 2^(7a) X_a and T = sum_b 2^(7b) T_b; A holds X_a[n]
+// in row 4n + a (128 x k) and B = [T_0 T_1 T_2 T_3] (k x 128), multiplied on the tensor cores in
+// fp16 with fp32 accumulation: every entry of A B is a sum of k products below 127^2, exact in fp32
+// for k <= 1040.  The recombination D = sum_{a,b} 2^(7(a+b)) (A B)[4n + a, 32b + j] is exact in 64
+// bits.  A is written by the slot's CTAs (each its 32 channels, as fp16 slices in the shared-memory
+// operand layout of tc_device.cuh) into a per-slot buffer in global memory; B is a class table in
+// the same layout.  Each CTA streams both through a ring of STAGES shared-memory stages, 64 columns
+// of k per stage, with bulk copies completed on mbarriers.  Issuing a bulk copy costs its thread a
+// few hundred cycles whatever its size, so every stage has two copy threads of its own (its A half
+// and its B half, each on its own mbarrier); thread 0 waits for each chunk and issues its tcgen05
+// products (128 x 128 x 16 each) into a 128-column tensor-memory accumulator, and the tensor core's
+// completion frees the stage.  The epilogue reads the accumulator back (warp w: lanes of numbers
+// 8 (w % 4) .. +7, all four data slices), sums the data slices across neighbouring lanes with
+// shuffles, and hands every thread the same 64-bit dot products the integer form computes.
+// Everything else is the integer kernel's.
 template <int K_, int W_, int WX_>
 struct BigTcCfg {
   static constexpr bool TC = true;
@@ -87,23 +90,23 @@ struct BigTcCfg {
   static constexpr int KC = 64;                       // columns of k per staged chunk
   static constexpr int NCH = (K + KC - 1) / KC;       // chunks per extension
   static constexpr int KP = NCH * KC;                 // padded k
-  static constexpr int STAGES = 5;
-  static constexpr int PRE = (STAGES - 1 < NCH) ? STAGES - 1 : NCH;  // chunks whose B is fetched at the barrier
+  static constexpr int STAGES = 6;                    // ring stages, two copy threads each
+  static constexpr int PRE = (STAGES < NCH) ? STAGES : NCH;  // chunks whose B is fetched at the barrier
   static constexpr uint32_t CHUNK_BYTES = 128u * KC * 2u;  // one operand chunk: 128 rows x 64 fp16
   static constexpr uint32_t TMEM_COLS = 128;
-  static constexpr int EX_LS = 17;                    // exchange: 64-bit words per lane (16 + 1 pad)
+  static constexpr int EX_LS = 33;                    // exchange: 64-bit words per number (32 + 1 pad)
   // shared memory (words)
   static constexpr int SM_RING = 0;                   // STAGES x [A chunk | B chunk]
   static constexpr int SM_T1 = SM_RING;               // staging area of the RNS -> binary conversion
-  static constexpr int SM_EX = SM_RING + STAGES * 2 * (int)CHUNK_BYTES / 4;  // [4 a][2 halves][32][EX_LS] u64
-  static constexpr int SM_C4A = SM_EX + 4 * 2 * 32 * EX_LS * 2;
+  static constexpr int SM_EX = SM_RING + STAGES * 2 * (int)CHUNK_BYTES / 4;  // [32 numbers][EX_LS] u64
+  static constexpr int SM_C4A = SM_EX + 32 * EX_LS * 2;
   static constexpr int SM_C4B = SM_C4A + 4 * SC;
   static constexpr int SM_C2A = SM_C4B + 4 * SC;
   static constexpr int SM_C2B = SM_C2A + 2 * SC;
   static constexpr int SM_KAW = SM_C2B + 2 * SC;
   static constexpr int SM_MISC = SM_KAW + NW * 32;
-  static constexpr int SM_MBAR = SM_MISC + 32;        // full[STAGES], empty[STAGES], done (8 bytes each)
-  static constexpr int SM_TMEM = SM_MBAR + 2 * (2 * STAGES + 1);
+  static constexpr int SM_MBAR = SM_MISC + 32;        // full_a[S], full_b[S], empty[S], done (8 bytes each)
+  static constexpr int SM_TMEM = SM_MBAR + 2 * (3 * STAGES + 1);
   static constexpr int SM_PH = SM_TMEM + 4;           // phase counters: BIG_PHASES sums, last time stamp (u64)
   static constexpr int SM_WORDS = SM_PH + 2 * (BIG_PHASES + 1);
   static constexpr int SMEM_BYTES = SM_WORDS * 4;
@@ -134,6 +137,8 @@ struct BigGroup {
   uint32_t chunk;      // tensor-core form: operand chunks staged so far (ring position and parities)
   uint32_t done_ph;    // tensor-core form: parity of the accumulator-complete mbarrier
   const uint8_t* btab; // tensor-core form: this slice's B operand chunks [extension][chunk]
+  uint32_t stag;       // tensor-core form: first chunk of k this block streams (the order is rotated per
+                       // block so that blocks sharing an operand do not read the same chunk at once)
   unsigned long long* phases;  // tensor-core form: phase counters of the launch, or nullptr
   int c, w, lane;
   // Phase counters: thread 0 closes the interval since the previous mark into phase i.
@@ -154,11 +159,9 @@ struct BigGroup {
 
   // All CTAs of the slot meet; false when the wait ran out or another CTA aborted.
   // Tensor-core form: `prefetch_b` (non-null) names the B operand of the extension that follows the
-  // barrier; thread 0 starts its first chunks' copies between arriving and waiting (B does not depend
-  // on the other CTAs), so their latency hides behind the wait.
-  // prefetch_a: the A operand of that extension, used only to complete the prefetched stages (and wait
-  // for them, bounded) when the barrier gives up, so that no copy is left in flight.
-  __device__ bool barrier(const uint8_t* prefetch_b = nullptr, const uint8_t* prefetch_a = nullptr);
+  // barrier; the B copy threads start its first chunks' copies while thread 0 arrives and waits (B
+  // does not depend on the other CTAs), so their latency hides behind the wait.
+  __device__ bool barrier(const uint8_t* prefetch_b = nullptr);
 
 };
 
@@ -244,7 +247,7 @@ __device__ bool big_ext(uint64_t (&acc)[C::NPT], BigGroup<C>& g, const uint32_t*
 }
 
 // Tensor-core form: this thread's four CRT coefficients (channels o0 .. o0+3 of number `lane`) as four
-// 7-bit fp16 slices into the A operand `aop` of an extension: row 32a + lane, columns o0 .. o0+3 of
+// 7-bit fp16 slices into the A operand `aop` of an extension: row 4 lane + a, columns o0 .. o0+3 of
 // slice a (one 8-byte store per slice; o0 is a multiple of 4).
 template <class C>
 __device__ __forceinline__ void tc_put_slices(uint8_t* aop, const uint32_t (&v)[4], int o0, int lane) {
@@ -256,7 +259,7 @@ __device__ __forceinline__ void tc_put_slices(uint8_t* aop, const uint32_t (&v)[
 #pragma unroll
     for (int s = 0; s < 4; s++) h[s] = __half_as_ushort(__uint2half_rn((v[s] >> (7 * a)) & 127u));
     const uint2 pk = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-    *reinterpret_cast<uint2*>(chunk + tc::tile_off(128, 32u * a + lane, col)) = pk;
+    *reinterpret_cast<uint2*>(chunk + tc::tile_off(128, 4u * lane + a, col)) = pk;
   }
 }
 
@@ -271,73 +274,97 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-// Thread 0: the B halves of the first PRE chunks of the next extension into their ring stages, each stage's
-// mbarrier expecting both halves (the A halves follow in tc_ext once the slot barrier has passed).  The
-// stages are free: every product of the previous extension has completed.
+// Copy threads: lanes 0 .. 2 STAGES - 1 of warp 1; lane 2 st + h copies half h (0: A, 1: B) of every
+// chunk that lands in stage st, completing on that half's own mbarrier.  A stage's two copy threads
+// alone refill it, so neither runs more than one mbarrier phase ahead.  Returns the lane, or -1.
 template <class C>
-__device__ __forceinline__ void tc_prefetch_b(BigGroup<C>& g, const uint8_t* bop) {
-  constexpr uint32_t CB = C::CHUNK_BYTES;
-  uint8_t* const ring = reinterpret_cast<uint8_t*>(g.s + C::SM_RING);
-  uint64_t* const full = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
-  for (int c = 0; c < C::PRE; c++) {
-    const uint32_t st = (g.chunk + c) % C::STAGES;
-    mbar_expect_tx(&full[st], 2 * CB);
-    bulk_g2s(ring + (size_t)st * 2 * CB + CB, bop + (size_t)c * CB, CB, &full[st]);
-  }
+__device__ __forceinline__ int tc_copier() {
+  return (threadIdx.x >= 32 && threadIdx.x < 32 + 2 * C::STAGES) ? (int)threadIdx.x - 32 : -1;
 }
 
-// Thread 0, abort path after tc_prefetch_b: issue the matching A halves (readable memory, whatever it holds)
-// so that every prefetched stage completes, and wait for them (bounded) before the block can exit.
+// The chunk of the extension starting at ring position g0 that is the first to land in stage st.
 template <class C>
-__device__ void tc_drain_prefetch(BigGroup<C>& g, const uint8_t* aop) {
+__device__ __forceinline__ int tc_first_chunk(uint32_t g0, int st) {
+  return (st - (int)(g0 % C::STAGES) + C::STAGES) % C::STAGES;
+}
+
+// B copy thread of stage st, at the slot barrier: the B half of the next extension's first chunk in
+// that stage (B does not depend on the other CTAs), so its latency hides behind the barrier.  The
+// stage is free: every product of the previous extension has completed.
+template <class C>
+__device__ __forceinline__ void tc_prefetch_b(BigGroup<C>& g, const uint8_t* bop, int st) {
   constexpr uint32_t CB = C::CHUNK_BYTES;
+  const int c = tc_first_chunk<C>(g.chunk, st);
+  if (c >= C::PRE) return;
   uint8_t* const ring = reinterpret_cast<uint8_t*>(g.s + C::SM_RING);
-  uint64_t* const full = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
-  for (int c = 0; c < C::PRE; c++) {
-    const uint32_t st = (g.chunk + c) % C::STAGES;
-    bulk_g2s(ring + (size_t)st * 2 * CB, aop + (size_t)c * CB, CB, &full[st]);
-  }
-  for (int c = 0; c < C::PRE; c++) {
-    const uint32_t gc = g.chunk + c;
-    mbar_wait(&full[gc % C::STAGES], (gc / C::STAGES) & 1u, g.spin_limit);
-  }
+  uint64_t* const full_b = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR) + C::STAGES;
+  mbar_expect_tx(&full_b[st], CB);
+  bulk_g2s(ring + (size_t)st * 2 * CB + CB, bop + (size_t)((c + g.stag) % C::NCH) * CB, CB, &full_b[st]);
+}
+
+// The same thread when the barrier gave up: wait (bounded) for the prefetched copy before the block
+// can exit.
+template <class C>
+__device__ void tc_drain_prefetch(BigGroup<C>& g, int st) {
+  const int c = tc_first_chunk<C>(g.chunk, st);
+  if (c >= C::PRE) return;
+  uint64_t* const full_b = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR) + C::STAGES;
+  mbar_wait(&full_b[st], ((g.chunk + c) / C::STAGES) & 1u, g.spin_limit);
 }
 
 // One base extension on the tensor cores (see BigTcCfg): acc[s] = sum_i X[lane][i] T[i][4w + s], exact,
 // from the slot's A operand `aop` (all slices written, the slot barrier passed) and this slice's B
-// operand `bop`.  False (abort raised) when a copy or the tensor core does not complete in time.
+// operand `bop`.  Thread 0 waits for each chunk and issues its products; the copy threads refill the
+// stages.  False (abort raised) when a copy or the tensor core does not complete in time.
 template <class C>
 __device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, const uint8_t* bop, int ph0) {
   constexpr int S = C::STAGES, NCH = C::NCH;
   constexpr uint32_t CB = C::CHUNK_BYTES;
   uint8_t* const ring = reinterpret_cast<uint8_t*>(g.s + C::SM_RING);
-  uint64_t* const full = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
-  uint64_t* const empty = full + S;
+  uint64_t* const full_a = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
+  uint64_t* const full_b = full_a + S;
+  uint64_t* const empty = full_b + S;
   uint64_t* const done = empty + S;
   const uint32_t taddr = g.s[C::SM_TMEM];
+  const uint32_t g0 = g.chunk;
   uint32_t ok = 1;
-  if (threadIdx.x == 0) {
-    asm volatile("fence.proxy.async.global;" ::: "memory");  // the slot's A stores, seen through its barrier
-    const uint32_t g0 = g.chunk;
-    auto load = [&](int c) {
-      const uint32_t st = (g0 + c) % S;
-      uint8_t* dst = ring + (size_t)st * 2 * CB;
-      if (c >= C::PRE) {  // the first PRE chunks' B halves were started at the barrier (tc_prefetch_b)
-        mbar_expect_tx(&full[st], 2 * CB);
-        bulk_g2s(dst + CB, bop + (size_t)c * CB, CB, &full[st]);
-      }
-      bulk_g2s(dst, aop + (size_t)c * CB, CB, &full[st]);
-    };
-    int issued = 0, consumed = 0;
-    for (int c = 0; c < S - 1 && c < NCH; c++, issued++) load(c);
-    constexpr uint32_t idesc = tc::idesc_f16_f32(128, 128);
-    for (int c = 0; c < NCH; c++) {
-      const uint32_t gc = g0 + c, st = gc % S;
-      if (!mbar_wait(&full[st], (gc / S) & 1u, g.spin_limit)) {
+  const int t = tc_copier<C>();
+  if (t >= 0) {
+    const int st = t >> 1, half = t & 1;
+    if (half == 0) {
+      // the slot's A stores: seen by thread 0's acquire at the slot barrier, ordered for this thread by
+      // the block barrier and this fence, then made visible to the copy engine (async proxy)
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    uint64_t* const fb = half ? &full_b[st] : &full_a[st];
+    const uint8_t* const src = half ? bop : aop;
+    uint8_t* const dst = ring + (size_t)st * 2 * CB + (half ? CB : 0);
+    int last = -1;
+    for (int c = tc_first_chunk<C>(g0, st); c < NCH; c += S) {
+      // the stage's previous chunk (c - S, or the previous extension's, complete) must have been
+      // consumed by the tensor core before the refill
+      if (c >= S && !mbar_wait(&empty[st], ((g0 + c - S) / S) & 1u, g.spin_limit)) {
         ok = 0;
         break;
       }
-      consumed = c + 1;
+      if (half == 1 && c < C::PRE) continue;  // the first chunks' B halves were started at the barrier
+      mbar_expect_tx(fb, CB);
+      bulk_g2s(dst, src + (size_t)((c + g.stag) % NCH) * CB, CB, fb);  // position c holds chunk c + stag
+      last = c;
+    }
+    if (!ok) {
+      atomicExch(g.abort, 1u);
+      if (last >= 0) mbar_wait(fb, ((g0 + last) / S) & 1u, g.spin_limit);  // no copy left in flight
+    }
+  } else if (threadIdx.x == 0) {
+    constexpr uint32_t idesc = tc::idesc_f16_f32(128, 128);
+    for (int c = 0; c < NCH; c++) {
+      const uint32_t gc = g0 + c, st = gc % S, par = (gc / S) & 1u;
+      if (!mbar_wait(&full_a[st], par, g.spin_limit) || !mbar_wait(&full_b[st], par, g.spin_limit)) {
+        ok = 0;
+        break;
+      }
       tc::fence_after_sync();
       const uint32_t a0 = smem_u32(ring + (size_t)st * 2 * CB), b0 = a0 + CB;
 #pragma unroll
@@ -348,76 +375,65 @@ __device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, c
         tc::mma_f16(taddr, ad, bd, idesc, (c | ks) ? 1u : 0u);
       }
       tc::mma_commit(&empty[st]);
-      const int cn = c + S - 1;  // refill the stage of chunk c - 1 once its products are done
-      if (cn < NCH) {
-        if (c >= 1 && !mbar_wait(&empty[(gc - 1) % S], ((gc - 1) / S) & 1u, g.spin_limit)) {
-          ok = 0;
-          break;
-        }
-        load(cn);
-        issued++;
-      }
     }
     tc::mma_commit(done);
-    // on failure, still give the issued products and copies a bounded chance to finish before the
-    // tensor memory is reused or the block exits
+    // on failure, still give the issued products a bounded chance to finish before the tensor memory is
+    // reused or the block exits
     if (!mbar_wait(done, g.done_ph, g.spin_limit)) ok = 0;
-    if (!ok) {
-      atomicExch(g.abort, 1u);
-      for (int c = consumed; c < issued; c++)
-        mbar_wait(&full[(g0 + c) % S], ((g0 + c) / S) & 1u, g.spin_limit);
-    }
+    if (!ok) atomicExch(g.abort, 1u);
     g.mark(ph0);
   }
   g.chunk += NCH;
   g.done_ph ^= 1u;
   if (__syncthreads_or(!ok)) return false;
   tc::fence_after_sync();
-  // epilogue: warp w reads the lanes of slice a = w % 4 (its number = lane), columns of the channels
-  // 16h .. 16h+15 (h = w / 4) of all four matrix slices; combines the matrix slices, then the four
-  // warps of each half combine the data slices through shared memory
-  const int qa = g.w & 3, h = g.w >> 2;
+  // epilogue: warp w reads the accumulator lanes 32 q .. 32 q + 31 (q = w % 4): number n = 8q + lane/4,
+  // data slice a = lane % 4; columns of the channels 16h .. 16h+15 (h = w / 4) of all four matrix
+  // slices.  It combines the matrix slices, scales by 2^(7a), sums the four data slices across the
+  // four neighbouring lanes, and passes each sum through shared memory to the thread that owns its
+  // channel (thread (w', n): channels 4w' .. 4w'+3 of number n).
+  const int q = g.w & 3, h = g.w >> 2, a = g.lane & 3, n = 8 * q + (g.lane >> 2);
   uint64_t part[16];
 #pragma unroll
   for (int j = 0; j < 16; j++) part[j] = 0;
 #pragma unroll
   for (int b = 0; b < 4; b++) {
     uint32_t v[16];
-    tc::tmem_ld16(taddr + ((uint32_t)(32 * qa) << 16) + 32u * b + 16u * h, v);
+    tc::tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + 32u * b + 16u * h, v);
     tc::tmem_ld_wait();
 #pragma unroll
     for (int j = 0; j < 16; j++) part[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) << (7 * b);
   }
   uint64_t* ex = reinterpret_cast<uint64_t*>(g.s + C::SM_EX);
 #pragma unroll
-  for (int j = 0; j < 16; j++) ex[((qa * 2 + h) * 32 + g.lane) * C::EX_LS + j] = part[j] << (7 * qa);
+  for (int j = 0; j < 16; j++) {
+    uint64_t v = part[j] << (7 * a);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    if ((j >> 2) == a) ex[n * C::EX_LS + 16 * h + j] = v;  // lane a of the four publishes channels 4a .. 4a+3
+  }
   tc::fence_before_sync();
   __syncthreads();
-  const int jb = 4 * g.w - 16 * h;  // this thread's channels 4w .. 4w+3 within half h
 #pragma unroll
-  for (int s = 0; s < 4; s++) {
-    uint64_t v = 0;
-#pragma unroll
-    for (int q = 0; q < 4; q++) v += ex[((q * 2 + h) * 32 + g.lane) * C::EX_LS + jb + s];
-    acc[s] = v;
-  }
+  for (int s = 0; s < 4; s++) acc[s] = ex[g.lane * C::EX_LS + 4 * g.w + s];
   g.mark(ph0 + 1);
   return true;
 }
 
 template <class C>
-__device__ bool BigGroup<C>::barrier(const uint8_t* prefetch_b, const uint8_t* prefetch_a) {
+__device__ bool BigGroup<C>::barrier(const uint8_t* prefetch_b) {
   nbar++;
   // the ring's generic accesses (the exit conversion stages through it) before any copy into it
   if constexpr (C::TC) tc::fence_smem_async();
   __syncthreads();
+  if constexpr (C::TC) {
+    const int t = tc_copier<C>();
+    if (prefetch_b && t >= 0 && (t & 1)) tc_prefetch_b<C>(*this, prefetch_b, t >> 1);
+  }
   if (threadIdx.x == 0) {
     const uint32_t target = nbar * (uint32_t)C::SLICES;
     __threadfence();
     atomicAdd(ctr, 1u);
-    if constexpr (C::TC) {
-      if (prefetch_b) tc_prefetch_b<C>(*this, prefetch_b);
-    }
     uint32_t ok = 1;
     for (uint32_t it = 0;; it++) {
       uint32_t v;
@@ -434,13 +450,15 @@ __device__ bool BigGroup<C>::barrier(const uint8_t* prefetch_b, const uint8_t* p
       }
       if (it >= 2048) __nanosleep(128);  // poll at L2 latency first, then back off
     }
-    if constexpr (C::TC) {
-      if (!ok && prefetch_b) tc_drain_prefetch<C>(*this, prefetch_a);
-    }
     s[C::SM_MISC] = ok;
   }
   __syncthreads();
-  return s[C::SM_MISC] != 0;
+  const bool passed = s[C::SM_MISC] != 0;
+  if constexpr (C::TC) {
+    const int t = tc_copier<C>();
+    if (!passed && prefetch_b && t >= 0 && (t & 1)) tc_drain_prefetch<C>(*this, t >> 1);
+  }
+  return passed;
 }
 
 // RNS Montgomery multiplication x <- x*y*M^-1 mod N (outputs below (k+1)N), this thread's channels.
@@ -463,11 +481,10 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
     const uint4 cp = g.b4(q);
     sp[s] = redc_lazy(mulw(xp[s], yp[s]), cp.x, cp.y);
   }
-  const uint8_t *pre1 = nullptr, *pa1 = nullptr;
+  const uint8_t* pre1 = nullptr;
   if constexpr (C::TC) {
     tc_put_slices<C>(reinterpret_cast<uint8_t*>(g.slot + C::AG1), xv, g.c * C::SC + g.w * NPT, g.lane);
     pre1 = g.btab;
-    pa1 = reinterpret_cast<const uint8_t*>(g.slot + C::AG1);
   } else {
 #pragma unroll
     for (int s = 0; s < NPT; s++) {
@@ -476,7 +493,7 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
     }
   }
   g.mark(0);
-  if (!g.barrier(pre1, pa1)) return false;
+  if (!g.barrier(pre1)) return false;
   g.mark(1);
   // 3. extension B -> B'
   uint64_t acc[NPT];
@@ -516,13 +533,12 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
     for (int u = 0; u < C::NW; u++) v += g.s[C::SM_KAW + u * 32 + g.lane];
     KAWg[g.c * 32 + g.lane] = v;
   }
-  const uint8_t *pre2 = nullptr, *pa2 = nullptr;
+  const uint8_t* pre2 = nullptr;
   if constexpr (C::TC) {
     pre2 = g.btab + (size_t)C::NCH * C::CHUNK_BYTES;
-    pa2 = reinterpret_cast<const uint8_t*>(g.slot + C::AG2);
   }
   g.mark(4);
-  if (!g.barrier(pre2, pa2)) return false;
+  if (!g.barrier(pre2)) return false;
   g.mark(5);
   // 6. exact extension B' -> B with a' from the slice partials (loaded before the dot products,
   //    summed after them); the correction -a'|M'| enters as a' E with E = -M' 2^64 mod m_i
@@ -878,11 +894,13 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
   g.done_ph = 0;
   g.btab = nullptr;
   g.phases = a.phases;
+  g.stag = 0;
+  if constexpr (C::TC) g.stag = (uint32_t)(g.c + slot_id) % C::NCH;
   if (g.c == a.absent_slice) return;  // test hook: this slice never arrives; the others time out
   if (threadIdx.x == 0) {
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem_raw + C::SM_MBAR);
     int nmb = 2;  // staging copies of the integer form
-    if constexpr (C::TC) nmb = 2 * C::STAGES + 1;  // full and empty per stage, accumulator complete
+    if constexpr (C::TC) nmb = 3 * C::STAGES + 1;  // A full, B full and empty per stage, accumulator complete
     for (int i = 0; i < nmb; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mb[i])));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }

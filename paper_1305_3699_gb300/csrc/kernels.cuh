@@ -89,13 +89,12 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   if (t == 0) bad = less_than(it.x, it.x_limbs, it.xlim, it.xlim_limbs) ? 0u : 1u;
   bad = __shfl_sync(0xffffffffu, bad, lane - t);
 
-  uint32_t kxi[NPT], cmul[NPT], cd[NPT];
+  uint32_t kxi[NPT], cmul[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
     kxi[s] = o < C::K ? __ldg(key + ko.kxi + o) : 0u;
     cmul[s] = o < C::K ? __ldg(key + ko.cmul + o) : 0u;
-    cd[s] = o < C::K ? __ldg(key + ko.cd + o) : 0u;
   }
 
   // entry into the Montgomery domain: x~ = MM(x_lo, M^2 mod N) [+ MM(x_hi, 2^L M^2 mod N)]
@@ -103,14 +102,14 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   const int nl0 = bad ? 0 : (int)(it.x_limbs < (uint32_t)C::W ? it.x_limbs : C::W);
   to_rns<C>(xb, xp, it.x, nl0, a.cls, sm, t);
   load_vec<C>(yb, yp, key + ko.r2, t);
-  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
+  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
   const bool two = !bad && it.x_limbs > (uint32_t)C::W;
   if (__any_sync(0xffffffffu, two)) {
     uint32_t hb[NPT], hp[NPT];
     const int nl1 = two ? min((int)it.x_limbs - C::W, C::W) : 0;
     to_rns<C>(hb, hp, it.x + C::W, nl1, a.cls, sm, t);
     load_vec<C>(yb, yp, key + ko.r2h, t);
-    mont_mul<C>(hb, hp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
+    mont_mul<C>(hb, hp, yb, yp, kxi, cmul, sm, xib, xpb, t);
     add_vec<C>(xb, xp, hb, hp, sm, t);
   }
 
@@ -166,7 +165,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
     }
     const int iters = uni_t ? E : E - 2;
     for (int j = 0; j < iters; j++) {
-      mont_mul<C>(cb, cp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
+      mont_mul<C>(cb, cp, yb, yp, kxi, cmul, sm, xib, xpb, t);
       // opaque to the compiler: keeps one copy of the loop (no peeled first iteration)
       int first = (uni_t && j == 0) ? 1 : 0;
       asm volatile("" : "+r"(first));
@@ -250,7 +249,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
       } else {
         tab_load<C>(wt, d, yb, yp, lane);
       }
-      mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
+      mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
     }
   }
 
@@ -260,7 +259,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
     yb[s] = sm.cb4(t, s).z;  // hat form of 1 = 2^32 mod m
     yp[s] = sm.cp4(t, s).z;
   }
-  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
+  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
   from_rns_reduce<C>(xb, a.cls, key, sm, xib, t, it.out, (int)it.out_limbs, live && !bad);
   if (live && t == 0) {
     if (bad)
@@ -314,13 +313,12 @@ __global__ void __launch_bounds__(C::THREADS) crt_kernel(LaunchArgs a) {
   uint32_t* xib = sm.xi(item_in_block);
   uint32_t* xpb = xib + C::KP;
 
-  uint32_t kxi[NPT], cmul[NPT], cd[NPT];
+  uint32_t kxi[NPT], cmul[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
     kxi[s] = o < C::K ? __ldg(key + ko.kxi + o) : 0u;
     cmul[s] = o < C::K ? __ldg(key + ko.cmul + o) : 0u;
-    cd[s] = o < C::K ? __ldg(key + ko.cd + o) : 0u;
   }
   // d = m_p + P2 - m_q  (a positive integer below 3 * 2^L, congruent to m_p - m_q mod p)
   uint32_t db[NPT], dp[NPT], qb[NPT], qp[NPT], yb[NPT], yp[NPT];
@@ -338,7 +336,7 @@ __global__ void __launch_bounds__(C::THREADS) crt_kernel(LaunchArgs a) {
   }
   // h = MM(d, qinv M mod p) = d qinv mod p, then to binary in [0, p)
   load_vec<C>(yb, yp, it.crt + cro.qm, t);
-  mont_mul<C>(db, dp, yb, yp, kxi, cmul, cd, sm, xib, xpb, t);
+  mont_mul<C>(db, dp, yb, yp, kxi, cmul, sm, xib, xpb, t);
   uint32_t h[W];
   from_rns_reduce<C>(db, a.cls, key, sm, xib, t, h, W, true);
   // m = m_q + h q  (2W limbs)

@@ -19,7 +19,7 @@ namespace mr {
 constexpr int KAW_Q = 22;  // fixed-point bits of the B'->B correction estimate
 
 // ---------------------------------------------------------------- size class
-// [m 2k][mi 2k][r32 2k][ahat k][ad k][ubp k][mphh k][mmiinv k][ub k]
+// [m 2k][mi 2k][r32 2k][ahat k][ad k][ubp k][mphh k][mmiinv k][ub k][xpc k][xpcs k]
 // [T1 k*k][T2 k*k][P W*2k][MD k*WX][ML WX]
 //   m      channel prime
 //   mi     -m^-1 mod 2^32
@@ -30,13 +30,15 @@ constexpr int KAW_Q = 22;  // fixed-point bits of the B'->B correction estimate
 //   mphh   (B)  |M'|_{m_i} * 2^64 mod m_i          (REDC(a * mphh) = hat(a M'))
 //   mmiinv (B)  |(M/m_i)^-1|_{m_i} plain           (RNS -> binary)
 //   ub     (B)  floor(2^(32+Q) / m_i)
+//   xpc    (B') |(M'/m'_j)^-1|_{m'_j} * 2^-32 mod m'_j  (xi'_j from the hat residue r_j by Shoup's product)
+//   xpcs   (B') floor(xpc * 2^32 / m'_j)           (its quotient factor)
 //   T1     row i (B), column j (B'): |M/m_i|_{m'_j} * 2^64 mod m'_j
 //   T2     row j (B'), column i (B): |M'/m'_j|_{m_i} * 2^64 mod m_i
 //   P      row w (limb), column c: 2^(32 w) * 2^64 mod m_c   (binary -> hat residues)
 //   MD     row i: the WX limbs of M/m_i
 //   ML     the WX limbs of M
 struct ClassOff {
-  uint32_t m, mi, r32, ahat, ad, ubp, mphh, mmiinv, ub, T1, T2, P, MD, ML, total;
+  uint32_t m, mi, r32, ahat, ad, ubp, mphh, mmiinv, ub, xpc, xpcs, T1, T2, P, MD, ML, total;
 };
 
 // Tensor-core operand layout in shared memory (K-major, no swizzling; tc_device.cuh): byte offset
@@ -59,7 +61,9 @@ MR_HD constexpr inline ClassOff class_offsets(uint32_t k, uint32_t W, uint32_t W
   o.mphh = 9 * k;
   o.mmiinv = 10 * k;
   o.ub = 11 * k;
-  o.T1 = 12 * k;
+  o.xpc = 12 * k;
+  o.xpcs = 13 * k;
+  o.T1 = 14 * k;
   o.T2 = o.T1 + k * k;
   o.P = o.T2 + k * k;
   o.MD = o.P + W * 2 * k;

@@ -18,8 +18,9 @@
 // 64-bit register with one mad.wide.u32 per term (two issue slots of the
 // integer-multiply pipe, the cheapest exact 32x32->64 product; a carry-chain
 // accumulation costs more) and is reduced once.  Residues are kept in
-// per-channel Montgomery form x*2^32 mod m ("hat"); reductions use mad.wide
-// (no mul.hi).
+// per-channel Montgomery form x*2^32 mod m ("hat"); reductions use mad.wide;
+// one product by a per-class constant uses Shoup's precomputed quotient
+// (mad.hi and two mad.lo).
 #pragma once
 #include <cstdint>
 
@@ -96,17 +97,18 @@ struct Cfg {
   // shared memory, in 16-byte units where vectors live
   static constexpr int SM_T1 = 0;
   static constexpr int SM_T2 = SM_T1 + K * ROW;
-  static constexpr int SM_CB4 = SM_T2 + K * ROW;  // uint4 {m, mi, r32, mphh}   B
-  static constexpr int SM_CP4 = SM_CB4 + 4 * SL;  // uint4 {m, mi, r32, ahat}   B'
-  static constexpr int SM_CB2 = SM_CP4 + 4 * SL;  // uint2 {mmiinv, ub}         B
-  static constexpr int SM_CP2 = SM_CB2 + 2 * SL;  // uint2 {ad, ubp}            B'
-  static constexpr int SM_XI = SM_CP2 + 2 * SL;   // IPB x XS
+  static constexpr int SM_CB4 = SM_T2 + K * ROW;  // uint4 {m, mi, r32, mphh}        B
+  static constexpr int SM_CP4 = SM_CB4 + 4 * SL;  // uint4 {m, mi, r32, ahat}        B'
+  static constexpr int SM_CPX = SM_CP4 + 4 * SL;  // uint4 {ad, ubp, xpc, xpcs}      B'
+  static constexpr int SM_CB2 = SM_CPX + 4 * SL;  // uint2 {mmiinv, ub}              B
+  static constexpr int SM_XI = SM_CB2 + 2 * SL;   // IPB x XS
   static constexpr int SM_WORDS = SM_XI + IPB * XS;
   static constexpr int SMEM_BYTES = SM_WORDS * 4;
   static_assert(TPI == 1 || TPI == 2 || TPI == 4 || TPI == 8 || TPI == 16 || TPI == 32, "TPI must divide 32");
   static_assert(K >= 16, "k >= 16 keeps every channel prime below isqrt(2^64/16) = 2^30 (lazy reductions)");
   static_assert(VEC == 2 || VEC == 4, "vector width");
-  static_assert((SM_T2 % 4) == 0 && (SM_CB4 % 4) == 0 && (SM_CB2 % 2) == 0 && (SM_XI % 4) == 0, "alignment");
+  static_assert((SM_T2 % 4) == 0 && (SM_CB4 % 4) == 0 && (SM_CPX % 4) == 0 && (SM_CB2 % 2) == 0 && (SM_XI % 4) == 0,
+                "alignment");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 };
 
@@ -119,7 +121,7 @@ struct Smem {
   __device__ uint4 cb4(int t, int s) const { return reinterpret_cast<const uint4*>(base + C::SM_CB4)[t * C::NPTC + s]; }
   __device__ uint4 cp4(int t, int s) const { return reinterpret_cast<const uint4*>(base + C::SM_CP4)[t * C::NPTC + s]; }
   __device__ uint2 cb2(int t, int s) const { return reinterpret_cast<const uint2*>(base + C::SM_CB2)[t * C::NPTC + s]; }
-  __device__ uint2 cp2(int t, int s) const { return reinterpret_cast<const uint2*>(base + C::SM_CP2)[t * C::NPTC + s]; }
+  __device__ uint4 cpx(int t, int s) const { return reinterpret_cast<const uint4*>(base + C::SM_CPX)[t * C::NPTC + s]; }
   __device__ uint32_t* xi(int item_in_block) const { return base + C::SM_XI + item_in_block * C::XS; }
 };
 
@@ -142,7 +144,7 @@ __device__ void load_class_smem(const Smem<C>& sm, const uint32_t* cls) {
     uint32_t* cb4 = s + C::SM_CB4 + 4 * q;
     uint32_t* cp4 = s + C::SM_CP4 + 4 * q;
     uint32_t* cb2 = s + C::SM_CB2 + 2 * q;
-    uint32_t* cp2 = s + C::SM_CP2 + 2 * q;
+    uint32_t* cpx = s + C::SM_CPX + 4 * q;
     cb4[0] = ok ? cls[o.m + ch] : 0u;
     cb4[1] = ok ? cls[o.mi + ch] : 0u;
     cb4[2] = ok ? cls[o.r32 + ch] : 0u;
@@ -153,8 +155,10 @@ __device__ void load_class_smem(const Smem<C>& sm, const uint32_t* cls) {
     cp4[3] = ok ? cls[o.ahat + ch] : 0u;
     cb2[0] = ok ? cls[o.mmiinv + ch] : 0u;
     cb2[1] = ok ? cls[o.ub + ch] : 0u;
-    cp2[0] = ok ? cls[o.ad + ch] : 0u;
-    cp2[1] = ok ? cls[o.ubp + ch] : 0u;
+    cpx[0] = ok ? cls[o.ad + ch] : 0u;
+    cpx[1] = ok ? cls[o.ubp + ch] : 0u;
+    cpx[2] = ok ? cls[o.xpc + ch] : 0u;
+    cpx[3] = ok ? cls[o.xpcs + ch] : 0u;
   }
   for (int idx = threadIdx.x; idx < C::IPB * C::XS; idx += blockDim.x) s[C::SM_XI + idx] = 0u;
 }
@@ -208,15 +212,14 @@ __device__ __forceinline__ void ext_dot(uint64_t (&acc)[C::NPT], const uint32_t*
 // outputs below (k+1)N for operands whose product is below 4(k+1)^2 2^L N.
 //   xb, xp: hat residues of x in this lane's B and B' channels (in/out)
 //   yb, yp: hat residues of y (may alias xb, xp for a squaring)
-//   kxi:    |-N^-1 (M/m_i)^-1|_{m_i} plain, cmul: |N M^-1|_{m'_j} hat,
-//   cd:     |N M^-1 (M'/m'_j)^-1|_{m'_j} plain                         (per modulus)
+//   kxi:    |-N^-1 (M/m_i)^-1|_{m_i} plain, cmul: |N M^-1|_{m'_j} hat   (per modulus)
 //   xib, xpb: this number's xi / xi' exchange buffers in shared memory
 // ------------------------------------------------------------------------
 template <class C>
 __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], const uint32_t (&yb)[C::NPT],
                                          const uint32_t (&yp)[C::NPT], const uint32_t (&kxi)[C::NPT],
-                                         const uint32_t (&cmul)[C::NPT], const uint32_t (&cd)[C::NPT],
-                                         const Smem<C>& sm, uint32_t* xib, uint32_t* xpb, int t) {
+                                         const uint32_t (&cmul)[C::NPT], const Smem<C>& sm, uint32_t* xib,
+                                         uint32_t* xpb, int t) {
   constexpr int NPT = C::NPT, K = C::K;
   uint32_t sp[NPT];
   // 1-2. s = x*y in both bases; xi_i = s_i |-N^-1 (M/m_i)^-1| (plain CRT coefficients of q)
@@ -234,32 +237,34 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
   // 3. extension B -> B': qhat_j = sum_i xi_i |M/m_i|_{m'_j}   (k-term 64-bit dot products)
   uint64_t acc[NPT];
   ext_dot<C>(acc, xib, sm.T1(), t);
-  // 4-5. r_j = s_j |M^-1| + qhat_j |N M^-1| (hat, the new B' residues) and, from the same two
-  //      values, xi'_j = r_j |(M'/m'_j)^-1| = s_j |M^-1 (M'/m'_j)^-1| + qhat_j |N M^-1 (M'/m'_j)^-1| (plain)
+  // 4-5. r_j = s_j |M^-1| + qhat_j |N M^-1| (hat, the new B' residues), then xi'_j = r_j |(M'/m'_j)^-1|
+  //      (plain) from hat(r_j) by Shoup's product with the constant xpc = |(M'/m'_j)^-1| 2^-32 and its
+  //      quotient factor xpcs = floor(xpc 2^32 / m'_j): hat(r_j) xpc - floor(hat(r_j) xpcs / 2^32) m'_j
+  //      lies in [0, 2m'_j) (one mad.hi and two mad.lo instead of two products and a reduction)
   uint32_t kaw = 0;
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
     const uint4 cp = sm.cp4(t, s);
-    const uint2 c2 = sm.cp2(t, s);
+    const uint4 cx = sm.cpx(t, s);  // {ad, ubp, xpc, xpcs}
     uint32_t qh = redc64_lazy(acc[s], cp.x, cp.y, cp.z);  // [0, 2m'): only multiplied again
     xp[s] = redc(madw(sp[s], cp.w, mulw(qh, cmul[s])), cp.x, cp.y);
-    uint32_t xpj = redc(madw(sp[s], c2.x, mulw(qh, cd[s])), cp.x, cp.y);
+    const uint32_t u = xp[s] * cx.z - __umulhi(xp[s], cx.w) * cp.x;
+    const uint32_t xpj = min(u, u - cp.x);
     if (o < K) xpb[o] = xpj;
-    kaw += hi32(mulw(xpj, c2.y));  // floor(xi'_j 2^Q / m'_j), up to 2 units low
+    kaw += hi32(mulw(xpj, cx.y));  // floor(xi'_j 2^Q / m'_j), up to 2 units low
   }
   __syncwarp();
   // 6. extension B' -> B, exact: a' = floor(sum xi'_j / m'_j) from the fixed-point sum with a 1/4 offset
   const uint32_t alpha = (group_sum<C::TPI>(kaw) + (1u << (KAW_Q - 2))) >> KAW_Q;
   ext_dot<C>(acc, xpb, sm.T2(), t);
-  // r_i = t_i - a' |M'|_{m_i}  (hat, the new B residues)
+  // r_i = t_i - a' |M'|_{m_i}  (hat, the new B residues): the correction enters the accumulator as
+  // a' (m_i - mphh) before its one reduction (mphh = |M'| 2^64 mod m_i; the sum stays below
+  // k m (m + 1) <= 2^64 - 1 for the class's primes)
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const uint4 cb = sm.cb4(t, s);
-    uint32_t th = redc64(acc[s], cb.x, cb.y, cb.z);
-    uint32_t corr = redc(mulw(alpha, cb.w), cb.x, cb.y);
-    uint32_t r = th + cb.x - corr;
-    xb[s] = min(r, r - cb.x);
+    xb[s] = redc64(madw(alpha, cb.x - cb.w, acc[s]), cb.x, cb.y, cb.z);
   }
 }
 

@@ -167,6 +167,10 @@ bool build_class(uint32_t L, ClassHost& c, std::string& err) {
     blk[o.ahat + j] = mulmod32(c.Minv_Bp[j], r32[k + j], m);
     blk[o.ad + j] = mulmod32(c.Minv_Bp[j], c.Mp_mj_inv[j], m);
     blk[o.ubp + j] = (uint32_t)((1ull << (32 + KAW_Q)) / m);
+    const uint32_t rinv = powmod32(r32[k + j], m - 2, m);  // 2^-32 mod m (m prime, Fermat)
+    const uint32_t xpc = mulmod32(c.Mp_mj_inv[j], rinv, m);
+    blk[o.xpc + j] = xpc;
+    blk[o.xpcs + j] = (uint32_t)(((uint64_t)xpc << 32) / m);
   }
   for (uint32_t i = 0; i < k; i++) {
     uint32_t m = B[i];
