@@ -457,6 +457,20 @@ mr_status mr_debug_tc_slices(uint32_t class_bits, uint32_t *out, size_t capacity
 mr_status mr_debug_tc_mma(mr_ctx *ctx, const uint16_t *a, const uint16_t *b, uint32_t n, uint32_t kdim,
                           uint32_t swap_strides, float *d, void *stream);
 
+/* Constant-time exponentiation schedule (the paper's square-and-multiply with
+ * precomputation, Sec. 3.1, in a form whose memory addresses and branches do
+ * not depend on exponent bits).  on != 0: later calls on this context, and
+ * plans created while it is on, run the lane-group size classes (512 to 4096
+ * bits) with fixed windows over every limb of each exponent row (leading zero
+ * limbs included), a multiplication for every window (a zero digit multiplies
+ * by the Montgomery form of 1), no sliding windows, and table entries read by
+ * touching every entry and keeping the wanted one by masking.  Results are
+ * identical; the cost is the extra multiplications and table reads.  The
+ * window width is still chosen from the exponents' bit lengths, and the large
+ * classes (8192, 16384 bits) keep their direct table lookups.  on == 0
+ * restores the default.  Errors: MR_ERR_ARG. */
+mr_status mr_set_constant_time(mr_ctx *ctx, int on);
+
 /* Phase counters of the tensor-core form of the large classes (instrumentation,
  * off by default).  on != 0: later calls on this context add, per thread block
  * (its thread 0), the SM clock cycles spent in each phase of every RNS

@@ -88,6 +88,7 @@ struct mr_ctx {
   uint32_t big_spin_limit = 0;  // large-class barrier polls before giving up (0: the kernel default)
   int32_t big_absent_slice = -1;  // test hook of mr_debug_big_wait
   unsigned long long* big_phases = nullptr;  // mr_debug_big_phases: device counters, or nullptr (off)
+  bool constant_time = false;  // mr_set_constant_time
   std::vector<cudaStream_t> side;     // streams for concurrent groups of one-shot mixed calls
   std::vector<cudaEvent_t> side_join;
   cudaEvent_t side_fork = nullptr;
@@ -445,7 +446,7 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
     const KernelVariant& k = b.ce->kv();
     if (!b.mx.empty()) {
       LaunchArgs a{b.ce->dev, base + b.off_mx, (uint32_t)b.mx.size(), b.wbits,
-                   reinterpret_cast<uint32_t*>(base + b.off_scratch), status};
+                   reinterpret_cast<uint32_t*>(base + b.off_scratch), status, nullptr, ctx->constant_time ? 1u : 0u};
       unsigned grid = (unsigned)((b.mx.size() + k.ipb - 1) / k.ipb);
       e = timed_launch(ctx, 0, stream, [&] { return k.modexp(a, grid, stream); });
       if (e != cudaSuccess) break;
@@ -478,6 +479,7 @@ struct GroupLaunch {
   size_t off_mx = 0, off_crt = 0, off_scratch = 0, off_half = 0;
   uint32_t grid = 0, crt_grid = 0;
   bool persistent = false;
+  bool ct = false;              // constant-time schedule (the context's setting when the group was built)
 };
 
 double mm_products(uint32_t k) { return 2.0 * k * k + 7.0 * k; }
@@ -498,6 +500,7 @@ mr_status build_groups(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* op
     groups.emplace_back();
     groups.back().ce = ce;
     groups.back().wbits = w;
+    groups.back().ct = ctx->constant_time;
     return groups.back();
   };
   for (size_t i = 0; i < n; i++) {
@@ -638,7 +641,8 @@ mr_status enqueue_groups(mr_ctx* ctx, std::vector<GroupLaunch>& groups, char* ba
     const KernelVariant& kv = g.ce->kv();
     if (e == cudaSuccess && !g.mx.empty()) {
       LaunchArgs a{g.ce->dev, base + g.off_mx, (uint32_t)g.mx.size(), g.wbits,
-                   reinterpret_cast<uint32_t*>(base + g.off_scratch), status, g.persistent ? queues + gi : nullptr};
+                   reinterpret_cast<uint32_t*>(base + g.off_scratch), status, g.persistent ? queues + gi : nullptr,
+                   g.ct ? 1u : 0u};
       e = kv.modexp(a, g.grid, s);
       (*launches)++;
     }
@@ -1793,6 +1797,12 @@ mr_status mr_debug_tc_mma(mr_ctx* ctx, const uint16_t* a, const uint16_t* b, uin
   cudaError_t e = mr::tensor_debug_mma(a, b, n, kdim, swap_strides, d, (cudaStream_t)stream);
   if (e == cudaErrorLaunchTimeout) return fail(ctx, MR_ERR_TIMEOUT, "tensor product: completion wait ran out");
   return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "tensor product");
+}
+
+mr_status mr_set_constant_time(mr_ctx* ctx, int on) {
+  if (!ctx) return MR_ERR_ARG;
+  ctx->constant_time = on != 0;
+  return MR_OK;
 }
 
 mr_status mr_debug_big_phases(mr_ctx* ctx, int on, uint64_t* out) {

@@ -66,9 +66,9 @@ struct BigCfg {
 // D (32 numbers x 32 channels) = X (32 x k) T (k x 32) of the CRT coefficients with its columns of
 // the class's extension matrix, every entry below 2^28 and the exact sum below 2^64.  Both factors
 // are split into four 7-bit slices, X = sum_a 2^(7a) X_a and T = sum_b 2^(7b) T_b; A holds X_a[n]
-// in row 4n + a (128 x k) and B = [T_0 T_1 T_2 T_3] (k x 128), multiplied on the tensor cores in
+// in row 32a + n (128 x k) and B = [T_0 T_1 T_2 T_3] (k x 128), multiplied on the tensor cores in
 // fp16 with fp32 accumulation: every entry of A B is a sum of k products below 127^2, exact in fp32
-// for k <= 1040.  The recombination D = sum_{a,b} 2^(7(a+b)) (A B)[4n + a, 32b + j] is exact in 64
+// for k <= 1040.  The recombination D = sum_{a,b} 2^(7(a+b)) (A B)[32a + n, 32b + j] is exact in 64
 // bits.  A is written by the slot's CTAs (each its 32 channels, as fp16 slices in the shared-memory
 // operand layout of tc_device.cuh) into a per-slot buffer in global memory; B is a class table in
 // the same layout.  Each CTA streams both through a ring of STAGES shared-memory stages, 64 columns
@@ -76,9 +76,9 @@ struct BigCfg {
 // few hundred cycles whatever its size, so every stage has two copy threads of its own (its A half
 // and its B half, each on its own mbarrier); thread 0 waits for each chunk and issues its tcgen05
 // products (128 x 128 x 16 each) into a 128-column tensor-memory accumulator, and the tensor core's
-// completion frees the stage.  The epilogue reads the accumulator back (warp w: lanes of numbers
-// 8 (w % 4) .. +7, all four data slices), sums the data slices across neighbouring lanes with
-// shuffles, and hands every thread the same 64-bit dot products the integer form computes.
+// completion frees the stage.  The epilogue reads the accumulator back (warp w: the lanes of data
+// slice w % 4), combines the slices through shared memory and hands every thread the same 64-bit
+// dot products the integer form computes.
 // Everything else is the integer kernel's.
 template <int K_, int W_, int WX_>
 struct BigTcCfg {
@@ -90,16 +90,16 @@ struct BigTcCfg {
   static constexpr int KC = 64;                       // columns of k per staged chunk
   static constexpr int NCH = (K + KC - 1) / KC;       // chunks per extension
   static constexpr int KP = NCH * KC;                 // padded k
-  static constexpr int STAGES = 6;                    // ring stages, two copy threads each
+  static constexpr int STAGES = 4;                    // ring stages, two copy threads each
   static constexpr int PRE = (STAGES < NCH) ? STAGES : NCH;  // chunks whose B is fetched at the barrier
   static constexpr uint32_t CHUNK_BYTES = 128u * KC * 2u;  // one operand chunk: 128 rows x 64 fp16
   static constexpr uint32_t TMEM_COLS = 128;
-  static constexpr int EX_LS = 33;                    // exchange: 64-bit words per number (32 + 1 pad)
+  static constexpr int EX_LS = 17;                    // exchange: 64-bit words per lane (16 + 1 pad)
   // shared memory (words)
   static constexpr int SM_RING = 0;                   // STAGES x [A chunk | B chunk]
   static constexpr int SM_T1 = SM_RING;               // staging area of the RNS -> binary conversion
-  static constexpr int SM_EX = SM_RING + STAGES * 2 * (int)CHUNK_BYTES / 4;  // [32 numbers][EX_LS] u64
-  static constexpr int SM_C4A = SM_EX + 32 * EX_LS * 2;
+  static constexpr int SM_EX = SM_RING + STAGES * 2 * (int)CHUNK_BYTES / 4;  // [4 a][2 halves][32][EX_LS] u64
+  static constexpr int SM_C4A = SM_EX + 4 * 2 * 32 * EX_LS * 2;
   static constexpr int SM_C4B = SM_C4A + 4 * SC;
   static constexpr int SM_C2A = SM_C4B + 4 * SC;
   static constexpr int SM_C2B = SM_C2A + 2 * SC;
@@ -247,7 +247,7 @@ __device__ bool big_ext(uint64_t (&acc)[C::NPT], BigGroup<C>& g, const uint32_t*
 }
 
 // Tensor-core form: this thread's four CRT coefficients (channels o0 .. o0+3 of number `lane`) as four
-// 7-bit fp16 slices into the A operand `aop` of an extension: row 4 lane + a, columns o0 .. o0+3 of
+// 7-bit fp16 slices into the A operand `aop` of an extension: row 32a + lane, columns o0 .. o0+3 of
 // slice a (one 8-byte store per slice; o0 is a multiple of 4).
 template <class C>
 __device__ __forceinline__ void tc_put_slices(uint8_t* aop, const uint32_t (&v)[4], int o0, int lane) {
@@ -259,7 +259,7 @@ __device__ __forceinline__ void tc_put_slices(uint8_t* aop, const uint32_t (&v)[
 #pragma unroll
     for (int s = 0; s < 4; s++) h[s] = __half_as_ushort(__uint2half_rn((v[s] >> (7 * a)) & 127u));
     const uint2 pk = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-    *reinterpret_cast<uint2*>(chunk + tc::tile_off(128, 4u * lane + a, col)) = pk;
+    *reinterpret_cast<uint2*>(chunk + tc::tile_off(128, 32u * a + lane, col)) = pk;
   }
 }
 
@@ -387,35 +387,34 @@ __device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, c
   g.done_ph ^= 1u;
   if (__syncthreads_or(!ok)) return false;
   tc::fence_after_sync();
-  // epilogue: warp w reads the accumulator lanes 32 q .. 32 q + 31 (q = w % 4): number n = 8q + lane/4,
-  // data slice a = lane % 4; columns of the channels 16h .. 16h+15 (h = w / 4) of all four matrix
-  // slices.  It combines the matrix slices, scales by 2^(7a), sums the four data slices across the
-  // four neighbouring lanes, and passes each sum through shared memory to the thread that owns its
-  // channel (thread (w', n): channels 4w' .. 4w'+3 of number n).
-  const int q = g.w & 3, h = g.w >> 2, a = g.lane & 3, n = 8 * q + (g.lane >> 2);
+  // epilogue: warp w reads the lanes of data slice a = w % 4 (its number = lane), columns of the channels
+  // 16h .. 16h+15 (h = w / 4) of all four matrix slices; combines the matrix slices, then the four
+  // warps of each half combine the data slices through shared memory
+  const int qa = g.w & 3, h = g.w >> 2;
   uint64_t part[16];
 #pragma unroll
   for (int j = 0; j < 16; j++) part[j] = 0;
 #pragma unroll
   for (int b = 0; b < 4; b++) {
     uint32_t v[16];
-    tc::tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + 32u * b + 16u * h, v);
+    tc::tmem_ld16(taddr + ((uint32_t)(32 * qa) << 16) + 32u * b + 16u * h, v);
     tc::tmem_ld_wait();
 #pragma unroll
     for (int j = 0; j < 16; j++) part[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) << (7 * b);
   }
   uint64_t* ex = reinterpret_cast<uint64_t*>(g.s + C::SM_EX);
 #pragma unroll
-  for (int j = 0; j < 16; j++) {
-    uint64_t v = part[j] << (7 * a);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    if ((j >> 2) == a) ex[n * C::EX_LS + 16 * h + j] = v;  // lane a of the four publishes channels 4a .. 4a+3
-  }
+  for (int j = 0; j < 16; j++) ex[((qa * 2 + h) * 32 + g.lane) * C::EX_LS + j] = part[j] << (7 * qa);
   tc::fence_before_sync();
   __syncthreads();
+  const int jb = 4 * g.w - 16 * h;  // this thread's channels 4w .. 4w+3 within half h
 #pragma unroll
-  for (int s = 0; s < 4; s++) acc[s] = ex[g.lane * C::EX_LS + 4 * g.w + s];
+  for (int s = 0; s < 4; s++) {
+    uint64_t v = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) v += ex[((q * 2 + h) * 32 + g.lane) * C::EX_LS + jb + s];
+    acc[s] = v;
+  }
   g.mark(ph0 + 1);
   return true;
 }

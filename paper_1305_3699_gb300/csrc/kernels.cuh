@@ -69,6 +69,32 @@ __device__ __forceinline__ void tab_load(const uint32_t* wt, int ent, uint32_t (
   }
 }
 
+// Constant-time form: reads all E entries and keeps entry `ent` by masking, so that neither the
+// addresses nor the branches depend on the (secret) index.
+template <class C>
+__device__ __forceinline__ void tab_load_ct(const uint32_t* wt, uint32_t ent, int E, uint32_t (&b)[C::NPT],
+                                            uint32_t (&p)[C::NPT], int lane) {
+#pragma unroll
+  for (int s = 0; s < C::NPT; s++) b[s] = p[s] = 0u;
+  for (int j = 0; j < E; j++) {
+    const uint32_t mask = 0u - (uint32_t)((uint32_t)j == ent);  // all ones for the wanted entry
+    const uint32_t* base = wt + (size_t)j * (2 * C::NPT) * 32 + lane;
+#pragma unroll
+    for (int s = 0; s < C::NPT; s++) {
+      b[s] |= base[s * 32] & mask;
+      p[s] |= base[(C::NPT + s) * 32] & mask;
+    }
+  }
+}
+
+// Table lookup of the exponentiation loop: masked over every entry when `ct`, else direct.
+template <class C>
+__device__ __forceinline__ void tab_get(const uint32_t* wt, uint32_t ent, int E, bool ct, uint32_t (&b)[C::NPT],
+                                        uint32_t (&p)[C::NPT], int lane) {
+  if (ct) tab_load_ct<C>(wt, ent, E, b, p, lane);
+  else tab_load<C>(wt, (int)ent, b, p, lane);
+}
+
 // One exponentiation per lane group (x^e mod N of work item g_raw); all lanes of the warp call it
 // together.  wt: this warp's window-table scratch.
 template <class C>
@@ -89,11 +115,12 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   if (t == 0) bad = less_than(it.x, it.x_limbs, it.xlim, it.xlim_limbs) ? 0u : 1u;
   bad = __shfl_sync(0xffffffffu, bad, lane - t);
 
-  uint32_t kxi[NPT], cmul[NPT];
+  uint32_t kxp[NPT], kxs[NPT], cmul[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
-    kxi[s] = o < C::K ? __ldg(key + ko.kxi + o) : 0u;
+    kxp[s] = o < C::K ? __ldg(key + ko.kxp + o) : 0u;
+    kxs[s] = o < C::K ? __ldg(key + ko.kxs + o) : 0u;
     cmul[s] = o < C::K ? __ldg(key + ko.cmul + o) : 0u;
   }
 
@@ -102,14 +129,14 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   const int nl0 = bad ? 0 : (int)(it.x_limbs < (uint32_t)C::W ? it.x_limbs : C::W);
   to_rns<C>(xb, xp, it.x, nl0, a.cls, sm, t);
   load_vec<C>(yb, yp, key + ko.r2, t);
-  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
   const bool two = !bad && it.x_limbs > (uint32_t)C::W;
   if (__any_sync(0xffffffffu, two)) {
     uint32_t hb[NPT], hp[NPT];
     const int nl1 = two ? min((int)it.x_limbs - C::W, C::W) : 0;
     to_rns<C>(hb, hp, it.x + C::W, nl1, a.cls, sm, t);
     load_vec<C>(yb, yp, key + ko.r2h, t);
-    mont_mul<C>(hb, hp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+    mont_mul<C>(hb, hp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
     add_vec<C>(xb, xp, hb, hp, sm, t);
   }
 
@@ -119,13 +146,17 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   // bits are used (left to right: a run of zero bits costs squarings only, a window starts and
   // ends on a set bit, so only odd powers are tabulated; about 4% fewer multiplications than fixed
   // windows for 1024-bit exponents, same table size).  Otherwise fixed wb-bit windows.
+  // Constant-time calls (a.ct): a regular schedule that depends on no exponent bit -- fixed windows
+  // over every limb of the exponent row, each window multiplied (entry 0 is the Montgomery form of
+  // 1), table entries read by masking -- instead of the data-dependent shortcuts below.
+  const bool ct = a.ct != 0;
   const int wb = (int)a.wbits, E = 1 << wb;
   const uint32_t el = it.e_limbs;
   uint32_t ebits = 0;
-  if (t == 0) ebits = bad ? 0u : exp_bits(it.e, el);
+  if (t == 0) ebits = bad ? 0u : (ct ? 32u * el : exp_bits(it.e, el));
   ebits = __shfl_sync(0xffffffffu, ebits, lane - t);
   bool uni = false;
-  if (wb >= 4) {
+  if (wb >= 4 && !ct) {
     const uint32_t* e0 = reinterpret_cast<const uint32_t*>(
         __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(it.e), 0));
     const uint32_t eb0 = __shfl_sync(0xffffffffu, ebits, 0);
@@ -165,7 +196,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
     }
     const int iters = uni_t ? E : E - 2;
     for (int j = 0; j < iters; j++) {
-      mont_mul<C>(cb, cp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+      mont_mul<C>(cb, cp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
       // opaque to the compiler: keeps one copy of the loop (no peeled first iteration)
       int first = (uni_t && j == 0) ? 1 : 0;
       asm volatile("" : "+r"(first));
@@ -195,7 +226,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   int cur = uni_f ? lo_first : (int)nwin - 2;
   asm volatile("" : "+r"(cur), "+r"(d));  // opaque start values: the loop is not peeled
   __syncwarp();
-  tab_load<C>(wt, d, xb, xp, lane);
+  tab_get<C>(wt, d, E, ct, xb, xp, lane);
   // each step: nsq squarings (a squaring passes x as both operands), then, when the step has a
   // window (fixed: any number of the warp has a non-zero digit), one multiplication by its entry
   for (;;) {
@@ -233,7 +264,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
       if (cur < 0) break;
       nsq = wb;
       d = bad ? 0u : exp_digit(it.e, el, (uint32_t)cur * wb, wb);
-      mul = __any_sync(0xffffffffu, d != 0);
+      mul = ct || __any_sync(0xffffffffu, d != 0);  // (ct is uniform: every lane takes the same path)
       cur--;
     }
     // one multiplication site for the squarings and the window product (the second operand is a
@@ -247,9 +278,9 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
           yp[s] = xp[s];
         }
       } else {
-        tab_load<C>(wt, d, yb, yp, lane);
+        tab_get<C>(wt, d, E, ct, yb, yp, lane);
       }
-      mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+      mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
     }
   }
 
@@ -259,7 +290,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
     yb[s] = sm.cb4(t, s).z;  // hat form of 1 = 2^32 mod m
     yp[s] = sm.cp4(t, s).z;
   }
-  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
   from_rns_reduce<C>(xb, a.cls, key, sm, xib, t, it.out, (int)it.out_limbs, live && !bad);
   if (live && t == 0) {
     if (bad)
@@ -313,11 +344,12 @@ __global__ void __launch_bounds__(C::THREADS) crt_kernel(LaunchArgs a) {
   uint32_t* xib = sm.xi(item_in_block);
   uint32_t* xpb = xib + C::KP;
 
-  uint32_t kxi[NPT], cmul[NPT];
+  uint32_t kxp[NPT], kxs[NPT], cmul[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
-    kxi[s] = o < C::K ? __ldg(key + ko.kxi + o) : 0u;
+    kxp[s] = o < C::K ? __ldg(key + ko.kxp + o) : 0u;
+    kxs[s] = o < C::K ? __ldg(key + ko.kxs + o) : 0u;
     cmul[s] = o < C::K ? __ldg(key + ko.cmul + o) : 0u;
   }
   // d = m_p + P2 - m_q  (a positive integer below 3 * 2^L, congruent to m_p - m_q mod p)
@@ -336,7 +368,7 @@ __global__ void __launch_bounds__(C::THREADS) crt_kernel(LaunchArgs a) {
   }
   // h = MM(d, qinv M mod p) = d qinv mod p, then to binary in [0, p)
   load_vec<C>(yb, yp, it.crt + cro.qm, t);
-  mont_mul<C>(db, dp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  mont_mul<C>(db, dp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
   uint32_t h[W];
   from_rns_reduce<C>(db, a.cls, key, sm, xib, t, h, W, true);
   // m = m_q + h q  (2W limbs)

@@ -17,6 +17,8 @@ struct LaunchArgs {
   uint32_t* scratch;     // window tables (modexp): per warp (1 << wbits) x 2 NPT x 32 words
   uint8_t* status;       // per-item status bytes or nullptr
   uint32_t* queue;       // persistent mode: work-group counter (zeroed before the launch), else nullptr
+  uint32_t ct;           // modexp: 1 = constant-time schedule (regular fixed windows over every exponent
+                         // limb, every window multiplied, table entries selected by masking)
 };
 
 struct MRArgs {

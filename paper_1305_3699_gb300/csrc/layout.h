@@ -17,9 +17,10 @@
 namespace mr {
 
 constexpr int KAW_Q = 22;  // fixed-point bits of the B'->B correction estimate
+constexpr int KAW_S = 17;  // the lane-group kernels weight xi' >> KAW_S (one 32-bit product per channel)
 
 // ---------------------------------------------------------------- size class
-// [m 2k][mi 2k][r32 2k][ahat k][ad k][ubp k][mphh k][mmiinv k][ub k][xpc k][xpcs k]
+// [m 2k][mi 2k][r32 2k][ahat k][ad k][ubp k][mphh k][mmiinv k][ub k][xpc k][xpcs k][ubs k]
 // [T1 k*k][T2 k*k][P W*2k][MD k*WX][ML WX]
 //   m      channel prime
 //   mi     -m^-1 mod 2^32
@@ -32,13 +33,14 @@ constexpr int KAW_Q = 22;  // fixed-point bits of the B'->B correction estimate
 //   ub     (B)  floor(2^(32+Q) / m_i)
 //   xpc    (B') |(M'/m'_j)^-1|_{m'_j} * 2^-32 mod m'_j  (xi'_j from the hat residue r_j by Shoup's product)
 //   xpcs   (B') floor(xpc * 2^32 / m'_j)           (its quotient factor)
+//   ubs    (B') floor(2^(Q+17) / m'_j)             (factor weights from the top bits: (xi' >> 17) ubs)
 //   T1     row i (B), column j (B'): |M/m_i|_{m'_j} * 2^64 mod m'_j
 //   T2     row j (B'), column i (B): |M'/m'_j|_{m_i} * 2^64 mod m_i
 //   P      row w (limb), column c: 2^(32 w) * 2^64 mod m_c   (binary -> hat residues)
 //   MD     row i: the WX limbs of M/m_i
 //   ML     the WX limbs of M
 struct ClassOff {
-  uint32_t m, mi, r32, ahat, ad, ubp, mphh, mmiinv, ub, xpc, xpcs, T1, T2, P, MD, ML, total;
+  uint32_t m, mi, r32, ahat, ad, ubp, mphh, mmiinv, ub, xpc, xpcs, ubs, T1, T2, P, MD, ML, total;
 };
 
 // Tensor-core operand layout in shared memory (K-major, no swizzling; tc_device.cuh): byte offset
@@ -63,7 +65,8 @@ MR_HD constexpr inline ClassOff class_offsets(uint32_t k, uint32_t W, uint32_t W
   o.ub = 11 * k;
   o.xpc = 12 * k;
   o.xpcs = 13 * k;
-  o.T1 = 14 * k;
+  o.ubs = 14 * k;
+  o.T1 = 15 * k;
   o.T2 = o.T1 + k * k;
   o.P = o.T2 + k * k;
   o.MD = o.P + W * 2 * k;
@@ -73,18 +76,20 @@ MR_HD constexpr inline ClassOff class_offsets(uint32_t k, uint32_t W, uint32_t W
 }
 
 // ------------------------------------------------------------------ modulus
-// [hdr 4][kxi k][cmul k][cd k][one 2k][r2 2k][r2h 2k][N W][exp W]
+// [hdr 4][kxi k][cmul k][cd k][kxp k][kxs k][one 2k][r2 2k][r2h 2k][N W][exp W]
 //   hdr    nbits(N), nlimbs(N), exp_bits (private exponent bit length or 0), 0
 //   kxi    (B)  |-N^-1 (M/m_i)^-1|_{m_i} plain
 //   cmul   (B') |N M^-1|_{m'_j} hat
 //   cd     (B') |N M^-1 (M'/m'_j)^-1|_{m'_j} plain
+//   kxp    (B)  kxi * 2^-32 mod m_i          (xi_i from hat(s_i) by Shoup's product)
+//   kxs    (B)  floor(kxp * 2^32 / m_i)      (its quotient factor)
 //   one    hat residues of M mod N           (1 in the Montgomery domain)
 //   r2     hat residues of M^2 mod N         (entry into the domain)
 //   r2h    hat residues of 2^L M^2 mod N     (entry of the high chunk of a 2L-bit input)
 //   N      W limbs of the modulus
 //   exp    W limbs: private CRT exponent (dp or dq) of an RSA half, zero otherwise
 struct KeyOff {
-  uint32_t hdr, kxi, cmul, cd, one, r2, r2h, N, exp, total;
+  uint32_t hdr, kxi, cmul, cd, kxp, kxs, one, r2, r2h, N, exp, total;
 };
 
 MR_HD constexpr inline KeyOff key_offsets(uint32_t k, uint32_t W) {
@@ -93,7 +98,9 @@ MR_HD constexpr inline KeyOff key_offsets(uint32_t k, uint32_t W) {
   o.kxi = 4;
   o.cmul = o.kxi + k;
   o.cd = o.cmul + k;
-  o.one = o.cd + k;
+  o.kxp = o.cd + k;
+  o.kxs = o.kxp + k;
+  o.one = o.kxs + k;
   o.r2 = o.one + 2 * k;
   o.r2h = o.r2 + 2 * k;
   o.N = o.r2h + 2 * k;

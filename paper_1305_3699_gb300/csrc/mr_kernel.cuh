@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
   __syncwarp();
 
   // 2. residues of N and the per-channel constants
-  uint32_t nb[NPT], np[NPT], kxi[NPT], cmul[NPT], cd[NPT], invb[NPT], invp[NPT];
+  uint32_t nb[NPT], np[NPT], kxi[NPT], kxp[NPT], kxs[NPT], cmul[NPT], cd[NPT], invb[NPT], invp[NPT];
   to_rns<C>(nb, np, N, special ? 0 : (int)min(nl, (uint32_t)W), a.cls, sm, t);
   bool coprime = true;
 #pragma unroll
@@ -214,6 +214,9 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
     // |-N^-1 (M/m_i)^-1|_{m_i} plain = REDC(hat(-N^-1) * |(M/m_i)^-1|)
     const uint32_t nib = ib == 0 ? 0u : cb.x - ib;
     kxi[s] = redc(mulw(nib, c2.x), cb.x, cb.y);
+    // Shoup pair of the multiplication: kxp = kxi 2^-32 mod m_i, kxs = floor(kxp 2^32 / m_i)
+    kxp[s] = redc(kxi[s], cb.x, cb.y);
+    kxs[s] = cb.x ? (uint32_t)(((uint64_t)kxp[s] << 32) / cb.x) : 0u;
     // |N M^-1|_{m'_j} hat = REDC(hat(N) * hat(M^-1)); |N M^-1 (M'/m'_j)^-1| plain = REDC(hat(N) * ad)
     cmul[s] = redc(mulw(np[s], cp.w), cp.x, cp.y);
     cd[s] = redc(mulw(np[s], sm.cpx(t, s).x), cp.x, cp.y);  // published by the test hook only
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
     const uint32_t* wit = a.witness + ((size_t)cidx * a.rounds + r) * nl;
     uint32_t xb[NPT], xp[NPT], yb[NPT], yp[NPT];
     to_rns<C>(xb, xp, wit, special ? 0 : (int)min(nl, (uint32_t)W), a.cls, sm, t);
-    mont_mul<C>(xb, xp, r2b, r2p, kxi, cmul, sm, xib, xpb, t);  // a~ = a M mod N
+    mont_mul<C>(xb, xp, r2b, r2p, kxp, kxs, cmul, sm, xib, xpb, t);  // a~ = a M mod N
     tab_store<C>(wt, 0, oneb, onep, lane);
     tab_store<C>(wt, 1, xb, xp, lane);
     {
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
         cp[s] = xp[s];
       }
       for (int j = 2; j < E; j++) {
-        mont_mul<C>(cb, cp, xb, xp, kxi, cmul, sm, xib, xpb, t);
+        mont_mul<C>(cb, cp, xb, xp, kxp, kxs, cmul, sm, xib, xpb, t);
         tab_store<C>(wt, j, cb, cp, lane);
       }
     }
@@ -286,11 +289,11 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
     __syncwarp();
     tab_load<C>(wt, d, xb, xp, lane);
     for (int widx = (int)nwin - 2; widx >= 0; widx--) {
-      for (int q = 0; q < wb; q++) mont_mul<C>(xb, xp, xb, xp, kxi, cmul, sm, xib, xpb, t);
+      for (int q = 0; q < wb; q++) mont_mul<C>(xb, xp, xb, xp, kxp, kxs, cmul, sm, xib, xpb, t);
       d = special ? 0u : exp_digit(N, nl, sbits + (uint32_t)widx * wb, (uint32_t)wb);
       if (__any_sync(0xffffffffu, d != 0)) {
         tab_load<C>(wt, d, yb, yp, lane);
-        mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+        mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
       }
     }
     // y == 1: y~ + (N - M mod N) is a multiple of N
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(C::THREADS) mr_kernel(MRArgs a) {
       if (i < my_s && m1) pass = true;
       const bool finished = pass || i + 1 >= my_s;
       if (__all_sync(0xffffffffu, finished)) break;
-      mont_mul<C>(xb, xp, xb, xp, kxi, cmul, sm, xib, xpb, t);
+      mont_mul<C>(xb, xp, xb, xp, kxp, kxs, cmul, sm, xib, xpb, t);
     }
     if (pass && r < 32) mask |= 1u << r;
     all_pass = all_pass && pass;

@@ -68,11 +68,12 @@ __global__ void __launch_bounds__(C::THREADS) modexp_packed_kernel(PackedArgs a)
   if (t == 0) bad = less_than(x, a.x_stride, key + ko.N, C::W) ? 0u : 1u;
   bad = __shfl_sync(0xffffffffu, bad, lane - t);
 
-  uint32_t kxi[NPT], cmul[NPT];
+  uint32_t kxp[NPT], kxs[NPT], cmul[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
-    kxi[s] = o < C::K ? __ldg(key + ko.kxi + o) : 0u;
+    kxp[s] = o < C::K ? __ldg(key + ko.kxp + o) : 0u;
+    kxs[s] = o < C::K ? __ldg(key + ko.kxs + o) : 0u;
     cmul[s] = o < C::K ? __ldg(key + ko.cmul + o) : 0u;
   }
 
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(C::THREADS) modexp_packed_kernel(PackedArgs a)
   const int nl0 = bad ? 0 : (int)(a.x_stride < (uint32_t)C::W ? a.x_stride : C::W);
   to_rns<C>(xb, xp, x, nl0, a.cls, sm, t);
   load_vec<C>(yb, yp, key + ko.r2, t);
-  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
 
   const int wb = (int)a.wbits, E = 1 << wb;
   load_vec<C>(yb, yp, key + ko.one, t);
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(C::THREADS) modexp_packed_kernel(PackedArgs a)
       cp[s] = xp[s];
     }
     for (int j = 2; j < E; j++) {
-      mont_mul<C>(cb, cp, xb, xp, kxi, cmul, sm, xib, xpb, t);
+      mont_mul<C>(cb, cp, xb, xp, kxp, kxs, cmul, sm, xib, xpb, t);
       tab_store<C>(wt, j, cb, cp, lane);
     }
   }
@@ -108,11 +109,11 @@ __global__ void __launch_bounds__(C::THREADS) modexp_packed_kernel(PackedArgs a)
   __syncwarp();
   tab_load<C>(wt, d, xb, xp, lane);
   for (int widx = (int)nwin - 2; widx >= 0; widx--) {
-    for (int q = 0; q < wb; q++) mont_mul<C>(xb, xp, xb, xp, kxi, cmul, sm, xib, xpb, t);
+    for (int q = 0; q < wb; q++) mont_mul<C>(xb, xp, xb, xp, kxp, kxs, cmul, sm, xib, xpb, t);
     d = bad ? 0u : exp_digit(e, a.e_stride, (uint32_t)widx * wb, wb);
     if (__any_sync(0xffffffffu, d != 0)) {
       tab_load<C>(wt, d, yb, yp, lane);
-      mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+      mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
     }
   }
 
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(C::THREADS) modexp_packed_kernel(PackedArgs a)
     yb[s] = sm.cb4(t, s).z;
     yp[s] = sm.cp4(t, s).z;
   }
-  mont_mul<C>(xb, xp, yb, yp, kxi, cmul, sm, xib, xpb, t);
+  mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
   from_rns_reduce<C>(xb, a.cls, key, sm, xib, t, out, (int)a.out_stride, live && !bad);
   if (live && t == 0) {
     if (bad)

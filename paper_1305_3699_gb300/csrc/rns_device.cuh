@@ -99,7 +99,7 @@ struct Cfg {
   static constexpr int SM_T2 = SM_T1 + K * ROW;
   static constexpr int SM_CB4 = SM_T2 + K * ROW;  // uint4 {m, mi, r32, mphh}        B
   static constexpr int SM_CP4 = SM_CB4 + 4 * SL;  // uint4 {m, mi, r32, ahat}        B'
-  static constexpr int SM_CPX = SM_CP4 + 4 * SL;  // uint4 {ad, ubp, xpc, xpcs}      B'
+  static constexpr int SM_CPX = SM_CP4 + 4 * SL;  // uint4 {ad, ubs, xpc, xpcs}      B'
   static constexpr int SM_CB2 = SM_CPX + 4 * SL;  // uint2 {mmiinv, ub}              B
   static constexpr int SM_XI = SM_CB2 + 2 * SL;   // IPB x XS
   static constexpr int SM_WORDS = SM_XI + IPB * XS;
@@ -156,7 +156,7 @@ __device__ void load_class_smem(const Smem<C>& sm, const uint32_t* cls) {
     cb2[0] = ok ? cls[o.mmiinv + ch] : 0u;
     cb2[1] = ok ? cls[o.ub + ch] : 0u;
     cpx[0] = ok ? cls[o.ad + ch] : 0u;
-    cpx[1] = ok ? cls[o.ubp + ch] : 0u;
+    cpx[1] = ok ? cls[o.ubs + ch] : 0u;
     cpx[2] = ok ? cls[o.xpc + ch] : 0u;
     cpx[3] = ok ? cls[o.xpcs + ch] : 0u;
   }
@@ -212,14 +212,15 @@ __device__ __forceinline__ void ext_dot(uint64_t (&acc)[C::NPT], const uint32_t*
 // outputs below (k+1)N for operands whose product is below 4(k+1)^2 2^L N.
 //   xb, xp: hat residues of x in this lane's B and B' channels (in/out)
 //   yb, yp: hat residues of y (may alias xb, xp for a squaring)
-//   kxi:    |-N^-1 (M/m_i)^-1|_{m_i} plain, cmul: |N M^-1|_{m'_j} hat   (per modulus)
+//   kxp:    |-N^-1 (M/m_i)^-1|_{m_i} 2^-32, kxs = floor(kxp 2^32 / m_i) (Shoup pair),
+//   cmul:   |N M^-1|_{m'_j} hat                                          (per modulus)
 //   xib, xpb: this number's xi / xi' exchange buffers in shared memory
 // ------------------------------------------------------------------------
 template <class C>
 __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], const uint32_t (&yb)[C::NPT],
-                                         const uint32_t (&yp)[C::NPT], const uint32_t (&kxi)[C::NPT],
-                                         const uint32_t (&cmul)[C::NPT], const Smem<C>& sm, uint32_t* xib,
-                                         uint32_t* xpb, int t) {
+                                         const uint32_t (&yp)[C::NPT], const uint32_t (&kxp)[C::NPT],
+                                         const uint32_t (&kxs)[C::NPT], const uint32_t (&cmul)[C::NPT],
+                                         const Smem<C>& sm, uint32_t* xib, uint32_t* xpb, int t) {
   constexpr int NPT = C::NPT, K = C::K;
   uint32_t sp[NPT];
   // 1-2. s = x*y in both bases; xi_i = s_i |-N^-1 (M/m_i)^-1| (plain CRT coefficients of q)
@@ -227,8 +228,10 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
   for (int s = 0; s < NPT; s++) {
     const int o = t * NPT + s;
     const uint4 cb = sm.cb4(t, s);
-    uint32_t sb = redc_lazy(mulw(xb[s], yb[s]), cb.x, cb.y);  // [0, 2m): only multiplied again
-    uint32_t xi = redc(mulw(sb, kxi[s]), cb.x, cb.y);
+    const uint32_t sb = redc_lazy(mulw(xb[s], yb[s]), cb.x, cb.y);  // hat(s_i) in [0, 2m)
+    // xi_i = hat(s_i) kxp mod m_i by Shoup's product: [0, 2m), one subtraction
+    const uint32_t u = sb * kxp[s] - __umulhi(sb, kxs[s]) * cb.x;
+    const uint32_t xi = min(u, u - cb.x);
     if (o < K) xib[o] = xi;
     const uint4 cp = sm.cp4(t, s);
     sp[s] = redc_lazy(mulw(xp[s], yp[s]), cp.x, cp.y);  // [0, 2m'): only multiplied again
@@ -252,7 +255,10 @@ __device__ __forceinline__ void mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[
     const uint32_t u = xp[s] * cx.z - __umulhi(xp[s], cx.w) * cp.x;
     const uint32_t xpj = min(u, u - cp.x);
     if (o < K) xpb[o] = xpj;
-    kaw += hi32(mulw(xpj, cx.y));  // floor(xi'_j 2^Q / m'_j), up to 2 units low
+    // xi'_j 2^Q / m'_j from the top bits: (xi' >> S) floor(2^(Q+S) / m'_j) is below it by less than
+    // 2^(Q+S) / m'_j + xi' / 2^S units; over the k channels of a lane-group class (k <= 145, primes
+    // above 2^27.4) that stays below 2^(Q-2), the margin of the 1/4 offset
+    kaw += (xpj >> KAW_S) * cx.y;
   }
   __syncwarp();
   // 6. extension B' -> B, exact: a' = floor(sum xi'_j / m'_j) from the fixed-point sum with a 1/4 offset

@@ -171,6 +171,7 @@ bool build_class(uint32_t L, ClassHost& c, std::string& err) {
     const uint32_t xpc = mulmod32(c.Mp_mj_inv[j], rinv, m);
     blk[o.xpc + j] = xpc;
     blk[o.xpcs + j] = (uint32_t)(((uint64_t)xpc << 32) / m);
+    blk[o.ubs + j] = (uint32_t)((1ull << (KAW_Q + KAW_S)) / m);
   }
   for (uint32_t i = 0; i < k; i++) {
     uint32_t m = B[i];
@@ -257,7 +258,13 @@ int build_key(const ClassHost& c, const Big& N, const Big* exp, KeyHost& out, st
   b[o.hdr + 0] = out.nbits;
   b[o.hdr + 1] = (out.nbits + 31) / 32;
   b[o.hdr + 2] = exp ? (uint32_t)exp->bits() : 0u;
-  for (uint32_t i = 0; i < k; i++) b[o.kxi + i] = out.kxi[i];
+  for (uint32_t i = 0; i < k; i++) {
+    const uint32_t m = c.B[i];
+    b[o.kxi + i] = out.kxi[i];
+    const uint32_t kxp = mulmod32(out.kxi[i], powmod32((uint32_t)((1ull << 32) % m), m - 2, m), m);
+    b[o.kxp + i] = kxp;
+    b[o.kxs + i] = (uint32_t)(((uint64_t)kxp << 32) / m);
+  }
   for (uint32_t j = 0; j < k; j++) {
     uint32_t m = c.Bp[j];
     b[o.cmul + j] = mulmod32(out.NMinv_Bp[j], (uint32_t)((1ull << 32) % m), m);

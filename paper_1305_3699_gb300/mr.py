@@ -33,6 +33,7 @@ EXPORTED = [
     "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
     "mr_get_tuning", "mr_set_tuning", "mr_debug_crt_bin_host", "mr_debug_big_variant",
     "mr_tensor_peak", "mr_debug_tc_mma", "mr_debug_tc_slices", "mr_big_variant_info", "mr_debug_big_phases",
+    "mr_set_constant_time",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -110,6 +111,7 @@ def _load() -> ctypes.CDLL:
         "mr_debug_tc_slices": (ctypes.c_int, [U32, PU32, SZ, ctypes.POINTER(SZ)]),
         "mr_big_variant_info": (ctypes.c_int, [U32, U32, PU32, PU32, PU32]),
         "mr_debug_big_phases": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+        "mr_set_constant_time": (ctypes.c_int, [P, ctypes.c_int]),
         "mr_autotune": (ctypes.c_int, [P, U32, U32, U32, ctypes.POINTER(TuneResult)]),
         "mr_debug_big_wait": (ctypes.c_int, [P, U32, ctypes.c_int32]),
     }
@@ -491,6 +493,10 @@ class Context:
         self._check(lib.mr_autotune(self.handle, class_bits, n_items, exp_bits, ctypes.byref(r)))
         return {"variant": r.variant, "lanes_per_number": r.lanes_per_number, "window": r.window,
                 "configs": r.configs, "ms": r.ms, "ms_default": r.ms_default}
+
+    def mr_set_constant_time(self, on: bool = True):
+        """Constant-time exponentiation schedule for later calls and plans (see mr.h)."""
+        self._check(lib.mr_set_constant_time(self.handle, 1 if on else 0))
 
     def mr_debug_big_phases(self, on: bool = True) -> List[int]:
         """Phase cycle counters of the large classes' tensor-core form (see mr.h): returns the 8 sums

@@ -219,3 +219,19 @@ def test_big_variant_info():
     assert mr.mr_big_variant_info(8192, 1)["slice_channels"] == 48
     with pytest.raises(mr.MRError):
         mr.mr_big_variant_info(1024, 0)
+
+
+def test_lane_group_factor_estimate_bound():
+    """The lane-group kernels estimate a' = floor(sum xi'_j / m'_j) from (xi'_j >> 17) floor(2^39 / m'_j)
+    (Q = 22 fixed-point bits, offset 1/4).  Each term is below its exact value by less than
+    2^39 / m'_j + (m'_j - 1) / 2^17 units of 2^-22; the estimate is exact when the k terms together
+    stay below 1/4 (2^20 units), and the sum must fit 32 bits.  Checked on every lane-group class's
+    actual primes B'."""
+    Q, S = 22, 17
+    for L in (512, 1024, 1536, 2048, 3072, 4096):
+        k = mr.mr_class_for_bits(L)[1]
+        bp = mr.mr_debug_class_table(L, "Bp")
+        assert len(bp) == k
+        err = sum(2 ** (Q + S) / m + (m - 1) / 2 ** S for m in bp)
+        assert err < 2 ** (Q - 2), (L, err / 2 ** Q)
+        assert k * 2 ** Q < 2 ** 32, L
