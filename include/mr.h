@@ -38,9 +38,9 @@
  * extension's coefficients through device memory, in one cooperative launch;
  * they serve mr_modexp_batch, mr_rsa_encrypt and the halves of mr_rsa_decrypt_crt
  * (16384-bit keys: 8192-bit halves, recombined in binary by one warp per
- * decryption).  Miller-Rabin, the prime test and mixed batches take at most
- * 4096-bit numbers, key generation primes of at most 2048 bits; larger inputs
- * return MR_ERR_SIZE.
+ * decryption) and the large requests of mr_rsa_mixed.  Miller-Rabin, the prime
+ * test and plans take at most 4096-bit numbers, key generation primes of at
+ * most 2048 bits; larger inputs return MR_ERR_SIZE.
  */
 #ifndef MR_H
 #define MR_H
@@ -206,7 +206,11 @@ enum { MR_OP_ENCRYPT = 0, MR_OP_DECRYPT = 1 };
  * n; in, out: device rows (strides in limbs; out_stride must hold every
  * modulus); dev_status as mr_modexp_batch; flags: MR_PLAN_CONCURRENT,
  * MR_PLAN_PERSISTENT, MR_PLAN_AUTOTUNE (MR_PLAN_GRAPH is ignored).  Results do not
- * depend on the flags.  Errors as mr_rsa_decrypt_crt. */
+ * depend on the flags.  Requests whose exponentiations fall in a large class
+ * (encryptions with keys above 4096 bits, decryptions whose CRT halves are above
+ * 4096 bits) run first, as the class batches of mr_rsa_encrypt and
+ * mr_rsa_decrypt_crt; the flags shape the launches of the others.  Errors as
+ * mr_rsa_decrypt_crt. */
 mr_status mr_rsa_mixed(mr_ctx *ctx, const mr_key *const *keys, const uint8_t *ops, size_t n, const uint32_t *in,
                        uint32_t in_stride, uint32_t *out, uint32_t out_stride, uint8_t *dev_status, uint32_t flags,
                        void *stream);
@@ -214,7 +218,10 @@ mr_status mr_rsa_mixed(mr_ctx *ctx, const mr_key *const *keys, const uint8_t *op
 /* A prepared mixed batch: the same requests (same buffers, same keys) launched
  * many times, e.g. by a serving loop that refills `in` between launches.  The
  * plan owns its device work lists and scratch (allocated here, released by
- * mr_plan_free); with MR_PLAN_GRAPH its launches are one CUDA-graph launch. */
+ * mr_plan_free); with MR_PLAN_GRAPH its launches are one CUDA-graph launch.
+ * Plans take requests of the lane-group classes only (keys of at most 4096 bits
+ * for encryptions, CRT halves of at most 4096 bits for decryptions; others:
+ * MR_ERR_SIZE). */
 typedef struct mr_plan mr_plan;
 
 mr_status mr_plan_create(mr_ctx *ctx, const mr_key *const *keys, const uint8_t *ops, size_t n, const uint32_t *in,

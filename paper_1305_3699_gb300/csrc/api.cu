@@ -489,8 +489,17 @@ double modexp_work(uint32_t k, uint32_t ebits, uint32_t w) {
   return (ebits + nwin + (double)(1u << w)) * mm_products(k);
 }
 
+// A request of a mixed batch whose exponentiations fall in a large size class (an encryption with a key
+// above 4096 bits, a CRT decryption with halves above 4096 bits).
+bool large_request(const mr_key* k, uint8_t op) {
+  return op == MR_OP_DECRYPT && k->priv ? k->p.cls->big() : k->pub.cls->big();
+}
+
+// Group the lane-group requests of a mixed batch by (size class, window).  Large requests are left out
+// and their indices appended to `large` when it is given (else they are refused).
 mr_status build_groups(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, size_t n, const uint32_t* in,
-                       uint32_t in_stride, uint32_t* out, uint32_t out_stride, std::vector<GroupLaunch>& groups) {
+                       uint32_t in_stride, uint32_t* out, uint32_t out_stride, std::vector<GroupLaunch>& groups,
+                       std::vector<size_t>* large = nullptr) {
   std::map<std::pair<ClassEntry*, uint32_t>, size_t> idx;
   auto group = [&](ClassEntry* ce, uint32_t w) -> GroupLaunch& {
     auto key = std::make_pair(ce, w);
@@ -509,7 +518,13 @@ mr_status build_groups(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* op
     if (out_stride < k->pub.nlimbs()) return fail(ctx, MR_ERR_ARG, "out_stride smaller than a modulus");
     const KeyEntry& pub = k->pub;
     const uint32_t* nlim = pub.dev + key_offsets(pub.cls->host.k, pub.cls->host.W).N;
-    if (pub.cls->big()) return fail(ctx, MR_ERR_SIZE, "mixed batches take keys of at most 4096 bits");
+    if (large_request(k, ops[i])) {
+      if (!large) return fail(ctx, MR_ERR_SIZE, "plans take keys of at most 4096 bits (halves for decryptions)");
+      if (ops[i] != MR_OP_ENCRYPT && ops[i] != MR_OP_DECRYPT)
+        return fail(ctx, MR_ERR_ARG, "unknown operation at index " + std::to_string(i));
+      large->push_back(i);
+      continue;
+    }
     if (ops[i] == MR_OP_ENCRYPT) {
       if (!k->dev_e) return fail(ctx, MR_ERR_KEY, "key has no public exponent");
       uint32_t eb = (uint32_t)k->e.bits();
@@ -921,6 +936,76 @@ ClassBatch& batch_for(std::vector<ClassBatch>& v, std::map<ClassEntry*, size_t>&
   v.emplace_back();
   v.back().ce = ce;
   return v.back();
+}
+
+// The large requests of a mixed batch: the class batches of mr_rsa_encrypt and mr_rsa_decrypt_crt
+// (cooperative large-class launches, then the binary Garner recombination), their items addressed at
+// the requests' own rows and status bytes.
+mr_status run_large_mixed(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* ops, const std::vector<size_t>& sel,
+                          const uint32_t* in, uint32_t in_stride, uint32_t* out, uint32_t out_stride,
+                          uint8_t* status, cudaStream_t st) {
+  std::vector<ClassBatch> enc, dec;
+  std::map<ClassEntry*, size_t> ie, id;
+  std::map<ClassEntry*, uint32_t> eb_enc, pop_enc, eb_dec;
+  uint32_t maxW = 0;
+  for (size_t i : sel) {
+    const mr_key* k = keys[i];
+    const KeyEntry& pub = k->pub;
+    const uint32_t* nlim = pub.dev + key_offsets(pub.cls->host.k, pub.cls->host.W).N;
+    if (ops[i] == MR_OP_ENCRYPT) {
+      if (!k->dev_e) return fail(ctx, MR_ERR_KEY, "key has no public exponent");
+      ClassBatch& b = batch_for(enc, ie, pub.cls);
+      MxItem it{};
+      it.key = pub.dev;
+      it.x = in + i * in_stride;
+      it.e = k->dev_e;
+      it.out = out + i * out_stride;
+      it.xlim = nlim;
+      it.x_limbs = in_stride;
+      it.e_limbs = k->e_limbs;
+      it.out_limbs = out_stride;
+      it.xlim_limbs = pub.cls->host.W;
+      it.status = (uint32_t)i;
+      b.mx.push_back(it);
+      eb_enc[pub.cls] = std::max<uint32_t>(eb_enc[pub.cls], (uint32_t)k->e.bits());
+      pop_enc[pub.cls] = std::max<uint32_t>(pop_enc[pub.cls], popcount_big(k->e));
+    } else {
+      if (!k->priv) return fail(ctx, MR_ERR_KEY, "key has no private CRT parts");
+      ClassEntry* ce = k->p.cls;
+      ClassBatch& b = batch_for(dec, id, ce);
+      const KeyOff ko = key_offsets(ce->host.k, ce->host.W);
+      for (int h = 0; h < 2; h++) {
+        const KeyEntry& ke = h == 0 ? k->p : k->q;
+        MxItem it{};
+        it.key = ke.dev;
+        it.x = in + i * in_stride;
+        it.e = ke.dev + ko.exp;
+        it.out = nullptr;  // patched to the half-result scratch
+        it.xlim = nlim;
+        it.x_limbs = in_stride;
+        it.e_limbs = ce->host.W;
+        it.out_limbs = ce->host.W;
+        it.xlim_limbs = pub.cls->host.W;
+        it.status = (uint32_t)i;
+        b.mx.push_back(it);
+      }
+      CrtItem ci{};
+      ci.keyp = k->p.dev;
+      ci.crt = k->dev_crt;
+      ci.out = out + i * out_stride;
+      ci.out_limbs = out_stride;
+      ci.status = (uint32_t)i;
+      b.crt.push_back(ci);
+      eb_dec[ce] = std::max<uint32_t>(eb_dec[ce], std::max(k->p.host.block[2], k->q.host.block[2]));
+      maxW = std::max(maxW, ce->host.W);
+    }
+  }
+  for (auto& b : enc) b.wbits = choose_window(eb_enc[b.ce], pop_enc[b.ce], window_cap(b.ce));
+  for (auto& b : dec) b.wbits = choose_window(eb_dec[b.ce], 0, window_cap(b.ce));
+  // encryption and decryption batches run separately: a decryption batch holds only CRT halves
+  mr_status s = enc.empty() ? MR_OK : run_batches(ctx, enc, status, st, 0);
+  if (!s && !dec.empty()) s = run_batches(ctx, dec, status, st, maxW);
+  return s;
 }
 
 }  // namespace
@@ -1529,8 +1614,14 @@ mr_status mr_rsa_mixed(mr_ctx* ctx, const mr_key* const* keys, const uint8_t* op
     std::vector<GroupLaunch> groups;
     mr_status s = (flags & MR_PLAN_AUTOTUNE) ? autotune_mixed(ctx, keys, ops, n) : MR_OK;
     if (s) return s;
-    s = build_groups(ctx, keys, ops, n, in, in_stride, out, out_stride, groups);
+    std::vector<size_t> large;
+    s = build_groups(ctx, keys, ops, n, in, in_stride, out, out_stride, groups, &large);
     if (s) return s;
+    if (!large.empty()) {
+      s = run_large_mixed(ctx, keys, ops, large, in, in_stride, out, out_stride, dev_status, st);
+      if (s) return s;
+    }
+    if (groups.empty()) return MR_OK;
     flags &= (MR_PLAN_CONCURRENT | MR_PLAN_PERSISTENT);
     size_t upload = 0, qoff = 0;
     size_t total = layout_groups(ctx, groups, flags, &upload, &qoff);

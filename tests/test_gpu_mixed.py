@@ -119,3 +119,34 @@ def test_mixed_range_errors(mr, setup):
     ctx.mr_rsa_mixed(keys, [0, 1] * 4, inp, out, st, flags=mr.MR_PLAN_PERSISTENT)
     torch.cuda.synchronize()
     assert st.cpu().tolist() == [5] * 8
+
+
+def test_mixed_batch_with_large_requests(mr):
+    """One mr_rsa_mixed call over 2048-, 8192- and 16384-bit keys: 8192-bit encryptions and 16384-bit
+    encryptions and decryptions run in the large classes (16384-bit decryptions as 8192-bit CRT halves
+    plus the binary recombination), 8192-bit decryptions as 4096-bit halves with the lane-group
+    requests; every result equals the oracle's, and a plan refuses the large requests."""
+    keys = load_keys("rsa2048_x16")[:3] + load_keys("rsa8192_x2") + load_keys("mod16384_x4")[:2]
+    r = SplitMix64(0x4C41524745)
+    with mr.Context(0) as ctx:
+        hk = [ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"]) for k in keys]
+        # key index, operation: small and large requests interleaved; 16384-bit decryptions kept few
+        # (the oracle takes seconds for each)
+        reqs = [(0, 0), (5, 0), (3, 1), (1, 1), (6, 0), (4, 0), (5, 1), (2, 0), (3, 0), (0, 1), (6, 0), (4, 1)]
+        xs = [r.below(keys[i]["N"]) for i, _ in reqs]
+        inp = mr.to_tensor(xs, 512)
+        out = torch.full_like(inp, -1)
+        st = torch.full((len(reqs),), 255, dtype=torch.uint8, device="cuda")
+        ctx.mr_rsa_mixed([hk[i] for i, _ in reqs], [o for _, o in reqs], inp, out, st,
+                         flags=mr.MR_PLAN_CONCURRENT)
+        torch.cuda.synchronize()
+        got = mr.from_tensor(out)
+        assert st.cpu().tolist() == [0] * len(reqs)
+        for j, (i, o) in enumerate(reqs):
+            k = keys[i]
+            want = plain.rsa_encrypt(xs[j], k["e"], k["N"]) if o == 0 else \
+                plain.rsa_decrypt_crt(xs[j], k["p"], k["q"], k["dp"], k["dq"], k["qinv"])
+            assert got[j] == want, (j, k["N"].bit_length(), o)
+        with pytest.raises(mr.MRError) as exc:
+            ctx.mr_plan_create([hk[5]], [0], inp[:1], out[:1])
+        assert exc.value.code == 4
