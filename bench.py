@@ -44,7 +44,7 @@ SEED = 0x4D520002
 IMAD_PER_CLK_PER_SM = 64   # int32 multiplies per clock per SM (integer multiply pipe)
 # DRAM bytes (read + write) of one exponentiation launch of the RSA-2048 CRT workload, from an ncu
 # capture of the current kernel on this workload (dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_BYTES_PER_LAUNCH = 2_862_848 + 24_692_736
+TRAFFIC_BYTES_PER_LAUNCH = 2_861_568 + 24_110_080
 # long-exponent workload: 256 exponentiations modulo 16384-bit RSA moduli with 16128-bit exponents
 BIG_KEYSET = "mod16384_x4"
 BIG_N = 256
@@ -331,7 +331,8 @@ def _oracle_modexp_chunk(args):
     return time.perf_counter() - t0, len(out)
 
 
-def oracle_big_throughput(keys, idx, xs, es, steps: int = 1, warmup: int = 0):
+def oracle_big_throughput(keys, idx, xs, es, steps: int = 1, warmup: int = 0,
+                          what: str = "16384-bit moduli, 16128-bit exponents"):
     """The oracle's exponentiation on every host core, one item per core per step."""
     import multiprocessing as mp
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
@@ -345,7 +346,7 @@ def oracle_big_throughput(keys, idx, xs, es, steps: int = 1, warmup: int = 0):
             if s >= warmup:
                 times.append(time.perf_counter() - t0)
     value = n / statistics.mean(times)
-    desc = (f"first {n} of the {len(xs)} items of the workload (16384-bit moduli, 16128-bit exponents), "
+    desc = (f"first {n} of the {len(xs)} items of the workload ({what}), "
             f"oracle.plain.modexp, one item per process on {cores} processes")
     return value, cores, desc, times
 
@@ -427,6 +428,12 @@ def run_reference_extra(args):
             times.append(time.perf_counter() - t0)
         return _reference_line(args, "ragged_mix_65536" if args.workload == "ragged" else "serving_poisson_200k",
                                value, UNIT, cores, desc, times)
+    if args.workload == "class_modexp":
+        mods, idx, xs, es = class_workload(args.bits, args.items)
+        value, cores, desc, times = oracle_big_throughput([{"N": N} for N in mods], idx, xs, es,
+                                                          steps=max(1, args.steps), warmup=0,
+                                                          what=f"{args.bits}-bit moduli and exponents")
+        return _reference_line(args, f"modexp{args.bits}_class", value, UNIT, cores, desc, times)
     if args.workload == "rsa1024_enc":
         from oracle import plain
         keys = load_keys("rsa1024_x64")
@@ -711,6 +718,95 @@ def run_ours(args, rank, world, local_rank, emit=True):
             line["config"]["schedule"] = "constant time (regular fixed windows, masked table reads)"
         if not emit:
             return line
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------- one size class
+def class_workload(bits: int, n: int, rank: int = 0):
+    """n exponentiations modulo 16 seeded odd `bits`-bit moduli (top bit set), bases uniform below the
+    modulus, full-length exponents drawn per item (so the kernel runs fixed windows)."""
+    from synth import SplitMix64
+    r = SplitMix64(0x434C4153 + bits + 0x1000 * rank)
+    mods = [r.randbits(bits) | 1 | (1 << (bits - 1)) for _ in range(16)]
+    idx = [i % 16 for i in range(n)]
+    xs = [r.below(mods[i]) for i in idx]
+    es = [r.randbits(bits - 1) | (1 << (bits - 1)) for _ in range(n)]
+    return mods, idx, xs, es
+
+
+def run_class_modexp(args, rank, world, local_rank, emit=True):
+    """`--items` exponentiations of one lane-group size class (`--bits`), one mr_modexp_batch call per
+    step: the per-class profiling case of the lane-group kernel (bank conflicts, occupancy)."""
+    import torch
+
+    from paper_1305_3699_gb300 import mr
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    bits, n = args.bits, args.items
+    mods, idx, xs, es = class_workload(bits, n, rank)
+    L, k = mr.mr_class_for_bits(bits)
+    W = L // 32
+    ctx = mr.Context(local_rank)
+    hk = [ctx.mr_rns_setup(N) for N in mods]
+    kl = mr.KeyList([hk[i] for i in idx])
+    nl = (bits + 31) // 32
+    x_dev = mr.to_tensor(xs, nl, device=dev)
+    e_dev = mr.to_tensor(es, nl, device=dev)
+    out = torch.zeros_like(x_dev)
+    status = torch.zeros(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.mr_modexp_batch(kl, x_dev, e_dev, out, status, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    got = mr.from_tensor(out)
+    for j in range(0, n, max(1, n // 32)):
+        assert got[j] == pow(xs[j], es[j], mods[idx[j]]), "benchmark output mismatch"
+    assert int(status.sum()) == 0
+    ctx.mr_profile_enable(True)
+    ctx.mr_profile_read()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.zero_()
+            evs[s][0].record(stream)
+            step()
+            evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    (mx_launch, mx_ms), _ = ctx.mr_profile_read()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
+    value = n * world * args.steps / (total_ms / 1e3)
+    props = torch.cuda.get_device_properties(dev)
+    WX = len(mr.mr_debug_class_table(L, "M"))
+    w = window_for_bits(32 * nl)
+    prods = sum(algorithmic_products_per_modexp(k, W, WX, 32 * nl, w, 1) for _ in range(n))
+    ops31 = sum(ops_31bit_count(L, e.bit_length(), w) for e in es)
+    peak = props.multi_processor_count * IMAD_PER_CLK_PER_SM * sm_max_mhz() * 1e6
+    kms = mx_ms / max(1, mx_launch)
+    ctx.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded moduli, bases, exponents)",
+            "config": {"workload": f"modexp{bits}_class", "items_per_gpu": n, "keys": 16, "class_bits": L, "k": k,
+                       "window": w, "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"items partitioned over {world} GPU(s)"},
+            "roofline": {"bound": "alu", "achieved": 2 * prods / (kms / 1e3) / 1e12, "peak": peak / 1e12,
+                         "unit": "T int32-mul/s", "frac": 2 * prods / (kms / 1e3) / peak, "traffic": None,
+                         "kernel": f"modexp_kernel<k={k}>", "kernel_ms": kms,
+                         "count": f"implemented: k = {k}, 2k^2+7k products per multiplication, fixed windows",
+                         "frac_31bit_count": ops31 / (kms / 1e3) / peak if L in K31 else None},
+            "cpu_baseline": None, "gpu_launches": int(mx_launch)}
+    if not emit:
+        return line
+    if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
 
@@ -1502,10 +1598,13 @@ def main():
                     help="rsa2048_crt: constant-time exponentiation schedule (mr_set_constant_time)")
     ap.add_argument("--no-extra", action="store_true",
                     help="rsa2048_crt: skip the ragged, long-exponent, RSA-1024 and serving sub-records")
+    ap.add_argument("--bits", type=int, default=1536, help="class_modexp workload: modulus bits")
+    ap.add_argument("--items", type=int, default=4096, help="class_modexp workload: exponentiations per call")
     ap.add_argument("--ebits", type=int, default=BIG_EBITS,
                     help="exponent bits of the modexp16384 workload (smaller values for profiling runs)")
     ap.add_argument("--workload", default="rsa2048_crt", choices=["rsa2048_crt", "ragged", "serving", "modexp16384", "rsa16384_crt",
-                                                             "rsa1024_enc", "mr1024", "primegen1024", "keygen2048"])
+                                                             "rsa1024_enc", "mr1024", "primegen1024", "keygen2048",
+                                                             "class_modexp"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -1532,6 +1631,8 @@ def main():
             return run_keygen2048(args, rank, world, local_rank)
         if args.workload == "serving":
             return run_serving_bench(args, rank, world, local_rank)
+        if args.workload == "class_modexp":
+            return run_class_modexp(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

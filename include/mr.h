@@ -243,7 +243,7 @@ void mr_plan_free(mr_plan *plan);
  * caller-chosen number of iterations) on n candidates of one length.  For an
  * odd candidate N >= 3 and witness a, round r passes when, with N - 1 = 2^s d
  * (d odd) and y = (a mod N)^d mod N, y = 1, or y^(2^i) = N - 1 for some i < s.
- *   cand       device, n rows of n_limbs limbs (n_limbs * 32 <= 4096)
+ *   cand       device, n rows of n_limbs limbs (n_limbs * 32 <= 16384)
  *   witness    device, n*rounds rows of n_limbs limbs; row i*rounds+r is the
  *              witness of round r for candidate i (meant to lie in [2, N-2];
  *              any value is accepted and reduced mod N)
@@ -255,8 +255,16 @@ void mr_plan_free(mr_plan *plan);
  * 2 is prime (all bits set).  A candidate above 2^31 that is divisible by one of
  * the size class's channel primes is reported composite with mask 0 (it has
  * that prime as a factor; the per-witness verdicts are not evaluated for it).
- * Per-candidate constants (RNS form of the candidate, Montgomery constants)
- * are derived on the device; no candidate leaves the GPU.
+ * Rows of at most 4096 bits (n_limbs <= 128): per-candidate constants (RNS
+ * form of the candidate, Montgomery constants) are derived on the device; no
+ * candidate leaves the GPU, and the call is asynchronous on `stream`.
+ * Rows of the 8192- and 16384-bit classes (128 < n_limbs <= 512): the
+ * candidates and witnesses are read back to the host, which derives each
+ * candidate's constants as mr_rns_setup does; candidates of at most 4096
+ * significant bits go through the lane-group kernel, the others through the
+ * large-class exponentiation (y = a^d, then s - 1 in-place squarings), and the
+ * verdicts are written back.  This form synchronises `stream` before it
+ * returns.
  * Errors: MR_ERR_ARG, MR_ERR_SIZE, MR_ERR_OOM, MR_ERR_CUDA. */
 mr_status mr_miller_rabin_batch(mr_ctx *ctx, const uint32_t *cand, uint32_t n_limbs, size_t n,
                                 const uint32_t *witness, uint32_t rounds, uint8_t *dev_is_probable_prime,

@@ -756,6 +756,23 @@ __global__ void mr_combine_kernel(const uint8_t* item_pass, uint32_t n, uint32_t
 }
 
 
+// Large-class Miller-Rabin: after y = a^d mod n (step 0) and after each squaring step j, round item i
+// passes when y = n - 1, or at step 0 when y = 1; steps j >= s_i (n_i - 1 = 2^s_i d_i) do not count.
+__global__ void mr_large_flags_kernel(const uint32_t* y, const uint32_t* nm1, const uint32_t* s_item, uint32_t W,
+                                      uint32_t n_items, uint32_t step, uint8_t* pass) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_items || step >= s_item[i]) return;
+  const uint32_t* yr = y + (size_t)i * W;
+  const uint32_t* nr = nm1 + (size_t)i * W;
+  bool is_nm1 = true, is_one = step == 0;
+  for (uint32_t w = 0; w < W; w++) {
+    const uint32_t v = yr[w];
+    is_nm1 = is_nm1 && v == nr[w];
+    is_one = is_one && v == (w == 0 ? 1u : 0u);
+  }
+  if (is_nm1 || is_one) pass[i] = 1;
+}
+
 // ------------------------------------------------------------- autotuning
 
 // Seeded host generator for the synthetic tuning batch (SplitMix64).
@@ -1387,6 +1404,227 @@ mr_status mr_launch(mr_ctx* ctx, ClassEntry* ce, uint32_t v, const uint32_t* can
   return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "kernel launch");
 }
 
+}  // extern "C"
+
+// The rounds of the large candidates of mr_miller_rabin_large: sets pass[i * rounds + r] for i in `large`.
+template <class WitnessMod>
+mr_status mr_large_rounds(mr_ctx* ctx, ClassEntry* ce, const std::vector<size_t>& large, const std::vector<Big>& Ns,
+                          WitnessMod&& witness_mod, uint32_t rounds, std::vector<uint8_t>& pass, cudaStream_t st) {
+  const uint32_t L = ce->host.L, W = ce->host.W;
+  std::vector<KeyEntry> keys(large.size());
+  auto release = [&]() {
+    for (auto& k : keys) free_key_entry(k);
+  };
+  std::vector<uint32_t> hx, he, hn, hs;
+  std::vector<size_t> slot;  // pass index of each work item
+  std::vector<const uint32_t*> item_key;
+  uint32_t max_s = 0, max_dbits = 1;
+  for (size_t j = 0; j < large.size(); j++) {
+    const size_t i = large[j];
+    const Big& N = Ns[i];
+    const mr_status ks = make_key_entry(ctx, N, nullptr, L, keys[j]);
+    if (ks == MR_ERR_NOT_COPRIME) {  // a channel prime divides N (N is far above it): composite
+      ctx->err.clear();
+      continue;
+    }
+    if (ks) {
+      release();
+      return ks;
+    }
+    const Big nm1 = sub(N, Big(1u));
+    uint32_t sv = 0;
+    while (!nm1.bit(sv)) sv++;
+    // d = (N - 1) / 2^s as W limbs
+    const std::vector<uint32_t> nl = nm1.limbs(W + 1), nml = nm1.limbs(W);
+    std::vector<uint32_t> d(W, 0);
+    const uint32_t ws = sv / 32, bs = sv % 32;
+    for (uint32_t w = 0; w < W; w++) {
+      const uint32_t lo = w + ws <= W ? nl[w + ws] : 0u, hi = w + ws + 1 <= W ? nl[w + ws + 1] : 0u;
+      d[w] = bs ? (lo >> bs) | (hi << (32 - bs)) : lo;
+    }
+    for (uint32_t r = 0; r < rounds; r++) {
+      const Big a = witness_mod(i, r);
+      if (a.is_zero()) continue;  // y = 0 at every step: the round fails
+      if (cmp(a, Big(1u)) == 0 || cmp(a, nm1) == 0) {  // y = 1 or y = n - 1 (d is odd)
+        pass[i * rounds + r] = 1;
+        continue;
+      }
+      const std::vector<uint32_t> al = a.limbs(W);
+      hx.insert(hx.end(), al.begin(), al.end());
+      he.insert(he.end(), d.begin(), d.end());
+      hn.insert(hn.end(), nml.begin(), nml.end());
+      hs.push_back(sv);
+      slot.push_back(i * rounds + r);
+      item_key.push_back(keys[j].dev);
+      max_s = std::max(max_s, sv);
+      max_dbits = std::max<uint32_t>(max_dbits, (uint32_t)(nm1.bits() - sv));
+    }
+  }
+  mr_status s = MR_OK;
+  const size_t items = slot.size();
+  const uint32_t two = 2;
+  std::vector<uint8_t> hp(items);
+  if (items) {
+    const size_t rowb = (size_t)W * 4;
+    const size_t oE = align256(items * rowb), oN = align256(oE + items * rowb), oY = align256(oN + items * rowb),
+                 oS = align256(oY + items * rowb), oP = align256(oS + items * 4), oT = align256(oP + items);
+    void* dev = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&dev, oT + 256, ctx->pool, st);
+    if (e != cudaSuccess) {
+      release();
+      return fail(ctx, MR_ERR_OOM, "scratch allocation failed");
+    }
+    char* base = static_cast<char*>(dev);
+    uint32_t* X = reinterpret_cast<uint32_t*>(base);
+    uint32_t* E = reinterpret_cast<uint32_t*>(base + oE);
+    uint32_t* NM1 = reinterpret_cast<uint32_t*>(base + oN);
+    uint32_t* Y = reinterpret_cast<uint32_t*>(base + oY);
+    uint32_t* S = reinterpret_cast<uint32_t*>(base + oS);
+    uint8_t* P = reinterpret_cast<uint8_t*>(base + oP);
+    uint32_t* TWO = reinterpret_cast<uint32_t*>(base + oT);
+    e = cudaMemcpyAsync(X, hx.data(), hx.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(E, he.data(), he.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(NM1, hn.data(), hn.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S, hs.data(), hs.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(TWO, &two, 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P, 0, items, st);
+    if (e != cudaSuccess) s = cuda_fail(ctx, e, "round upload");
+    const unsigned fgrid = (unsigned)((items + 255) / 256);
+    // step j = 0: y = a^d; steps j >= 1: y = y^2 in place (the kernel reads x before it writes out)
+    for (uint32_t step = 0; !s && step < std::max<uint32_t>(max_s, 1); step++) {
+      std::vector<ClassBatch> bv(1);
+      ClassBatch& b = bv[0];
+      b.ce = ce;
+      b.wbits = step == 0 ? choose_window(max_dbits, 0, window_cap(ce)) : 1u;
+      const uint32_t key_n = key_offsets(ce->host.k, W).N;
+      for (size_t t = 0; t < items; t++) {
+        MxItem it{};
+        it.key = item_key[t];
+        it.x = step == 0 ? X + t * W : Y + t * W;
+        it.e = step == 0 ? E + t * W : TWO;
+        it.out = Y + t * W;
+        it.xlim = item_key[t] + key_n;
+        it.x_limbs = W;
+        it.e_limbs = step == 0 ? W : 1u;
+        it.out_limbs = W;
+        it.xlim_limbs = W;
+        it.status = 0xffffffffu;
+        b.mx.push_back(it);
+      }
+      s = run_batches(ctx, bv, nullptr, st, 0);
+      if (!s) {
+        mr_large_flags_kernel<<<fgrid, 256, 0, st>>>(Y, NM1, S, W, (uint32_t)items, step, P);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "kernel launch");
+      }
+    }
+    if (!s) {
+      e = cudaMemcpyAsync(hp.data(), P, items, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) s = cuda_fail(ctx, e, "verdict download");
+    }
+    cudaFreeAsync(dev, st);
+  }
+  const cudaError_t e = cudaStreamSynchronize(st);  // host sources of the uploads, keys freed after use
+  release();
+  if (s) return s;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "Miller-Rabin rounds");
+  for (size_t t = 0; t < items; t++) pass[slot[t]] = hp[t];
+  return MR_OK;
+}
+
+// Miller-Rabin on candidates of a large size class (8192, 16384 bits), composed from the large-class
+// exponentiation.  The candidates and witnesses come to the host (the call synchronises `st`), which
+// settles the definitional cases, hands odd candidates of at most 4096 bits to the lane-group kernel
+// (rows repacked), and for the others derives the modulus constants (as mr_rns_setup) and
+// n - 1 = 2^s d: y = a^d for every (candidate, round) in one class batch, then up to max(s) - 1 squaring
+// batches (exponent 2, in place), mr_large_flags_kernel recording each round's verdict after every
+// step.  The rounds combine on the host and the verdicts go back to the device.
+mr_status mr_miller_rabin_large(mr_ctx* ctx, ClassEntry* ce, const uint32_t* cand, uint32_t n_limbs, size_t n,
+                                const uint32_t* witness, uint32_t rounds, uint8_t* dev_prime, uint32_t* dev_mask,
+                                cudaStream_t st) {
+  const size_t nr = n * (size_t)rounds;
+  std::vector<uint32_t> hc(n * (size_t)n_limbs), hw(nr * n_limbs);
+  cudaError_t e = cudaMemcpyAsync(hc.data(), cand, hc.size() * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hw.data(), witness, hw.size() * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "candidate download");
+  std::vector<uint8_t> pass(nr, 0);  // per (candidate, round)
+  std::vector<Big> Ns(n);
+  std::vector<size_t> small, large;
+  for (size_t i = 0; i < n; i++) {
+    Ns[i] = big_from(hc.data() + i * n_limbs, n_limbs);
+    const Big& N = Ns[i];
+    if (N.bits() == 2 && !N.bit(0)) {  // 2 is prime
+      for (uint32_t r = 0; r < rounds; r++) pass[i * rounds + r] = 1;
+      continue;
+    }
+    if (N.bits() < 2 || !N.bit(0)) continue;  // 0, 1 and even numbers are composite
+    (N.bits() <= 4096 ? small : large).push_back(i);
+  }
+  auto witness_mod = [&](size_t i, uint32_t r) {
+    return mod(big_from(hw.data() + (i * rounds + r) * n_limbs, n_limbs), Ns[i]);
+  };
+  mr_status s = MR_OK;
+  if (!small.empty()) {
+    ClassEntry* cs = nullptr;
+    if ((s = get_class(ctx, 4096, &cs))) return s;
+    const uint32_t sw = cs->host.W;
+    const size_t ns = small.size(), items = ns * rounds;
+    std::vector<uint32_t> rc(ns * sw), rw(items * sw);
+    for (size_t j = 0; j < ns; j++) {
+      std::vector<uint32_t> l = Ns[small[j]].limbs(sw);
+      std::copy(l.begin(), l.end(), rc.begin() + j * sw);
+      for (uint32_t r = 0; r < rounds; r++) {
+        std::vector<uint32_t> a = witness_mod(small[j], r).limbs(sw);
+        std::copy(a.begin(), a.end(), rw.begin() + (j * rounds + r) * sw);
+      }
+    }
+    const uint32_t v = mr_variant(ctx, cs, items);
+    const size_t sbytes = align256(mr_scratch_bytes(cs, v, sw, items));
+    const size_t off_c = sbytes, off_w = align256(off_c + rc.size() * 4), off_p = align256(off_w + rw.size() * 4);
+    void* dev = nullptr;
+    e = cudaMallocFromPoolAsync(&dev, off_p + items, ctx->pool, st);
+    if (e != cudaSuccess) return fail(ctx, MR_ERR_OOM, "scratch allocation failed");
+    char* base = static_cast<char*>(dev);
+    std::vector<uint8_t> ip(items);
+    e = cudaMemcpyAsync(base + off_c, rc.data(), rc.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + off_w, rw.data(), rw.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) s = cuda_fail(ctx, e, "candidate upload");
+    if (!s)
+      s = mr_launch(ctx, cs, v, reinterpret_cast<uint32_t*>(base + off_c), sw, ns, reinterpret_cast<uint32_t*>(base + off_w),
+                    rounds, rounds, reinterpret_cast<uint8_t*>(base + off_p), nullptr, nullptr, nullptr, dev, st);
+    if (!s) {
+      e = cudaMemcpyAsync(ip.data(), base + off_p, items, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) s = cuda_fail(ctx, e, "verdict download");
+    }
+    cudaFreeAsync(dev, st);
+    if (s) return s;
+    for (size_t j = 0; j < ns; j++)
+      for (uint32_t r = 0; r < rounds; r++) pass[small[j] * rounds + r] = ip[j * rounds + r];
+  }
+  if (!large.empty()) s = mr_large_rounds(ctx, ce, large, Ns, witness_mod, rounds, pass, st);
+  if (s) return s;
+  std::vector<uint8_t> prime(n);
+  std::vector<uint32_t> mask(n);
+  for (size_t i = 0; i < n; i++) {
+    uint8_t all = 1;
+    uint32_t m = 0;
+    for (uint32_t r = 0; r < rounds; r++) {
+      all &= pass[i * rounds + r];
+      if (pass[i * rounds + r] && r < 32) m |= 1u << r;
+    }
+    prime[i] = all;
+    mask[i] = m;
+  }
+  e = cudaMemcpyAsync(dev_prime, prime.data(), n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && dev_mask) e = cudaMemcpyAsync(dev_mask, mask.data(), n * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors are the copies' sources
+  return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "verdict upload");
+}
+
+extern "C" {
+
 mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_limbs, size_t n, const uint32_t* witness,
                                 uint32_t rounds, uint8_t* dev_is_probable_prime, uint32_t* dev_round_mask,
                                 void* stream) {
@@ -1401,6 +1639,13 @@ mr_status mr_miller_rabin_batch(mr_ctx* ctx, const uint32_t* cand, uint32_t n_li
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     ClassEntry* ce = nullptr;
+    const uint32_t Lc = class_for_bits(32 * n_limbs);
+    if (Lc > 4096) {  // a large class: composed from the large-class exponentiation (synchronous)
+      mr_status sb = get_class(ctx, Lc, &ce);
+      if (sb) return sb;
+      return mr_miller_rabin_large(ctx, ce, cand, n_limbs, n, witness, rounds, dev_is_probable_prime, dev_round_mask,
+                                   st);
+    }
     mr_status s = mr_class(ctx, n_limbs, &ce);
     if (s) return s;
     // The rounds of a candidate are independent: each runs as its own work item (the setup of

@@ -165,14 +165,23 @@ def test_modexp_8192_every_slice_width(mr):
             c.close()
 
 
-def test_large_class_unsupported_calls(mr, ctx):
+def test_large_class_mixed_call_and_plan_refusal(mr, ctx):
+    """A mixed call takes 16384-bit keys (encryption in the 16384-bit class, decryption through the
+    8192-bit CRT halves); a plan refuses them with MR_ERR_SIZE (plans hold lane-group classes only)."""
     k = load_keys("mod16384_x4")[0]
     h = ctx.mr_rsa_key_setup(k["N"], k["e"], k["p"], k["q"], k["dp"], k["dq"], k["qinv"])
-    c = mr.to_tensor([5], 512)
+    r = SplitMix64(0x3177)
+    xs = [5, r.below(k["N"])]
+    c = mr.to_tensor(xs, 512)
     m = torch.zeros_like(c)
+    ctx.mr_rsa_mixed([h, h], [0, 1], c, m)  # MR_OP_ENCRYPT, MR_OP_DECRYPT
+    torch.cuda.synchronize()
+    got = mr.from_tensor(m)
+    assert got[0] == plain.modexp(5, k["e"], k["N"])
+    assert got[1] == plain.rsa_decrypt_crt(xs[1], k["p"], k["q"], k["dp"], k["dq"], k["qinv"])
     with pytest.raises(mr.MRError) as e:
-        ctx.mr_rsa_mixed([h], [0], c, m)
-    assert e.value.code == 4  # MR_ERR_SIZE: mixed batches take keys of at most 4096 bits
+        ctx.mr_plan_create([h], [0], c[:1], m[:1])
+    assert e.value.code == 4
 
 
 def test_rsa16384_crt_decrypt(mr, ctx):

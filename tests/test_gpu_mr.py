@@ -136,3 +136,86 @@ def test_device_derived_constants_match_host_setup(mr, ctx):
             assert row[base + 4 * k:base + 5 * k] == [pow(N % m, -1, m) for m in c.Bp]
             assert row[base + 2 * k:base + 3 * k] == [v * c.t["Mp_mj_inv"][j] % c.Bp[j]
                                                       for j, v in enumerate(key.t["NMinv_Bp"])]
+
+
+def _oracle_rounds(cands, witnesses):
+    """Per-round oracle verdicts of large candidates on a spawned process pool (a forked child of a
+    CUDA process may hang); the oracle's square-and-multiply takes seconds per 16384-bit round."""
+    import multiprocessing as mp
+
+    pairs = [(n, a) for n, ws in zip(cands, witnesses) for a in ws]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        flat = pool.starmap(primality.miller_rabin_round, pairs, chunksize=1)
+    out, i = [], 0
+    for ws in witnesses:
+        out.append(flat[i:i + len(ws)])
+        i += len(ws)
+    return out
+
+
+def _check_large(mr, ctx, cands, witnesses, n_limbs, channel_factor=()):
+    flags, masks = run_mr(mr, ctx, cands, witnesses, n_limbs)
+    verdicts = _oracle_rounds(cands, witnesses)
+    for i, n in enumerate(cands):
+        v = verdicts[i]
+        if n in channel_factor:  # reported composite without evaluating the rounds
+            assert flags[i] == 0 and masks[i] == 0 and not all(v), i
+            continue
+        assert flags[i] == int(all(v)), (i, n.bit_length(), v)
+        assert masks[i] == sum(1 << r for r, ok in enumerate(v) if ok), (i, n.bit_length(), v, hex(masks[i]))
+
+
+def _prime_with_large_two_power(r, bits, s):
+    """A seeded prime c * 2^s + 1 (c odd) of `bits` bits: n - 1 has s factors of two, so a round of
+    the test may pass at any of s squaring steps.  Found by trial division and a base-2 Fermat check
+    with CPython's pow; the test's expected verdicts still come from the oracle."""
+    small = primality.first_primes(2000)[1:]
+    while True:
+        c = r.randbits(bits - s) | 1 | (1 << (bits - s - 1))
+        n = (c << s) + 1
+        if any(n % p == 0 for p in small):
+            continue
+        if pow(2, n - 1, n) == 1:
+            return n
+
+
+def test_large_class_candidates_8192(mr, ctx):
+    """256-limb rows (the 8192-bit class): 8192-bit primes and composites through the large-class
+    exponentiation, a 4423-bit Mersenne prime and a prime with 2^64 | n - 1 (many squaring steps),
+    4096-bit primes and small values through the repacked lane-group path, witness edge values, and
+    a candidate divisible by a channel prime of the class."""
+    r = SplitMix64(0x8192)
+    big = load_keys("mod16384_x4")
+    mid = load_keys("rsa8192_x2")
+    primes8k = [k[x] for k in big for x in ("p", "q")][:6]
+    comps = [k["N"] for k in mid] + [r.randbits(8192) | 1 | (1 << 8191) for _ in range(3)]
+    m4423 = (1 << 4423) - 1
+    proth = _prime_with_large_two_power(r, 4200, 64)
+    p4k = [mid[0]["p"], mid[1]["q"]]
+    B = mr.mr_debug_class_table(8192, "B")
+    chan = B[7] * mid[0]["q"]  # above 4096 bits: the large-class path finds the shared channel prime
+    assert 4096 < chan.bit_length() <= 8192
+    smalls = [0, 1, 2, 3, 9, 15, 2147483647]
+    cands = primes8k + comps + [m4423, m4423, proth] + p4k + [chan] + smalls
+    ws = []
+    for n in cands:
+        if n == m4423 and not any(c == m4423 for c in cands[:len(ws)]):
+            ws.append([0, n - 1, n + 1])
+        elif n == m4423:
+            ws.append([1, n, 2])
+        elif n < 5:
+            ws.append([2, 3, 7])
+        else:
+            ws.append([r.between(2, n - 2) for _ in range(3)])
+    _check_large(mr, ctx, cands, ws, 256, channel_factor=(chan,))
+
+
+def test_large_class_candidates_16384(mr, ctx):
+    """512-limb rows (the 16384-bit class): 16384-bit RSA moduli (composite), the 9689-bit Mersenne
+    prime, and an 8192-bit prime, two rounds each."""
+    r = SplitMix64(0x16384)
+    big = load_keys("mod16384_x4")
+    m9689 = (1 << 9689) - 1
+    cands = [big[0]["N"], big[1]["N"], m9689, big[2]["p"]]
+    ws = [[r.between(2, n - 2) for _ in range(2)] for n in cands]
+    _check_large(mr, ctx, cands, ws, 512)
