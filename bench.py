@@ -1290,14 +1290,16 @@ def run_ragged(args, rank, world, local_rank, emit=True):
                 prods += (algorithmic_products_sliding(kk, L // 32, WX, h, w, 2) if w >= 4 else
                           algorithmic_products_per_modexp(kk, L // 32, WX, h.bit_length(), w, 2))
                 ops31 += ops_31bit_count(L, h.bit_length(), w)
-    rp = res["ragged_persistent_graph"]
     best = min(res, key=lambda m: res[m]["ms_per_step"])
+    # the value is the faster of the two single-replay plan forms (both one CUDA-graph launch per step)
+    vmode = min(("ragged_concurrent_graph", "ragged_persistent_graph"), key=lambda m: res[m]["ms_per_step"])
+    rp = res[vmode]
     for r in res.values():
         r["frac"] = 2 * prods / (r["ms_per_step"] / 1e3) / peak
         r["frac_31bit_count"] = ops31 / (r["ms_per_step"] / 1e3) / peak
     roofline = {"bound": "alu", "achieved": 2 * prods / (rp["ms_per_step"] / 1e3) / 1e12, "peak": peak / 1e12,
                 "unit": "T int32-mul/s", "frac": 2 * prods / (rp["ms_per_step"] / 1e3) / peak, "traffic": None,
-                "kernel": "whole step of the persistent graph-captured plan (all kernels)",
+                "kernel": f"whole step of the {vmode} plan (all kernels)",
                 "frac_31bit_count": ops31 / (rp["ms_per_step"] / 1e3) / peak,
                 "int32_mul_ops_per_step": 2 * prods, "int32_mul_ops_per_step_31bit_count": ops31,
                 "count": "implemented k, 2k^2+7k products per multiplication, the kernels' window schedules",
@@ -1309,12 +1311,14 @@ def run_ragged(args, rank, world, local_rank, emit=True):
             "config": {"workload": "ragged_mix_65536", "requests": len(xs), "modexps_per_step": modexps,
                        "keys": 256, "mix_bits": [b for b, _ in MIX], "mix_weights": [w for _, w in MIX],
                        "l2": "flushed between timed steps (512 MB write)", "modes": res,
-                       "fastest_mode": best,
+                       "fastest_mode": best, "value_mode": vmode,
                        "exact": "all modes identical; 256 seeded samples equal x^e mod N",
                        "autotune": {str(L): v for L, v in tuning.items()},
                        "speedup_vs_per_size_plain": res["per_size_plain"]["ms_per_step"] / rp["ms_per_step"],
                        "speedup_concurrent_vs_per_size_plain":
-                           res["per_size_plain"]["ms_per_step"] / res["ragged_concurrent_graph"]["ms_per_step"]},
+                           res["per_size_plain"]["ms_per_step"] / res["ragged_concurrent_graph"]["ms_per_step"],
+                       "speedup_persistent_vs_per_size_plain":
+                           res["per_size_plain"]["ms_per_step"] / res["ragged_persistent_graph"]["ms_per_step"]},
             "roofline": roofline, "cpu_baseline": cpu}
     ctx.close()
     if not emit:

@@ -370,7 +370,7 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
       if (!choose_big_variant(ctx, b.ce, b.mx.size(), &b.bigv, &b.slots))
         return fail(ctx, MR_ERR_CUDA, "large-class kernel does not fit the device");
       const BigKernel& bk = b.ce->kern->big[b.bigv];
-      b.scratch_words = (size_t)b.slots * bk.slot_words(b.wbits) + align256((b.slots + 1) * 4) / 4;
+      b.scratch_words = (size_t)b.slots * bk.slot_words(b.wbits) + align256(big_sync_words(b.slots) * 4) / 4;
     } else {
       b.scratch_words = modexp_scratch_words(b.ce->kv(), (uint32_t)b.mx.size(), b.wbits);
     }
@@ -431,7 +431,7 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
       BigArgs a{b.ce->dev, b.ce->tslice[b.bigv], reinterpret_cast<const MxItem*>(base + b.off_mx), (uint32_t)b.mx.size(),
                 b.wbits, scr, status, sync, b.slots, ctx->big_spin_limit ? ctx->big_spin_limit : BIG_SPIN_POLLS,
                 ctx->big_absent_slice, ctx->big_phases};
-      e = cudaMemsetAsync(sync, 0, (b.slots + 1) * 4, stream);
+      e = cudaMemsetAsync(sync, 0, big_sync_words(b.slots) * 4, stream);
       if (e == cudaSuccess) e = timed_launch(ctx, 0, stream, [&] { return bk.modexp(a, stream); });
       if (e == cudaSuccess && !b.crt.empty()) {
         const uint32_t n_off = key_offsets(b.ce->host.k, b.ce->host.W).N;
@@ -2127,7 +2127,7 @@ mr_status mr_debug_tc_mma(mr_ctx* ctx, const uint16_t* a, const uint16_t* b, uin
   // with exchanged offsets the tensor core reads up to 16 x 16 * rows bytes past each operand's start:
   // inside the 32 KB operand regions only for a single K step
   if (!ctx || !a || !b || !d || n < 16 || n > 128 || n % 16 || kdim < 16 || kdim > 64 || kdim % 16 ||
-      (swap_strides && kdim != 16))
+      swap_strides > 2 || (swap_strides == 1 && kdim != 16))
     return fail(ctx, MR_ERR_ARG, "bad arguments");
   cudaSetDevice(ctx->device);
   cudaError_t e = mr::tensor_debug_mma(a, b, n, kdim, swap_strides, d, (cudaStream_t)stream);

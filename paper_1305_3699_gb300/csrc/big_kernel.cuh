@@ -54,6 +54,7 @@ struct BigCfg {
   static constexpr int SMEM_BYTES = SM_WORDS * 4;
   // per-slot global scratch (words): xi, xi', slice partials, then the window table
   static constexpr size_t XG = 0, XPG = (size_t)K * 32, KAWG = (size_t)2 * K * 32;
+  static constexpr size_t KAWX = KAWG;  // slice partials of the exit conversion (barriers separate the uses)
   static constexpr size_t TAB = KAWG + (size_t)SLICES * 32;
   MR_HD static constexpr size_t slot_words(uint32_t wbits) { return TAB + ((size_t)1 << wbits) * 2 * K * 32; }
   static_assert(NPT == 4, "four channels per thread and base (one 16-byte matrix load per row)");
@@ -65,20 +66,30 @@ struct BigCfg {
 // Tensor-core form of the same kernel.  The two base extensions of a slice's CTA are the product
 // D (32 numbers x 32 channels) = X (32 x k) T (k x 32) of the CRT coefficients with its columns of
 // the class's extension matrix, every entry below 2^28 and the exact sum below 2^64.  Both factors
-// are split into four 7-bit slices, X = sum_a 2^(7a) X_a and T = sum_b 2^(7b) T_b; A holds X_a[n]
-// in row 32a + n (128 x k) and B = [T_0 T_1 T_2 T_3] (k x 128), multiplied on the tensor cores in
-// fp16 with fp32 accumulation: every entry of A B is a sum of k products below 127^2, exact in fp32
-// for k <= 1040.  The recombination D = sum_{a,b} 2^(7(a+b)) (A B)[32a + n, 32b + j] is exact in 64
-// bits.  A is written by the slot's CTAs (each its 32 channels, as fp16 slices in the shared-memory
-// operand layout of tc_device.cuh) into a per-slot buffer in global memory; B is a class table in
-// the same layout.  Each CTA streams both through a ring of STAGES shared-memory stages, 64 columns
-// of k per stage, with bulk copies completed on mbarriers.  Issuing a bulk copy costs its thread a
-// few hundred cycles whatever its size, so every stage has two copy threads of its own (its A half
-// and its B half, each on its own mbarrier); thread 0 waits for each chunk and issues its tcgen05
-// products (128 x 128 x 16 each) into a 128-column tensor-memory accumulator, and the tensor core's
-// completion frees the stage.  The epilogue reads the accumulator back (warp w: the lanes of data
-// slice w % 4), combines the slices through shared memory and hands every thread the same 64-bit
-// dot products the integer form computes.
+// are split into four 7-bit slices, X = sum_a 2^(7a) X_a and T = sum_b 2^(7b) T_b, and multiplied on
+// the tensor cores in fp16 with fp32 accumulation: every entry of a slice product is a sum of k
+// products below 127^2, exact in fp32 for k <= 1040, and the recombination
+// sum_{a,b} 2^(7(a+b)) X_a T_b is exact in 64 bits.  The data slices form a 128 x k operand, row
+// 32a + n, written by the slot's CTAs (each its 32 channels, in the shared-memory operand layout of
+// tc_device.cuh) into a per-slot buffer in global memory; the matrix slices form a k x 128 operand,
+// row 32b + j, of a class table in the same layout.  The first extension's matrix slices stay in
+// tensor memory for the whole launch (the A operand, columns TM_T1 ..; the product is
+// D^T = T1^T X^T, accumulator row 32b + j, column 32a + n), so that extension streams only the
+// data; the second streams data and T2 chunks (D = X T2, accumulator row 32a + n, column 32b + j).
+// A block publishes its slices of a data operand with a release increment of that chunk's counter
+// (two blocks write each chunk of 64 columns); the copy of a data chunk waits (acquire) for its
+// counter to reach the multiplication's target, so the chunks of early blocks stream while the last
+// ones are still being written, and no slot barrier separates the multiplications' exchanges.  Every
+// extension reads every chunk, so a block that has passed an extension knows that all blocks have
+// finished the previous one (the buffers' reuse is ordered without a barrier).
+// Everything streamed passes through a ring of STAGES 16 KB shared-memory stages (64 columns of k
+// of one operand each) filled by bulk copies completing on mbarriers, one copy thread per stage:
+// the stream is bound by the round trip of a stage (copy latency from L2 plus the products), so
+// the ring is as deep as shared memory allows.  Thread 0 waits for each chunk and issues its tcgen05
+// products (128 x 128 x 16 each) into a 128-column accumulator; the tensor core's completion frees
+// the stages.  The epilogue reads the accumulator back, combines the slices through shared memory
+// (aliasing the idle ring) and hands every thread the same 64-bit dot products the integer form
+// computes.
 // Everything else is the integer kernel's.
 template <int K_, int W_, int WX_>
 struct BigTcCfg {
@@ -88,41 +99,52 @@ struct BigTcCfg {
   static constexpr int SLICES = (K + SC - 1) / SC;
   static constexpr int THREADS = NW * 32;
   static constexpr int KC = 64;                       // columns of k per staged chunk
-  static constexpr int NCH = (K + KC - 1) / KC;       // chunks per extension
+  static constexpr int NCH = (K + KC - 1) / KC;       // chunks per operand
   static constexpr int KP = NCH * KC;                 // padded k
-  static constexpr int STAGES = 4;                    // ring stages, two copy threads each
-  static constexpr int PRE = (STAGES < NCH) ? STAGES : NCH;  // chunks whose B is fetched at the barrier
+  static constexpr int STAGES = 14;                   // ring stages of one operand chunk each
   static constexpr uint32_t CHUNK_BYTES = 128u * KC * 2u;  // one operand chunk: 128 rows x 64 fp16
-  static constexpr uint32_t TMEM_COLS = 128;
-  static constexpr int EX_LS = 17;                    // exchange: 64-bit words per lane (16 + 1 pad)
+  static constexpr uint32_t TMEM_COLS = 512;
+  static constexpr uint32_t TM_T1 = 128;              // first tensor-memory column of the resident T1 slices
+  static constexpr int EX_LS = 17;                    // second-extension exchange: 64-bit words per lane
+  static constexpr int EX1_LS = 33;                   // first-extension exchange: 32-bit words per row
   // shared memory (words)
-  static constexpr int SM_RING = 0;                   // STAGES x [A chunk | B chunk]
-  static constexpr int SM_T1 = SM_RING;               // staging area of the RNS -> binary conversion
-  static constexpr int SM_EX = SM_RING + STAGES * 2 * (int)CHUNK_BYTES / 4;  // [4 a][2 halves][32][EX_LS] u64
-  static constexpr int SM_C4A = SM_EX + 4 * 2 * 32 * EX_LS * 2;
+  static constexpr int SM_RING = 0;                   // STAGES operand chunks
+  static constexpr int SM_T1 = SM_RING;               // staging of the RNS -> binary conversion
+  static constexpr int SM_EX = SM_RING;               // exchange buffers of the epilogues (ring, idle then)
+  static constexpr int SM_C4A = SM_RING + STAGES * (int)CHUNK_BYTES / 4;
   static constexpr int SM_C4B = SM_C4A + 4 * SC;
   static constexpr int SM_C2A = SM_C4B + 4 * SC;
   static constexpr int SM_C2B = SM_C2A + 2 * SC;
   static constexpr int SM_KAW = SM_C2B + 2 * SC;
   static constexpr int SM_MISC = SM_KAW + NW * 32;
-  static constexpr int SM_MBAR = SM_MISC + 32;        // full_a[S], full_b[S], empty[S], done (8 bytes each)
-  static constexpr int SM_TMEM = SM_MBAR + 2 * (3 * STAGES + 1);
+  static constexpr int SM_MBAR = SM_MISC + 32;        // full[S], empty[S], done (8 bytes each)
+  static constexpr int SM_TMEM = SM_MBAR + 2 * (2 * STAGES + 1);
   static constexpr int SM_PH = SM_TMEM + 4;           // phase counters: BIG_PHASES sums, last time stamp (u64)
   static constexpr int SM_WORDS = SM_PH + 2 * (BIG_PHASES + 1);
   static constexpr int SMEM_BYTES = SM_WORDS * 4;
-  // per-slot global scratch (words): the A operands of the two extensions, the plain CRT coefficients
-  // of the exit conversion, slice partials, then the window table
+  // per-slot global scratch (words): the data operands of the two extensions, the plain CRT
+  // coefficients of the exit conversion, slice partials, then the window table
   static constexpr size_t AOP_WORDS = (size_t)NCH * CHUNK_BYTES / 4;
   static constexpr size_t AG1 = 0, AG2 = AOP_WORDS, XG = 2 * AOP_WORDS, KAWG = XG + (size_t)K * 32;
-  static constexpr size_t TAB = KAWG + (size_t)SLICES * 32;
+  // the exit conversion's slice partials: a buffer of their own, since no barrier separates them from the
+  // last multiplication's partials, which slower blocks may still be reading
+  static constexpr size_t KAWX = KAWG + (size_t)SLICES * 32;
+  static constexpr size_t TAB = KAWX + (size_t)SLICES * 32;
   MR_HD static constexpr size_t slot_words(uint32_t wbits) { return TAB + ((size_t)1 << wbits) * 2 * K * 32; }
-  // class table: [slice][extension][chunk] operand chunks of B
+  // class table: [slice][extension][chunk] operand chunks of the matrix slices
   static constexpr size_t BTAB_BYTES = (size_t)2 * SLICES * NCH * CHUNK_BYTES;
-  static_assert(K * 32 <= STAGES * 2 * (int)CHUNK_BYTES / 4, "RNS -> binary staging fits the ring");
+  static_assert(K * 32 <= SM_C4A, "RNS -> binary staging fits the ring");
+  static_assert(4 * 2 * 32 * EX_LS * 2 <= SM_C4A, "second exchange fits the ring");
+  static_assert(2 * 4 * 32 * EX1_LS <= SM_C4A, "first exchange fits the ring");
+  static_assert(TM_T1 + KP / 2 <= TMEM_COLS, "accumulator and resident T1 fit tensor memory");
   static_assert(SLICES * SC <= KP, "every slice's columns lie inside the padded operand");
-  static_assert((SM_MBAR % 2) == 0 && (SM_C4A % 4) == 0 && (SM_EX % 2) == 0 && (SM_PH % 2) == 0, "alignment");
+  static_assert((SM_MBAR % 2) == 0 && (SM_C4A % 4) == 0 && (SM_PH % 2) == 0, "alignment");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
   static_assert(K <= 1040, "7-bit slices: k * 127^2 < 2^24 keeps every fp32 partial sum exact");
+  static_assert(STAGES <= 32, "copy threads are lanes of warp 1");
+  static_assert(2 * NCH <= (int)BIG_FLAG_WORDS, "chunk-ready counters");
+  // blocks (channel slices) writing chunk c of a data operand: slices 2c and 2c + 1
+  __device__ static constexpr uint32_t producers(int c) { return SLICES - 2 * c >= 2 ? 2u : 1u; }
 };
 
 template <class C>
@@ -131,6 +153,8 @@ struct BigGroup {
   uint32_t* slot;      // this slot's global scratch
   uint32_t* ctr;       // this slot's barrier counter
   uint32_t* abort;     // launch-wide abort flag
+  uint32_t* flags;     // tensor-core form: this slot's chunk-ready counters [extension][chunk]
+  uint32_t nmul;       // tensor-core form: multiplications started by this block
   uint32_t nbar;       // barriers passed so far (target = nbar * SLICES)
   uint32_t spin_limit; // polls before a wait gives up
   uint32_t ph;         // parity bits of the two staging mbarriers
@@ -158,10 +182,7 @@ struct BigGroup {
   __device__ uint2 b2(int q) const { return reinterpret_cast<const uint2*>(s + C::SM_C2B)[q]; }
 
   // All CTAs of the slot meet; false when the wait ran out or another CTA aborted.
-  // Tensor-core form: `prefetch_b` (non-null) names the B operand of the extension that follows the
-  // barrier; the B copy threads start its first chunks' copies while thread 0 arrives and waits (B
-  // does not depend on the other CTAs), so their latency hides behind the wait.
-  __device__ bool barrier(const uint8_t* prefetch_b = nullptr);
+  __device__ bool barrier();
 
 };
 
@@ -274,107 +295,132 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-// Copy threads: lanes 0 .. 2 STAGES - 1 of warp 1; lane 2 st + h copies half h (0: A, 1: B) of every
-// chunk that lands in stage st, completing on that half's own mbarrier.  A stage's two copy threads
-// alone refill it, so neither runs more than one mbarrier phase ahead.  Returns the lane, or -1.
+// Copy threads: lanes 0 .. STAGES - 1 of warp 1; lane st copies every operand chunk that lands in
+// stage st, completing on that stage's mbarrier.  A stage's copy thread alone refills it, so it never
+// runs more than one mbarrier phase ahead.  Returns the stage, or -1.
 template <class C>
 __device__ __forceinline__ int tc_copier() {
-  return (threadIdx.x >= 32 && threadIdx.x < 32 + 2 * C::STAGES) ? (int)threadIdx.x - 32 : -1;
+  return (threadIdx.x >= 32 && threadIdx.x < 32 + C::STAGES) ? (int)threadIdx.x - 32 : -1;
 }
 
-// The chunk of the extension starting at ring position g0 that is the first to land in stage st.
+// The unit (operand chunk) of the extension starting at ring position g0 that is the first to land in
+// stage st.
 template <class C>
-__device__ __forceinline__ int tc_first_chunk(uint32_t g0, int st) {
+__device__ __forceinline__ int tc_first_unit(uint32_t g0, int st) {
   return (st - (int)(g0 % C::STAGES) + C::STAGES) % C::STAGES;
 }
 
-// B copy thread of stage st, at the slot barrier: the B half of the next extension's first chunk in
-// that stage (B does not depend on the other CTAs), so its latency hides behind the barrier.  The
-// stage is free: every product of the previous extension has completed.
+// Tensor-core form: publish this block's slices of the data operand of extension e (every thread has
+// stored its part; the counter of the chunk they lie in is raised with release semantics).  The proxy
+// fences make each thread's generic stores visible to the copy engines (async proxy) of the readers,
+// and order its generic accesses to the ring before the copies that refill it.
 template <class C>
-__device__ __forceinline__ void tc_prefetch_b(BigGroup<C>& g, const uint8_t* bop, int st) {
-  constexpr uint32_t CB = C::CHUNK_BYTES;
-  const int c = tc_first_chunk<C>(g.chunk, st);
-  if (c >= C::PRE) return;
-  uint8_t* const ring = reinterpret_cast<uint8_t*>(g.s + C::SM_RING);
-  uint64_t* const full_b = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR) + C::STAGES;
-  mbar_expect_tx(&full_b[st], CB);
-  bulk_g2s(ring + (size_t)st * 2 * CB + CB, bop + (size_t)((c + g.stag) % C::NCH) * CB, CB, &full_b[st]);
+__device__ __forceinline__ void tc_publish(BigGroup<C>& g, int e) {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  // and this thread's generic accesses to the ring (epilogue exchanges) before the next copies into it
+  tc::fence_smem_async();
+  __syncthreads();
+  if (threadIdx.x == 0)  // release, cumulative over the block's stores ordered by the barrier
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(g.flags + e * (BIG_FLAG_WORDS / 2) + g.c / 2)
+                 : "memory");
 }
 
-// The same thread when the barrier gave up: wait (bounded) for the prefetched copy before the block
-// can exit.
+// Wait (acquire) until chunk c of extension e's data operand holds every producer's slices for this
+// block's current multiplication; false when the wait ran out (abort raised) or another block aborted.
 template <class C>
-__device__ void tc_drain_prefetch(BigGroup<C>& g, int st) {
-  const int c = tc_first_chunk<C>(g.chunk, st);
-  if (c >= C::PRE) return;
-  uint64_t* const full_b = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR) + C::STAGES;
-  mbar_wait(&full_b[st], ((g.chunk + c) / C::STAGES) & 1u, g.spin_limit);
+__device__ __forceinline__ bool tc_wait_chunk(const BigGroup<C>& g, int e, int c) {
+  const uint32_t target = g.nmul * C::producers(c);
+  const uint32_t* f = g.flags + e * (BIG_FLAG_WORDS / 2) + c;
+  for (uint32_t it = 0;; it++) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    if ((int32_t)(v - target) >= 0) return true;
+    if (*(volatile uint32_t*)g.abort) return false;
+    if (it >= g.spin_limit) {
+      atomicExch(g.abort, 1u);
+      return false;
+    }
+    if (it >= 2048) __nanosleep(128);
+  }
 }
 
 // One base extension on the tensor cores (see BigTcCfg): acc[s] = sum_i X[lane][i] T[i][4w + s], exact,
-// from the slot's A operand `aop` (all slices written, the slot barrier passed) and this slice's B
-// operand `bop`.  Thread 0 waits for each chunk and issues its products; the copy threads refill the
-// stages.  False (abort raised) when a copy or the tensor core does not complete in time.
-template <class C>
-__device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, const uint8_t* bop, int ph0) {
-  constexpr int S = C::STAGES, NCH = C::NCH;
+// from the slot's data operand `aop` (all slices written, the slot barrier passed).  E = 1: the first
+// extension, T1 resident in tensor memory (D^T = T1^T X^T), one streamed unit per chunk of k (data);
+// E = 2: the second, two units per chunk (data, then this slice's T2 chunk `bop`).  Chunk positions
+// are rotated by the block's offset so that blocks sharing an operand do not read the same chunk at
+// once.  Thread 0 waits for each chunk and issues its products; the copy threads refill the stages.
+// False (abort raised) when a copy or the tensor core does not complete in time.
+template <class C, int E>
+__device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, const uint8_t* bop, int ph0,
+                       const uint32_t* kawg = nullptr, uint32_t* ksum = nullptr) {
+  constexpr int S = C::STAGES, NCH = C::NCH, U = E * NCH;  // units streamed by this extension
   constexpr uint32_t CB = C::CHUNK_BYTES;
   uint8_t* const ring = reinterpret_cast<uint8_t*>(g.s + C::SM_RING);
-  uint64_t* const full_a = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
-  uint64_t* const full_b = full_a + S;
-  uint64_t* const empty = full_b + S;
+  uint64_t* const full = reinterpret_cast<uint64_t*>(g.s + C::SM_MBAR);
+  uint64_t* const empty = full + S;
   uint64_t* const done = empty + S;
   const uint32_t taddr = g.s[C::SM_TMEM];
   const uint32_t g0 = g.chunk;
   uint32_t ok = 1;
   const int t = tc_copier<C>();
   if (t >= 0) {
-    const int st = t >> 1, half = t & 1;
-    if (half == 0) {
-      // the slot's A stores: seen by thread 0's acquire at the slot barrier, ordered for this thread by
-      // the block barrier and this fence, then made visible to the copy engine (async proxy)
-      asm volatile("fence.acq_rel.gpu;" ::: "memory");
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-    }
-    uint64_t* const fb = half ? &full_b[st] : &full_a[st];
-    const uint8_t* const src = half ? bop : aop;
-    uint8_t* const dst = ring + (size_t)st * 2 * CB + (half ? CB : 0);
+    const int st = t;
+    uint8_t* const dst = ring + (size_t)st * CB;
     int last = -1;
-    for (int c = tc_first_chunk<C>(g0, st); c < NCH; c += S) {
-      // the stage's previous chunk (c - S, or the previous extension's, complete) must have been
+    for (int u = tc_first_unit<C>(g0, st); u < U; u += S) {
+      // the stage's previous unit (u - S, or the previous extension's, complete) must have been
       // consumed by the tensor core before the refill
-      if (c >= S && !mbar_wait(&empty[st], ((g0 + c - S) / S) & 1u, g.spin_limit)) {
+      if (u >= S && !mbar_wait(&empty[st], ((g0 + u - S) / S) & 1u, g.spin_limit)) {
         ok = 0;
         break;
       }
-      if (half == 1 && c < C::PRE) continue;  // the first chunks' B halves were started at the barrier
-      mbar_expect_tx(fb, CB);
-      bulk_g2s(dst, src + (size_t)((c + g.stag) % NCH) * CB, CB, fb);  // position c holds chunk c + stag
-      last = c;
+      const int c = (u / E + g.stag) % NCH;  // position u / E holds chunk u / E + stag
+      const bool data = !(E == 2 && (u & 1));
+      if (data && !tc_wait_chunk<C>(g, E - 1, c)) {  // the producers' slices of this chunk are published
+        ok = 0;
+        break;
+      }
+      const uint8_t* src = data ? aop + (size_t)c * CB : bop + (size_t)c * CB;
+      mbar_expect_tx(&full[st], CB);
+      bulk_g2s(dst, src, CB, &full[st]);
+      last = u;
     }
     if (!ok) {
       atomicExch(g.abort, 1u);
-      if (last >= 0) mbar_wait(fb, ((g0 + last) / S) & 1u, g.spin_limit);  // no copy left in flight
+      if (last >= 0) mbar_wait(&full[st], ((g0 + last) / S) & 1u, g.spin_limit);  // no copy left in flight
     }
   } else if (threadIdx.x == 0) {
     constexpr uint32_t idesc = tc::idesc_f16_f32(128, 128);
-    for (int c = 0; c < NCH; c++) {
-      const uint32_t gc = g0 + c, st = gc % S, par = (gc / S) & 1u;
-      if (!mbar_wait(&full_a[st], par, g.spin_limit) || !mbar_wait(&full_b[st], par, g.spin_limit)) {
-        ok = 0;
-        break;
+    for (int c = 0; c < NCH && ok; c++) {
+      const uint32_t cc = (c + g.stag) % NCH;  // the chunk of k at position c
+      uint32_t sx = 0, sb = 0;                 // stages of the data and (second extension) T2 units
+#pragma unroll
+      for (int e = 0; e < E; e++) {
+        const uint32_t gu = g0 + E * c + e, st = gu % S;
+        if (!mbar_wait(&full[st], (gu / S) & 1u, g.spin_limit)) {
+          ok = 0;
+          break;
+        }
+        if (e == 0) sx = st;
+        else sb = st;
       }
+      if (!ok) break;
       tc::fence_after_sync();
-      const uint32_t a0 = smem_u32(ring + (size_t)st * 2 * CB), b0 = a0 + CB;
+      const uint32_t x0 = smem_u32(ring + (size_t)sx * CB), b0 = smem_u32(ring + (size_t)sb * CB);
 #pragma unroll
       for (int ks = 0; ks < C::KC / 16; ks++) {
-        // K step: column groups 2ks, 2ks + 1 (leading offset 16 x 128 rows, stride offset 128 bytes)
-        const uint64_t ad = tc::sdesc(a0 + ks * 4096u, 2048u, 128u);
-        const uint64_t bd = tc::sdesc(b0 + ks * 4096u, 2048u, 128u);
-        tc::mma_f16(taddr, ad, bd, idesc, (c | ks) ? 1u : 0u);
+        // K step ks: column groups 2ks, 2ks + 1 (leading offset 16 x 128 rows, stride offset 128 bytes)
+        const uint64_t xd = tc::sdesc(x0 + ks * 4096u, 2048u, 128u);
+        const uint32_t acc_in = (c | ks) ? 1u : 0u;
+        if constexpr (E == 1) {
+          tc::mma_f16_ts(taddr, taddr + C::TM_T1 + 32u * cc + 8u * ks, xd, idesc, acc_in);
+        } else {
+          tc::mma_f16(taddr, xd, tc::sdesc(b0 + ks * 4096u, 2048u, 128u), idesc, acc_in);
+        }
       }
-      tc::mma_commit(&empty[st]);
+      tc::mma_commit(&empty[sx]);
+      if constexpr (E == 2) tc::mma_commit(&empty[sb]);
     }
     tc::mma_commit(done);
     // on failure, still give the issued products a bounded chance to finish before the tensor memory is
@@ -383,52 +429,91 @@ __device__ bool tc_ext(uint64_t (&acc)[4], BigGroup<C>& g, const uint8_t* aop, c
     if (!ok) atomicExch(g.abort, 1u);
     g.mark(ph0);
   }
-  g.chunk += NCH;
+  g.chunk += U;
   g.done_ph ^= 1u;
   if (__syncthreads_or(!ok)) return false;
   tc::fence_after_sync();
-  // epilogue: warp w reads the lanes of data slice a = w % 4 (its number = lane), columns of the channels
-  // 16h .. 16h+15 (h = w / 4) of all four matrix slices; combines the matrix slices, then the four
-  // warps of each half combine the data slices through shared memory
-  const int qa = g.w & 3, h = g.w >> 2;
-  uint64_t part[16];
+  // second extension: every chunk has been seen (acquire, then the block barrier above), so every
+  // block's correction-factor partial is visible; the loads overlap the epilogue
+  uint32_t kp[E == 2 ? C::SLICES : 1];
+  if constexpr (E == 2) {
 #pragma unroll
-  for (int j = 0; j < 16; j++) part[j] = 0;
-#pragma unroll
-  for (int b = 0; b < 4; b++) {
-    uint32_t v[16];
-    tc::tmem_ld16(taddr + ((uint32_t)(32 * qa) << 16) + 32u * b + 16u * h, v);
-    tc::tmem_ld_wait();
-#pragma unroll
-    for (int j = 0; j < 16; j++) part[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) << (7 * b);
+    for (int u = 0; u < C::SLICES; u++) kp[u] = __ldcg(kawg + u * 32 + g.lane);
   }
-  uint64_t* ex = reinterpret_cast<uint64_t*>(g.s + C::SM_EX);
+  if constexpr (E == 1) {
+    // epilogue of D^T: warp w reads lane quarter b = w % 4 (matrix slice b, channel j = lane) and the
+    // columns of data slices 2h, 2h + 1 (h = w / 4) of all 32 numbers; the two data slices combine in
+    // 32 bits (below 2^24 + 2^31), then the owner of (number, channel) sums the eight partials
+    const int b = g.w & 3, h = g.w >> 2;
+    uint32_t* ex = g.s + C::SM_EX;  // [2 h][4 b][32 j][EX1_LS] u32
+    uint32_t* row = ex + ((h * 4 + b) * 32 + g.lane) * C::EX1_LS;
 #pragma unroll
-  for (int j = 0; j < 16; j++) ex[((qa * 2 + h) * 32 + g.lane) * C::EX_LS + j] = part[j] << (7 * qa);
-  tc::fence_before_sync();
-  __syncthreads();
-  const int jb = 4 * g.w - 16 * h;  // this thread's channels 4w .. 4w+3 within half h
+    for (int nn = 0; nn < 32; nn += 16) {
+      uint32_t va[16], vb[16];
+      tc::tmem_ld16(taddr + ((uint32_t)(32 * b) << 16) + 64u * h + nn, va);
+      tc::tmem_ld16(taddr + ((uint32_t)(32 * b) << 16) + 64u * h + 32u + nn, vb);
+      tc::tmem_ld_wait();
 #pragma unroll
-  for (int s = 0; s < 4; s++) {
-    uint64_t v = 0;
+      for (int j = 0; j < 16; j++)
+        row[nn + j] = __float2uint_rn(__uint_as_float(va[j])) + (__float2uint_rn(__uint_as_float(vb[j])) << 7);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 4; q++) v += ex[((q * 2 + h) * 32 + g.lane) * C::EX_LS + jb + s];
-    acc[s] = v;
+    for (int s = 0; s < 4; s++) {
+      const int ch = 4 * g.w + s;
+      uint64_t v = 0;
+#pragma unroll
+      for (int q = 0; q < 8; q++)  // q = 4 hh + bb: shift 7 (2 hh + bb)
+        v += (uint64_t)ex[(q * 32 + ch) * C::EX1_LS + g.lane] << (7 * (2 * (q >> 2) + (q & 3)));
+      acc[s] = v;
+    }
+  } else {
+    // epilogue of D: warp w reads the lanes of data slice a = w % 4 (its number = lane), columns of the
+    // channels 16h .. 16h+15 (h = w / 4) of all four matrix slices; combines the matrix slices, then
+    // the four warps of each half combine the data slices through shared memory
+    const int qa = g.w & 3, h = g.w >> 2;
+    uint64_t part[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) part[j] = 0;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      uint32_t v[16];
+      tc::tmem_ld16(taddr + ((uint32_t)(32 * qa) << 16) + 32u * b + 16u * h, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 16; j++) part[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) << (7 * b);
+    }
+    uint64_t* ex = reinterpret_cast<uint64_t*>(g.s + C::SM_EX);
+#pragma unroll
+    for (int j = 0; j < 16; j++) ex[((qa * 2 + h) * 32 + g.lane) * C::EX_LS + j] = part[j] << (7 * qa);
+    tc::fence_before_sync();
+    __syncthreads();
+    const int jb = 4 * g.w - 16 * h;  // this thread's channels 4w .. 4w+3 within half h
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+      uint64_t v = 0;
+#pragma unroll
+      for (int q = 0; q < 4; q++) v += ex[((q * 2 + h) * 32 + g.lane) * C::EX_LS + jb + s];
+      acc[s] = v;
+    }
+  }
+  if constexpr (E == 2) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int u = 0; u < C::SLICES; u++) v += kp[u];
+    *ksum = v;
   }
   g.mark(ph0 + 1);
   return true;
 }
 
 template <class C>
-__device__ bool BigGroup<C>::barrier(const uint8_t* prefetch_b) {
+__device__ bool BigGroup<C>::barrier() {
   nbar++;
-  // the ring's generic accesses (the exit conversion stages through it) before any copy into it
+  // the ring's generic accesses (epilogue exchanges, the exit conversion's staging) before any copy into it
   if constexpr (C::TC) tc::fence_smem_async();
   __syncthreads();
-  if constexpr (C::TC) {
-    const int t = tc_copier<C>();
-    if (prefetch_b && t >= 0 && (t & 1)) tc_prefetch_b<C>(*this, prefetch_b, t >> 1);
-  }
   if (threadIdx.x == 0) {
     const uint32_t target = nbar * (uint32_t)C::SLICES;
     __threadfence();
@@ -452,12 +537,7 @@ __device__ bool BigGroup<C>::barrier(const uint8_t* prefetch_b) {
     s[C::SM_MISC] = ok;
   }
   __syncthreads();
-  const bool passed = s[C::SM_MISC] != 0;
-  if constexpr (C::TC) {
-    const int t = tc_copier<C>();
-    if (!passed && prefetch_b && t >= 0 && (t & 1)) tc_drain_prefetch<C>(*this, t >> 1);
-  }
-  return passed;
+  return s[C::SM_MISC] != 0;
 }
 
 // RNS Montgomery multiplication x <- x*y*M^-1 mod N (outputs below (k+1)N), this thread's channels.
@@ -480,26 +560,27 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
     const uint4 cp = g.b4(q);
     sp[s] = redc_lazy(mulw(xp[s], yp[s]), cp.x, cp.y);
   }
-  const uint8_t* pre1 = nullptr;
   if constexpr (C::TC) {
+    g.nmul++;
     tc_put_slices<C>(reinterpret_cast<uint8_t*>(g.slot + C::AG1), xv, g.c * C::SC + g.w * NPT, g.lane);
-    pre1 = g.btab;
+    g.mark(0);
+    tc_publish<C>(g, 0);
   } else {
 #pragma unroll
     for (int s = 0; s < NPT; s++) {
       const int o = g.c * C::SC + g.w * NPT + s;
       if (o < K) g.slot[C::XG + (size_t)o * 32 + g.lane] = xv[s];
     }
+    g.mark(0);
+    if (!g.barrier()) return false;
   }
-  g.mark(0);
-  if (!g.barrier(pre1)) return false;
   g.mark(1);
   // 3. extension B -> B'
   uint64_t acc[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; s++) acc[s] = 0;
   if constexpr (C::TC) {
-    if (!tc_ext<C>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG1), g.btab, 2)) return false;
+    if (!tc_ext<C, 1>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG1), nullptr, 2)) return false;
   } else {
     if (!big_ext<C>(acc, g, g.slot + C::XG, g.s + C::SM_T1)) return false;
   }
@@ -532,30 +613,29 @@ __device__ bool big_mont_mul(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], con
     for (int u = 0; u < C::NW; u++) v += g.s[C::SM_KAW + u * 32 + g.lane];
     KAWg[g.c * 32 + g.lane] = v;
   }
-  const uint8_t* pre2 = nullptr;
-  if constexpr (C::TC) {
-    pre2 = g.btab + (size_t)C::NCH * C::CHUNK_BYTES;
-  }
   g.mark(4);
-  if (!g.barrier(pre2)) return false;
-  g.mark(5);
-  // 6. exact extension B' -> B with a' from the slice partials (loaded before the dot products,
-  //    summed after them); the correction -a'|M'| enters as a' E with E = -M' 2^64 mod m_i
-  uint32_t kp[C::SLICES];
-#pragma unroll
-  for (int u = 0; u < C::SLICES; u++) kp[u] = __ldcg(KAWg + u * 32 + g.lane);
+  // 6. exact extension B' -> B with a' from the slice partials; the correction -a'|M'| enters as a' E
+  //    with E = -M' 2^64 mod m_i
 #pragma unroll
   for (int s = 0; s < NPT; s++) acc[s] = 0;
+  uint32_t ks = 0;
   if constexpr (C::TC) {
-    if (!tc_ext<C>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG2), g.btab + (size_t)C::NCH * C::CHUNK_BYTES,
-                   6))
+    tc_publish<C>(g, 1);  // after the partial: every block's partial is visible once its chunk is
+    g.mark(5);
+    if (!tc_ext<C, 2>(acc, g, reinterpret_cast<const uint8_t*>(g.slot + C::AG2),
+                      g.btab + (size_t)C::NCH * C::CHUNK_BYTES, 6, KAWg, &ks))
       return false;
   } else {
-    if (!big_ext<C>(acc, g, g.slot + C::XPG, g.s + C::SM_T2)) return false;
-  }
-  uint32_t ks = 0;
+    if (!g.barrier()) return false;
+    g.mark(5);
+    // loaded before the dot products, summed after them
+    uint32_t kp[C::SLICES];
 #pragma unroll
-  for (int u = 0; u < C::SLICES; u++) ks += kp[u];
+    for (int u = 0; u < C::SLICES; u++) kp[u] = __ldcg(KAWg + u * 32 + g.lane);
+    if (!big_ext<C>(acc, g, g.slot + C::XPG, g.s + C::SM_T2)) return false;
+#pragma unroll
+    for (int u = 0; u < C::SLICES; u++) ks += kp[u];
+  }
   const uint32_t alpha = (ks + (1u << (KAW_Q - 2))) >> KAW_Q;
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
@@ -654,7 +734,7 @@ __device__ void big_from_rns(const MxItem& it, const uint32_t* cls, bool write, 
   __syncthreads();
   if (g.w != 0) return;
   uint32_t ks = 0;
-  for (int u = 0; u < C::SLICES; u++) ks += __ldcg(g.slot + C::KAWG + u * 32 + g.lane);
+  for (int u = 0; u < C::SLICES; u++) ks += __ldcg(g.slot + C::KAWX + u * 32 + g.lane);
   const uint32_t alpha = (ks + (1u << (KAW_Q - 2))) >> KAW_Q;
   uint32_t X[WX];
   const uint32_t* MD = cls + co.MD;
@@ -859,7 +939,7 @@ __device__ bool big_modexp_group(const BigArgs& a, BigGroup<C>& g, uint32_t grp)
   if (g.w == 0) {
     uint32_t v = 0;
     for (int u = 0; u < C::NW; u++) v += g.s[C::SM_KAW + u * 32 + g.lane];
-    g.slot[C::KAWG + g.c * 32 + g.lane] = v;
+    g.slot[C::KAWX + g.c * 32 + g.lane] = v;
   }
   if (!g.barrier()) return false;
   if (g.c == 0) {
@@ -886,6 +966,8 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
   g.slot = a.scratch + (size_t)slot_id * C::slot_words(a.wbits);
   g.ctr = a.sync + slot_id;
   g.abort = a.sync + a.slots;
+  g.flags = a.sync + a.slots + 1 + (size_t)slot_id * BIG_FLAG_WORDS;
+  g.nmul = 0;
   g.nbar = 0;
   g.spin_limit = a.spin_limit;
   g.ph = 0;
@@ -899,7 +981,7 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
   if (threadIdx.x == 0) {
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem_raw + C::SM_MBAR);
     int nmb = 2;  // staging copies of the integer form
-    if constexpr (C::TC) nmb = 3 * C::STAGES + 1;  // A full, B full and empty per stage, accumulator complete
+    if constexpr (C::TC) nmb = 2 * C::STAGES + 1;  // full and empty per stage, accumulator complete
     for (int i = 0; i < nmb; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mb[i])));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -927,6 +1009,22 @@ __global__ void __launch_bounds__(C::THREADS, 1) big_modexp_kernel(BigArgs a) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    // this slice's T1 slices into tensor memory for the whole launch: row r = 32b + j in lane r, k in
+    // columns TM_T1 + k / 2; warp w writes its lane quarter w % 4, half w / 4 of the columns
+    {
+      const uint32_t taddr = smem_raw[C::SM_TMEM];
+      const int q = g.w & 3, h = g.w >> 2, r = 32 * q + g.lane;
+      constexpr int G8 = C::KP / 8;  // groups of 8 values of k: 16 bytes of a row, 4 columns
+      for (int kg = h * (G8 / 2); kg < (h + 1) * (G8 / 2); kg++) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(g.btab + (size_t)(kg / 8) * C::CHUNK_BYTES +
+                                                             tc::tile_off(128, r, (kg % 8) * 8)));
+        tc::tmem_st4(taddr + ((uint32_t)(32 * q) << 16) + C::TM_T1 + 4u * kg, v);
+      }
+      tc::tmem_st_wait();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    }
   }
   big_load_consts<C>(smem_raw, a.cls, g.c);
   const uint32_t n_groups = (a.n_items + 31) / 32;

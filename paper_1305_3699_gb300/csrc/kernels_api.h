@@ -50,7 +50,8 @@ struct BigArgs {
   uint32_t wbits;          // window width, 1..8
   uint32_t* scratch;       // per group slot: slot_words(wbits) words
   uint8_t* status;         // per-item status bytes or nullptr
-  uint32_t* sync;          // [slots] barrier counters, then the abort flag; zeroed before the launch
+  uint32_t* sync;          // [slots] barrier counters, the abort flag, then [slots][BIG_FLAG_WORDS] chunk-ready
+                           // counters (tensor-core form); zeroed before the launch (big_sync_words)
   uint32_t slots;          // item groups in flight (grid = slots * slices)
   uint32_t spin_limit;     // barrier polls before a wait gives up
   int32_t absent_slice;    // test hook: CTAs of this channel slice leave at once (-1: none)
@@ -63,6 +64,11 @@ struct BigArgs {
 // up to the second exchange, second barrier, second extension's copies and products, its epilogue and the
 // final channel work.
 constexpr int BIG_PHASES = 8;
+
+// Chunk-ready counters per slot of the tensor-core form: [2 extensions][16 chunks of k].
+constexpr uint32_t BIG_FLAG_WORDS = 32;
+// Words of a launch's sync area (zeroed before the launch).
+inline size_t big_sync_words(uint32_t slots) { return (size_t)slots * (1 + BIG_FLAG_WORDS) + 1; }
 
 // [special, s, nbits, 0][M mod N: W][M^2 mod N: W][kxi: k][N M^-1 (plain): k][cd: k][N^-1 mod m_i: k][N^-1 mod m'_j: k]
 MR_HD inline uint32_t mr_debug_words(uint32_t k, uint32_t W) { return 4 + 2 * W + 5 * k; }

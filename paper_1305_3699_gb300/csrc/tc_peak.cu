@@ -160,14 +160,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_debug_mma_kernel(const uint1
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t taddr = *tslot;
+  const bool a_tmem = swap_strides == 2;  // A from tensor memory, columns n .. n + kdim/2 - 1
+  if (a_tmem) {
+    // row 32 w + lane of A into lane 32 w + lane: two fp16 values of K per column, lower index low
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31, row = 32 * w + lane;
+    for (uint32_t k0 = 0; k0 < kdim; k0 += 8) {
+      uint32_t p[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) p[j] = (uint32_t)A[row * kdim + k0 + 2 * j] | ((uint32_t)A[row * kdim + k0 + 2 * j + 1] << 16);
+      tc::tmem_st4(taddr + ((32 * w) << 16) + n + k0 / 2, make_uint4(p[0], p[1], p[2], p[3]));
+    }
+    tc::tmem_st_wait();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
   if (threadIdx.x == 0) {
     const uint32_t id = tc::idesc_f16_f32(TC_M, n);
     for (uint32_t s = 0; s < kdim / 16; s++) {
       // K step s: column groups 2s, 2s+1
       const uint32_t a0 = tc::saddr(as) + 2 * s * 16 * TC_M, b0 = tc::saddr(bs) + 2 * s * 16 * n;
-      const uint64_t ad = swap_strides ? tc::sdesc(a0, 128, 16 * TC_M) : tc::sdesc(a0, 16 * TC_M, 128);
-      const uint64_t bd = swap_strides ? tc::sdesc(b0, 128, 16 * n) : tc::sdesc(b0, 16 * n, 128);
-      tc::mma_f16(taddr, ad, bd, id, s > 0 ? 1u : 0u);
+      const bool sw = swap_strides == 1;
+      const uint64_t ad = sw ? tc::sdesc(a0, 128, 16 * TC_M) : tc::sdesc(a0, 16 * TC_M, 128);
+      const uint64_t bd = sw ? tc::sdesc(b0, 128, 16 * n) : tc::sdesc(b0, 16 * n, 128);
+      if (a_tmem)
+        tc::mma_f16_ts(taddr, taddr + n + 8 * s, bd, id, s > 0 ? 1u : 0u);
+      else
+        tc::mma_f16(taddr, ad, bd, id, s > 0 ? 1u : 0u);
     }
     tc::mma_commit(mbar);
   }

@@ -20,10 +20,12 @@ def _ints(r, rows, cols, hi):
     return np.array([[r.below(hi) for _ in range(cols)] for _ in range(rows)], dtype=np.float64)
 
 
+@pytest.mark.parametrize("a_in_tmem", [0, 1])
 @pytest.mark.parametrize("n,kdim", [(128, 64), (16, 16), (64, 32), (128, 16)])
-def test_tc_mma_exact_small_integers(n, kdim):
+def test_tc_mma_exact_small_integers(n, kdim, a_in_tmem):
     """7-bit integers (the slice width of the extension): every partial sum stays below 2^24, so
-    fp32 accumulation is exact and D must equal the integer product A B^T exactly."""
+    fp32 accumulation is exact and D must equal the integer product A B^T exactly; with A in
+    shared memory and with A in tensor memory (the resident-matrix layout)."""
     _need_gpu()
     from paper_1305_3699_gb300 import mr
 
@@ -31,7 +33,7 @@ def test_tc_mma_exact_small_integers(n, kdim):
     a = _ints(r, 128, kdim, 128)
     b = _ints(r, n, kdim, 128)
     with mr.Context(0) as ctx:
-        d = ctx.mr_debug_tc_mma(a, b)
+        d = ctx.mr_debug_tc_mma(a, b, swap_strides=2 if a_in_tmem else 0)
     want = a @ b.T
     assert np.array_equal(d.astype(np.float64), want), np.argwhere(d != want)[:8]
 
@@ -51,7 +53,9 @@ def test_tc_mma_distinguishes_rows_and_columns():
         b[j, (3 * j) % kdim] = 1 + j % 7
     with mr.Context(0) as ctx:
         d = ctx.mr_debug_tc_mma(a, b)
+        d2 = ctx.mr_debug_tc_mma(a, b, swap_strides=2)
     assert np.array_equal(d.astype(np.float64), a @ b.T)
+    assert np.array_equal(d2.astype(np.float64), a @ b.T)
 
 
 def test_tensor_peaks_plausible():
