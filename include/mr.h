@@ -469,7 +469,8 @@ mr_status mr_debug_tc_slices(uint32_t class_bits, uint32_t *out, size_t capacity
  * only; kdim must then be 16); swap_strides = 2 takes A from tensor memory
  * instead (row r in lane r, two fp16 values of K per 32-bit column, the lower
  * K index in the low half: the layout of the extension's resident matrix).
- * 16 <= n <= 128 and 16 <= kdim <= 64, both multiples of 16.
+ * 16 <= n <= 256 (n <= 128 with swap_strides 1 or 2) and 16 <= kdim <= 64, both
+ * multiples of 16.
  * Synchronises `stream`.  Errors: MR_ERR_ARG, MR_ERR_TIMEOUT, MR_ERR_CUDA. */
 mr_status mr_debug_tc_mma(mr_ctx *ctx, const uint16_t *a, const uint16_t *b, uint32_t n, uint32_t kdim,
                           uint32_t swap_strides, float *d, void *stream);

@@ -12,12 +12,14 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-# L: (k, W, WX, [(TPI, THREADS, VEC, MINB), ...]).  MINB is the exponentiation kernel's minimum
+# L: (k, W, WX, [(TPI, THREADS, VEC, MINB[, TC]), ...]).  MINB is the exponentiation kernel's minimum
 # resident blocks per SM (its register budget, 0 = compiler's choice), picked per variant by timing
-# each value on 1024-16384 numbers of the class with full-length exponents.
+# each value on 1024-16384 numbers of the class with full-length exponents.  TC = 1: the base
+# extensions of the exponentiation kernel run on the tensor cores (rns_tc.cuh; 32 numbers per block, 4
+# lanes per number in one warp or 8 in two warps, at most two blocks per SM).
 CLASSES = {
     512: (18, 16, 17, [(2, 128, 4, 2), (4, 128, 4, 4)]),
-    1024: (36, 32, 34, [(4, 128, 4, 3), (8, 128, 4, 4)]),
+    1024: (36, 32, 34, [(4, 128, 4, 3), (8, 128, 4, 4), (4, 128, 4, 2, 1), (8, 256, 4, 2, 1)]),
     1536: (54, 48, 50, [(8, 128, 4, 0)]),
     2048: (72, 64, 66, [(8, 128, 4, 0), (16, 128, 4, 1)]),
     3072: (108, 96, 97, [(16, 256, 4, 0)]),
@@ -71,25 +73,28 @@ def unit(L, k, W, WX, variants):
     out = [f"// Kernels of the {L}-bit size class (k = {k} channels per base). Generated by gen_kernels.py.",
            '#include "kernels.cuh"', '#include "kernels_api.h"', '#include "mr_kernel.cuh"', "", "namespace mr {", ""]
     entries = []
-    for v, (tpi, th, vec, minb) in enumerate(variants):
+    for v, var in enumerate(variants):
+        tpi, th, vec, minb = var[:4]
+        tc = var[4] if len(var) > 4 else 0
         C = f"C{L}v{v}"
-        out.append(f"using {C} = Cfg<{k}, {W}, {WX}, {tpi}, {th}, {vec}, {minb}>;")
-        for kind, kern, argt in (("modexp", "modexp_kernel", "LaunchArgs"), ("crt", "crt_kernel", "LaunchArgs"),
-                                 ("mr", "mr_kernel", "MRArgs")):
+        out.append(f"using {C} = Cfg<{k}, {W}, {WX}, {tpi}, {th}, {vec}, {minb}, {tc}>;")
+        for kind, kern, argt, sm in (("modexp", "modexp_kernel", "LaunchArgs", "SMEM_MODEXP_BYTES"),
+                                     ("crt", "crt_kernel", "LaunchArgs", "SMEM_BYTES"),
+                                     ("mr", "mr_kernel", "MRArgs", "SMEM_BYTES")):
             out += [f"static cudaError_t launch_{kind}_{L}_{v}(const {argt}& a, unsigned grid, cudaStream_t s) {{",
-                    f"  {kern}<{C}><<<grid, {C}::THREADS, {C}::SMEM_BYTES, s>>>(a);",
+                    f"  {kern}<{C}><<<grid, {C}::THREADS, {C}::{sm}, s>>>(a);",
                     "  return cudaGetLastError();", "}", ""]
         out += [f"static cudaError_t prepare_{L}_{v}() {{",
                 "  cudaError_t e = cudaSuccess, r;",
-                f"  if ((r = cudaFuncSetAttribute(modexp_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES)) != cudaSuccess) e = r;",
+                f"  if ((r = cudaFuncSetAttribute(modexp_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_MODEXP_BYTES)) != cudaSuccess) e = r;",
                 f"  if ((r = cudaFuncSetAttribute(crt_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES)) != cudaSuccess) e = r;",
                 f"  if ((r = cudaFuncSetAttribute(mr_kernel<{C}>, cudaFuncAttributeMaxDynamicSharedMemorySize, {C}::SMEM_BYTES)) != cudaSuccess) e = r;",
                 "  return e;", "}", "",
                 f"static int occupancy_{L}_{v}() {{",
                 "  int n = 0;",
-                f"  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<{C}>, {C}::THREADS, {C}::SMEM_BYTES) != cudaSuccess) n = 1;",
+                f"  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<{C}>, {C}::THREADS, {C}::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;",
                 "  return n > 0 ? n : 1;", "}", ""]
-        entries.append(f"     {{{C}::TPI, {C}::THREADS, {C}::IPB, {C}::NPT, {C}::SMEM_BYTES, launch_modexp_{L}_{v}, "
+        entries.append(f"     {{{C}::TPI, {C}::THREADS, {C}::IPB, {C}::NPT, {C}::SMEM_MODEXP_BYTES, launch_modexp_{L}_{v}, "
                        f"launch_crt_{L}_{v}, launch_mr_{L}_{v}, prepare_{L}_{v}, occupancy_{L}_{v}}}")
     out.append(f"extern const ClassKernels kClass{L} = {{")
     out.append(f"    {L}, {k}, {W}, {WX}, {len(variants)},")

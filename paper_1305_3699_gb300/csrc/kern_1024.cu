@@ -5,9 +5,9 @@
 
 namespace mr {
 
-using C1024v0 = Cfg<36, 32, 34, 4, 128, 4, 3>;
+using C1024v0 = Cfg<36, 32, 34, 4, 128, 4, 3, 0>;
 static cudaError_t launch_modexp_1024_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  modexp_kernel<C1024v0><<<grid, C1024v0::THREADS, C1024v0::SMEM_BYTES, s>>>(a);
+  modexp_kernel<C1024v0><<<grid, C1024v0::THREADS, C1024v0::SMEM_MODEXP_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -23,7 +23,7 @@ static cudaError_t launch_mr_1024_0(const MRArgs& a, unsigned grid, cudaStream_t
 
 static cudaError_t prepare_1024_0() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = cudaFuncSetAttribute(modexp_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_MODEXP_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(crt_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(mr_kernel<C1024v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v0::SMEM_BYTES)) != cudaSuccess) e = r;
   return e;
@@ -31,13 +31,13 @@ static cudaError_t prepare_1024_0() {
 
 static int occupancy_1024_0() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1024v0>, C1024v0::THREADS, C1024v0::SMEM_BYTES) != cudaSuccess) n = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1024v0>, C1024v0::THREADS, C1024v0::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;
   return n > 0 ? n : 1;
 }
 
-using C1024v1 = Cfg<36, 32, 34, 8, 128, 4, 4>;
+using C1024v1 = Cfg<36, 32, 34, 8, 128, 4, 4, 0>;
 static cudaError_t launch_modexp_1024_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  modexp_kernel<C1024v1><<<grid, C1024v1::THREADS, C1024v1::SMEM_BYTES, s>>>(a);
+  modexp_kernel<C1024v1><<<grid, C1024v1::THREADS, C1024v1::SMEM_MODEXP_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -53,7 +53,7 @@ static cudaError_t launch_mr_1024_1(const MRArgs& a, unsigned grid, cudaStream_t
 
 static cudaError_t prepare_1024_1() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = cudaFuncSetAttribute(modexp_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_MODEXP_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(crt_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(mr_kernel<C1024v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v1::SMEM_BYTES)) != cudaSuccess) e = r;
   return e;
@@ -61,15 +61,77 @@ static cudaError_t prepare_1024_1() {
 
 static int occupancy_1024_1() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1024v1>, C1024v1::THREADS, C1024v1::SMEM_BYTES) != cudaSuccess) n = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1024v1>, C1024v1::THREADS, C1024v1::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;
+  return n > 0 ? n : 1;
+}
+
+using C1024v2 = Cfg<36, 32, 34, 4, 128, 4, 2, 1>;
+static cudaError_t launch_modexp_1024_2(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  modexp_kernel<C1024v2><<<grid, C1024v2::THREADS, C1024v2::SMEM_MODEXP_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_crt_1024_2(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  crt_kernel<C1024v2><<<grid, C1024v2::THREADS, C1024v2::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mr_1024_2(const MRArgs& a, unsigned grid, cudaStream_t s) {
+  mr_kernel<C1024v2><<<grid, C1024v2::THREADS, C1024v2::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t prepare_1024_2() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C1024v2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v2::SMEM_MODEXP_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(crt_kernel<C1024v2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v2::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(mr_kernel<C1024v2>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v2::SMEM_BYTES)) != cudaSuccess) e = r;
+  return e;
+}
+
+static int occupancy_1024_2() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1024v2>, C1024v2::THREADS, C1024v2::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;
+  return n > 0 ? n : 1;
+}
+
+using C1024v3 = Cfg<36, 32, 34, 8, 256, 4, 2, 1>;
+static cudaError_t launch_modexp_1024_3(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  modexp_kernel<C1024v3><<<grid, C1024v3::THREADS, C1024v3::SMEM_MODEXP_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_crt_1024_3(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
+  crt_kernel<C1024v3><<<grid, C1024v3::THREADS, C1024v3::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_mr_1024_3(const MRArgs& a, unsigned grid, cudaStream_t s) {
+  mr_kernel<C1024v3><<<grid, C1024v3::THREADS, C1024v3::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t prepare_1024_3() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C1024v3>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v3::SMEM_MODEXP_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(crt_kernel<C1024v3>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v3::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(mr_kernel<C1024v3>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1024v3::SMEM_BYTES)) != cudaSuccess) e = r;
+  return e;
+}
+
+static int occupancy_1024_3() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1024v3>, C1024v3::THREADS, C1024v3::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;
   return n > 0 ? n : 1;
 }
 
 extern const ClassKernels kClass1024 = {
-    1024, 36, 32, 34, 2,
+    1024, 36, 32, 34, 4,
     {
-     {C1024v0::TPI, C1024v0::THREADS, C1024v0::IPB, C1024v0::NPT, C1024v0::SMEM_BYTES, launch_modexp_1024_0, launch_crt_1024_0, launch_mr_1024_0, prepare_1024_0, occupancy_1024_0},
-     {C1024v1::TPI, C1024v1::THREADS, C1024v1::IPB, C1024v1::NPT, C1024v1::SMEM_BYTES, launch_modexp_1024_1, launch_crt_1024_1, launch_mr_1024_1, prepare_1024_1, occupancy_1024_1}},
+     {C1024v0::TPI, C1024v0::THREADS, C1024v0::IPB, C1024v0::NPT, C1024v0::SMEM_MODEXP_BYTES, launch_modexp_1024_0, launch_crt_1024_0, launch_mr_1024_0, prepare_1024_0, occupancy_1024_0},
+     {C1024v1::TPI, C1024v1::THREADS, C1024v1::IPB, C1024v1::NPT, C1024v1::SMEM_MODEXP_BYTES, launch_modexp_1024_1, launch_crt_1024_1, launch_mr_1024_1, prepare_1024_1, occupancy_1024_1},
+     {C1024v2::TPI, C1024v2::THREADS, C1024v2::IPB, C1024v2::NPT, C1024v2::SMEM_MODEXP_BYTES, launch_modexp_1024_2, launch_crt_1024_2, launch_mr_1024_2, prepare_1024_2, occupancy_1024_2},
+     {C1024v3::TPI, C1024v3::THREADS, C1024v3::IPB, C1024v3::NPT, C1024v3::SMEM_MODEXP_BYTES, launch_modexp_1024_3, launch_crt_1024_3, launch_mr_1024_3, prepare_1024_3, occupancy_1024_3}},
     nullptr, 0};
 
 }  // namespace mr

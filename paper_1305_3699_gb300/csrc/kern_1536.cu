@@ -5,9 +5,9 @@
 
 namespace mr {
 
-using C1536v0 = Cfg<54, 48, 50, 8, 128, 4, 0>;
+using C1536v0 = Cfg<54, 48, 50, 8, 128, 4, 0, 0>;
 static cudaError_t launch_modexp_1536_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  modexp_kernel<C1536v0><<<grid, C1536v0::THREADS, C1536v0::SMEM_BYTES, s>>>(a);
+  modexp_kernel<C1536v0><<<grid, C1536v0::THREADS, C1536v0::SMEM_MODEXP_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -23,7 +23,7 @@ static cudaError_t launch_mr_1536_0(const MRArgs& a, unsigned grid, cudaStream_t
 
 static cudaError_t prepare_1536_0() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = cudaFuncSetAttribute(modexp_kernel<C1536v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1536v0::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C1536v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1536v0::SMEM_MODEXP_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(crt_kernel<C1536v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1536v0::SMEM_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(mr_kernel<C1536v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C1536v0::SMEM_BYTES)) != cudaSuccess) e = r;
   return e;
@@ -31,14 +31,14 @@ static cudaError_t prepare_1536_0() {
 
 static int occupancy_1536_0() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1536v0>, C1536v0::THREADS, C1536v0::SMEM_BYTES) != cudaSuccess) n = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C1536v0>, C1536v0::THREADS, C1536v0::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;
   return n > 0 ? n : 1;
 }
 
 extern const ClassKernels kClass1536 = {
     1536, 54, 48, 50, 1,
     {
-     {C1536v0::TPI, C1536v0::THREADS, C1536v0::IPB, C1536v0::NPT, C1536v0::SMEM_BYTES, launch_modexp_1536_0, launch_crt_1536_0, launch_mr_1536_0, prepare_1536_0, occupancy_1536_0}},
+     {C1536v0::TPI, C1536v0::THREADS, C1536v0::IPB, C1536v0::NPT, C1536v0::SMEM_MODEXP_BYTES, launch_modexp_1536_0, launch_crt_1536_0, launch_mr_1536_0, prepare_1536_0, occupancy_1536_0}},
     nullptr, 0};
 
 }  // namespace mr

@@ -5,9 +5,9 @@
 
 namespace mr {
 
-using C3072v0 = Cfg<108, 96, 97, 16, 256, 4, 0>;
+using C3072v0 = Cfg<108, 96, 97, 16, 256, 4, 0, 0>;
 static cudaError_t launch_modexp_3072_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  modexp_kernel<C3072v0><<<grid, C3072v0::THREADS, C3072v0::SMEM_BYTES, s>>>(a);
+  modexp_kernel<C3072v0><<<grid, C3072v0::THREADS, C3072v0::SMEM_MODEXP_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -23,7 +23,7 @@ static cudaError_t launch_mr_3072_0(const MRArgs& a, unsigned grid, cudaStream_t
 
 static cudaError_t prepare_3072_0() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = cudaFuncSetAttribute(modexp_kernel<C3072v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C3072v0::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C3072v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C3072v0::SMEM_MODEXP_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(crt_kernel<C3072v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C3072v0::SMEM_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(mr_kernel<C3072v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C3072v0::SMEM_BYTES)) != cudaSuccess) e = r;
   return e;
@@ -31,14 +31,14 @@ static cudaError_t prepare_3072_0() {
 
 static int occupancy_3072_0() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C3072v0>, C3072v0::THREADS, C3072v0::SMEM_BYTES) != cudaSuccess) n = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C3072v0>, C3072v0::THREADS, C3072v0::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;
   return n > 0 ? n : 1;
 }
 
 extern const ClassKernels kClass3072 = {
     3072, 108, 96, 97, 1,
     {
-     {C3072v0::TPI, C3072v0::THREADS, C3072v0::IPB, C3072v0::NPT, C3072v0::SMEM_BYTES, launch_modexp_3072_0, launch_crt_3072_0, launch_mr_3072_0, prepare_3072_0, occupancy_3072_0}},
+     {C3072v0::TPI, C3072v0::THREADS, C3072v0::IPB, C3072v0::NPT, C3072v0::SMEM_MODEXP_BYTES, launch_modexp_3072_0, launch_crt_3072_0, launch_mr_3072_0, prepare_3072_0, occupancy_3072_0}},
     nullptr, 0};
 
 }  // namespace mr

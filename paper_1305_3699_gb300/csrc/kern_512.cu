@@ -5,9 +5,9 @@
 
 namespace mr {
 
-using C512v0 = Cfg<18, 16, 17, 2, 128, 4, 2>;
+using C512v0 = Cfg<18, 16, 17, 2, 128, 4, 2, 0>;
 static cudaError_t launch_modexp_512_0(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  modexp_kernel<C512v0><<<grid, C512v0::THREADS, C512v0::SMEM_BYTES, s>>>(a);
+  modexp_kernel<C512v0><<<grid, C512v0::THREADS, C512v0::SMEM_MODEXP_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -23,7 +23,7 @@ static cudaError_t launch_mr_512_0(const MRArgs& a, unsigned grid, cudaStream_t 
 
 static cudaError_t prepare_512_0() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = cudaFuncSetAttribute(modexp_kernel<C512v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v0::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C512v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v0::SMEM_MODEXP_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(crt_kernel<C512v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v0::SMEM_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(mr_kernel<C512v0>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v0::SMEM_BYTES)) != cudaSuccess) e = r;
   return e;
@@ -31,13 +31,13 @@ static cudaError_t prepare_512_0() {
 
 static int occupancy_512_0() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C512v0>, C512v0::THREADS, C512v0::SMEM_BYTES) != cudaSuccess) n = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C512v0>, C512v0::THREADS, C512v0::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;
   return n > 0 ? n : 1;
 }
 
-using C512v1 = Cfg<18, 16, 17, 4, 128, 4, 4>;
+using C512v1 = Cfg<18, 16, 17, 4, 128, 4, 4, 0>;
 static cudaError_t launch_modexp_512_1(const LaunchArgs& a, unsigned grid, cudaStream_t s) {
-  modexp_kernel<C512v1><<<grid, C512v1::THREADS, C512v1::SMEM_BYTES, s>>>(a);
+  modexp_kernel<C512v1><<<grid, C512v1::THREADS, C512v1::SMEM_MODEXP_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -53,7 +53,7 @@ static cudaError_t launch_mr_512_1(const MRArgs& a, unsigned grid, cudaStream_t 
 
 static cudaError_t prepare_512_1() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = cudaFuncSetAttribute(modexp_kernel<C512v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v1::SMEM_BYTES)) != cudaSuccess) e = r;
+  if ((r = cudaFuncSetAttribute(modexp_kernel<C512v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v1::SMEM_MODEXP_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(crt_kernel<C512v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v1::SMEM_BYTES)) != cudaSuccess) e = r;
   if ((r = cudaFuncSetAttribute(mr_kernel<C512v1>, cudaFuncAttributeMaxDynamicSharedMemorySize, C512v1::SMEM_BYTES)) != cudaSuccess) e = r;
   return e;
@@ -61,15 +61,15 @@ static cudaError_t prepare_512_1() {
 
 static int occupancy_512_1() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C512v1>, C512v1::THREADS, C512v1::SMEM_BYTES) != cudaSuccess) n = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<C512v1>, C512v1::THREADS, C512v1::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;
   return n > 0 ? n : 1;
 }
 
 extern const ClassKernels kClass512 = {
     512, 18, 16, 17, 2,
     {
-     {C512v0::TPI, C512v0::THREADS, C512v0::IPB, C512v0::NPT, C512v0::SMEM_BYTES, launch_modexp_512_0, launch_crt_512_0, launch_mr_512_0, prepare_512_0, occupancy_512_0},
-     {C512v1::TPI, C512v1::THREADS, C512v1::IPB, C512v1::NPT, C512v1::SMEM_BYTES, launch_modexp_512_1, launch_crt_512_1, launch_mr_512_1, prepare_512_1, occupancy_512_1}},
+     {C512v0::TPI, C512v0::THREADS, C512v0::IPB, C512v0::NPT, C512v0::SMEM_MODEXP_BYTES, launch_modexp_512_0, launch_crt_512_0, launch_mr_512_0, prepare_512_0, occupancy_512_0},
+     {C512v1::TPI, C512v1::THREADS, C512v1::IPB, C512v1::NPT, C512v1::SMEM_MODEXP_BYTES, launch_modexp_512_1, launch_crt_512_1, launch_mr_512_1, prepare_512_1, occupancy_512_1}},
     nullptr, 0};
 
 }  // namespace mr

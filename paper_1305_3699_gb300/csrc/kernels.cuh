@@ -9,6 +9,7 @@
 
 #include "kernels_api.h"
 #include "rns_device.cuh"
+#include "rns_tc.cuh"
 
 namespace mr {
 
@@ -95,14 +96,52 @@ __device__ __forceinline__ void tab_get(const uint32_t* wt, uint32_t ent, int E,
   else tab_load<C>(wt, (int)ent, b, p, lane);
 }
 
-// One exponentiation per lane group (x^e mod N of work item g_raw); all lanes of the warp call it
-// together.  wt: this warp's window-table scratch.
+// Schedule votes.  The integer form runs the numbers of a warp in lockstep; the tensor-core form
+// (C::TC) runs the whole block in lockstep (every multiplication is a block-wide product), so its
+// votes are block-wide.  All threads of the warp (block) must call them.
 template <class C>
-__device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& sm, uint32_t g_raw, uint32_t* wt) {
+__device__ __forceinline__ bool vote_any(bool p) {
+  if constexpr (C::TC) return __syncthreads_or(p) != 0;
+  else return __any_sync(0xffffffffu, p);
+}
+template <class C>
+__device__ __forceinline__ uint32_t vote_max(uint32_t v, const TcSmem<C>& ts) {
+  v = __reduce_max_sync(0xffffffffu, v);
+  if constexpr (C::TC) {
+    uint32_t* word = ts.vote() + 4;
+    __syncthreads();
+    if (threadIdx.x == 0) *word = 0u;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(word, v);
+    __syncthreads();
+    v = *word;
+  }
+  return v;
+}
+
+// One RNS Montgomery multiplication in the kernel's form.
+template <class C>
+__device__ __forceinline__ void mm(uint32_t (&xb)[C::NPT], uint32_t (&xp)[C::NPT], const uint32_t (&yb)[C::NPT],
+                                   const uint32_t (&yp)[C::NPT], const uint32_t (&kxp)[C::NPT],
+                                   const uint32_t (&kxs)[C::NPT], const uint32_t (&cmul)[C::NPT], const Smem<C>& sm,
+                                   uint32_t* xib, uint32_t* xpb, int t, const TcSmem<C>& ts, TcState& st) {
+  if constexpr (C::TC) mont_mul_tc<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, ts, st, t);
+  else mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
+}
+
+// One exponentiation per lane group (x^e mod N of work item g_raw); all lanes of the warp (of the
+// block, tensor-core form) call it together.  wt: this warp's window-table scratch.
+template <class C>
+__device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& sm, uint32_t g_raw, uint32_t* wt,
+                                            const TcSmem<C>& ts, TcState& st) {
   constexpr int NPT = C::NPT, TPI = C::TPI;
   const int lane = threadIdx.x & 31;
-  const int t = threadIdx.x % TPI;
-  const int item_in_block = threadIdx.x / TPI;
+  // lane t of the number, the number's slot in the block, and the first lane of this thread's group
+  // within its warp (the tensor-core block splits a number's 8 lanes over two warps, 4 in each)
+  const int t = C::TC ? tc_lane_t<C>() : (int)(threadIdx.x % TPI);
+  const int item_in_block = C::TC ? tc_number<C>() : (int)(threadIdx.x / TPI);
+  const int glead = C::TC ? (lane & ~3) : lane - t;
+  const bool leader = lane == glead;
   const bool live = g_raw < a.n_items;
   const uint32_t g = live ? g_raw : a.n_items - 1;  // idle groups shadow the last item, write nothing
   const MxItem it = reinterpret_cast<const MxItem*>(a.items)[g];
@@ -112,8 +151,8 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   uint32_t* xpb = xib + C::KP;
   // input range check: x < xlim
   uint32_t bad = 0;
-  if (t == 0) bad = less_than(it.x, it.x_limbs, it.xlim, it.xlim_limbs) ? 0u : 1u;
-  bad = __shfl_sync(0xffffffffu, bad, lane - t);
+  if (leader) bad = less_than(it.x, it.x_limbs, it.xlim, it.xlim_limbs) ? 0u : 1u;
+  bad = __shfl_sync(0xffffffffu, bad, glead);
 
   uint32_t kxp[NPT], kxs[NPT], cmul[NPT];
 #pragma unroll
@@ -129,14 +168,14 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   const int nl0 = bad ? 0 : (int)(it.x_limbs < (uint32_t)C::W ? it.x_limbs : C::W);
   to_rns<C>(xb, xp, it.x, nl0, a.cls, sm, t);
   load_vec<C>(yb, yp, key + ko.r2, t);
-  mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
+  mm<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t, ts, st);
   const bool two = !bad && it.x_limbs > (uint32_t)C::W;
-  if (__any_sync(0xffffffffu, two)) {
+  if (vote_any<C>(two)) {
     uint32_t hb[NPT], hp[NPT];
     const int nl1 = two ? min((int)it.x_limbs - C::W, C::W) : 0;
     to_rns<C>(hb, hp, it.x + C::W, nl1, a.cls, sm, t);
     load_vec<C>(yb, yp, key + ko.r2h, t);
-    mont_mul<C>(hb, hp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
+    mm<C>(hb, hp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t, ts, st);
     add_vec<C>(xb, xp, hb, hp, sm, t);
   }
 
@@ -153,22 +192,37 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   const int wb = (int)a.wbits, E = 1 << wb;
   const uint32_t el = it.e_limbs;
   uint32_t ebits = 0;
-  if (t == 0) ebits = bad ? 0u : (ct ? 32u * el : exp_bits(it.e, el));
-  ebits = __shfl_sync(0xffffffffu, ebits, lane - t);
+  if (leader) ebits = bad ? 0u : (ct ? 32u * el : exp_bits(it.e, el));
+  ebits = __shfl_sync(0xffffffffu, ebits, glead);
   bool uni = false;
   if (wb >= 4 && !ct) {
-    const uint32_t* e0 = reinterpret_cast<const uint32_t*>(
-        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(it.e), 0));
-    const uint32_t eb0 = __shfl_sync(0xffffffffu, ebits, 0);
+    // the exponent of the first number of the warp (of the block, tensor-core form)
+    const uint32_t* e0;
+    uint32_t eb0;
+    if constexpr (C::TC) {
+      unsigned long long* vp = reinterpret_cast<unsigned long long*>(ts.vote());
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        vp[0] = reinterpret_cast<unsigned long long>(it.e);
+        ts.vote()[2] = ebits;
+      }
+      __syncthreads();
+      e0 = reinterpret_cast<const uint32_t*>(vp[0]);
+      eb0 = ts.vote()[2];
+    } else {
+      e0 = reinterpret_cast<const uint32_t*>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(it.e), 0));
+      eb0 = __shfl_sync(0xffffffffu, ebits, 0);
+    }
     int eq = ebits == eb0 && eb0 != 0u;
-    if (eq && t == 0)
+    if (eq && leader)
       for (uint32_t w = 0; w < (ebits + 31) / 32; w++)
         if (it.e[w] != e0[w]) {
           eq = 0;
           break;
         }
-    eq = __shfl_sync(0xffffffffu, eq, lane - t);
-    uni = __all_sync(0xffffffffu, eq);
+    eq = __shfl_sync(0xffffffffu, eq, glead);
+    if constexpr (C::TC) uni = __syncthreads_and(eq) != 0;
+    else uni = __all_sync(0xffffffffu, eq);
   }
 
   // The schedule flag is passed through an empty asm at each place it steers (the table, the
@@ -196,7 +250,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
     }
     const int iters = uni_t ? E : E - 2;
     for (int j = 0; j < iters; j++) {
-      mont_mul<C>(cb, cp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
+      mm<C>(cb, cp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t, ts, st);
       // opaque to the compiler: keeps one copy of the loop (no peeled first iteration)
       int first = (uni_t && j == 0) ? 1 : 0;
       asm volatile("" : "+r"(first));
@@ -218,7 +272,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
   // the next window.  Both schedules' values are formed and one is selected (no branch here, so
   // that the compiler keeps a single copy of the loop below).
   const int ws = wb + 1;  // sliding window width
-  const uint32_t nwin = __reduce_max_sync(0xffffffffu, (ebits + wb - 1) / wb);
+  const uint32_t nwin = vote_max<C>((ebits + wb - 1) / wb, ts);
   const uint32_t d_fixed = (nwin && !bad) ? exp_digit(it.e, el, (nwin - 1) * wb, wb) : 0u;
   int lo_first = 0;
   const uint32_t d_slide = uni_f ? slide_window(it.e, el, (int)ebits - 1, ws, &lo_first) : 0u;
@@ -264,7 +318,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
       if (cur < 0) break;
       nsq = wb;
       d = bad ? 0u : exp_digit(it.e, el, (uint32_t)cur * wb, wb);
-      mul = ct || __any_sync(0xffffffffu, d != 0);  // (ct is uniform: every lane takes the same path)
+      mul = ct || vote_any<C>(d != 0);  // (ct is uniform: every lane takes the same path)
       cur--;
     }
     // one multiplication site for the squarings and the window product (the second operand is a
@@ -280,7 +334,7 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
       } else {
         tab_get<C>(wt, d, E, ct, yb, yp, lane);
       }
-      mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
+      mm<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t, ts, st);
     }
   }
 
@@ -290,37 +344,64 @@ __device__ __forceinline__ void modexp_item(const LaunchArgs& a, const Smem<C>& 
     yb[s] = sm.cb4(t, s).z;  // hat form of 1 = 2^32 mod m
     yp[s] = sm.cp4(t, s).z;
   }
-  mont_mul<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t);
-  from_rns_reduce<C>(xb, a.cls, key, sm, xib, t, it.out, (int)it.out_limbs, live && !bad);
+  mm<C>(xb, xp, yb, yp, kxp, kxs, cmul, sm, xib, xpb, t, ts, st);
+  from_rns_reduce<C, C::TC != 0>(xb, a.cls, key, sm, xib, t, it.out, (int)it.out_limbs, live && !bad, ts.part());
+  // tensor-core form: a completion wait that ran out leaves the block's results undefined (status 8)
+  bool failed = false;
+  if constexpr (C::TC) failed = *ts.abort_flag() != 0u;
   if (live && t == 0) {
     if (bad)
       for (uint32_t w = 0; w < it.out_limbs; w++) it.out[w] = 0u;
-    if (a.status && it.status != 0xffffffffu) a.status[it.status] = bad ? 5u : 0u;
+    if (a.status && it.status != 0xffffffffu) a.status[it.status] = bad ? 5u : (failed ? 8u : 0u);
   }
 }
 
 template <class C>
 __global__ void __launch_bounds__(C::THREADS, C::MINB) modexp_kernel(LaunchArgs a) {
-  extern __shared__ __align__(16) uint32_t smem_raw[];
+  extern __shared__ __align__(128) uint32_t smem_raw[];
   Smem<C> sm{smem_raw};
   load_class_smem<C>(sm, a.cls);
+  const TcSmem<C> ts{reinterpret_cast<uint8_t*>(smem_raw)};
+  TcState st{0u, 0u};
+  if constexpr (C::TC) tc_prologue<C>(ts, a.cls);
   __syncthreads();
   const int warp_global = (blockIdx.x * C::THREADS + threadIdx.x) >> 5;
   uint32_t* wt = a.scratch + (size_t)warp_global * ((size_t)1 << a.wbits) * (2 * C::NPT) * 32;
-  // plain launch: warp w of the grid runs group w once.  Persistent launch: each warp takes the
-  // next group of 32/TPI items from the queue (items are ordered by cost, largest first) until it
-  // is empty.  One call site for both keeps a single copy of the exponentiation code.
-  const uint32_t n_groups = (a.n_items + C::IPW - 1) / C::IPW;
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    uint32_t wg = (uint32_t)warp_global;
-    if (a.queue) {
-      if (lane == 0) wg = atomicAdd(a.queue, 1u);
-      wg = __shfl_sync(0xffffffffu, wg, 0);
-      if (wg >= n_groups) break;
+  if constexpr (C::TC) {
+    // tensor-core form: the block runs its 32 numbers in lockstep.  Plain launch: block b runs item group
+    // b; persistent launch: the block takes the next group of 32 items from the queue until it is empty
+    tc::fence_after_sync();
+    st.tmem = *ts.tslot();
+    const uint32_t n_groups = (a.n_items + C::IPB - 1) / C::IPB;
+    uint32_t bg = blockIdx.x;
+    for (;;) {
+      if (a.queue) {
+        __syncthreads();
+        if (threadIdx.x == 0) ts.vote()[6] = atomicAdd(a.queue, 1u);
+        __syncthreads();
+        bg = ts.vote()[6];
+        if (bg >= n_groups) break;
+      }
+      modexp_item<C>(a, sm, bg * C::IPB + tc_number<C>(), wt, ts, st);
+      if (!a.queue) break;
     }
-    modexp_item<C>(a, sm, wg * C::IPW + (lane / C::TPI), wt);
-    if (!a.queue) break;
+    tc_release<C>(ts, st);
+  } else {
+    // plain launch: warp w of the grid runs group w once.  Persistent launch: each warp takes the
+    // next group of 32/TPI items from the queue (items are ordered by cost, largest first) until it
+    // is empty.  One call site for both keeps a single copy of the exponentiation code.
+    const uint32_t n_groups = (a.n_items + C::IPW - 1) / C::IPW;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+      uint32_t wg = (uint32_t)warp_global;
+      if (a.queue) {
+        if (lane == 0) wg = atomicAdd(a.queue, 1u);
+        wg = __shfl_sync(0xffffffffu, wg, 0);
+        if (wg >= n_groups) break;
+      }
+      modexp_item<C>(a, sm, wg * C::IPW + (lane / C::TPI), wt, ts, st);
+      if (!a.queue) break;
+    }
   }
 }
 

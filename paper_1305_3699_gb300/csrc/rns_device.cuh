@@ -71,10 +71,12 @@ __device__ __forceinline__ void mac96(uint32_t& s0, uint32_t& s1, uint32_t& s2, 
       : "r"(a), "r"(b));
 }
 
-template <int K_, int W_, int WX_, int TPI_, int THREADS_, int VEC_, int MINB_ = 0>
+template <int K_, int W_, int WX_, int TPI_, int THREADS_, int VEC_, int MINB_ = 0, int TC_ = 0>
 struct Cfg {
   static constexpr int MINB = MINB_;             // exponentiation kernel's minimum resident blocks per SM
                                                   // (register budget; 0 leaves the choice to the compiler)
+  static constexpr int TC = TC_;                  // 1: the exponentiation kernel forms the two base
+                                                  // extensions on the tensor cores (rns_tc.cuh)
   static constexpr int K = K_;                    // channels per base
   static constexpr int W = W_;                    // limbs of the class bound
   static constexpr int WX = WX_;                  // limbs of k*M (RNS -> binary)
@@ -110,6 +112,33 @@ struct Cfg {
   static_assert((SM_T2 % 4) == 0 && (SM_CB4 % 4) == 0 && (SM_CPX % 4) == 0 && (SM_CB2 % 2) == 0 && (SM_XI % 4) == 0,
                 "alignment");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+
+  // Tensor-core form (TC = 1, rns_tc.cuh).  The block's 32 numbers x 4 byte slices are the 128 rows of
+  // the data operand (row 4n + a: byte a of number n's CRT coefficients).  Lane t of number n has its
+  // NPT input channels in K columns [NPTK t, NPTK t + NPT); the rest is zero except one offset column
+  // (K index NPT) whose product 2048 * 4096 = 2^23 is added to every accumulator.  With TPI = 4 the
+  // number's lanes are 4n .. 4n + 3 of the block; with TPI = 8 they are split over two warps of the
+  // same tensor-memory lane quarter (lane t = 4 h + u in warp half h).  The matrix operand has
+  // NB = 16 NPT TPI / 4 rows, row 16 NPT h + 16 s + 4 u + b holding byte b of the matrix column of
+  // output channel (4 h + u) NPT + s, so that warp half h reads its channels' accumulators from its
+  // own 16 NPT columns.
+  static constexpr int NPTK = (NPT / 4 + 1) * 4;  // K columns per lane's channel set (>= NPT + 1)
+  static constexpr int KA = TPI * NPTK;            // K extent, a multiple of 16
+  static constexpr int NB = 4 * NPT * TPI;         // accumulator columns (N of the product)
+  static constexpr int TC_A = (SMEM_BYTES + 127) / 128 * 128;  // byte offsets of the operand tiles
+  static constexpr int TC_B1 = TC_A + 128 * KA * 2;
+  static constexpr int TC_B2 = TC_B1 + NB * KA * 2;
+  static constexpr int TC_MISC = TC_B2 + NB * KA * 2;  // mbarrier, tensor-memory address, abort flag, votes,
+                                                       // then [2 warp halves][32 numbers] partial sums
+  static constexpr int TC_END = TC_MISC + 64 + 256;
+  // the tensor-core kernel asks for at least 80 KB so that at most two blocks share an SM: two
+  // accumulators of 256 columns fill the SM's 512 columns of tensor memory
+  static constexpr int SMEM_MODEXP_BYTES = TC ? (TC_END > 81920 ? TC_END : 81920) : SMEM_BYTES;
+  static_assert(!TC || (TPI == 4 && THREADS == 128) || (TPI == 8 && THREADS == 256),
+                "tensor-core form: 32 numbers x 4 or 8 lanes");
+  static_assert(!TC || NB <= 256, "tensor-core form: N <= 256 accumulator columns");
+  static_assert(!TC || K <= 64, "tensor-core form: K * 255^2 < 2^22 keeps the fp32 sums exact");
+  static_assert(SMEM_MODEXP_BYTES <= 227 * 1024, "shared memory");
 };
 
 template <class C>
@@ -161,6 +190,40 @@ __device__ void load_class_smem(const Smem<C>& sm, const uint32_t* cls) {
     cpx[3] = ok ? cls[o.xpcs + ch] : 0u;
   }
   for (int idx = threadIdx.x; idx < C::IPB * C::XS; idx += blockDim.x) s[C::SM_XI + idx] = 0u;
+}
+
+// Thread roles of a tensor-core block (rns_tc.cuh): number n (0..31) and the number's lane t = 4 h + u,
+// u the position in a group of four lanes.  TPI = 4: one warp per 8 numbers (h = 0).  TPI = 8: the two
+// groups of four of number n sit in warps n / 8 (h = 0) and n / 8 + 4 (h = 1).
+template <class C>
+__device__ __forceinline__ int tc_number() {
+  if constexpr (C::TPI == 8) return 8 * ((threadIdx.x >> 5) & 3) + ((threadIdx.x & 31) >> 2);
+  else return (int)(threadIdx.x >> 2);
+}
+template <class C>
+__device__ __forceinline__ int tc_half() {
+  if constexpr (C::TPI == 8) return (int)(threadIdx.x >> 7);
+  else return 0;
+}
+template <class C>
+__device__ __forceinline__ int tc_lane_t() { return 4 * tc_half<C>() + (int)(threadIdx.x & 3); }
+
+// Sum of v over a tensor-core block number's lanes; with two warp halves through `part` ([2][32]
+// words of shared memory, two block barriers).  Every thread of the block calls it; shared-memory
+// stores of the number's lanes before the call are visible to all of them after it.
+template <class C>
+__device__ __forceinline__ uint32_t tc_number_sum(uint32_t v, uint32_t* part) {
+  if constexpr (C::TPI != 8) __syncwarp();
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  if constexpr (C::TPI == 8) {
+    const int n = tc_number<C>(), h = tc_half<C>();
+    __syncthreads();
+    if ((threadIdx.x & 3) == 0) part[32 * h + n] = v;
+    __syncthreads();
+    v += part[32 * (1 - h) + n];
+  }
+  return v;
 }
 
 // Sum a value over the TPI lanes of this lane's group.
@@ -354,9 +417,12 @@ __device__ __forceinline__ bool less_than(const uint32_t* a, int na, const uint3
 // sum; then X mod N by a quotient estimate from the top bits and at most a few
 // corrective subtractions.  All lanes of the group must call it; lane 0 of the
 // group does the serial carry work.
-template <class C>
+// BLOCK = false: a lane group within one warp.  BLOCK = true: a tensor-core block (a number's lanes in
+// two warps; every thread of the block calls it) with its [2][32]-word partial-sum area tc_part.
+template <class C, bool BLOCK = false>
 __device__ void from_rns_reduce(const uint32_t (&xb)[C::NPT], const uint32_t* cls, const uint32_t* key,
-                                const Smem<C>& sm, uint32_t* xib, int t, uint32_t* dst, int dst_limbs, bool write) {
+                                const Smem<C>& sm, uint32_t* xib, int t, uint32_t* dst, int dst_limbs, bool write,
+                                uint32_t* tc_part = nullptr) {
   constexpr int NPT = C::NPT, K = C::K, WX = C::WX, W = C::W;
   const ClassOff co = class_offsets(C::K, C::W, C::WX);
   const KeyOff ko = key_offsets(C::K, C::W);
@@ -370,8 +436,14 @@ __device__ void from_rns_reduce(const uint32_t (&xb)[C::NPT], const uint32_t* cl
     if (o < K) xib[o] = xi;
     kaw += hi32(mulw(xi, c2.y));
   }
-  __syncwarp();
-  const uint32_t alpha = (group_sum<C::TPI>(kaw) + (1u << (KAW_Q - 2))) >> KAW_Q;
+  uint32_t kaw_sum;
+  if constexpr (BLOCK) {
+    kaw_sum = tc_number_sum<C>(kaw, tc_part);  // also publishes xib to the number's lanes
+  } else {
+    __syncwarp();
+    kaw_sum = group_sum<C::TPI>(kaw);
+  }
+  const uint32_t alpha = (kaw_sum + (1u << (KAW_Q - 2))) >> KAW_Q;
   if (t == 0) {
     uint32_t X[WX];
     const uint32_t* MD = cls + co.MD;
@@ -438,7 +510,8 @@ __device__ void from_rns_reduce(const uint32_t (&xb)[C::NPT], const uint32_t* cl
     if (write)
       for (int w = 0; w < dst_limbs; w++) dst[w] = w < WX ? X[w] : 0u;
   }
-  __syncwarp();
+  if constexpr (BLOCK) __syncthreads();
+  else __syncwarp();
 }
 
 }  // namespace mr

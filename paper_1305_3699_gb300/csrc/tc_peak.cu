@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) mma_f16_rate_kernel(int iters, uint32_t s
 // One CTA: D (128 x n, fp32) = A (128 x kdim, fp16, row-major in global) * B^T (B: n x kdim,
 // row-major), with both tiles staged in the K-major layout of tc_device.cuh.  swap_strides
 // exchanges the two descriptor offsets (layout diagnosis only; the reads stay inside the
-// 32 KB regions reserved per operand for n <= 128, kdim <= 64).
+// 32 KB regions reserved per operand for n <= 256, kdim <= 64).
 constexpr uint32_t DBG_REGION = 32768;
 constexpr uint32_t DBG_BYTES = 2 * DBG_REGION + 16;
 

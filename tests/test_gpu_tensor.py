@@ -38,6 +38,32 @@ def test_tc_mma_exact_small_integers(n, kdim, a_in_tmem):
     assert np.array_equal(d.astype(np.float64), want), np.argwhere(d != want)[:8]
 
 
+@pytest.mark.parametrize("n,kdim,off_col", [(96, 32, 3), (160, 64, 5), (224, 64, 7)])
+def test_tc_mma_lane_group_extension_shape(n, kdim, off_col):
+    """The lane-group extension's product: 8-bit integer slices in fp16, N = 32 x (channels per lane)
+    columns, and one K column of 2048 x 4096 that adds 2^23 to every accumulator.  Every sum lies in
+    [2^23, 2^24) and must come back exact (the integer is then the fp32 value's mantissa)."""
+    _need_gpu()
+    from paper_1305_3699_gb300 import mr
+
+    r = np.random.default_rng(n)
+    a = r.integers(0, 256, size=(128, kdim)).astype(np.float64)
+    b = r.integers(0, 256, size=(n, kdim)).astype(np.float64)
+    a[:, off_col] = 2048.0
+    b[:, off_col] = 4096.0
+    a[:3, :] = 255.0  # the largest sums
+    b[:3, :] = 255.0
+    a[:3, off_col] = 2048.0
+    b[:3, off_col] = 4096.0
+    want = a @ b.T
+    assert want.min() >= 2 ** 23 and want.max() < 2 ** 24
+    with mr.Context(0) as ctx:
+        d = ctx.mr_debug_tc_mma(a, b)
+    assert np.array_equal(d.astype(np.float64), want), np.argwhere(d != want)[:8]
+    bits = d.view(np.uint32)
+    assert np.array_equal((bits & 0x7FFFFF).astype(np.float64), want - 2 ** 23)
+
+
 def test_tc_mma_distinguishes_rows_and_columns():
     """A one-hot pattern: row i of A and row j of B share exactly one non-zero column, so each
     output names the pair it came from (a transposed or shifted operand would move the values)."""
