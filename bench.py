@@ -43,8 +43,9 @@ SEED = 0x4D520002
 # Peak of the 32x32->64-bit multiply-add pipe: SMs x 64 per clock x max SM clock
 IMAD_PER_CLK_PER_SM = 64   # int32 multiplies per clock per SM (integer multiply pipe)
 # DRAM bytes (read + write) of one exponentiation launch of the RSA-2048 CRT workload, from an ncu
-# capture of the current kernel on this workload (dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_BYTES_PER_LAUNCH = 2_861_568 + 24_110_080
+# capture on this workload (dram__bytes_read.sum + dram__bytes_write.sum), per kernel form of the
+# 1024-bit class: the integer form and the tensor-core form (None until captured for the current code)
+TRAFFIC_BYTES_PER_LAUNCH = {"integer": 2_861_568 + 24_110_080, "tensor": None}
 # long-exponent workload: 256 exponentiations modulo 16384-bit RSA moduli with 16128-bit exponents
 BIG_KEYSET = "mod16384_x4"
 BIG_N = 256
@@ -637,12 +638,15 @@ def run_ours(args, rank, world, local_rank, emit=True):
     # the kernel runs the sliding-window schedule (w >= 4) for all of them
     prods = 0
     ops31 = 0
+    n_mm = 0  # RNS Montgomery multiplications of the launch (all 8192 exponentiations)
     for i in idx:
         for dpq in (keys[i]["dp"], keys[i]["dq"]):
             if w >= 4:
                 prods += algorithmic_products_sliding(k, W, WX, dpq, w, 2)
+                n_mm += mms_sliding(dpq, w, 2)
             else:
                 prods += algorithmic_products_per_modexp(k, W, WX, dpq.bit_length(), w, 2)
+                n_mm += 2 + (2 ** w - 2) + (w + 1) * (math.ceil(dpq.bit_length() / w) - 1) + 1
             ops31 += ops_31bit_count(1024, dpq.bit_length(), w)
     ops_per_launch = 2 * prods  # one exponentiation launch per call covers all 8192 halves
     max_mhz = sm_max_mhz()
@@ -658,9 +662,15 @@ def run_ours(args, rank, world, local_rank, emit=True):
               "mma_sync_f16_ops_per_s": ctx.mr_tensor_peak(2, stream),
               "tcgen05_kind_i8": "not available on sm_103a (ptxas: feature not supported on this target)"}
     achieved31 = ops31 / (mx_avg_ms / 1e3)
+    # the kernel form the 1024-bit class runs by default: the base extensions on the tensor cores
+    # (8-bit slices, exact fp32 sums) or as mad.wide dot products on the integer pipe
+    vinfo = mr.mr_lane_variant_info(L_half, 0)
+    form = "tensor" if vinfo["tensor"] else "integer"
+    kname = (f"modexp_kernel<k={k},TPI={vinfo['lanes_per_number']}"
+             + (", base extensions on tcgen05 (8-bit slices)>" if vinfo["tensor"] else ">"))
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T int32-mul/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
-                "kernel": f"modexp_kernel<k={k},TPI=4>", "kernel_ms": mx_avg_ms,
+                "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH[form],
+                "kernel": kname, "kernel_ms": mx_avg_ms,
                 "int32_mul_ops_per_launch": ops_per_launch, "wide_products_per_launch": prods,
                 "count": f"implemented: k = {k} channels per base, 2k^2+7k products per multiplication, "
                          "the kernel's window schedule",
@@ -675,6 +685,23 @@ def run_ours(args, rank, world, local_rank, emit=True):
                                "peak_int32_mul_per_s": 2 * wide_rate, "frac": achieved / (2 * wide_rate),
                                "tensor_peaks": tensor},
                 "crt_kernel_ms": crt_ms / max(1, crt_launch)}
+    if vinfo["tensor"]:
+        # the two extensions' slice products: 16 pairs of 8-bit slices, 2 k^2 operations each, per
+        # number and multiplication; executed: the 128-row products with the zero columns and the offset
+        # column (2 x 128 x (16 ceil(k/4)) x (4 (ceil(k/4)/4 + 1) 4) per block of 32 numbers)
+        npt = -(-k // 4)
+        kcols = 4 * ((npt // 4 + 1) * 4)
+        t_alg = n_mm * 2 * 16 * 2 * k * k
+        t_exec = (n_mm / 32) * 2 * 2 * 128 * (16 * npt) * kcols
+        tpeak = measured_peak("bf16_tflops", 1.9e15 / 1e12) * 1e12
+        t_s = mx_avg_ms / 1e3
+        roofline["extensions"] = "tcgen05.mma kind::f16, fp32 accumulators in tensor memory (exact below 2^24)"
+        roofline["count"] += "; the two extensions (2k^2 of the products) run on the tensor cores"
+        roofline["tensor"] = {"achieved": t_alg / t_s / 1e12, "peak": tpeak / 1e12, "unit": "TFLOP/s",
+                              "frac": t_alg / t_s / tpeak, "tensor_ops_per_launch": t_alg,
+                              "executed_tensor_ops_per_launch": t_exec, "frac_executed": t_exec / t_s / tpeak,
+                              "peak_def": "MEASURED_PEAKS bf16 burst (fp16 and bf16 share the tensor rate)",
+                              "count": "2 extensions x 16 slice pairs x 2 k^2 per number and multiplication"}
     if clocks and clocks.get("sm_mhz"):
         roofline["frac_at_observed_clock"] = achieved / (props.multi_processor_count * IMAD_PER_CLK_PER_SM *
                                                           clocks["sm_mhz"] * 1e6)

@@ -355,6 +355,14 @@ mr_status mr_modexp_batch_noalloc(mr_ctx *ctx, const mr_key *key, size_t n, cons
  * Errors: MR_ERR_SIZE (no such class). */
 mr_status mr_class_variants(uint32_t class_bits, uint32_t *count, uint32_t *lanes_per_number, uint32_t capacity);
 
+/* One lane mapping of a size class of at most 4096 bits: out[0] lanes per
+ * number, out[1] threads per block, out[2] numbers per block, out[3] 1 when the
+ * exponentiation kernel forms the two base extensions (Sec. 3.1: products with
+ * the class's constant extension matrices) on the tensor cores, as exact
+ * products of 8-bit slices, else 0.  out: host, 4 words.  Errors: MR_ERR_SIZE
+ * (no such lane-group class), MR_ERR_ARG. */
+mr_status mr_lane_variant_info(uint32_t class_bits, uint32_t variant, uint32_t *out);
+
 /* Select the lane mapping later calls on this context use for a size class
  * (variant < count of mr_class_variants; variant 0 is the default).  Results do
  * not depend on the choice, only speed does.  Errors: MR_ERR_ARG, MR_ERR_SIZE. */

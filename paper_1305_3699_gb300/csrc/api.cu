@@ -2207,6 +2207,18 @@ mr_status mr_class_variants(uint32_t class_bits, uint32_t* count, uint32_t* lane
   return MR_OK;
 }
 
+mr_status mr_lane_variant_info(uint32_t class_bits, uint32_t variant, uint32_t* out) {
+  const ClassKernels* k = class_kernels(class_bits);
+  if (!k || k->big) return MR_ERR_SIZE;
+  if (!out || variant >= k->n_variants) return MR_ERR_ARG;
+  const KernelVariant& v = k->var[variant];
+  out[0] = v.tpi;
+  out[1] = v.threads;
+  out[2] = v.ipb;
+  out[3] = v.tc;
+  return MR_OK;
+}
+
 mr_status mr_set_variant(mr_ctx* ctx, uint32_t class_bits, uint32_t variant) {
   if (!ctx) return MR_ERR_ARG;
   return guarded(ctx, [&]() -> mr_status {

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # lanes per number in one warp or 8 in two warps, at most two blocks per SM).
 CLASSES = {
     512: (18, 16, 17, [(2, 128, 4, 2), (4, 128, 4, 4)]),
-    1024: (36, 32, 34, [(4, 128, 4, 3), (8, 128, 4, 4), (4, 128, 4, 2, 1), (8, 256, 4, 2, 1)]),
+    1024: (36, 32, 34, [(4, 128, 4, 2, 1), (4, 128, 4, 3), (8, 128, 4, 4)]),
     1536: (54, 48, 50, [(8, 128, 4, 0)]),
     2048: (72, 64, 66, [(8, 128, 4, 0), (16, 128, 4, 1)]),
     3072: (108, 96, 97, [(16, 256, 4, 0)]),
@@ -94,7 +94,7 @@ def unit(L, k, W, WX, variants):
                 "  int n = 0;",
                 f"  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, modexp_kernel<{C}>, {C}::THREADS, {C}::SMEM_MODEXP_BYTES) != cudaSuccess) n = 1;",
                 "  return n > 0 ? n : 1;", "}", ""]
-        entries.append(f"     {{{C}::TPI, {C}::THREADS, {C}::IPB, {C}::NPT, {C}::SMEM_MODEXP_BYTES, launch_modexp_{L}_{v}, "
+        entries.append(f"     {{{C}::TPI, {C}::THREADS, {C}::IPB, {C}::NPT, {C}::SMEM_MODEXP_BYTES, {C}::TC, launch_modexp_{L}_{v}, "
                        f"launch_crt_{L}_{v}, launch_mr_{L}_{v}, prepare_{L}_{v}, occupancy_{L}_{v}}}")
     out.append(f"extern const ClassKernels kClass{L} = {{")
     out.append(f"    {L}, {k}, {W}, {WX}, {len(variants)},")

@@ -38,7 +38,7 @@ static int occupancy_1536_0() {
 extern const ClassKernels kClass1536 = {
     1536, 54, 48, 50, 1,
     {
-     {C1536v0::TPI, C1536v0::THREADS, C1536v0::IPB, C1536v0::NPT, C1536v0::SMEM_MODEXP_BYTES, launch_modexp_1536_0, launch_crt_1536_0, launch_mr_1536_0, prepare_1536_0, occupancy_1536_0}},
+     {C1536v0::TPI, C1536v0::THREADS, C1536v0::IPB, C1536v0::NPT, C1536v0::SMEM_MODEXP_BYTES, C1536v0::TC, launch_modexp_1536_0, launch_crt_1536_0, launch_mr_1536_0, prepare_1536_0, occupancy_1536_0}},
     nullptr, 0};
 
 }  // namespace mr

@@ -68,8 +68,8 @@ static int occupancy_2048_1() {
 extern const ClassKernels kClass2048 = {
     2048, 72, 64, 66, 2,
     {
-     {C2048v0::TPI, C2048v0::THREADS, C2048v0::IPB, C2048v0::NPT, C2048v0::SMEM_MODEXP_BYTES, launch_modexp_2048_0, launch_crt_2048_0, launch_mr_2048_0, prepare_2048_0, occupancy_2048_0},
-     {C2048v1::TPI, C2048v1::THREADS, C2048v1::IPB, C2048v1::NPT, C2048v1::SMEM_MODEXP_BYTES, launch_modexp_2048_1, launch_crt_2048_1, launch_mr_2048_1, prepare_2048_1, occupancy_2048_1}},
+     {C2048v0::TPI, C2048v0::THREADS, C2048v0::IPB, C2048v0::NPT, C2048v0::SMEM_MODEXP_BYTES, C2048v0::TC, launch_modexp_2048_0, launch_crt_2048_0, launch_mr_2048_0, prepare_2048_0, occupancy_2048_0},
+     {C2048v1::TPI, C2048v1::THREADS, C2048v1::IPB, C2048v1::NPT, C2048v1::SMEM_MODEXP_BYTES, C2048v1::TC, launch_modexp_2048_1, launch_crt_2048_1, launch_mr_2048_1, prepare_2048_1, occupancy_2048_1}},
     nullptr, 0};
 
 }  // namespace mr

@@ -38,7 +38,7 @@ static int occupancy_3072_0() {
 extern const ClassKernels kClass3072 = {
     3072, 108, 96, 97, 1,
     {
-     {C3072v0::TPI, C3072v0::THREADS, C3072v0::IPB, C3072v0::NPT, C3072v0::SMEM_MODEXP_BYTES, launch_modexp_3072_0, launch_crt_3072_0, launch_mr_3072_0, prepare_3072_0, occupancy_3072_0}},
+     {C3072v0::TPI, C3072v0::THREADS, C3072v0::IPB, C3072v0::NPT, C3072v0::SMEM_MODEXP_BYTES, C3072v0::TC, launch_modexp_3072_0, launch_crt_3072_0, launch_mr_3072_0, prepare_3072_0, occupancy_3072_0}},
     nullptr, 0};
 
 }  // namespace mr

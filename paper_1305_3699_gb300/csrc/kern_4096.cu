@@ -38,7 +38,7 @@ static int occupancy_4096_0() {
 extern const ClassKernels kClass4096 = {
     4096, 145, 128, 129, 1,
     {
-     {C4096v0::TPI, C4096v0::THREADS, C4096v0::IPB, C4096v0::NPT, C4096v0::SMEM_MODEXP_BYTES, launch_modexp_4096_0, launch_crt_4096_0, launch_mr_4096_0, prepare_4096_0, occupancy_4096_0}},
+     {C4096v0::TPI, C4096v0::THREADS, C4096v0::IPB, C4096v0::NPT, C4096v0::SMEM_MODEXP_BYTES, C4096v0::TC, launch_modexp_4096_0, launch_crt_4096_0, launch_mr_4096_0, prepare_4096_0, occupancy_4096_0}},
     nullptr, 0};
 
 }  // namespace mr

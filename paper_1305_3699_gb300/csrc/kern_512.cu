@@ -68,8 +68,8 @@ static int occupancy_512_1() {
 extern const ClassKernels kClass512 = {
     512, 18, 16, 17, 2,
     {
-     {C512v0::TPI, C512v0::THREADS, C512v0::IPB, C512v0::NPT, C512v0::SMEM_MODEXP_BYTES, launch_modexp_512_0, launch_crt_512_0, launch_mr_512_0, prepare_512_0, occupancy_512_0},
-     {C512v1::TPI, C512v1::THREADS, C512v1::IPB, C512v1::NPT, C512v1::SMEM_MODEXP_BYTES, launch_modexp_512_1, launch_crt_512_1, launch_mr_512_1, prepare_512_1, occupancy_512_1}},
+     {C512v0::TPI, C512v0::THREADS, C512v0::IPB, C512v0::NPT, C512v0::SMEM_MODEXP_BYTES, C512v0::TC, launch_modexp_512_0, launch_crt_512_0, launch_mr_512_0, prepare_512_0, occupancy_512_0},
+     {C512v1::TPI, C512v1::THREADS, C512v1::IPB, C512v1::NPT, C512v1::SMEM_MODEXP_BYTES, C512v1::TC, launch_modexp_512_1, launch_crt_512_1, launch_mr_512_1, prepare_512_1, occupancy_512_1}},
     nullptr, 0};
 
 }  // namespace mr

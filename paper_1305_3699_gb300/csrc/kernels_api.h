@@ -76,6 +76,7 @@ MR_HD inline uint32_t mr_debug_words(uint32_t k, uint32_t W) { return 4 + 2 * W 
 // One compiled lane mapping of a size class.
 struct KernelVariant {
   uint32_t tpi, threads, ipb, npt, smem_bytes;
+  uint32_t tc;  // 1: the exponentiation kernel forms the base extensions on the tensor cores (rns_tc.cuh)
   cudaError_t (*modexp)(const LaunchArgs&, unsigned grid, cudaStream_t);
   cudaError_t (*crt)(const LaunchArgs&, unsigned grid, cudaStream_t);
   cudaError_t (*mr)(const MRArgs&, unsigned grid, cudaStream_t);

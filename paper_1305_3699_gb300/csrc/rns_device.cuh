@@ -130,7 +130,7 @@ struct Cfg {
   static constexpr int TC_B2 = TC_B1 + NB * KA * 2;
   static constexpr int TC_MISC = TC_B2 + NB * KA * 2;  // mbarrier, tensor-memory address, abort flag, votes,
                                                        // then [2 warp halves][32 numbers] partial sums
-  static constexpr int TC_END = TC_MISC + 64 + 256;
+  static constexpr int TC_END = TC_MISC + 128 + 256;
   // the tensor-core kernel asks for at least 80 KB so that at most two blocks share an SM: two
   // accumulators of 256 columns fill the SM's 512 columns of tensor memory
   static constexpr int SMEM_MODEXP_BYTES = TC ? (TC_END > 81920 ? TC_END : 81920) : SMEM_BYTES;

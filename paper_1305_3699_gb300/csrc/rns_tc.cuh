@@ -43,7 +43,7 @@ constexpr uint64_t LG_TC_WAIT_NS = 1000000000ull;
 
 struct TcState {
   uint32_t tmem;   // accumulator base address in tensor memory
-  uint32_t phase;  // parity of the next completion of the block's mbarrier (tracked by thread 0)
+  uint32_t phase;  // parity of the next completion of the block's mbarrier
 };
 
 template <class C>
@@ -53,10 +53,10 @@ struct TcSmem {
   __device__ uint8_t* B1() const { return base + C::TC_B1; }
   __device__ uint8_t* B2() const { return base + C::TC_B2; }
   __device__ uint64_t* mbar() const { return reinterpret_cast<uint64_t*>(base + C::TC_MISC); }
-  __device__ uint32_t* tslot() const { return reinterpret_cast<uint32_t*>(base + C::TC_MISC + 8); }
-  __device__ volatile uint32_t* abort_flag() const { return reinterpret_cast<volatile uint32_t*>(base + C::TC_MISC + 12); }
-  __device__ uint32_t* vote() const { return reinterpret_cast<uint32_t*>(base + C::TC_MISC + 16); }  // 8 words
-  __device__ uint32_t* part() const { return reinterpret_cast<uint32_t*>(base + C::TC_MISC + 64); }   // [2][32]
+  __device__ uint32_t* tslot() const { return reinterpret_cast<uint32_t*>(base + C::TC_MISC + 32); }
+  __device__ volatile uint32_t* abort_flag() const { return reinterpret_cast<volatile uint32_t*>(base + C::TC_MISC + 36); }
+  __device__ uint32_t* vote() const { return reinterpret_cast<uint32_t*>(base + C::TC_MISC + 64); }  // 8 words
+  __device__ uint32_t* part() const { return reinterpret_cast<uint32_t*>(base + C::TC_MISC + 128); }  // [2][32]
 };
 
 // K column of lane t's channel slot s is NPTK t + tc_kslot(t, s): with NPTK = 8 the two groups of four
@@ -113,8 +113,8 @@ __device__ void tc_prologue(const TcSmem<C>& ts, const uint32_t* cls) {
 
 // Write byte slices of this lane's coefficients v (its NPT channels; lane t of number n) into rows
 // 4n + a of the data operand: four consecutive K columns per 8-byte store.  A byte b becomes the fp16
-// value b as the bit pattern of 1024 + b minus 1024.  Step a of lane l writes slice (a + l / 8) % 4, so
-// that the rows of one store instruction cover all 8 rows of a core matrix (distinct banks).
+// value b as the bit pattern of 1024 + b minus 1024.  Step a of lane l writes slice (a + l_1 + 2 l_3) % 4
+// (l_i: bit i of l), so that each half-warp's 8-byte stores reach 32 distinct banks.
 template <class C>
 __device__ __forceinline__ void tc_publish(const TcSmem<C>& ts, const uint32_t (&v)[C::NPT], int n, int t) {
   constexpr int NPT = C::NPT, NPTK = C::NPTK, K = C::K;
@@ -129,7 +129,7 @@ __device__ __forceinline__ void tc_publish(const TcSmem<C>& ts, const uint32_t (
       x[q] = (s < NPT && t * NPT + s < K) ? v[s < NPT ? s : 0] : 0u;
     }
     const bool has_off = (t == 0) && (4 * g <= NPT) && (NPT < 4 * g + 4);  // the 2^23 offset column
-    const int rot = (int)((threadIdx.x & 31) >> 3);
+    const int rot = (int)(((threadIdx.x >> 1) & 1) + 2 * ((threadIdx.x >> 3) & 1));
 #pragma unroll
     for (int a0 = 0; a0 < 4; a0++) {
       const int a = (a0 + rot) & 3;
@@ -191,38 +191,41 @@ __device__ __forceinline__ uint64_t tc_combine(const uint32_t (&r)[16], int a) {
 }
 
 // One base extension: the block's data operand (already published) times matrix operand B; acc[s]
-// receives the k-term dot product of this lane's output channel t NPT + s.
+// receives the k-term dot product of this lane's output channel t NPT + s.  Thread 0 issues the
+// product (one tcgen05.mma per K step of 16 and warp half); every thread waits for its completion on
+// the block's mbarrier.
 template <class C>
 __device__ __forceinline__ void tc_extension(const TcSmem<C>& ts, TcState& st, const uint8_t* B,
                                              uint64_t (&acc)[C::NPT], int t) {
-  constexpr int NPT = C::NPT, KA = C::KA, NB = C::NB;
+  constexpr int NPT = C::NPT, KA = C::KA, NB = C::NB, HALVES = C::TPI / 4;
   tc::fence_smem_async();   // the generic-proxy stores of the data operand, visible to the tensor core
   tc::fence_before_sync();  // the previous extension's accumulator loads complete before the barrier
   __syncthreads();
-  // thread 0 issues the product and alone waits for its completion; the others wait at the block
-  // barrier (no issue slots spent polling)
   if (threadIdx.x == 0 && *ts.abort_flag() == 0u) {
     tc::fence_after_sync();
-    constexpr uint32_t idesc = tc::idesc_f16_f32(128, NB);
+    constexpr uint32_t idesc = tc::idesc_f16_f32(128, 16 * NPT);
     const uint32_t a0 = tc::saddr(ts.A()), b0 = tc::saddr(B);
 #pragma unroll
-    for (int ks = 0; ks < KA / 16; ks++) {
-      const uint64_t ad = tc::sdesc(a0 + ks * (2 * 16 * 128), 16 * 128, 128);
-      const uint64_t bd = tc::sdesc(b0 + ks * (2 * 16 * NB), 16 * NB, 128);
-      tc::mma_f16(st.tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+    for (int h = 0; h < HALVES; h++) {
+      const int row0 = 16 * NPT * h;  // first matrix row = first accumulator column of warp half h
+#pragma unroll
+      for (int ks = 0; ks < KA / 16; ks++) {
+        const uint64_t ad = tc::sdesc(a0 + ks * (2 * 16 * 128), 16 * 128, 128);
+        const uint64_t bd = tc::sdesc(b0 + ks * (2 * 16 * NB) + (row0 / 8) * 128, 16 * NB, 128);
+        tc::mma_f16(st.tmem + row0, ad, bd, idesc, ks > 0 ? 1u : 0u);
+      }
     }
     tc::mma_commit(ts.mbar());
-    if (tc::mbar_wait_ns(ts.mbar(), st.phase, LG_TC_WAIT_NS)) st.phase ^= 1u;
-    else *ts.abort_flag() = 1u;  // st.phase stays the parity of the product still in flight
   }
-  __syncthreads();
+  if (*ts.abort_flag() == 0u && !tc::mbar_wait_ns(ts.mbar(), st.phase, LG_TC_WAIT_NS)) *ts.abort_flag() = 1u;
+  st.phase ^= 1u;
   tc::fence_after_sync();
   const int warp = threadIdx.x >> 5;
   // lane quarter warp % 4; warp half h reads its 16 NPT columns
   const uint32_t lane_base = st.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * NPT * tc_half<C>());
   const int a = threadIdx.x & 3;
 #pragma unroll
-  for (int j0 = 0; j0 < NPT; j0 += 3) {
+  for (int j0 = 0; j0 < NPT; j0 += 3) {  // loads and combines in groups of 3 slots
     uint32_t r[3][16];
 #pragma unroll
     for (int q = 0; q < 3; q++)
@@ -298,7 +301,7 @@ __device__ void tc_release(const TcSmem<C>& ts, const TcState& st) {
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (*ts.abort_flag() != 0u && threadIdx.x == 0) (void)tc::mbar_wait_ns(ts.mbar(), st.phase, LG_TC_WAIT_NS);
+  if (*ts.abort_flag() != 0u && threadIdx.x == 0) (void)tc::mbar_wait_ns(ts.mbar(), st.phase ^ 1u, LG_TC_WAIT_NS);
   __syncthreads();
   if (threadIdx.x < 32) tc::tmem_dealloc(st.tmem, 256);
 }

@@ -27,7 +27,7 @@ EXPORTED = [
     "mr_init", "mr_shutdown", "mr_last_error", "mr_class_for_bits", "mr_rns_setup", "mr_rsa_key_setup",
     "mr_key_info", "mr_key_free", "mr_modexp_batch", "mr_rsa_encrypt", "mr_rsa_decrypt_crt",
     "mr_miller_rabin_batch", "mr_debug_table", "mr_debug_key_table_host", "mr_profile_enable", "mr_profile_read",
-    "mr_modexp_batch_noalloc", "mr_class_variants", "mr_set_variant", "mr_debug_mr_setup",
+    "mr_modexp_batch_noalloc", "mr_class_variants", "mr_lane_variant_info", "mr_set_variant", "mr_debug_mr_setup",
     "mr_rsa_mixed", "mr_plan_create", "mr_plan_launch", "mr_plan_info", "mr_plan_free",
     "mr_imad_peak", "mr_autotune", "mr_debug_big_wait", "mr_prime_test_batch", "mr_debug_trial_table",
     "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
@@ -97,6 +97,7 @@ def _load() -> ctypes.CDLL:
         "mr_profile_enable": (ctypes.c_int, [P, ctypes.c_int]),
         "mr_modexp_batch_noalloc": (ctypes.c_int, [P, P, SZ, P, U32, P, U32, P, U32, P, P]),
         "mr_class_variants": (ctypes.c_int, [U32, PU32, PU32, U32]),
+        "mr_lane_variant_info": (ctypes.c_int, [U32, U32, PU32]),
         "mr_set_variant": (ctypes.c_int, [P, U32, U32]),
         "mr_debug_mr_setup": (ctypes.c_int, [P, P, U32, SZ, P, P]),
         "mr_rsa_mixed": (ctypes.c_int, [P, P, P, SZ, P, U32, P, U32, P, U32, P]),
@@ -167,6 +168,15 @@ def mr_class_for_bits(bits: int):
     if rc:
         raise MRError(rc, f"no size class for {bits} bits")
     return L.value, k.value
+
+
+def mr_lane_variant_info(class_bits: int, variant: int) -> dict:
+    """One lane mapping of a lane-group size class (see mr.h)."""
+    out = (ctypes.c_uint32 * 4)()
+    rc = lib.mr_lane_variant_info(class_bits, variant, out)
+    if rc != 0:
+        raise MRError(rc, "mr_lane_variant_info")
+    return {"lanes_per_number": out[0], "threads": out[1], "numbers_per_block": out[2], "tensor": bool(out[3])}
 
 
 def mr_class_variants(class_bits: int) -> List[int]:
