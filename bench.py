@@ -43,9 +43,10 @@ SEED = 0x4D520002
 # Peak of the 32x32->64-bit multiply-add pipe: SMs x 64 per clock x max SM clock
 IMAD_PER_CLK_PER_SM = 64   # int32 multiplies per clock per SM (integer multiply pipe)
 # DRAM bytes (read + write) of one exponentiation launch of the RSA-2048 CRT workload, from an ncu
-# capture on this workload (dram__bytes_read.sum + dram__bytes_write.sum), per kernel form of the
-# 1024-bit class: the integer form and the tensor-core form (None until captured for the current code)
-TRAFFIC_BYTES_PER_LAUNCH = {"integer": 2_861_568 + 24_110_080, "tensor": None}
+# capture on this workload, per kernel form of the 1024-bit class: the integer form
+# (dram__bytes_read.sum + dram__bytes_write.sum) and the tensor-core form (dram__bytes.sum.per_second
+# x gpu__time_duration.sum: 6.5965 GB/s x 3.96816 ms)
+TRAFFIC_BYTES_PER_LAUNCH = {"integer": 2_861_568 + 24_110_080, "tensor": 26_176_000}
 # long-exponent workload: 256 exponentiations modulo 16384-bit RSA moduli with 16128-bit exponents
 BIG_KEYSET = "mod16384_x4"
 BIG_N = 256

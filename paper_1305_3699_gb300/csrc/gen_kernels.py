@@ -16,12 +16,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # resident blocks per SM (its register budget, 0 = compiler's choice), picked per variant by timing
 # each value on 1024-16384 numbers of the class with full-length exponents.  TC = 1: the base
 # extensions of the exponentiation kernel run on the tensor cores (rns_tc.cuh; 32 numbers per block, 4
-# lanes per number in one warp or 8 in two warps, at most two blocks per SM).
+# lanes per number in one warp or 8 in two warps; as many blocks per SM as their accumulators fit in
+# tensor memory).
 CLASSES = {
-    512: (18, 16, 17, [(2, 128, 4, 2), (4, 128, 4, 4)]),
+    512: (18, 16, 17, [(2, 128, 4, 2), (4, 128, 4, 4), (4, 128, 4, 4, 1)]),
     1024: (36, 32, 34, [(4, 128, 4, 2, 1), (4, 128, 4, 3), (8, 128, 4, 4)]),
-    1536: (54, 48, 50, [(8, 128, 4, 0)]),
-    2048: (72, 64, 66, [(8, 128, 4, 0), (16, 128, 4, 1)]),
+    1536: (54, 48, 50, [(8, 256, 4, 2, 1), (8, 128, 4, 0)]),
+    2048: (72, 64, 66, [(8, 256, 4, 1, 1), (8, 128, 4, 0), (16, 128, 4, 1)]),
     3072: (108, 96, 97, [(16, 256, 4, 0)]),
     4096: (145, 128, 129, [(16, 384, 2, 0)]),
 }

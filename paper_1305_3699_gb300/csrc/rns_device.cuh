@@ -131,13 +131,17 @@ struct Cfg {
   static constexpr int TC_MISC = TC_B2 + NB * KA * 2;  // mbarrier, tensor-memory address, abort flag, votes,
                                                        // then [2 warp halves][32 numbers] partial sums
   static constexpr int TC_END = TC_MISC + 128 + 256;
-  // the tensor-core kernel asks for at least 80 KB so that at most two blocks share an SM: two
-  // accumulators of 256 columns fill the SM's 512 columns of tensor memory
-  static constexpr int SMEM_MODEXP_BYTES = TC ? (TC_END > 81920 ? TC_END : 81920) : SMEM_BYTES;
+  // accumulator columns allocated per block (a power of two), and the blocks that fit the SM's 512
+  static constexpr int TMEM_COLS = NB <= 32 ? 32 : NB <= 64 ? 64 : NB <= 128 ? 128 : NB <= 256 ? 256 : 512;
+  static constexpr int TC_BLOCKS = 512 / TMEM_COLS;
+  // the tensor-core kernel asks for enough shared memory that no more than TC_BLOCKS blocks share an SM
+  // (228 KB per SM, 1 KB reserved per block)
+  static constexpr int TC_SMEM_MIN = TC_BLOCKS >= 4 ? 0 : 233472 / (TC_BLOCKS + 1) - 1024 + 128;
+  static constexpr int SMEM_MODEXP_BYTES = TC ? (TC_END > TC_SMEM_MIN ? TC_END : TC_SMEM_MIN) : SMEM_BYTES;
   static_assert(!TC || (TPI == 4 && THREADS == 128) || (TPI == 8 && THREADS == 256),
                 "tensor-core form: 32 numbers x 4 or 8 lanes");
-  static_assert(!TC || NB <= 256, "tensor-core form: N <= 256 accumulator columns");
-  static_assert(!TC || K <= 64, "tensor-core form: K * 255^2 < 2^22 keeps the fp32 sums exact");
+  static_assert(!TC || (16 * NPT <= 256 && NB <= 512), "tensor-core form: N <= 256 per warp half");
+  static_assert(!TC || K * 255 * 255 < (1 << 23), "tensor-core form: every fp32 sum stays below 2^23");
   static_assert(SMEM_MODEXP_BYTES <= 227 * 1024, "shared memory");
 };
 

@@ -9,7 +9,7 @@
 // (k >= 16 keeps the channel primes there), so each splits into four 8-bit
 // slices, xi = sum_a 2^(8a) X_a, T = sum_b 2^(8b) T_b, and each slice is an fp16
 // integer.  One product forms every P_ab(j) = sum_i X_a[i] T_b[i][j] for the 32
-// numbers of the block: a sum of k <= 64 products below 255^2, i.e. below 2^22,
+// numbers of the block: a sum of k products below 255^2, below 2^23 for k <= 129,
 // so the fp32 accumulator holds it exactly.  An extra K column of 2048 x 4096
 // adds 2^23 to every accumulator; a value in [2^23, 2^24) has the integer
 // sum as its 23 mantissa bits.  The 64-bit dot product sum_a sum_b 2^(8(a+b))
@@ -104,7 +104,7 @@ __device__ void tc_prologue(const TcSmem<C>& ts, const uint32_t* cls) {
     for (int q = 0; q < 8; q++) ts.vote()[q] = 0u;
   }
   if (threadIdx.x < 32) {
-    tc::tmem_alloc(ts.tslot(), 256);
+    tc::tmem_alloc(ts.tslot(), C::TMEM_COLS);
     tc::tmem_relinquish();
   }
   tc::fence_smem_async();
@@ -192,11 +192,11 @@ __device__ __forceinline__ uint64_t tc_combine(const uint32_t (&r)[16], int a) {
 
 // One base extension: the block's data operand (already published) times matrix operand B; acc[s]
 // receives the k-term dot product of this lane's output channel t NPT + s.  Thread 0 issues the
-// product (one tcgen05.mma per K step of 16 and warp half); every thread waits for its completion on
-// the block's mbarrier.
-template <class C>
+// product (one tcgen05.mma per K step of 16 and warp half); every thread runs `overlap` and then
+// waits for the product's completion on the block's mbarrier.
+template <class C, class Overlap>
 __device__ __forceinline__ void tc_extension(const TcSmem<C>& ts, TcState& st, const uint8_t* B,
-                                             uint64_t (&acc)[C::NPT], int t) {
+                                             uint64_t (&acc)[C::NPT], int t, Overlap&& overlap) {
   constexpr int NPT = C::NPT, KA = C::KA, NB = C::NB, HALVES = C::TPI / 4;
   tc::fence_smem_async();   // the generic-proxy stores of the data operand, visible to the tensor core
   tc::fence_before_sync();  // the previous extension's accumulator loads complete before the barrier
@@ -217,6 +217,7 @@ __device__ __forceinline__ void tc_extension(const TcSmem<C>& ts, TcState& st, c
     }
     tc::mma_commit(ts.mbar());
   }
+  overlap();  // work that does not depend on the product
   if (*ts.abort_flag() == 0u && !tc::mbar_wait_ns(ts.mbar(), st.phase, LG_TC_WAIT_NS)) *ts.abort_flag() = 1u;
   st.phase ^= 1u;
   tc::fence_after_sync();
@@ -249,20 +250,24 @@ __device__ __forceinline__ void mont_mul_tc(uint32_t (&xb)[C::NPT], uint32_t (&x
   constexpr int NPT = C::NPT;
   const int n = tc_number<C>();
   uint32_t sp[NPT], xi[NPT];
-  // 1-2. s = x*y in both bases; xi_i = s_i |-N^-1 (M/m_i)^-1| (plain)
+  // 1-2. s = x*y in B; xi_i = s_i |-N^-1 (M/m_i)^-1| (plain)
 #pragma unroll
   for (int s = 0; s < NPT; s++) {
     const uint4 cb = sm.cb4(t, s);
     const uint32_t sb = redc_lazy(mulw(xb[s], yb[s]), cb.x, cb.y);
     const uint32_t u = sb * kxp[s] - __umulhi(sb, kxs[s]) * cb.x;
     xi[s] = min(u, u - cb.x);
-    const uint4 cp = sm.cp4(t, s);
-    sp[s] = redc_lazy(mulw(xp[s], yp[s]), cp.x, cp.y);
   }
   tc_publish<C>(ts, xi, n, t);
-  // 3. extension B -> B'
+  // 3. extension B -> B'; s = x*y in B' is formed while the product runs
   uint64_t acc[NPT];
-  tc_extension<C>(ts, st, ts.B1(), acc, t);
+  tc_extension<C>(ts, st, ts.B1(), acc, t, [&] {
+#pragma unroll
+    for (int s = 0; s < NPT; s++) {
+      const uint4 cp = sm.cp4(t, s);
+      sp[s] = redc_lazy(mulw(xp[s], yp[s]), cp.x, cp.y);
+    }
+  });
   // 4-5. new B' residues and xi'_j (as in mont_mul)
   uint32_t kaw = 0;
 #pragma unroll
@@ -284,7 +289,7 @@ __device__ __forceinline__ void mont_mul_tc(uint32_t (&xb)[C::NPT], uint32_t (&x
   if constexpr (C::TPI == 8)
     if ((threadIdx.x & 3) == 0) ts.part()[32 * tc_half<C>() + n] = kaw;
   // 6. extension B' -> B, exact, with the correction folded into the accumulator
-  tc_extension<C>(ts, st, ts.B2(), acc, t);
+  tc_extension<C>(ts, st, ts.B2(), acc, t, [] {});
   if constexpr (C::TPI == 8) kaw += ts.part()[32 * (1 - tc_half<C>()) + n];
   const uint32_t alpha = (kaw + (1u << (KAW_Q - 2))) >> KAW_Q;
 #pragma unroll
@@ -303,7 +308,7 @@ __device__ void tc_release(const TcSmem<C>& ts, const TcState& st) {
   tc::fence_after_sync();
   if (*ts.abort_flag() != 0u && threadIdx.x == 0) (void)tc::mbar_wait_ns(ts.mbar(), st.phase ^ 1u, LG_TC_WAIT_NS);
   __syncthreads();
-  if (threadIdx.x < 32) tc::tmem_dealloc(st.tmem, 256);
+  if (threadIdx.x < 32) tc::tmem_dealloc(st.tmem, C::TMEM_COLS);
 }
 
 }  // namespace mr
