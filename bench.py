@@ -1586,7 +1586,8 @@ def run_serving_bench(args, rank, world, local_rank, emit=True):
         rows[i] = np.frombuffer(x.to_bytes(512, "little"), dtype="<u4")
     rows = rows.view(np.int32)
     arrivals = poisson_arrivals(rate, n, 0x4D520005 + rank)
-    srv = Server(ctx, hk, capacity=args.serve_capacity, slots=args.serve_slots)
+    srv = Server(ctx, hk, capacity=args.serve_capacity, slots=args.serve_slots,
+                 latency_mappings=args.serve_mappings == "widest")
     # warm-up on a slice
     w = min(n, 8192)
     srv.run(arrivals[:w] - arrivals[0], np.array(idx[:w]), np.array(ops[:w]), rows[:w])
@@ -1623,6 +1624,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="ragged workload: keep the default configurations")
     ap.add_argument("--serve-capacity", type=int, default=4096, help="serving workload: requests per batch slot")
     ap.add_argument("--serve-slots", type=int, default=3, help="serving workload: batch slots in flight")
+    ap.add_argument("--serve-mappings", default="widest", choices=["widest", "default"],
+                    help="serving workload: each class's widest lane mapping, or its default one")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--repeats", type=int, default=8,
                     help="rsa2048_crt: calls per step (each after an L2 flush, each inside its own events)")

@@ -520,6 +520,16 @@ mr_status mr_debug_big_phases(mr_ctx *ctx, int on, uint64_t *out);
  * hook off.  Errors: MR_ERR_ARG. */
 mr_status mr_debug_big_wait(mr_ctx *ctx, uint32_t spin_limit, int32_t absent_slice);
 
+/* Test hook of the bounded completion wait of the lane-group classes' tensor-core
+ * kernels (the base extensions of Sec. 3.1 as tcgen05 products).  With skip != 0,
+ * later batch calls on this context (mr_modexp_batch, mr_rsa_encrypt,
+ * mr_rsa_decrypt_crt and the calls built on them; not plans) launch those
+ * kernels with no product issued, so every block's first completion wait runs
+ * out after about one second: the call completes, every item of such a kernel
+ * reports MR_ERR_TIMEOUT and the context stays usable.  skip = 0 turns the hook
+ * off.  Errors: MR_ERR_ARG. */
+mr_status mr_debug_lane_tc_wait(mr_ctx *ctx, int skip);
+
 /* ------------------------------------------------------------ inspection -- */
 
 /* Copy one precomputed table of a size class (or of a key when key != NULL) to

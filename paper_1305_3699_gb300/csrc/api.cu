@@ -87,6 +87,7 @@ struct mr_ctx {
   uint32_t* mr_dbg = nullptr;  // test hook of mr_debug_mr_setup
   uint32_t big_spin_limit = 0;  // large-class barrier polls before giving up (0: the kernel default)
   int32_t big_absent_slice = -1;  // test hook of mr_debug_big_wait
+  bool lane_tc_skip = false;       // test hook of mr_debug_lane_tc_wait
   unsigned long long* big_phases = nullptr;  // mr_debug_big_phases: device counters, or nullptr (off)
   bool constant_time = false;  // mr_set_constant_time
   std::vector<cudaStream_t> side;     // streams for concurrent groups of one-shot mixed calls
@@ -446,7 +447,8 @@ mr_status run_batches(mr_ctx* ctx, std::vector<ClassBatch>& batches, uint8_t* st
     const KernelVariant& k = b.ce->kv();
     if (!b.mx.empty()) {
       LaunchArgs a{b.ce->dev, base + b.off_mx, (uint32_t)b.mx.size(), b.wbits,
-                   reinterpret_cast<uint32_t*>(base + b.off_scratch), status, nullptr, ctx->constant_time ? 1u : 0u};
+                   reinterpret_cast<uint32_t*>(base + b.off_scratch), status, nullptr, ctx->constant_time ? 1u : 0u,
+                   ctx->lane_tc_skip ? 1u : 0u};
       unsigned grid = (unsigned)((b.mx.size() + k.ipb - 1) / k.ipb);
       e = timed_launch(ctx, 0, stream, [&] { return k.modexp(a, grid, stream); });
       if (e != cudaSuccess) break;
@@ -2165,6 +2167,12 @@ mr_status mr_debug_big_phases(mr_ctx* ctx, int on, uint64_t* out) {
     ctx->big_phases = nullptr;
   }
   return e == cudaSuccess ? MR_OK : cuda_fail(ctx, e, "phase counters");
+}
+
+mr_status mr_debug_lane_tc_wait(mr_ctx* ctx, int skip) {
+  if (!ctx) return MR_ERR_ARG;
+  ctx->lane_tc_skip = skip != 0;
+  return MR_OK;
 }
 
 mr_status mr_debug_big_wait(mr_ctx* ctx, uint32_t spin_limit, int32_t absent_slice) {

@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(C::THREADS, C::MINB) modexp_kernel(LaunchArgs 
   Smem<C> sm{smem_raw};
   load_class_smem<C>(sm, a.cls);
   const TcSmem<C> ts{reinterpret_cast<uint8_t*>(smem_raw)};
-  TcState st{0u, 0u};
+  TcState st{0u, 0u, a.tc_skip};
   if constexpr (C::TC) tc_prologue<C>(ts, a.cls);
   __syncthreads();
   const int warp_global = (blockIdx.x * C::THREADS + threadIdx.x) >> 5;

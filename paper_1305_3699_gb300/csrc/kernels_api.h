@@ -19,6 +19,8 @@ struct LaunchArgs {
   uint32_t* queue;       // persistent mode: work-group counter (zeroed before the launch), else nullptr
   uint32_t ct;           // modexp: 1 = constant-time schedule (regular fixed windows over every exponent
                          // limb, every window multiplied, table entries selected by masking)
+  uint32_t tc_skip;      // test hook of the tensor-core form's bounded completion wait: 1 = no product is
+                         // issued, so every wait runs out (mr_debug_lane_tc_wait); 0 otherwise
 };
 
 struct MRArgs {

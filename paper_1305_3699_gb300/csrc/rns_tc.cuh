@@ -44,6 +44,7 @@ constexpr uint64_t LG_TC_WAIT_NS = 1000000000ull;
 struct TcState {
   uint32_t tmem;   // accumulator base address in tensor memory
   uint32_t phase;  // parity of the next completion of the block's mbarrier
+  uint32_t skip;   // test hook: thread 0 issues no product (every completion wait runs out)
 };
 
 template <class C>
@@ -201,7 +202,7 @@ __device__ __forceinline__ void tc_extension(const TcSmem<C>& ts, TcState& st, c
   tc::fence_smem_async();   // the generic-proxy stores of the data operand, visible to the tensor core
   tc::fence_before_sync();  // the previous extension's accumulator loads complete before the barrier
   __syncthreads();
-  if (threadIdx.x == 0 && *ts.abort_flag() == 0u) {
+  if (threadIdx.x == 0 && *ts.abort_flag() == 0u && !st.skip) {
     tc::fence_after_sync();
     constexpr uint32_t idesc = tc::idesc_f16_f32(128, 16 * NPT);
     const uint32_t a0 = tc::saddr(ts.A()), b0 = tc::saddr(B);
@@ -300,7 +301,7 @@ __device__ __forceinline__ void mont_mul_tc(uint32_t (&xb)[C::NPT], uint32_t (&x
 }
 
 // Block epilogue: wait (bounded) for a product still in flight after an abort, then free the
-// accumulator columns.
+// accumulator columns.  (With the skip hook nothing is in flight and this wait also runs out.)
 template <class C>
 __device__ void tc_release(const TcSmem<C>& ts, const TcState& st) {
   tc::fence_before_sync();

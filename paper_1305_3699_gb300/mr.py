@@ -33,7 +33,7 @@ EXPORTED = [
     "mr_rsa_keygen_batch", "mr_rsa_message_blocks", "mr_rsa_encrypt_message", "mr_rsa_decrypt_message",
     "mr_get_tuning", "mr_set_tuning", "mr_debug_crt_bin_host", "mr_debug_big_variant",
     "mr_tensor_peak", "mr_debug_tc_mma", "mr_debug_tc_slices", "mr_big_variant_info", "mr_debug_big_phases",
-    "mr_set_constant_time",
+    "mr_set_constant_time", "mr_debug_lane_tc_wait",
 ]
 
 MR_OP_ENCRYPT = 0
@@ -115,6 +115,7 @@ def _load() -> ctypes.CDLL:
         "mr_set_constant_time": (ctypes.c_int, [P, ctypes.c_int]),
         "mr_autotune": (ctypes.c_int, [P, U32, U32, U32, ctypes.POINTER(TuneResult)]),
         "mr_debug_big_wait": (ctypes.c_int, [P, U32, ctypes.c_int32]),
+        "mr_debug_lane_tc_wait": (ctypes.c_int, [P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -514,6 +515,10 @@ class Context:
         buf = (ctypes.c_uint64 * 9)()
         self._check(lib.mr_debug_big_phases(self.handle, 1 if on else 0, buf))
         return [int(v) for v in buf]
+
+    def mr_debug_lane_tc_wait(self, skip: bool):
+        """Test hook: the lane-group tensor-core kernels issue no product (see mr.h)."""
+        self._check(lib.mr_debug_lane_tc_wait(self.handle, 1 if skip else 0))
 
     def mr_debug_big_wait(self, spin_limit: int = 0, absent_slice: int = -1):
         """Test hook of the large classes' bounded waits (see mr.h)."""

@@ -96,3 +96,37 @@ def test_tensor_peaks_plausible():
         for kind in (0, 1, 2, 3):
             v = ctx.mr_imad_peak(kind)
             assert 1e11 < v < 1e14, (kind, v)
+
+
+def test_lane_tc_bounded_wait_times_out_and_context_recovers():
+    """The 1024-bit class's tensor-core kernel with no product issued (test hook): every block's
+    completion wait runs out after its limit (about a second), the call completes, every item reports
+    MR_ERR_TIMEOUT (8), and the next call on the same context gives the oracle's results."""
+    _need_gpu()
+    from oracle import plain
+    from paper_1305_3699_gb300 import mr
+
+    assert mr.mr_lane_variant_info(1024, 0)["tensor"]
+    r = SplitMix64(4242)
+    n = 40  # two blocks, the second one ragged
+    N = r.randbits(1024) | 1 | (1 << 1023)
+    xs = [r.below(N) for _ in range(n)]
+    es = [r.randbits(1024) for _ in range(n)]
+    with mr.Context(0) as ctx:
+        h = ctx.mr_rns_setup(N)
+        x, e = mr.to_tensor(xs, 32), mr.to_tensor(es, 32)
+        out = torch.zeros_like(x)
+        st = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+        ctx.mr_debug_lane_tc_wait(True)
+        try:
+            ctx.mr_modexp_batch([h] * n, x, e, out, st)
+            torch.cuda.synchronize()
+        finally:
+            ctx.mr_debug_lane_tc_wait(False)
+        assert st.cpu().tolist() == [8] * n
+        st.fill_(255)
+        ctx.mr_modexp_batch([h] * n, x, e, out, st)
+        torch.cuda.synchronize()
+        assert st.cpu().tolist() == [0] * n
+        got = mr.from_tensor(out)
+    assert got == [plain.modexp(a, b, N) for a, b in zip(xs, es)]
