@@ -476,7 +476,9 @@ mr_status mr_debug_tc_slices(uint32_t class_bits, uint32_t *out, size_t capacity
  * swap_strides = 1 exchanges the descriptor's two byte offsets (diagnosis
  * only; kdim must then be 16); swap_strides = 2 takes A from tensor memory
  * instead (row r in lane r, two fp16 values of K per 32-bit column, the lower
- * K index in the low half: the layout of the extension's resident matrix).
+ * K index in the low half: the layout of the extension's resident matrix);
+ * swap_strides = 3 computes the product as 0 does and reads D back with the
+ * 16x256b tensor-memory load shape (the lane-group extensions' epilogue).
  * 16 <= n <= 256 (n <= 128 with swap_strides 1 or 2) and 16 <= kdim <= 64, both
  * multiples of 16.
  * Synchronises `stream`.  Errors: MR_ERR_ARG, MR_ERR_TIMEOUT, MR_ERR_CUDA. */

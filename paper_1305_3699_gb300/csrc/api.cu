@@ -2129,9 +2129,9 @@ mr_status mr_debug_tc_mma(mr_ctx* ctx, const uint16_t* a, const uint16_t* b, uin
   // with exchanged offsets the tensor core reads up to 16 x 16 * rows bytes past each operand's start:
   // inside the 32 KB operand regions only for a single K step; A in tensor memory takes columns
   // n .. n + kdim/2 of the 256 allocated, so n <= 128 there; otherwise n <= 256 (32 KB of B at kdim 64)
-  const uint32_t n_max = swap_strides == 0 ? 256u : 128u;
+  const uint32_t n_max = (swap_strides == 0 || swap_strides == 3) ? 256u : 128u;
   if (!ctx || !a || !b || !d || n < 16 || n > n_max || n % 16 || kdim < 16 || kdim > 64 || kdim % 16 ||
-      swap_strides > 2 || (swap_strides == 1 && kdim != 16))
+      swap_strides > 3 || (swap_strides == 1 && kdim != 16))
     return fail(ctx, MR_ERR_ARG, "bad arguments");
   cudaSetDevice(ctx->device);
   cudaError_t e = mr::tensor_debug_mma(a, b, n, kdim, swap_strides, d, (cudaStream_t)stream);

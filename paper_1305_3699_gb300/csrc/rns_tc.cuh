@@ -12,22 +12,23 @@
 // numbers of the block: a sum of k products below 255^2, below 2^23 for k <= 129,
 // so the fp32 accumulator holds it exactly.  An extra K column of 2048 x 4096
 // adds 2^23 to every accumulator; a value in [2^23, 2^24) has the integer
-// sum as its 23 mantissa bits.  The 64-bit dot product sum_a sum_b 2^(8(a+b))
-// P_ab(j) is then rebuilt in integers: each lane combines its own slice a over
-// b, shifts by 8a and the four lanes of the number add their parts in a
-// reduce-scatter that leaves channel j's sum in the lane that owns channel j.
-// The result is bit for bit the integer form's accumulator.
+// sum as its 23 mantissa bits.
 //
-// Block shape.  32 numbers x 8 lanes (256 threads).  The 4 data slices of
-// number n are tensor-memory lanes 4n + a, i.e. lanes 4(n % 8) + a of the
-// lane quarter n / 8, which warps n / 8 and n / 8 + 4 both read: lane u of the
-// number's group of four in warp half h is the number's lane t = 4h + u, reads
-// accumulator row 4n + u (its data slice a = u) in its half's columns and ends
-// with the channels of lane t.  Two warps per number give the SM 16 warps with
-// two blocks (the accumulators of two blocks fill tensor memory).  All warps
-// take part in every multiplication (two block barriers and two tensor-core
-// waits per multiplication), so the exponent schedule of a block is uniform
-// (kernels.cuh).
+// Layout.  The 4 data slices of number n are accumulator rows 8a + n % 8 of the
+// tensor-memory lane quarter n / 8, and the 16 columns of one channel slot hold
+// the 4 matrix bytes of the slot's channel for each of the number's 4 lanes, in
+// the order the 16x256b load shape delivers them: lane u of the number receives
+// all 16 sums P_ab of its own channel (rows n % 8 and n % 8 + 8 of each 16-lane
+// half, columns 2u, 2u + 1 of each 8-column group) and forms the 64-bit dot
+// product sum_{a,b} 2^(8(a+b)) P_ab alone -- bit for bit the integer form's
+// accumulator, with no exchange between lanes.
+//
+// Block shape.  32 numbers; TPI = 4: 4 lanes per number in one warp (lane 4(n % 8)
+// + u of warp n / 8); TPI = 8: the number's two groups of four in warps n / 8
+// (h = 0) and n / 8 + 4 (h = 1), which read the same lane quarter, each half its
+// own 16 NPT accumulator columns.  All warps take part in every multiplication
+// (two block barriers and two tensor-core waits per multiplication), so the
+// exponent schedule of a block is uniform (kernels.cuh).
 #pragma once
 #include <cuda_fp16.h>
 
@@ -85,7 +86,9 @@ __device__ void tc_prologue(const TcSmem<C>& ts, const uint32_t* cls) {
   uint8_t* B2 = ts.B2();
   for (int idx = threadIdx.x; idx < NB * KA; idx += C::THREADS) {
     const int c = idx / KA, col = idx % KA;
-    const int h = c / (16 * NPT), jj = (c / 16) % NPT, u = (c / 4) % 4, b = c % 4;
+    // column c = 16 NPT h + 16 jj + 8 (b / 2) + 2 u + b % 2 (the 16x256b load order)
+    const int h = c / (16 * NPT), jj = (c / 16) % NPT, r16 = c % 16;
+    const int u = (r16 % 8) / 2, b = 2 * (r16 / 8) + (r16 % 2);
     const int j = (4 * h + u) * NPT + jj;            // output channel
     const int ti = col / NPTK, si = tc_kslot<C>(ti, col % NPTK);
     const int i = ti * NPT + si;                     // input channel
@@ -114,8 +117,9 @@ __device__ void tc_prologue(const TcSmem<C>& ts, const uint32_t* cls) {
 
 // Write byte slices of this lane's coefficients v (its NPT channels; lane t of number n) into rows
 // 4n + a of the data operand: four consecutive K columns per 8-byte store.  A byte b becomes the fp16
-// value b as the bit pattern of 1024 + b minus 1024.  Step a of lane l writes slice (a + l_1 + 2 l_3) % 4
-// (l_i: bit i of l), so that each half-warp's 8-byte stores reach 32 distinct banks.
+// value b as the bit pattern of 1024 + b minus 1024.  The rows of one store instruction are the 8
+// numbers of the lane quarter (distinct rows of a core matrix), so a warp's stores need the minimum
+// two shared-memory wavefronts.
 template <class C>
 __device__ __forceinline__ void tc_publish(const TcSmem<C>& ts, const uint32_t (&v)[C::NPT], int n, int t) {
   constexpr int NPT = C::NPT, NPTK = C::NPTK, K = C::K;
@@ -130,10 +134,9 @@ __device__ __forceinline__ void tc_publish(const TcSmem<C>& ts, const uint32_t (
       x[q] = (s < NPT && t * NPT + s < K) ? v[s < NPT ? s : 0] : 0u;
     }
     const bool has_off = (t == 0) && (4 * g <= NPT) && (NPT < 4 * g + 4);  // the 2^23 offset column
-    const int rot = (int)(((threadIdx.x >> 1) & 1) + 2 * ((threadIdx.x >> 3) & 1));
+    const int row0 = 32 * (n / 8) + n % 8;  // row of data slice a: row0 + 8 a
 #pragma unroll
-    for (int a0 = 0; a0 < 4; a0++) {
-      const int a = (a0 + rot) & 3;
+    for (int a = 0; a < 4; a++) {
       uint32_t w[2];
 #pragma unroll
       for (int p = 0; p < 2; p++) {
@@ -153,42 +156,39 @@ __device__ __forceinline__ void tc_publish(const TcSmem<C>& ts, const uint32_t (
         if (q == 2) w[1] = (w[1] & 0xFFFF0000u) | off;
         if (q == 3) w[1] = (w[1] & 0x0000FFFFu) | (off << 16);
       }
-      *reinterpret_cast<uint2*>(A + tc::tile_off(128, 4 * n + a, NPTK * t + tc_kslot<C>(t, 4 * g))) =
+      *reinterpret_cast<uint2*>(A + tc::tile_off(128, row0 + 8 * a, NPTK * t + tc_kslot<C>(t, 4 * g))) =
           make_uint2(w[0], w[1]);
     }
   }
 }
 
-__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
-  const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
-  const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
-  return ((uint64_t)hi << 32) | lo;
-}
-
-// One channel slot's accumulators r[16] (column 4u + b: slice b of the output channel of lane 4h + u,
-// this lane's data slice a = its position in the group of four): the exact 64-bit dot product of
-// this lane's own output channel.
-__device__ __forceinline__ uint64_t tc_combine(const uint32_t (&r)[16], int a) {
-  constexpr uint32_t OFF = 0x4B000000u;           // bit pattern of 2^23
-  constexpr uint32_t OFF2 = OFF + (OFF << 8);     // two offsets, the second shifted by 8 (mod 2^32)
-  uint64_t q[4];
-#pragma unroll
-  for (int u = 0; u < 4; u++) {
-    const uint32_t lo = r[4 * u] + (r[4 * u + 1] << 8) - OFF2;      // v0 + 2^8 v1 < 2^31
-    const uint32_t hi = r[4 * u + 2] + (r[4 * u + 3] << 8) - OFF2;  // v2 + 2^8 v3 < 2^31
-    const uint64_t p = (uint64_t)lo + ((uint64_t)hi << 16);           // sum_b 2^(8b) v_b
-    q[u] = p << (8 * a);
+// One channel slot's 16 accumulators of this lane's channel, from the two 16x256b loads of the slot
+// (lo: the rows of data slices 0, 1; hi: those of slices 2, 3; element [4p + 2e + f] holds data slice
+// e (e + 2 for hi) times matrix byte 2p + f), each the bit pattern of 2^23 + P_ab: the exact 64-bit sum
+// sum_{a,b} 2^(8(a+b)) P_ab, formed from the digit sums w_s = sum_{a+b=s} P_ab (each below 2^24; a
+// pair w_s + 2^8 w_(s+1) stays below 2^32 while the second digit has at most 2 terms, or 4 with k <= 64).
+template <int K>
+__device__ __forceinline__ uint64_t tc_combine(const uint32_t (&lo)[8], const uint32_t (&hi)[8]) {
+  constexpr uint32_t OFF = 0x4B000000u;  // bit pattern of 2^23, carried once per summed accumulator
+  const uint32_t w0 = lo[0];
+  const uint32_t w1 = lo[1] + lo[2];
+  const uint32_t w2 = lo[4] + lo[3] + hi[0];
+  const uint32_t w3 = lo[5] + lo[6] + hi[1] + hi[2];
+  const uint32_t w4 = lo[7] + hi[4] + hi[3];
+  const uint32_t w5 = hi[5] + hi[6];
+  const uint32_t w6 = hi[7];
+  // digits and pairs of digits with the offsets removed (mod 2^32; each true value is below 2^32)
+  const uint32_t x0 = w0 + (w1 << 8) - (uint32_t)(1u * OFF + ((2u * OFF) << 8));
+  const uint32_t x2 = w4 + (w5 << 8) - (uint32_t)(3u * OFF + ((2u * OFF) << 8));
+  const uint32_t x3 = w6 - OFF;
+  if constexpr ((uint64_t)K * 65025u * (4u * 256u + 3u) < (1ull << 32)) {
+    const uint32_t x1 = w2 + (w3 << 8) - (uint32_t)(3u * OFF + ((4u * OFF) << 8));
+    return (uint64_t)x0 + ((uint64_t)x1 << 16) + ((uint64_t)x2 << 32) + ((uint64_t)x3 << 48);
+  } else {
+    const uint32_t y2 = w2 - 3u * OFF, y3 = w3 - 4u * OFF;
+    return (uint64_t)x0 + ((uint64_t)y2 << 16) + ((uint64_t)y3 << 24) + ((uint64_t)x2 << 32) +
+           ((uint64_t)x3 << 48);
   }
-  // reduce-scatter over the four lanes: after the xor-2 step lanes 0, 1 hold channels u = 0, 1 and
-  // lanes 2, 3 hold u = 2, 3 (sums of two slices); after the xor-1 step lane a holds u = a
-  const bool up = (a & 2) != 0;
-  const uint64_t s0 = up ? q[0] : q[2], s1 = up ? q[1] : q[3];
-  uint64_t k0 = up ? q[2] : q[0], k1 = up ? q[3] : q[1];
-  k0 += shfl_xor_u64(s0, 2);
-  k1 += shfl_xor_u64(s1, 2);
-  const bool odd = (a & 1) != 0;
-  const uint64_t sb = odd ? k0 : k1, kb = odd ? k1 : k0;
-  return kb + shfl_xor_u64(sb, 1);
 }
 
 // One base extension: the block's data operand (already published) times matrix operand B; acc[s]
@@ -223,19 +223,22 @@ __device__ __forceinline__ void tc_extension(const TcSmem<C>& ts, TcState& st, c
   st.phase ^= 1u;
   tc::fence_after_sync();
   const int warp = threadIdx.x >> 5;
-  // lane quarter warp % 4; warp half h reads its 16 NPT columns
-  const uint32_t lane_base = st.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * NPT * tc_half<C>());
-  const int a = threadIdx.x & 3;
+  // lane quarter warp % 4 (its two 16-lane halves: data slices 0, 1 and 2, 3); warp half h reads its
+  // 16 NPT columns
+  const uint32_t base = st.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * NPT * tc_half<C>());
 #pragma unroll
   for (int j0 = 0; j0 < NPT; j0 += 3) {  // loads and combines in groups of 3 slots
-    uint32_t r[3][16];
+    uint32_t lo[3][8], hi[3][8];
 #pragma unroll
     for (int q = 0; q < 3; q++)
-      if (j0 + q < NPT) tc::tmem_ld16(lane_base + 16 * (j0 + q), r[q]);
+      if (j0 + q < NPT) {
+        tc::tmem_ld16x256b_x2(base + 16 * (j0 + q), lo[q]);
+        tc::tmem_ld16x256b_x2(base + (16u << 16) + 16 * (j0 + q), hi[q]);
+      }
     tc::tmem_ld_wait();
 #pragma unroll
     for (int q = 0; q < 3; q++)
-      if (j0 + q < NPT) acc[j0 + q] = tc_combine(r[q], a);
+      if (j0 + q < NPT) acc[j0 + q] = tc_combine<C::K>(lo[q], hi[q]);
   }
 }
 

@@ -138,6 +138,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr)
       : "memory");
 }
+// 16x256b shape, two repetitions (16 lanes x 16 columns): thread i of the warp receives, for
+// repetition p (columns 8p .. 8p + 7 from the address's column), r[4p], r[4p + 1] = lane i / 4, columns
+// 8p + 2 (i % 4) and + 1, and r[4p + 2], r[4p + 3] = lane i / 4 + 8, the same columns (the lane field
+// of taddr names the first of the 16 lanes, inside the warp's quarter).
+__device__ __forceinline__ void tmem_ld16x256b_x2(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // 4 consecutive columns of this thread's lane from registers (same 32x32b lane rule as the loads).

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_debug_mma_kernel(const uint1
   tc::fence_after_sync();
   const uint32_t taddr = *tslot;
   const bool a_tmem = swap_strides == 2;  // A from tensor memory, columns n .. n + kdim/2 - 1
+  // (swap_strides 3: the product as for 0, read back with the 16x256b load shape)
   if (a_tmem) {
     // row 32 w + lane of A into lane 32 w + lane: two fp16 values of K per column, lower index low
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31, row = 32 * w + lane;
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_debug_mma_kernel(const uint1
     for (uint32_t s = 0; s < kdim / 16; s++) {
       // K step s: column groups 2s, 2s+1
       const uint32_t a0 = tc::saddr(as) + 2 * s * 16 * TC_M, b0 = tc::saddr(bs) + 2 * s * 16 * n;
-      const bool sw = swap_strides == 1;
+      const bool sw = swap_strides == 1;  // (3 reads D differently, the product is that of 0)
       const uint64_t ad = sw ? tc::sdesc(a0, 128, 16 * TC_M) : tc::sdesc(a0, 16 * TC_M, 128);
       const uint64_t bd = sw ? tc::sdesc(b0, 128, 16 * n) : tc::sdesc(b0, 16 * n, 128);
       if (a_tmem)
@@ -194,6 +195,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_debug_mma_kernel(const uint1
   if (threadIdx.x == 0) ok = tc::mbar_wait_ns(mbar, 0, TC_WAIT_NS);
   if (!__syncthreads_and(ok)) {
     if (threadIdx.x == 0) atomicExch(err, 1u);
+  } else if (swap_strides == 3) {
+    // D read back with the 16x256b shape (two 16-lane halves of each warp's quarter, 16 columns per
+    // load) and stored by the register layout tc_device.cuh states for it
+    tc::fence_after_sync();
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (uint32_t half = 0; half < 2; half++)
+      for (uint32_t c0 = 0; c0 < n; c0 += 16) {
+        uint32_t v[8];
+        tc::tmem_ld16x256b_x2(taddr + ((32 * w + 16 * half) << 16) + c0, v);
+        tc::tmem_ld_wait();
+        const uint32_t r0 = 32 * w + 16 * half + lane / 4, col = c0 + 2 * (lane % 4);
+#pragma unroll
+        for (uint32_t p = 0; p < 2; p++) {
+          D[r0 * n + col + 8 * p] = __uint_as_float(v[4 * p]);
+          D[r0 * n + col + 8 * p + 1] = __uint_as_float(v[4 * p + 1]);
+          D[(r0 + 8) * n + col + 8 * p] = __uint_as_float(v[4 * p + 2]);
+          D[(r0 + 8) * n + col + 8 * p + 1] = __uint_as_float(v[4 * p + 3]);
+        }
+      }
   } else {
     tc::fence_after_sync();
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;

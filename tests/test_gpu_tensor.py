@@ -64,6 +64,26 @@ def test_tc_mma_lane_group_extension_shape(n, kdim, off_col):
     assert np.array_equal((bits & 0x7FFFFF).astype(np.float64), want - 2 ** 23)
 
 
+def test_tc_ld_16x256b_layout():
+    """The 16x256b tensor-memory load returns, to thread i of a warp, lane i / 4 and lane i / 4 + 8 of
+    each 16-lane half at columns 2 (i % 4) and + 1 of each 8-column group: D[r][c] = 256 r + c read back
+    through that layout (swap_strides 3) lands at every (r, c)."""
+    _need_gpu()
+    from paper_1305_3699_gb300 import mr
+
+    for n in (16, 144):
+        a = np.zeros((128, 16))
+        b = np.zeros((n, 16))
+        a[:, 0] = np.arange(128)
+        b[:, 0] = 256.0
+        a[:, 1] = 1.0
+        b[:, 1] = np.arange(n)
+        with mr.Context(0) as ctx:
+            d = ctx.mr_debug_tc_mma(a, b, swap_strides=3)
+        want = a @ b.T
+        assert np.array_equal(d.astype(np.float64), want), d[:2, :16]
+
+
 def test_tc_mma_distinguishes_rows_and_columns():
     """A one-hot pattern: row i of A and row j of B share exactly one non-zero column, so each
     output names the pair it came from (a transposed or shifted operand would move the values)."""
