@@ -45,8 +45,8 @@ IMAD_PER_CLK_PER_SM = 64   # int32 multiplies per clock per SM (integer multiply
 # DRAM bytes (read + write) of one exponentiation launch of the RSA-2048 CRT workload, from an ncu
 # capture on this workload, per kernel form of the 1024-bit class: the integer form
 # (dram__bytes_read.sum + dram__bytes_write.sum) and the tensor-core form (dram__bytes.sum.per_second
-# x gpu__time_duration.sum: 6.5965 GB/s x 3.96816 ms)
-TRAFFIC_BYTES_PER_LAUNCH = {"integer": 2_861_568 + 24_110_080, "tensor": 26_176_000}
+# x gpu__time_duration.sum: 8.259067 GB/s x 3.064288 ms)
+TRAFFIC_BYTES_PER_LAUNCH = {"integer": 2_861_568 + 24_110_080, "tensor": 25_308_000}
 # long-exponent workload: 256 exponentiations modulo 16384-bit RSA moduli with 16128-bit exponents
 BIG_KEYSET = "mod16384_x4"
 BIG_N = 256
