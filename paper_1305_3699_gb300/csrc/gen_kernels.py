@@ -35,7 +35,7 @@ CLASSES = {
 # extensions run on the tensor cores (BigTcCfg: 8 warps, 32-channel slices).  The relative group
 # times were measured with the variants in one wave on GB300.
 BIG = {
-    8192: (295, 256, 258, 4, [(8, 1.0, 0), (12, 1.33, 0)]),
+    8192: (295, 256, 258, 4, [(8, 1.0, 0), (12, 1.33, 0), (8, 0.495, 1)]),
     16384: (599, 512, 513, 4, [(8, 1.0, 0), (8, 0.434, 1)]),
 }
 

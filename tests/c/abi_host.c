@@ -64,11 +64,12 @@ int main(void) {
   uint32_t nvar = 0, lanes[8];
   check(mr_class_variants(1024, &nvar, lanes, 8) == MR_OK && nvar >= 1 && lanes[0] == 4,
         "1024-bit class: variant 0 has 4 lanes per number");
-  check(mr_class_variants(8192, &nvar, lanes, 8) == MR_OK && nvar == 2 && lanes[0] == 80 && lanes[1] == 84,
-        "8192-bit class: slice widths of 10 x 8 and 7 x 12 lanes per number");
+  check(mr_class_variants(8192, &nvar, lanes, 8) == MR_OK && nvar == 3 && lanes[0] == 80 && lanes[1] == 84 &&
+            lanes[2] == 80,
+        "8192-bit class: slice widths of 10 x 8 and 7 x 12 lanes per number, tensor-core form 10 x 8");
   uint32_t v = 9, slots = 0;
-  check(mr_debug_big_variant(8192, 512, 152, 1, &v, &slots) == MR_OK && v == 1 && slots == 16,
-        "16 groups of the 8192-bit class take the wide slices in one wave");
+  check(mr_debug_big_variant(8192, 512, 152, 1, &v, &slots) == MR_OK && v == 2 && slots == 15,
+        "16 groups of the 8192-bit class take the tensor-core form in two waves of 15");
   check(mr_debug_table(NULL, 512, NULL, "B", NULL, 0, &count) == MR_OK && count == 18, "class table B: k primes");
 
   check(mr_init(0, NULL) == MR_ERR_ARG, "mr_init without an output pointer: MR_ERR_ARG");

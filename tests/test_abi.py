@@ -91,13 +91,12 @@ def test_trial_table_matches_oracle():
 
 
 def test_large_class_wave_policy():
-    """The slice width a large-class launch picks on 152 SMs with one block per SM: the 8192-bit
-    class fits 15 groups per wave at 32 channels per block and 21 at 48 (1.33x the time per group):
-    8 and 15 groups stay on the narrow slices, 16-21 groups take one wide wave, 30 groups two
-    narrow waves, 42 groups two wide waves (2.66 against 3); the 16384-bit class has one width
-    (8 groups per wave) in two forms and picks the tensor-core form of the base extensions (less
-    time per group)."""
-    cases = {256: (0, 8), 480: (0, 15), 512: (1, 16), 672: (1, 21), 960: (0, 15), 1344: (1, 21)}
+    """The variant a large-class launch picks on 152 SMs with one block per SM, by waves x time per
+    group: the 8192-bit class fits 15 groups per wave at 32 channels per block (integer form, 1.0),
+    21 at 48 (integer form, 1.33) and 15 in the tensor-core form (0.495), which wins at every group
+    count (two of its waves, 0.99, against one wide integer wave, 1.33, for 16-21 groups); the
+    16384-bit class has one width (8 groups per wave) in two forms and picks the tensor-core form."""
+    cases = {256: (2, 8), 480: (2, 15), 512: (2, 15), 672: (2, 15), 960: (2, 15), 1344: (2, 15)}
     for n, want in cases.items():
         assert mr.mr_debug_big_variant(8192, n) == want, n
     assert mr.mr_debug_big_variant(16384, 256) == (1, 8)
@@ -217,6 +216,7 @@ def test_big_variant_info():
     assert mr.mr_big_variant_info(16384, 1) == {"slice_channels": 32, "slices": 19, "tensor": True}
     assert mr.mr_big_variant_info(8192, 0)["slice_channels"] == 32
     assert mr.mr_big_variant_info(8192, 1)["slice_channels"] == 48
+    assert mr.mr_big_variant_info(8192, 2) == {"slice_channels": 32, "slices": 10, "tensor": True}
     with pytest.raises(mr.MRError):
         mr.mr_big_variant_info(1024, 0)
 
