@@ -299,7 +299,7 @@ mr_status mr_prime_test_batch(mr_ctx *ctx, const uint32_t *cand, uint32_t n_limb
  * dq = Arazi(e, q-1) (so dp = d mod (p-1), dq = d mod (q-1)) and
  * qinv = q^-1 mod p; Arazi(e, f) = (1 + f t) / e with t = -f^-1 mod e.  The
  * private parts are written to device memory only.
- *   half_limbs  limbs of each candidate (2..64: primes of up to 2048 bits)
+ *   half_limbs  limbs of each candidate (2..128: primes of up to 4096 bits)
  *   n_keys, pool
  *   cand        device, n_keys * 2 * pool rows of half_limbs limbs: rows
  *               [2k pool, 2k pool + pool) are key k's p candidates, the next

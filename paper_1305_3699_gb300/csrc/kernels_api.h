@@ -132,7 +132,7 @@ cudaError_t launch_prime_combine(const uint8_t* item_pass, const uint32_t* slot,
 // [2k pool, 2k pool + pool) with verdict 2 and gcd(e, p-1) = 1, q likewise in the next pool rows
 // (q != p); out row k (9 half_limbs words): N 2H | d 2H | p | q | dp | dq | qinv.  status[k]:
 // 0, 5 (a pool has no usable prime) or 3 (an inverse does not exist).
-constexpr uint32_t KEYGEN_MAX_HALF_LIMBS = 64;
+constexpr uint32_t KEYGEN_MAX_HALF_LIMBS = 128;
 cudaError_t launch_keygen(const uint32_t* cand, const uint8_t* verdict, uint32_t n_keys, uint32_t pool,
                           uint32_t half_limbs, uint32_t e, uint32_t* out, uint8_t* status, cudaStream_t s);
 

@@ -114,137 +114,170 @@ __device__ bool kg_arazi(uint32_t* d, const uint32_t* f, int n, uint32_t e) {
   return rem == 0;
 }
 
-// ---- warp-cooperative multi-limb arithmetic: limb i = 32 j + lane (j = 0, 1), n <= 64 limbs;
-// limbs at or above n are zero.  Every lane of the warp calls these together.
+// ---- warp-cooperative multi-limb arithmetic: limb i = 32 j + lane (j < R registers per lane),
+// n <= 32 R limbs; limbs at or above n are zero.  Every lane of the warp calls these together.
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ uint64_t w_ballot64(bool b0, bool b1) {
-  return (uint64_t)__ballot_sync(FULL, b0) | ((uint64_t)__ballot_sync(FULL, b1) << 32);
-}
-
 // r = a + b + cin over n limbs; returns the carry out of limb n-1
-__device__ uint32_t w_add(uint32_t (&r)[2], const uint32_t (&a)[2], const uint32_t (&b)[2], uint32_t cin, int n,
+template <int R>
+__device__ uint32_t w_add(uint32_t (&r)[R], const uint32_t (&a)[R], const uint32_t (&b)[R], uint32_t cin, int n,
                           int lane) {
-  uint32_t sm[2];
-  bool g[2], pr[2];
+  uint32_t sm[R], C[R];
+  // carry into limb i = carry into bit i of the integer sum G + (G | P) + cin, G the limbs that
+  // generate a carry and P those that pass one on (32 R-bit masks from ballots, one word per register)
+  uint32_t cy = cin;
 #pragma unroll
-  for (int j = 0; j < 2; j++) {
+  for (int j = 0; j < R; j++) {
     sm[j] = a[j] + b[j];
-    g[j] = sm[j] < a[j];          // the limb generates a carry
-    pr[j] = sm[j] == 0xffffffffu;  // the limb passes an incoming carry on
+    const uint32_t G = __ballot_sync(FULL, sm[j] < a[j]);
+    const uint32_t X = G | __ballot_sync(FULL, sm[j] == 0xffffffffu);
+    const uint64_t t = (uint64_t)G + X + cy;
+    cy = (uint32_t)(t >> 32);
+    C[j] = (uint32_t)t ^ G ^ X;
   }
-  // carry into limb i = carry into bit i of the integer sum G + (G | P) + cin
-  const uint64_t G = w_ballot64(g[0], g[1]), X = G | w_ballot64(pr[0], pr[1]);
-  const uint64_t s1 = G + X;
-  const bool o1 = s1 < G;
-  const uint64_t s2 = s1 + cin;
-  const bool o2 = s2 < s1;
-  const uint64_t C = s2 ^ G ^ X;
+  uint32_t out = cy;  // n = 32 R: the carry out of the top word
 #pragma unroll
-  for (int j = 0; j < 2; j++) {
+  for (int j = 0; j < R; j++) {
     const int i = 32 * j + lane;
-    r[j] = i < n ? sm[j] + (uint32_t)((C >> i) & 1u) : 0u;
+    r[j] = i < n ? sm[j] + ((C[j] >> lane) & 1u) : 0u;
+    if (n < 32 * R && (n >> 5) == j) out = (C[j] >> (n & 31)) & 1u;
   }
-  return n < 64 ? (uint32_t)((C >> n) & 1u) : (uint32_t)(o1 || o2);
+  return out;
 }
 
 // r = a - b over n limbs; returns the borrow
-__device__ uint32_t w_sub(uint32_t (&r)[2], const uint32_t (&a)[2], const uint32_t (&b)[2], int n, int lane) {
-  uint32_t nb[2];
+template <int R>
+__device__ uint32_t w_sub(uint32_t (&r)[R], const uint32_t (&a)[R], const uint32_t (&b)[R], int n, int lane) {
+  uint32_t nb[R];
 #pragma unroll
-  for (int j = 0; j < 2; j++) nb[j] = 32 * j + lane < n ? ~b[j] : 0u;
-  return 1u - w_add(r, a, nb, 1u, n, lane);
+  for (int j = 0; j < R; j++) nb[j] = 32 * j + lane < n ? ~b[j] : 0u;
+  return 1u - w_add<R>(r, a, nb, 1u, n, lane);
 }
 
 // v = (top : v) / 2, top in {0, 1} being limb n
-__device__ void w_shr1(uint32_t (&v)[2], uint32_t top, int n, int lane) {
-  const uint32_t up0 = __shfl_down_sync(FULL, v[0], 1), up1 = __shfl_down_sync(FULL, v[1], 1);
-  const uint32_t w10 = __shfl_sync(FULL, v[1], 0);
+template <int R>
+__device__ void w_shr1(uint32_t (&v)[R], uint32_t top, int n, int lane) {
+  uint32_t up[R], first[R];
 #pragma unroll
-  for (int j = 0; j < 2; j++) {
+  for (int j = 0; j < R; j++) {
+    up[j] = __shfl_down_sync(FULL, v[j], 1);  // limb i + 1 within the register word
+    first[j] = __shfl_sync(FULL, v[j], 0);    // limb 32 j, the successor of limb 32 j - 1
+  }
+#pragma unroll
+  for (int j = 0; j < R; j++) {
     const int i = 32 * j + lane;
-    const uint32_t nb = i + 1 == n ? top : (lane < 31 ? (j ? up1 : up0) : (j ? 0u : w10));
+    const uint32_t nb = i + 1 == n ? top : (lane < 31 ? up[j] : (j + 1 < R ? first[j + 1 < R ? j + 1 : j] : 0u));
     v[j] = i < n ? (v[j] >> 1) | (nb << 31) : 0u;
   }
 }
 
 // v = 2 v + bit0 over n limbs
-__device__ void w_shl1(uint32_t (&v)[2], uint32_t bit0, int n, int lane) {
-  const uint32_t dn0 = __shfl_up_sync(FULL, v[0], 1), dn1 = __shfl_up_sync(FULL, v[1], 1);
-  const uint32_t w031 = __shfl_sync(FULL, v[0], 31);
+template <int R>
+__device__ void w_shl1(uint32_t (&v)[R], uint32_t bit0, int n, int lane) {
+  uint32_t dn[R], last[R];
 #pragma unroll
-  for (int j = 0; j < 2; j++) {
+  for (int j = 0; j < R; j++) {
+    dn[j] = __shfl_up_sync(FULL, v[j], 1);  // limb i - 1 within the register word
+    last[j] = __shfl_sync(FULL, v[j], 31);  // limb 32 j + 31, the predecessor of limb 32 (j + 1)
+  }
+#pragma unroll
+  for (int j = 0; j < R; j++) {
     const int i = 32 * j + lane;
-    const uint32_t lo = i == 0 ? (bit0 << 31) : (lane > 0 ? (j ? dn1 : dn0) : w031);
+    const uint32_t lo = i == 0 ? (bit0 << 31) : (lane > 0 ? dn[j] : last[j > 0 ? j - 1 : 0]);
     v[j] = i < n ? (v[j] << 1) | (lo >> 31) : 0u;
   }
 }
 
-__device__ __forceinline__ bool w_is_zero(const uint32_t (&v)[2]) { return !__any_sync(FULL, (v[0] | v[1]) != 0u); }
-
-__device__ __forceinline__ bool w_is_one(const uint32_t (&v)[2], int lane) {
-  return __all_sync(FULL, v[1] == 0u && v[0] == (lane == 0 ? 1u : 0u));
+template <int R>
+__device__ __forceinline__ bool w_is_zero(const uint32_t (&v)[R]) {
+  uint32_t o = 0;
+#pragma unroll
+  for (int j = 0; j < R; j++) o |= v[j];
+  return !__any_sync(FULL, o != 0u);
 }
 
-__device__ __forceinline__ uint32_t w_low_bit(const uint32_t (&v)[2]) { return __shfl_sync(FULL, v[0], 0) & 1u; }
+template <int R>
+__device__ __forceinline__ bool w_is_one(const uint32_t (&v)[R], int lane) {
+  uint32_t o = 0;
+#pragma unroll
+  for (int j = 1; j < R; j++) o |= v[j];
+  return __all_sync(FULL, o == 0u && v[0] == (lane == 0 ? 1u : 0u));
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t w_low_bit(const uint32_t (&v)[R]) { return __shfl_sync(FULL, v[0], 0) & 1u; }
 
 // bit `bit` of v (uniform)
-__device__ __forceinline__ uint32_t w_bit(const uint32_t (&v)[2], int bit) {
+template <int R>
+__device__ __forceinline__ uint32_t w_bit(const uint32_t (&v)[R], int bit) {
   const int li = bit >> 5;
-  const uint32_t word = __shfl_sync(FULL, (li >> 5) ? v[1] : v[0], li & 31);
+  uint32_t sel = v[0];
+#pragma unroll
+  for (int j = 1; j < R; j++)
+    if ((li >> 5) == j) sel = v[j];
+  const uint32_t word = __shfl_sync(FULL, sel, li & 31);
   return (word >> (bit & 31)) & 1u;
 }
 
 // r = u mod p by binary long division (32n steps)
-__device__ void w_mod(uint32_t (&r)[2], const uint32_t (&u)[2], const uint32_t (&p)[2], int n, int lane) {
-  r[0] = r[1] = 0u;
+template <int R>
+__device__ void w_mod(uint32_t (&r)[R], const uint32_t (&u)[R], const uint32_t (&p)[R], int n, int lane) {
+#pragma unroll
+  for (int j = 0; j < R; j++) r[j] = 0u;
   for (int bit = 32 * n - 1; bit >= 0; bit--) {
-    const uint32_t t = w_bit(r, 32 * n - 1);  // the bit shifted out of limb n-1
-    w_shl1(r, w_bit(u, bit), n, lane);
-    uint32_t d[2];
-    const uint32_t br = w_sub(d, r, p, n, lane);
+    const uint32_t t = w_bit<R>(r, 32 * n - 1);  // the bit shifted out of limb n-1
+    w_shl1<R>(r, w_bit<R>(u, bit), n, lane);
+    uint32_t d[R];
+    const uint32_t br = w_sub<R>(d, r, p, n, lane);
     if (t || !br) {  // 2r + bit >= p (the value is below 2p)
-      r[0] = d[0];
-      r[1] = d[1];
+#pragma unroll
+      for (int j = 0; j < R; j++) r[j] = d[j];
     }
   }
 }
 
 // r = u^-1 mod p (p odd) by the binary extended Euclidean algorithm, with a bounded step count;
 // false when u has no inverse (or the bound ran out)
-__device__ bool w_inv(uint32_t (&r)[2], const uint32_t (&u)[2], const uint32_t (&p)[2], int n, int lane) {
-  uint32_t a[2], b[2] = {p[0], p[1]}, x1[2] = {lane == 0 ? 1u : 0u, 0u}, x2[2] = {0u, 0u};
-  w_mod(a, u, p, n, lane);
-  if (w_is_zero(a)) return false;
+template <int R>
+__device__ bool w_inv(uint32_t (&r)[R], const uint32_t (&u)[R], const uint32_t (&p)[R], int n, int lane) {
+  uint32_t a[R], b[R], x1[R], x2[R];
+#pragma unroll
+  for (int j = 0; j < R; j++) {
+    b[j] = p[j];
+    x1[j] = (j == 0 && lane == 0) ? 1u : 0u;
+    x2[j] = 0u;
+  }
+  w_mod<R>(a, u, p, n, lane);
+  if (w_is_zero<R>(a)) return false;
   const int limit = 8 * 32 * n + 64;
   int steps = 0;
-  while (!w_is_one(a, lane) && !w_is_one(b, lane)) {
-    if (w_is_zero(a) || w_is_zero(b) || ++steps > limit) return false;
-    while (!w_low_bit(a) && steps++ <= limit) {
-      w_shr1(a, 0u, n, lane);
+  while (!w_is_one<R>(a, lane) && !w_is_one<R>(b, lane)) {
+    if (w_is_zero<R>(a) || w_is_zero<R>(b) || ++steps > limit) return false;
+    while (!w_low_bit<R>(a) && steps++ <= limit) {
+      w_shr1<R>(a, 0u, n, lane);
       uint32_t cy = 0u;
-      if (w_low_bit(x1)) cy = w_add(x1, x1, p, 0u, n, lane);
-      w_shr1(x1, cy, n, lane);
+      if (w_low_bit<R>(x1)) cy = w_add<R>(x1, x1, p, 0u, n, lane);
+      w_shr1<R>(x1, cy, n, lane);
     }
-    while (!w_low_bit(b) && steps++ <= limit) {
-      w_shr1(b, 0u, n, lane);
+    while (!w_low_bit<R>(b) && steps++ <= limit) {
+      w_shr1<R>(b, 0u, n, lane);
       uint32_t cy = 0u;
-      if (w_low_bit(x2)) cy = w_add(x2, x2, p, 0u, n, lane);
-      w_shr1(x2, cy, n, lane);
+      if (w_low_bit<R>(x2)) cy = w_add<R>(x2, x2, p, 0u, n, lane);
+      w_shr1<R>(x2, cy, n, lane);
     }
-    uint32_t d[2];
-    if (!w_sub(d, a, b, n, lane)) {  // a >= b
-      a[0] = d[0];
-      a[1] = d[1];
-      if (w_sub(x1, x1, x2, n, lane)) w_add(x1, x1, p, 0u, n, lane);
+    uint32_t d[R];
+    if (!w_sub<R>(d, a, b, n, lane)) {  // a >= b
+#pragma unroll
+      for (int j = 0; j < R; j++) a[j] = d[j];
+      if (w_sub<R>(x1, x1, x2, n, lane)) w_add<R>(x1, x1, p, 0u, n, lane);
     } else {
-      w_sub(b, b, a, n, lane);
-      if (w_sub(x2, x2, x1, n, lane)) w_add(x2, x2, p, 0u, n, lane);
+      w_sub<R>(b, b, a, n, lane);
+      if (w_sub<R>(x2, x2, x1, n, lane)) w_add<R>(x2, x2, p, 0u, n, lane);
     }
   }
-  const bool one_a = w_is_one(a, lane);
-  r[0] = one_a ? x1[0] : x2[0];
-  r[1] = one_a ? x1[1] : x2[1];
+  const bool one_a = w_is_one<R>(a, lane);
+#pragma unroll
+  for (int j = 0; j < R; j++) r[j] = one_a ? x1[j] : x2[j];
   return true;
 }
 
@@ -263,6 +296,8 @@ __device__ int kg_pick(const uint32_t* cand, const uint8_t* verdict, uint32_t fi
   return -1;
 }
 
+// R: registers per lane of the warp-wide inversion (32 R >= H)
+template <int R>
 __global__ void __launch_bounds__(32) keygen_kernel(const uint32_t* cand, const uint8_t* verdict, uint32_t pool,
                                                     int H, uint32_t e, uint32_t* out, uint8_t* status) {
   __shared__ uint32_t sp[KEYGEN_MAX_HALF_LIMBS], sq[KEYGEN_MAX_HALF_LIMBS];
@@ -309,16 +344,16 @@ __global__ void __launch_bounds__(32) keygen_kernel(const uint32_t* cand, const 
   __syncwarp();
   uint32_t st = sst;
   if (st == 0) {  // qinv = q^-1 mod p on the whole warp
-    uint32_t pw[2], qw[2], r[2];
+    uint32_t pw[R], qw[R], r[R];
 #pragma unroll
-    for (int j = 0; j < 2; j++) {
+    for (int j = 0; j < R; j++) {
       const int i = 32 * j + lane;
       pw[j] = i < H ? sp[i] : 0u;
       qw[j] = i < H ? sq[i] : 0u;
     }
-    const bool ok = w_inv(r, qw, pw, H, lane);
+    const bool ok = w_inv<R>(r, qw, pw, H, lane);
 #pragma unroll
-    for (int j = 0; j < 2; j++) {
+    for (int j = 0; j < R; j++) {
       const int i = 32 * j + lane;
       if (i < H) o[8 * H + i] = ok ? r[j] : 0u;
     }
@@ -336,7 +371,10 @@ cudaError_t launch_keygen(const uint32_t* cand, const uint8_t* verdict, uint32_t
   if (n_keys == 0) return cudaSuccess;
   if (half_limbs < 2 || half_limbs > KEYGEN_MAX_HALF_LIMBS || pool == 0 || e < 3 || !(e & 1u))
     return cudaErrorInvalidValue;
-  keygen_kernel<<<n_keys, 32, 0, s>>>(cand, verdict, pool, (int)half_limbs, e, out, status);
+  if (half_limbs <= 64)
+    keygen_kernel<2><<<n_keys, 32, 0, s>>>(cand, verdict, pool, (int)half_limbs, e, out, status);
+  else
+    keygen_kernel<4><<<n_keys, 32, 0, s>>>(cand, verdict, pool, (int)half_limbs, e, out, status);
   return cudaGetLastError();
 }
 

@@ -121,3 +121,37 @@ def test_keygen_argument_errors(mr, ctx):
     with pytest.raises(mr.MRError) as e:
         ctx.mr_rsa_keygen_batch(c, c, 1, 1, 1, out, e=4)
     assert e.value.code == 1
+
+
+def test_keygen_8192_bit_keys_from_known_primes(mr, ctx):
+    """RSA-8192 keys (4096-bit primes; the warp-wide inversion with four limbs per lane): each pool
+    hides one of the seeded 4096-bit primes behind random odd candidates, and the key the GPU
+    assembles equals the oracle's rsa_key_from_pools part by part, and encrypts and decrypts."""
+    from synth import load_keys
+    known = load_keys("rsa8192_x2")
+    r = SplitMix64(0x4B4C)
+    bits, pool, rounds, n_keys = 4096, 6, 4, 2
+    H = bits // 32
+    pools, wits = [], []
+    for k in range(n_keys):
+        for prime in (known[k]["p"], known[k]["q"]):
+            pl = [r.randbits(bits) | (3 << (bits - 2)) | 1 for _ in range(pool - 1)] + [prime]
+            pools.append(pl)
+            wits.append([[r.between(2, c - 2) for _ in range(rounds)] for c in pl])
+    got, st = _run(mr, ctx, pools, wits, n_keys, pool, H, rounds, 65537)
+    for k in range(n_keys):
+        want = keygen.rsa_key_from_pools(pools[2 * k], wits[2 * k], pools[2 * k + 1], wits[2 * k + 1], 65537)
+        assert want is not None and st[k] == 0, k
+        for part in ("N", "d", "p", "q", "dp", "dq", "qinv"):
+            assert got[k][part] == want[part], (k, part)
+        key = got[k]
+        h = ctx.mr_rsa_key_setup(key["N"], 65537, key["p"], key["q"], key["dp"], key["dq"], key["qinv"])
+        m = r.below(key["N"])
+        mt = mr.to_tensor([m], 2 * H)
+        ct = torch.zeros_like(mt)
+        back = torch.zeros_like(mt)
+        ctx.mr_rsa_encrypt([h], mt, ct)
+        ctx.mr_rsa_decrypt_crt([h], ct, back)
+        torch.cuda.synchronize()
+        assert mr.from_tensor(ct) == [pow(m, 65537, key["N"])]
+        assert mr.from_tensor(back) == [m]
