@@ -219,8 +219,10 @@ __device__ __forceinline__ void tc_extension(const TcSmem<C>& ts, TcState& st, c
     tc::mma_commit(ts.mbar());
   }
   overlap();  // work that does not depend on the product
-  if (*ts.abort_flag() == 0u && !tc::mbar_wait_ns(ts.mbar(), st.phase, LG_TC_WAIT_NS)) *ts.abort_flag() = 1u;
-  st.phase ^= 1u;
+  if (*ts.abort_flag() == 0u) {
+    if (tc::mbar_wait_ns(ts.mbar(), st.phase, LG_TC_WAIT_NS)) st.phase ^= 1u;
+    else *ts.abort_flag() = 1u;  // st.phase stays the parity of the product that may still be in flight
+  }
   tc::fence_after_sync();
   const int warp = threadIdx.x >> 5;
   // lane quarter warp % 4 (its two 16-lane halves: data slices 0, 1 and 2, 3); warp half h reads its
@@ -310,7 +312,7 @@ __device__ void tc_release(const TcSmem<C>& ts, const TcState& st) {
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (*ts.abort_flag() != 0u && threadIdx.x == 0) (void)tc::mbar_wait_ns(ts.mbar(), st.phase ^ 1u, LG_TC_WAIT_NS);
+  if (*ts.abort_flag() != 0u && threadIdx.x == 0) (void)tc::mbar_wait_ns(ts.mbar(), st.phase, LG_TC_WAIT_NS);
   __syncthreads();
   if (threadIdx.x < 32) tc::tmem_dealloc(st.tmem, C::TMEM_COLS);
 }
