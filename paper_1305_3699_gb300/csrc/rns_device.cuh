@@ -114,14 +114,14 @@ struct Cfg {
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 
   // Tensor-core form (TC = 1, rns_tc.cuh).  The block's 32 numbers x 4 byte slices are the 128 rows of
-  // the data operand (row 4n + a: byte a of number n's CRT coefficients).  Lane t of number n has its
-  // NPT input channels in K columns [NPTK t, NPTK t + NPT); the rest is zero except one offset column
-  // (K index NPT) whose product 2048 * 4096 = 2^23 is added to every accumulator.  With TPI = 4 the
-  // number's lanes are 4n .. 4n + 3 of the block; with TPI = 8 they are split over two warps of the
-  // same tensor-memory lane quarter (lane t = 4 h + u in warp half h).  The matrix operand has
-  // NB = 16 NPT TPI / 4 rows, row 16 NPT h + 16 s + 4 u + b holding byte b of the matrix column of
-  // output channel (4 h + u) NPT + s, so that warp half h reads its channels' accumulators from its
-  // own 16 NPT columns.
+  // the data operand (row 32 (n / 8) + 8 a + n % 8: byte a of number n's CRT coefficients).  Lane t of
+  // number n has its NPT input channels in K columns [NPTK t, NPTK t + NPT); the rest is zero except
+  // one offset column (K index NPT) whose product 2048 * 4096 = 2^23 is added to every accumulator.
+  // With TPI = 4 the number's lanes are 4n .. 4n + 3 of the block; with TPI = 8 they are split over
+  // two warps of the same tensor-memory lane quarter (lane t = 4 h + u in warp half h).  The matrix
+  // operand has NB = 16 NPT TPI / 4 rows, row 16 NPT h + 16 s + 8 (b / 2) + 2 u + b % 2 holding byte b
+  // of the matrix column of output channel (4 h + u) NPT + s (the 16x256b load order), so that warp
+  // half h reads its channels' accumulators from its own 16 NPT columns.
   static constexpr int NPTK = (NPT / 4 + 1) * 4;  // K columns per lane's channel set (>= NPT + 1)
   static constexpr int KA = TPI * NPTK;            // K extent, a multiple of 16
   static constexpr int NB = 4 * NPT * TPI;         // accumulator columns (N of the product)

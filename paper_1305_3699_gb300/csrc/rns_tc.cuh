@@ -116,7 +116,7 @@ __device__ void tc_prologue(const TcSmem<C>& ts, const uint32_t* cls) {
 }
 
 // Write byte slices of this lane's coefficients v (its NPT channels; lane t of number n) into rows
-// 4n + a of the data operand: four consecutive K columns per 8-byte store.  A byte b becomes the fp16
+// 32 (n / 8) + 8 a + n % 8 of the data operand: four consecutive K columns per 8-byte store.  A byte b becomes the fp16
 // value b as the bit pattern of 1024 + b minus 1024.  The rows of one store instruction are the 8
 // numbers of the lane quarter (distinct rows of a core matrix), so a warp's stores need the minimum
 // two shared-memory wavefronts.
